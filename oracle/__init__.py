@@ -1,0 +1,221 @@
+"""FP64 CPU oracle for the Lennard-Jones cell-list MD path (test infrastructure).
+
+This package is the slow, plain reference that the CUDA library is checked
+against.  It is test infrastructure: only ``tests/``, ``__graft_entry__.smoke``
+and the CPU-baseline leg of ``bench.py`` may import it.  It shares no code
+with ``paper_0709_3225_gb300`` and never imports it.
+
+The arithmetic lives in ``lj_oracle.c`` (plain C, IEEE double, built with
+``-ffp-contract=off``); this module compiles it with gcc on first use and
+wraps it with ctypes over numpy arrays.  Every function cites the passage of
+van Meel et al., arXiv:0709.3225, that it follows.
+
+Parity status of each function (what pins it, in tests/test_oracle_*.py):
+  pair          -- special values at 2^(1/6) sigma, F = -dU/dr, asymptotes,
+                   scaling laws (pinned)
+  ncells        -- the paper's worked example L = 11, rc = 2.5 -> 4 (pinned)
+  bin           -- independent interval test per particle, counts, edge
+                   cases (pinned)
+  forces_brute  -- Newton III, F = -grad E, two-body closed form (pinned)
+  forces_cells  -- equals forces_brute; invariance under subdivision,
+                   translation and axis permutation (pinned)
+  vv            -- time reversibility, second-order energy error (pinned)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lj_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liblj_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile lj_oracle.c into liblj_oracle.so (gcc, OpenMP if available)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
+            "-o", _LIB_PATH + ".tmp", _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True, text=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True, text=True)
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        lib.or_pair.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, _D, _D]
+        lib.or_pair.restype = None
+        lib.or_ncells.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        lib.or_ncells.restype = ctypes.c_int
+        lib.or_bin.argtypes = [ctypes.c_int64, _D, ctypes.c_double, ctypes.c_int,
+                               _I32, _I32, _I32, _I32]
+        lib.or_bin.restype = None
+        lib.or_forces_brute.argtypes = [ctypes.c_int64, _D] + [ctypes.c_double] * 4 + \
+            [ctypes.c_int, _D, _D, _D, _D]
+        lib.or_forces_brute.restype = None
+        lib.or_forces_cells.argtypes = [ctypes.c_int64, _D] + [ctypes.c_double] * 4 + \
+            [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+        lib.or_forces_cells.restype = ctypes.c_int
+        lib.or_force_one.argtypes = [ctypes.c_int64, _D] + [ctypes.c_double] * 4 + \
+            [ctypes.c_int, ctypes.c_int64, _D, _D]
+        lib.or_force_one.restype = None
+        lib.or_near_cutoff.argtypes = [ctypes.c_int64, _D, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_double, _I32]
+        lib.or_near_cutoff.restype = None
+        lib.or_ekin.argtypes = [ctypes.c_int64, _D, ctypes.c_double]
+        lib.or_ekin.restype = ctypes.c_double
+        lib.or_vv.argtypes = [ctypes.c_int64, _D, _D, _D] + [ctypes.c_double] * 4 + \
+            [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D, _D]
+        lib.or_vv.restype = ctypes.c_int
+        lib.or_set_threads.argtypes = [ctypes.c_int]
+        lib.or_set_threads.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(_I32)
+
+
+def _pos(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.ndim != 2 or x.shape[1] != 3:
+        raise ValueError("positions must have shape (n, 3)")
+    return x
+
+
+def set_threads(n: int = 0) -> int:
+    """OpenMP threads for the cell-list loops (0 = leave as is); returns count."""
+    return _load().or_set_threads(int(n))
+
+
+def pair(r: float, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5,
+         mode: int = 1) -> tuple[float, float]:
+    """(F, U) of one pair at distance r (Section 2, LJ pair force and its
+    truncated/shifted form; F = -dU/dr, positive repulsive)."""
+    F = ctypes.c_double()
+    U = ctypes.c_double()
+    _load().or_pair(float(r), float(eps), float(sigma), float(rc), int(mode),
+                    ctypes.byref(F), ctypes.byref(U))
+    return F.value, U.value
+
+
+def ncells(L: float, rc: float = 2.5, k: int = 1) -> int:
+    """Cells per dimension n = int[k L / rc] (Section 3.2, worked example)."""
+    return int(_load().or_ncells(float(L), float(rc), int(k)))
+
+
+def bin_cells(x, L: float, nc: int):
+    """Serial counting sort (Section 3.1 cell lists in CSR form).
+
+    Returns (cell_of[n], count[nc^3], start[nc^3+1], perm[n]) as int32."""
+    x = _pos(x)
+    n = x.shape[0]
+    ncell = nc ** 3
+    cell_of = np.empty(n, np.int32)
+    count = np.empty(ncell, np.int32)
+    start = np.empty(ncell + 1, np.int32)
+    perm = np.empty(n, np.int32)
+    _load().or_bin(n, _dp(x), float(L), int(nc), _ip(cell_of), _ip(count), _ip(start), _ip(perm))
+    return cell_of, count, start, perm
+
+
+def forces_brute(x, L: float, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5,
+                 mode: int = 1):
+    """O(N^2) forces by Eq. (n2_force) at the minimum image.
+
+    Returns (f[n,3], e_part[n], e_pot, virial)."""
+    x = _pos(x)
+    n = x.shape[0]
+    f = np.empty((n, 3))
+    ep = np.empty(n)
+    E = ctypes.c_double()
+    W = ctypes.c_double()
+    _load().or_forces_brute(n, _dp(x), float(L), float(eps), float(sigma), float(rc), int(mode),
+                            _dp(f), _dp(ep), ctypes.byref(E), ctypes.byref(W))
+    return f, ep, E.value, W.value
+
+
+def forces_cells(x, L: float, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5,
+                 mode: int = 1, k: int = 1):
+    """Cell-list forces (Section 3) over a (2k+1)^3 stencil.
+
+    Returns (f[n,3], e_part[n], e_pot, virial)."""
+    x = _pos(x)
+    n = x.shape[0]
+    f = np.empty((n, 3))
+    ep = np.empty(n)
+    E = ctypes.c_double()
+    W = ctypes.c_double()
+    rc_ = _load().or_forces_cells(n, _dp(x), float(L), float(eps), float(sigma), float(rc),
+                                  int(mode), int(k), _dp(f), _dp(ep), ctypes.byref(E),
+                                  ctypes.byref(W))
+    if rc_ != 0:
+        raise ValueError("box too small for the cell stencil (need nc >= 2k+1)")
+    return f, ep, E.value, W.value
+
+
+def force_one(x, L: float, i: int, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5,
+              mode: int = 1):
+    """Force and half pair energy on particle i alone, by definition (O(N))."""
+    x = _pos(x)
+    fi = np.empty(3)
+    ei = ctypes.c_double()
+    _load().or_force_one(x.shape[0], _dp(x), float(L), float(eps), float(sigma), float(rc),
+                         int(mode), int(i), _dp(fi), ctypes.byref(ei))
+    return fi, ei.value
+
+
+def near_cutoff(x, L: float, rc: float = 2.5, band: float = 1e-5, k: int = 1) -> np.ndarray:
+    """Boolean mask of particles with a partner at | r - rc | < band."""
+    x = _pos(x)
+    near = np.empty(x.shape[0], np.int32)
+    _load().or_near_cutoff(x.shape[0], _dp(x), float(L), float(rc), int(k), float(band), _ip(near))
+    return near.astype(bool)
+
+
+def ekin(v, mass: float = 1.0) -> float:
+    """Kinetic energy (1/2) m sum v^2."""
+    v = _pos(v)
+    return float(_load().or_ekin(v.shape[0], _dp(v), float(mass)))
+
+
+def vv(x, v, f, L: float, nsteps: int, dt: float = 0.005, eps: float = 1.0,
+       sigma: float = 1.0, rc: float = 2.5, mode: int = 1, k: int = 1, mass: float = 1.0):
+    """Velocity Verlet (Section 2) for nsteps; x, v, f are updated IN PLACE
+    (f must hold F(x) on entry).  Returns (e_pot, virial) at the end."""
+    for a in (x, v, f):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                and a.ndim == 2 and a.shape[1] == 3):
+            raise ValueError("x, v, f must be C-contiguous float64 arrays of shape (n, 3)")
+    E = ctypes.c_double()
+    W = ctypes.c_double()
+    r = _load().or_vv(x.shape[0], _dp(x), _dp(v), _dp(f), float(L), float(eps), float(sigma),
+                      float(rc), int(mode), int(k), float(dt), float(mass), int(nsteps),
+                      ctypes.byref(E), ctypes.byref(W))
+    if r != 0:
+        raise ValueError("box too small for the cell stencil")
+    return E.value, W.value

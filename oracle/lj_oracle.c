@@ -1,0 +1,370 @@
+/*
+ * FP64 CPU oracle for the short-ranged Lennard-Jones MD path of van Meel,
+ * Arnold, Frenkel, Portegies Zwart and Belleman, "Harvesting graphics power
+ * for MD simulations" (arXiv:0709.3225).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * reference that the CUDA library is checked against.  It shares no code,
+ * header, table or constant with the CUDA path, and nothing in the product
+ * path may load it: only tests/, the smoke check and the CPU-baseline leg of
+ * bench.py do.
+ *
+ * Everything is IEEE double precision.  Compile with -ffp-contract=off so
+ * that every product and sum is rounded on its own (the binning rule below
+ * is defined with separately rounded operations).
+ *
+ * Readings of the paper that this file encodes (each one restated next to
+ * the function that uses it):
+ *   - pair force: Section 2, LJ pair force equation, read with the missing
+ *     1/sigma factor restored, i.e. F(r) = -dU/dr for
+ *     U(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6];
+ *   - truncation at rc (Section 2, truncated and shifted force): mode 0 plain
+ *     truncation, mode 1 energy shift, mode 2 the paper's force shift;
+ *   - periodic cubic box, minimum image (implied by the 26 neighbour cells
+ *     of Section 3);
+ *   - cell count per dimension n = int[L / rc] (Section 3.2, worked example
+ *     L = 11 sigma, rc = 2.5 sigma -> n = 4), generalised to a subdivision k:
+ *     n = int[k L / rc] with a (2k+1)^3 stencil;
+ *   - velocity Verlet (Section 2, last paragraph; the equations are not in
+ *     the paper): kick-drift-kick with mass m.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Pair interaction (Section 2: LJ pair force, truncated and shifted force). */
+
+/* Full LJ pair force F_LJ(r) = (24 eps / sigma) [2 (sigma/r)^13 - (sigma/r)^7]
+ * (positive = repulsive) and potential U_LJ(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6]. */
+static void lj_full(double r, double eps, double sigma, double *F, double *U)
+{
+    double s = sigma / r;
+    double s6 = s * s * s * s * s * s;
+    double s7 = s6 * s;
+    double s12 = s6 * s6;
+    double s13 = s12 * s;
+    *F = (24.0 * eps / sigma) * (2.0 * s13 - s7);
+    *U = 4.0 * eps * (s12 - s6);
+}
+
+/* Truncated pair force and energy at distance r.
+ *   mode 0: F = F_LJ, U = U_LJ for r < rc; 0 beyond.
+ *   mode 1: energy shift: F = F_LJ, U = U_LJ - U_LJ(rc) for r < rc.
+ *   mode 2: force shift of Section 2: F = F_LJ - F_LJ(rc), and the matching
+ *           U = U_LJ - U_LJ(rc) + (r - rc) F_LJ(rc), so that F = -dU/dr.
+ * The cutoff is strict: r >= rc gives exactly zero. */
+void or_pair(double r, double eps, double sigma, double rc, int mode,
+             double *F, double *U)
+{
+    if (!(r < rc)) { *F = 0.0; *U = 0.0; return; }
+    double f, u;
+    lj_full(r, eps, sigma, &f, &u);
+    if (mode == 1 || mode == 2) {
+        double fc, uc;
+        lj_full(rc, eps, sigma, &fc, &uc);
+        u = u - uc;
+        if (mode == 2) {
+            f = f - fc;
+            u = u + (r - rc) * fc;
+        }
+    }
+    *F = f;
+    *U = u;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Box geometry (Section 3 and the worked example of Section 3.2).           */
+
+/* Number of cells per dimension, n = int[k L / rc]. */
+int or_ncells(double L, double rc, int k)
+{
+    return (int)floor(((double)k * L) / rc);
+}
+
+/* Wrap one coordinate into the primary box: w = x - L floor(x / L); a value
+ * that rounds up to L is moved to w - L. */
+static double wrap1(double x, double L)
+{
+    double q = floor(x / L);
+    double w = x - L * q;
+    if (w >= L) w = w - L;
+    return w;
+}
+
+/* Cell coordinate of a wrapped coordinate: c = trunc(w * s) with s = n / L,
+ * clamped to [0, n-1]. */
+static int cell1(double w, double s, int n)
+{
+    int c = (int)(w * s);
+    if (c >= n) c = n - 1;
+    if (c < 0) c = 0;
+    return c;
+}
+
+/* Minimum-image displacement component. */
+static double min_image(double d, double L)
+{
+    return d - L * nearbyint(d / L);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Binning: serial counting sort of particles into cells (the CSR form of the
+ * cell lists of Section 3.1).                                               */
+
+/* Outputs (caller-allocated): cell_of[n], count[nc^3], start[nc^3 + 1],
+ * perm[n].  Within a cell, particles are in increasing index order.  x is
+ * (n, 3) row-major and is not modified. */
+void or_bin(int64_t n, const double *x, double L, int nc,
+            int32_t *cell_of, int32_t *count, int32_t *start, int32_t *perm)
+{
+    int64_t ncell = (int64_t)nc * nc * nc;
+    double s = (double)nc / L;
+    for (int64_t c = 0; c < ncell; c++) count[c] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int cx = cell1(wrap1(x[3 * i + 0], L), s, nc);
+        int cy = cell1(wrap1(x[3 * i + 1], L), s, nc);
+        int cz = cell1(wrap1(x[3 * i + 2], L), s, nc);
+        int32_t c = (int32_t)(cx + (int64_t)nc * (cy + (int64_t)nc * cz));
+        cell_of[i] = c;
+        count[c] += 1;
+    }
+    start[0] = 0;
+    for (int64_t c = 0; c < ncell; c++) start[c + 1] = start[c] + count[c];
+    int32_t *fill = (int32_t *)calloc((size_t)ncell, sizeof(int32_t));
+    for (int64_t i = 0; i < n; i++) {
+        int32_t c = cell_of[i];
+        perm[start[c] + fill[c]] = (int32_t)i;
+        fill[c] += 1;
+    }
+    free(fill);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forces.                                                                   */
+
+/* Eq. (n2_force): f_i = -sum_{j != i} f(|r_j - r_i|) (r_j - r_i)/|r_j - r_i|,
+ * i.e. f_i = sum_j F(r_ij) d_ij / r_ij with d_ij = r_i - r_j taken at the
+ * minimum image.  O(N^2) brute force over all pairs i < j.
+ * Outputs: f (n, 3); e_part[n] = half the pair energies of each particle
+ * (may be NULL); *e_pot = sum over pairs of U; *virial = sum over pairs of
+ * r F(r). */
+void or_forces_brute(int64_t n, const double *x, double L, double eps,
+                     double sigma, double rc, int mode, double *f,
+                     double *e_part, double *e_pot, double *virial)
+{
+    double E = 0.0, W = 0.0;
+    for (int64_t i = 0; i < 3 * n; i++) f[i] = 0.0;
+    if (e_part) for (int64_t i = 0; i < n; i++) e_part[i] = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t j = i + 1; j < n; j++) {
+            double d[3];
+            for (int k = 0; k < 3; k++)
+                d[k] = min_image(x[3 * i + k] - x[3 * j + k], L);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < rc * rc)) continue;
+            double r = sqrt(r2);
+            double F, U;
+            or_pair(r, eps, sigma, rc, mode, &F, &U);
+            for (int k = 0; k < 3; k++) {
+                f[3 * i + k] += F * d[k] / r;
+                f[3 * j + k] -= F * d[k] / r;
+            }
+            if (e_part) { e_part[i] += 0.5 * U; e_part[j] += 0.5 * U; }
+            E += U;
+            W += r * F;
+        }
+    }
+    *e_pot = E;
+    *virial = W;
+}
+
+/* Cell-list forces (Section 3): each particle interacts with the particles
+ * of its own cell and of the surrounding cells of a (2k+1)^3 stencil, all
+ * wrapped periodically; the pair vector is the minimum image.  Requires
+ * nc >= 2k+1 so that every stencil cell is distinct.  Every particle sums
+ * over all its partners (no third-law halving), in the order: stencil cells
+ * dz, dy, dx from -k to k, then particles of the cell in index order.
+ * Outputs as or_forces_brute.  Returns -1 if nc < 2k+1. */
+int or_forces_cells(int64_t n, const double *x, double L, double eps,
+                    double sigma, double rc, int mode, int k, double *f,
+                    double *e_part, double *e_pot, double *virial)
+{
+    int nc = or_ncells(L, rc, k);
+    if (nc < 2 * k + 1) return -1;
+    int64_t ncell = (int64_t)nc * nc * nc;
+    int32_t *cell_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *count = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncell);
+    int32_t *start = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncell + 1));
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    or_bin(n, x, L, nc, cell_of, count, start, perm);
+
+    double E = 0.0, W = 0.0;
+    double rc2 = rc * rc;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : E, W)
+    for (int64_t i = 0; i < n; i++) {
+        int32_t c = cell_of[i];
+        int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+        double fi[3] = {0.0, 0.0, 0.0};
+        double ei = 0.0, wi = 0.0;
+        for (int dz = -k; dz <= k; dz++)
+            for (int dy = -k; dy <= k; dy++)
+                for (int dx = -k; dx <= k; dx++) {
+                    int ux = (cx + dx + nc) % nc;
+                    int uy = (cy + dy + nc) % nc;
+                    int uz = (cz + dz + nc) % nc;
+                    int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
+                    for (int32_t s = start[cn]; s < start[cn + 1]; s++) {
+                        int32_t j = perm[s];
+                        if (j == i) continue;
+                        double d[3];
+                        for (int q = 0; q < 3; q++)
+                            d[q] = min_image(x[3 * i + q] - x[3 * (int64_t)j + q], L);
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (!(r2 < rc2)) continue;
+                        double r = sqrt(r2);
+                        double F, U;
+                        or_pair(r, eps, sigma, rc, mode, &F, &U);
+                        for (int q = 0; q < 3; q++) fi[q] += F * d[q] / r;
+                        ei += 0.5 * U;
+                        wi += 0.5 * r * F;
+                    }
+                }
+        for (int q = 0; q < 3; q++) f[3 * i + q] = fi[q];
+        if (e_part) e_part[i] = ei;
+        E += ei;
+        W += wi;
+    }
+    *e_pot = E;
+    *virial = W;
+    free(cell_of); free(count); free(start); free(perm);
+    return 0;
+}
+
+/* Force on ONE particle i by the definition (all j != i, minimum image,
+ * strict cutoff).  Used to check sampled outputs of very large systems. */
+void or_force_one(int64_t n, const double *x, double L, double eps,
+                  double sigma, double rc, int mode, int64_t i, double *fi,
+                  double *ei)
+{
+    double acc[3] = {0.0, 0.0, 0.0};
+    double e = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+        if (j == i) continue;
+        double d[3];
+        for (int q = 0; q < 3; q++)
+            d[q] = min_image(x[3 * i + q] - x[3 * j + q], L);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (!(r2 < rc * rc)) continue;
+        double r = sqrt(r2);
+        double F, U;
+        or_pair(r, eps, sigma, rc, mode, &F, &U);
+        for (int q = 0; q < 3; q++) acc[q] += F * d[q] / r;
+        e += 0.5 * U;
+    }
+    for (int q = 0; q < 3; q++) fi[q] = acc[q];
+    *ei = e;
+}
+
+/* Smallest |r - rc| over all pairs of particle i within rc + band, as a
+ * diagnostic for pairs whose in/out decision is below working precision.
+ * Writes 1 to near[i] if particle i has a partner with |r - rc| < band. */
+void or_near_cutoff(int64_t n, const double *x, double L, double rc, int k,
+                    double band, int32_t *near)
+{
+    int nc = or_ncells(L, rc + band, k);
+    if (nc < 2 * k + 1) nc = 0;
+    for (int64_t i = 0; i < n; i++) near[i] = 0;
+    if (nc == 0) {
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t j = 0; j < n; j++) {
+                if (j == i) continue;
+                double d[3];
+                for (int q = 0; q < 3; q++) d[q] = min_image(x[3 * i + q] - x[3 * j + q], L);
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                if (fabs(r - rc) < band) near[i] = 1;
+            }
+        return;
+    }
+    int64_t ncell = (int64_t)nc * nc * nc;
+    int32_t *cell_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *count = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncell);
+    int32_t *start = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncell + 1));
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    or_bin(n, x, L, nc, cell_of, count, start, perm);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        int32_t c = cell_of[i];
+        int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+        for (int dz = -k; dz <= k; dz++)
+            for (int dy = -k; dy <= k; dy++)
+                for (int dx = -k; dx <= k; dx++) {
+                    int64_t cn = (cx + dx + nc) % nc + (int64_t)nc * ((cy + dy + nc) % nc + (int64_t)nc * ((cz + dz + nc) % nc));
+                    for (int32_t s = start[cn]; s < start[cn + 1]; s++) {
+                        int32_t j = perm[s];
+                        if (j == i) continue;
+                        double d[3];
+                        for (int q = 0; q < 3; q++) d[q] = min_image(x[3 * i + q] - x[3 * (int64_t)j + q], L);
+                        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                        if (fabs(r - rc) < band) near[i] = 1;
+                    }
+                }
+    }
+    free(cell_of); free(count); free(start); free(perm);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Observables.                                                              */
+
+/* Kinetic energy (1/2) m sum v^2 in FP64. */
+double or_ekin(int64_t n, const double *v, double mass)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < 3 * n; i++) s += v[i] * v[i];
+    return 0.5 * mass * s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Velocity Verlet (Section 2, last paragraph; standard kick-drift-kick):
+ *   v <- v + (dt / 2m) f;  x <- x + dt v;  x <- wrap(x);  f <- F(x);
+ *   v <- v + (dt / 2m) f.
+ * On entry f must hold F(x) (as returned by or_forces_cells); on exit it
+ * holds the forces at the final positions.  The cell list is rebuilt from
+ * scratch at every force evaluation.  e_pot/virial receive the values at the
+ * final positions.  Returns -1 on a bad box. */
+int or_vv(int64_t n, double *x, double *v, double *f, double L, double eps,
+          double sigma, double rc, int mode, int k, double dt, double mass,
+          int nsteps, double *e_pot, double *virial)
+{
+    double h = 0.5 * dt / mass;
+    double E = 0.0, W = 0.0;
+    for (int step = 0; step < nsteps; step++) {
+        for (int64_t q = 0; q < 3 * n; q++) {
+            v[q] = v[q] + h * f[q];
+            x[q] = wrap1(x[q] + dt * v[q], L);
+        }
+        if (or_forces_cells(n, x, L, eps, sigma, rc, mode, k, f, NULL, &E, &W) != 0)
+            return -1;
+        for (int64_t q = 0; q < 3 * n; q++) v[q] = v[q] + h * f[q];
+    }
+    if (e_pot) *e_pot = E;
+    if (virial) *virial = W;
+    return 0;
+}
+
+/* Threads the OpenMP loops may use (no-op without OpenMP); returns the
+ * number in effect. */
+int or_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
