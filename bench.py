@@ -1,0 +1,360 @@
+"""Benchmark: velocity-Verlet MD steps/s of the 4,000,000-particle LJ fluid.
+
+One step = the whole hot path: kick + drift + wrap + cell binning (count,
+scan, scatter) + cell-list LJ forces + closing kick, FP32-mixed precision.
+Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the path needs no exchange between replicas); value = all ranks'
+steps / max-over-ranks time.  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LJ steps/s & pair-interactions/s at N=4M, FP32-mixed vs FP64, % FP32 peak"
+WORKLOAD = "fluid-4m"
+FLOPS_PER_PAIR = 20          # flop convention per in-range pair evaluation
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+
+
+def unique_pairs(n: int, rho: float, rc: float) -> float:
+    """Expected unique pairs within rc of a homogeneous fluid: N (2/3) pi rc^3 rho."""
+    return n * (2.0 / 3.0) * math.pi * rc ** 3 * rho
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                p = [q.strip() for q in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    rows.append((float(p[1]), float(p[2]), p[5], p[6], p[7], p[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        mx = max(r[1] for r in rows)
+        loaded = [r for r in rows if r[0] > 0.5 * mx] or rows
+        reasons = set()
+        for r in rows:
+            for name, flag in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                  r[2:]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(x, v, L, w, max_seconds: float = 20.0, max_steps: int = 3):
+    """The FP64 oracle as it stands, on this host's cores: full velocity-Verlet
+    steps of the same workload until ~max_seconds of work, scaled to steps/s."""
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    used = oracle.set_threads(cores)
+    xo, vo = x.copy(), v.copy()
+    t0 = time.perf_counter()
+    fo = oracle.forces_cells(xo, L, rc=w.rc, mode=1)[0]
+    t_force = time.perf_counter() - t0
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < max_steps:
+        oracle.vv(xo, vo, fo, L, 1, dt=w.dt, rc=w.rc, mode=1)
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": steps / dt, "unit": "steps/s", "cores": used, "kind": "oracle",
+            "sample": f"{steps} full FP64 velocity-Verlet step(s) of the {w.n}-particle workload "
+                      f"(plus one initial force evaluation, {t_force:.1f} s, untimed)",
+            "pair_interactions_per_s": unique_pairs(w.n, w.rho, w.rc) * steps / dt}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, same metric and workload."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_0709_3225_gb300 import inputs
+    x, v, L, w = inputs.workload_state(WORKLOAD)
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    used = oracle.set_threads(cores)
+    xo, vo = x.copy(), v.copy()
+    fo = oracle.forces_cells(xo, L, rc=w.rc, mode=1)[0]
+    # bounded: at most one warm-up step and as many timed steps as fit ~90 s
+    t0 = time.perf_counter()
+    oracle.vv(xo, vo, fo, L, 1, dt=w.dt, rc=w.rc, mode=1)
+    t_step = time.perf_counter() - t0
+    k = max(1, min(args.steps, int(90.0 / max(t_step, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.vv(xo, vo, fo, L, k, dt=w.dt, rc=w.rc, mode=1)
+    T = time.perf_counter() - t0
+    value = k / T
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": k, "warmup": 1, "ms_per_step": 1e3 * T / k, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": w.n, "rho": w.rho, "T": w.temperature, "rc": w.rc, "dt": w.dt,
+                   "start": "fcc", "requested_steps": args.steps, "requested_warmup": args.warmup},
+        "pair_interactions_per_s": unique_pairs(w.n, w.rho, w.rc) * value,
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": used, "kind": "oracle",
+                         "sample": f"{k} of {args.steps} requested steps timed (bounded to ~90 s), 1 warm-up"},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    from paper_0709_3225_gb300 import inputs, lj
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    x, v, L, w = inputs.workload_state(WORKLOAD)
+    n = w.n
+    pairs = unique_pairs(n, w.rho, w.rc)
+
+    # ---- FP32-mixed, device-resident (the headline `value`) --------------
+    s = lj.System(x, v, L, precision="mixed", dt=w.dt, rc=w.rc)
+    s.forces()
+    s.step(args.warmup)
+    s.check()
+    lj.lj_set_timing(s.ctx, True)
+    _, _, k0 = lj.lj_read_timing(s.ctx)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        lj.lj_step(s.ctx, s.x, s.v, s.f, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms_total = ev0.elapsed_time(ev1)
+    s.check()
+    force_ms, force_n, k1 = lj.lj_read_timing(s.ctx)
+    lj.lj_set_timing(s.ctx, False)
+    launches = k1 - k0
+    ms_total = max_over_ranks(world, ms_total)
+    ms_step = ms_total / args.steps
+    value = world * args.steps / (ms_total / 1e3)
+    force_avg_ms = force_ms / max(force_n, 1)
+    achieved_tflops = FLOPS_PER_PAIR * pairs / (force_avg_ms / 1e3) / 1e12
+    clocks = clk.summary()
+
+    # HBM view of the non-force kernels: algorithmic bytes per particle per step
+    # (kick-drift-bin 120 B, scatter 56 B, force in/out 32 B).
+    other_ms = ms_step - force_avg_ms
+
+    # ---- end to end through the host-buffer entry point ------------------
+    e2e_steps = max(3, min(20, args.steps))
+    xh = torch.from_numpy(s.x.cpu().numpy()).pin_memory()
+    vh = torch.from_numpy(s.v.cpu().numpy()).pin_memory()
+    fh = torch.from_numpy(s.f.cpu().numpy()).pin_memory()
+    lj.lj_step_host(s.ctx, xh, vh, fh, 1)           # warm the staging buffers
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lj.lj_step_host(s.ctx, xh, vh, fh, 1)
+    t_e2e = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_value = world * e2e_steps / t_e2e
+    bytes_h2d = n * (3 * 8 + 3 * 8 + 4 * 4)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+
+    # ---- plain FP64 GPU path on the same workload --------------------------
+    s64 = lj.System(x, v, L, precision="fp64", dt=w.dt, rc=w.rc)
+    s64.forces()
+    s64.step(2)
+    k64 = max(3, min(10, args.steps))
+    lj.lj_set_timing(s64.ctx, True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    lj.lj_step(s64.ctx, s64.x, s64.v, s64.f, k64)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    s64.check()
+    ms64 = ev0.elapsed_time(ev1) / k64
+    f64_ms, f64_n, _ = lj.lj_read_timing(s64.ctx)
+    s64.close()
+    del s64
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    peaks = read_peaks()
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "force_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as fh:
+            t = json.load(fh)
+        if t.get("kernel_rev") == FORCE_KERNEL_REV:
+            traffic = t.get("bytes_per_launch")
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "rho": w.rho, "T": w.temperature, "rc": w.rc, "dt": w.dt,
+                   "start": "fcc lattice", "precision": "mixed (FP32 pairs, FP64 x/v/energy)",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (x, v 96 MB each, forces and sorted positions 64 MB each)"},
+        "pair_interactions_per_s": pairs * value,
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "k_force (mixed)", "force_ms_per_launch": force_avg_ms,
+                     "flops_per_launch": FLOPS_PER_PAIR * pairs,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+        "other_kernels_ms_per_step": other_ms,
+        "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
+                 "force_ms_per_launch": f64_ms / max(f64_n, 1),
+                 "pair_interactions_per_s": pairs * 1e3 / ms64},
+        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": bytes_h2d,
+                "d2h_bytes_per_step": bytes_h2d, "steps": e2e_steps,
+                "api": "lj_step_host, pinned host x, v, f; 1 step per call"},
+        "clocks": clocks,
+        "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(x, v, L, w)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+# Revision tag of the force kernel the committed ncu traffic figure belongs
+# to; bump when the kernel changes so a stale figure is reported as null.
+FORCE_KERNEL_REV = "v1"
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=180)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    from __graft_entry__ import build
+    build()
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

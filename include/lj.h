@@ -1,0 +1,172 @@
+/*
+ * lj.h -- C ABI of liblj.so, a GB300 (sm_103a) implementation of the
+ * short-ranged molecular-dynamics hot path of van Meel, Arnold, Frenkel,
+ * Portegies Zwart and Belleman, "Harvesting graphics power for MD
+ * simulations" (arXiv:0709.3225):
+ *
+ *   - periodic Lennard-Jones forces over cell lists with cutoff rc and the
+ *     minimum image (Section 2, Eq. n2_force and the truncated/shifted LJ
+ *     force; Section 3, cell lists over the centre cell and its 26
+ *     neighbours);
+ *   - the cell lists rebuilt at every step by a counting sort (Section 3.1
+ *     places particles physically together per cell; here: count, scan and
+ *     scatter into one sorted array);
+ *   - velocity-Verlet integration (Section 2, last paragraph), run entirely
+ *     on the GPU (Section 1).
+ *
+ * Conventions shared by every entry point:
+ *   - Reduced units.  Positions x and velocities v are row-major (n, 3)
+ *     IEEE double arrays.  Forces f are (n, 4): float x, y, z, e for
+ *     LJ_PREC_MIXED, double x, y, z, e for LJ_PREC_FP64, where e is the
+ *     particle's share (half of each pair energy) of the potential energy
+ *     when energies were requested and 0 otherwise.
+ *   - Unless the name ends in _host, array arguments are DEVICE pointers on
+ *     the context's device, owned by the caller, 16-byte aligned (any
+ *     cudaMalloc / torch allocation is), and must stay valid until the work
+ *     queued on the context's stream has finished.
+ *   - Work is queued asynchronously on the stream given to lj_create.  Calls
+ *     that return host scalars (e_pot, virial, lj_energy, lj_check,
+ *     lj_read_timing, lj_step_host) synchronize that stream first.
+ *   - Every call returns an lj_status; nothing crosses the ABI as an
+ *     exception.  Errors found inside kernels (non-finite coordinates, a
+ *     wait that timed out) are latched on the device and returned by the
+ *     next synchronizing call.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef LJ_H
+#define LJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LJ_ABI_VERSION 1
+
+typedef enum lj_status {
+    LJ_OK = 0,
+    LJ_EINVAL = 1,      /* bad argument (NULL, size, mode, misaligned pointer) */
+    LJ_EBOX = 2,        /* box too small: fewer than 2k+1 cells per side */
+    LJ_ECUDA = 3,       /* a CUDA runtime call failed */
+    LJ_ENONFINITE = 4,  /* a position was NaN or infinite */
+    LJ_ETIMEOUT = 5,    /* a bounded device wait expired */
+    LJ_EOVERFLOW = 6,   /* an index would not fit in 32 bits */
+    LJ_ENOMEM = 7       /* device or host allocation failed */
+} lj_status;
+
+typedef enum lj_shift {
+    LJ_SHIFT_NONE = 0,   /* plain truncation at rc */
+    LJ_SHIFT_ENERGY = 1, /* U - U(rc) for r < rc: energy continuous at rc */
+    LJ_SHIFT_FORCE = 2   /* F - F(rc) (the paper's Section 2 form) and the
+                            matching energy U - U(rc) + (r - rc) F(rc) */
+} lj_shift;
+
+typedef enum lj_precision {
+    LJ_PREC_MIXED = 0,   /* FP32 pair arithmetic and per-particle sums,
+                            FP64 positions, integrator, energy and virial */
+    LJ_PREC_FP64 = 1     /* FP64 throughout */
+} lj_precision;
+
+/* Simulation parameters (Section 2 and 3: N, box, eps, sigma, rc, dt). */
+typedef struct lj_params {
+    int64_t n;           /* number of particles, 0 <= n < 2^31 */
+    double box;          /* cubic periodic box side L > 0 */
+    double eps;          /* LJ well depth, >= 0 */
+    double sigma;        /* LJ diameter, > 0 */
+    double rc;           /* cutoff radius, > 0 (the paper uses 2.5 sigma) */
+    double dt;           /* time step for lj_step */
+    double mass;         /* particle mass, > 0 */
+    int32_t shift_mode;  /* lj_shift */
+    int32_t precision;   /* lj_precision */
+    int32_t cell_subdiv; /* cells per rc along each axis: 1 (27-cell stencil,
+                            Section 3) or 0 for the default (1) */
+    int32_t flags;       /* 0 or LJ_FLAG_NO_STAGING */
+} lj_params;
+
+/* lj_params.flags: the force kernel reads neighbour cells straight from
+ * global memory instead of staging them in shared memory with bulk copies
+ * (same results; for comparison and diagnosis). */
+#define LJ_FLAG_NO_STAGING 1
+
+typedef struct lj_ctx lj_ctx;
+
+/* Library ABI version (LJ_ABI_VERSION). Host only. */
+int lj_version(void);
+
+/* Human-readable name of a status code. Host only; never NULL. */
+const char *lj_strerror(int code);
+
+/* Cells per box side for these parameters, n_x = int[k L / rc]
+ * (Section 3.2, worked example L = 11 sigma, rc = 2.5 sigma -> 4), and
+ * validation of p.  Host only, needs no GPU.  Returns LJ_EBOX when
+ * n_x < 2k + 1 (Section 3.2 requires at least 3 cells per dimension),
+ * LJ_EINVAL for bad parameters. */
+int lj_grid(const lj_params *p, int32_t *nc_out);
+
+/* Create a context on the current CUDA device.  Allocates all device
+ * scratch (cell arrays, sorted positions, partial sums) once; no later call
+ * allocates on the device except lj_step_host and lj_energy, which allocate
+ * their staging buffers on first use.  stream is a cudaStream_t (NULL = the
+ * legacy default stream).  On error *out is NULL. */
+int lj_create(lj_ctx **out, const lj_params *p, void *stream);
+
+/* Free a context (synchronizes its stream).  NULL is ignored. */
+void lj_destroy(lj_ctx *ctx);
+
+/* Bin x into cells (counting sort): for each particle the wrapped position
+ * w = x - L floor(x / L) (w >= L folds to w - L), the cell coordinate
+ * c = trunc(w * (n_x / L)) clamped to [0, n_x - 1] per axis, the linear id
+ * c_x + n_x (c_y + n_x c_z); per-cell counts and exclusive starts; the
+ * sorted order.  x: device (n, 3) double, not modified. */
+int lj_bin(lj_ctx *ctx, const double *x);
+
+/* Copy the result of the last binning to caller-owned DEVICE arrays (any
+ * may be NULL): cell_of[n], count[n_x^3], start[n_x^3 + 1], perm[n], where
+ * perm[start[c] .. start[c+1]) lists the particles of cell c (their order
+ * within a cell is unspecified). */
+int lj_get_cells(lj_ctx *ctx, int32_t *cell_of, int32_t *count, int32_t *start, int32_t *perm);
+
+/* Bin x, then f_i = sum_{j != i, r_ij < rc} F(r_ij) (x_i - x_j)/r_ij over
+ * the 27 surrounding cells at the minimum image (Eq. n2_force restricted to
+ * the cutoff, Section 3).  f: device (n, 4) float or double per the
+ * precision.  If e_pot or virial is non-NULL the potential energy
+ * sum_{i<j} U(r_ij) and the virial sum_{i<j} r_ij F(r_ij) (FP64) are written
+ * to those HOST addresses (synchronizes), and f[:, 3] holds per-particle
+ * energies. */
+int lj_forces(lj_ctx *ctx, const double *x, void *f, double *e_pot, double *virial);
+
+/* nsteps velocity-Verlet steps (Section 2): v += dt/(2m) f; x += dt v;
+ * x wrapped into [0, L); cells rebuilt; f = F(x); v += dt/(2m) f.
+ * x, v: device (n, 3) double, updated in place.  f: device (n, 4), must hold
+ * F(x) on entry (from lj_forces or a previous lj_step) and holds F at the
+ * final positions on return. */
+int lj_step(lj_ctx *ctx, double *x, double *v, void *f, int32_t nsteps);
+
+/* As lj_step on HOST arrays (pageable or pinned): copies x, v, f to the
+ * device, steps, copies them back, synchronizes. */
+int lj_step_host(lj_ctx *ctx, double *x, double *v, void *f, int32_t nsteps);
+
+/* out[0] = kinetic energy (1/2) m sum v^2, out[1] = potential energy at x,
+ * out[2] = their sum; FP64; out is a HOST array of 3.  x, v: device.
+ * Synchronizes. */
+int lj_energy(lj_ctx *ctx, const double *x, const double *v, double *out);
+
+/* Synchronize the stream and return (and clear) any error latched by a
+ * kernel since the last check. */
+int lj_check(lj_ctx *ctx);
+
+/* Enable (1) or disable (0) CUDA-event timing of the force kernel on the
+ * context's stream; enabling resets the counters. */
+int lj_set_timing(lj_ctx *ctx, int32_t enable);
+
+/* Synchronize and read: total milliseconds spent in force-kernel launches
+ * timed since timing was enabled, their number, and the number of kernels
+ * this context has launched since creation.  Any pointer may be NULL. */
+int lj_read_timing(lj_ctx *ctx, double *force_ms, int64_t *force_launches, int64_t *kernel_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LJ_H */

@@ -1,0 +1,404 @@
+// C ABI of liblj.so (declared in include/lj.h): context management,
+// argument checking and the sequencing of the kernels of one MD step.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lj_internal.cuh"
+
+namespace {
+
+constexpr int kEventPool = 2 * 8192;
+
+int map_cuda(cudaError_t e)
+{
+    return e == cudaErrorMemoryAllocation ? LJ_ENOMEM : LJ_ECUDA;
+}
+
+#define LJ_CK(call)                                     \
+    do {                                                \
+        cudaError_t lj_ck_e_ = (call);                  \
+        if (lj_ck_e_ != cudaSuccess) return map_cuda(lj_ck_e_); \
+    } while (0)
+
+int validate(const lj_params *p, int *nc_out)
+{
+    if (!p) return LJ_EINVAL;
+    if (p->n < 0) return LJ_EINVAL;
+    if (p->n >= INT32_MAX) return LJ_EOVERFLOW;
+    if (!(p->box > 0.0) || !isfinite(p->box)) return LJ_EINVAL;
+    if (!(p->sigma > 0.0) || !isfinite(p->sigma)) return LJ_EINVAL;
+    if (!(p->rc > 0.0) || !isfinite(p->rc)) return LJ_EINVAL;
+    if (!(p->mass > 0.0) || !isfinite(p->mass)) return LJ_EINVAL;
+    if (!(p->eps >= 0.0) || !isfinite(p->eps)) return LJ_EINVAL;
+    if (!isfinite(p->dt)) return LJ_EINVAL;
+    if (p->shift_mode < LJ_SHIFT_NONE || p->shift_mode > LJ_SHIFT_FORCE) return LJ_EINVAL;
+    if (p->precision != LJ_PREC_MIXED && p->precision != LJ_PREC_FP64) return LJ_EINVAL;
+    if (p->cell_subdiv != 0 && p->cell_subdiv != 1) return LJ_EINVAL;
+    if ((p->flags & ~LJ_FLAG_NO_STAGING) != 0) return LJ_EINVAL;
+    const int k = 1;
+    double q = floor(((double)k * p->box) / p->rc);
+    if (!(q >= 2.0 * k + 1.0)) return LJ_EBOX;
+    if (q > 1290.0) return LJ_EOVERFLOW;   // nc^3 + 1 must fit in int32
+    if (nc_out) *nc_out = (int)q;
+    return LJ_OK;
+}
+
+// Device (or managed) memory check for caller arrays.
+int check_dev_ptr(const void *ptr, size_t align)
+{
+    if (!ptr) return LJ_EINVAL;
+    if (((uintptr_t)ptr) % align != 0) return LJ_EINVAL;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LJ_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return LJ_EINVAL;
+    return LJ_OK;
+}
+
+size_t force_vsize(const lj_ctx *c)
+{
+    return c->p.precision == LJ_PREC_FP64 ? sizeof(double4_16a) : sizeof(float4);
+}
+
+void free_ctx(lj_ctx *c)
+{
+    if (!c) return;
+    cudaFree(c->cell_of);
+    cudaFree(c->rank);
+    cudaFree(c->count);
+    cudaFree(c->start);
+    cudaFree(c->perm);
+    cudaFree(c->pos);
+    cudaFree(c->tile_sum);
+    cudaFree(c->partial);
+    cudaFree(c->ekin_partial);
+    cudaFree(c->scalars);
+    cudaFree(c->err);
+    cudaFree(c->xs);
+    cudaFree(c->vs);
+    cudaFree(c->fs);
+    if (c->host_scalars) cudaFreeHost(c->host_scalars);
+    if (c->host_err) cudaFreeHost(c->host_err);
+    if (c->ev) {
+        for (int i = 0; i < c->nev; i++) cudaEventDestroy(c->ev[i]);
+        free(c->ev);
+    }
+    free(c);
+}
+
+// Synchronize, read and clear latched kernel errors.
+int sync_and_check(lj_ctx *c)
+{
+    LJ_CK(cudaStreamSynchronize(c->stream));
+    LJ_CK(cudaMemcpyAsync(c->host_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    LJ_CK(cudaStreamSynchronize(c->stream));
+    int32_t bits = *c->host_err;
+    if (bits) {
+        LJ_CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
+        LJ_CK(cudaStreamSynchronize(c->stream));
+    }
+    if (bits & LJ_ERRBIT_NONFINITE) return LJ_ENONFINITE;
+    if (bits & LJ_ERRBIT_TIMEOUT) return LJ_ETIMEOUT;
+    if (bits & LJ_ERRBIT_SCAN) return LJ_ECUDA;
+    return LJ_OK;
+}
+
+int do_bin(lj_ctx *c, const double *x, bool wrap_in_scatter)
+{
+    LJ_CK(launch_bin_count(c, x));
+    LJ_CK(launch_scan(c));
+    LJ_CK(launch_scatter(c, x, wrap_in_scatter));
+    return LJ_OK;
+}
+
+int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps)
+{
+    for (int s = 0; s < nsteps; s++) {
+        LJ_CK(launch_kick_drift_bin(c, x, v, f, s == 0 ? 1 : 2));
+        LJ_CK(launch_scan(c));
+        LJ_CK(launch_scatter(c, x, false));
+        LJ_CK(launch_force(c, f, false));
+    }
+    if (nsteps > 0) LJ_CK(launch_kick(c, v, f));
+    return LJ_OK;
+}
+
+int ensure_staging(lj_ctx *c)
+{
+    size_t n1 = (size_t)(c->p.n > 0 ? c->p.n : 1);
+    if (!c->xs) LJ_CK(cudaMalloc(&c->xs, 3 * n1 * sizeof(double)));
+    if (!c->vs) LJ_CK(cudaMalloc(&c->vs, 3 * n1 * sizeof(double)));
+    if (!c->fs) LJ_CK(cudaMalloc(&c->fs, n1 * force_vsize(c)));
+    return LJ_OK;
+}
+
+}  // namespace
+
+extern "C" int lj_version(void) { return LJ_ABI_VERSION; }
+
+extern "C" const char *lj_strerror(int code)
+{
+    switch (code) {
+        case LJ_OK: return "ok";
+        case LJ_EINVAL: return "invalid argument";
+        case LJ_EBOX: return "box too small for the cell stencil (need at least 3 cells per side)";
+        case LJ_ECUDA: return "CUDA runtime error";
+        case LJ_ENONFINITE: return "non-finite particle coordinate";
+        case LJ_ETIMEOUT: return "bounded device wait timed out";
+        case LJ_EOVERFLOW: return "size exceeds 32-bit indexing";
+        case LJ_ENOMEM: return "out of memory";
+        default: return "unknown lj status";
+    }
+}
+
+extern "C" int lj_grid(const lj_params *p, int32_t *nc_out)
+{
+    int nc = 0;
+    int r = validate(p, &nc);
+    if (r != LJ_OK) return r;
+    if (nc_out) *nc_out = nc;
+    return LJ_OK;
+}
+
+extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
+{
+    if (!out) return LJ_EINVAL;
+    *out = nullptr;
+    int nc = 0;
+    int r = validate(p, &nc);
+    if (r != LJ_OK) return r;
+    lj_ctx *c = (lj_ctx *)calloc(1, sizeof(lj_ctx));
+    if (!c) return LJ_ENOMEM;
+    c->p = *p;
+    if (c->p.cell_subdiv == 0) c->p.cell_subdiv = 1;
+    c->nc = nc;
+    c->ncell = (int64_t)nc * nc * nc;
+    c->inv_cw = (double)nc / p->box;
+    c->cw = p->box / (double)nc;
+    c->stream = (cudaStream_t)stream;
+    c->use_tma = (p->flags & LJ_FLAG_NO_STAGING) ? 0 : 1;
+
+#define LJ_CREATE_CK(call)            \
+    do {                              \
+        cudaError_t e_ = (call);      \
+        if (e_ != cudaSuccess) {      \
+            free_ctx(c);              \
+            return map_cuda(e_);      \
+        }                             \
+    } while (0)
+
+    LJ_CREATE_CK(cudaGetDevice(&c->device));
+    LJ_CREATE_CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+    const size_t n1 = (size_t)(p->n > 0 ? p->n : 1);
+    LJ_CREATE_CK(cudaMalloc(&c->cell_of, n1 * sizeof(int32_t)));
+    LJ_CREATE_CK(cudaMalloc(&c->rank, n1 * sizeof(int32_t)));
+    LJ_CREATE_CK(cudaMalloc(&c->perm, n1 * sizeof(int32_t)));
+    LJ_CREATE_CK(cudaMalloc(&c->count, (size_t)c->ncell * sizeof(int32_t)));
+    LJ_CREATE_CK(cudaMalloc(&c->start, (size_t)(c->ncell + 1) * sizeof(int32_t)));
+    LJ_CREATE_CK(cudaMalloc(&c->pos, n1 * force_vsize(c)));
+    c->ntiles = (int)((c->ncell + kScanTile - 1) / kScanTile);
+    LJ_CREATE_CK(cudaMalloc(&c->tile_sum, (size_t)c->ntiles * sizeof(int32_t)));
+    LJ_CREATE_CK(force_configure(c));
+    LJ_CREATE_CK(cudaMalloc(&c->partial, 2 * (size_t)c->force_grid * sizeof(double)));
+    int64_t eb = (3 * (int64_t)n1 + kReduceThreads - 1) / kReduceThreads;
+    c->ekin_grid = (int)(eb < 4 * (int64_t)c->nsm ? eb : 4 * (int64_t)c->nsm);
+    LJ_CREATE_CK(cudaMalloc(&c->ekin_partial, (size_t)c->ekin_grid * sizeof(double)));
+    LJ_CREATE_CK(cudaMalloc(&c->scalars, 4 * sizeof(double)));
+    LJ_CREATE_CK(cudaMalloc(&c->err, sizeof(int32_t)));
+    LJ_CREATE_CK(cudaMallocHost(&c->host_scalars, 4 * sizeof(double)));
+    LJ_CREATE_CK(cudaMallocHost(&c->host_err, sizeof(int32_t)));
+    LJ_CREATE_CK(cudaMemsetAsync(c->count, 0, (size_t)c->ncell * sizeof(int32_t), c->stream));
+    LJ_CREATE_CK(cudaMemsetAsync(c->start, 0, (size_t)(c->ncell + 1) * sizeof(int32_t), c->stream));
+    LJ_CREATE_CK(cudaMemsetAsync(c->scalars, 0, 4 * sizeof(double), c->stream));
+    LJ_CREATE_CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
+    LJ_CREATE_CK(cudaStreamSynchronize(c->stream));
+#undef LJ_CREATE_CK
+    *out = c;
+    return LJ_OK;
+}
+
+extern "C" void lj_destroy(lj_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+extern "C" int lj_bin(lj_ctx *c, const double *x)
+{
+    if (!c) return LJ_EINVAL;
+    if (c->p.n > 0) {
+        int r = check_dev_ptr(x, 8);
+        if (r) return r;
+    }
+    return do_bin(c, x, true);
+}
+
+extern "C" int lj_get_cells(lj_ctx *c, int32_t *cell_of, int32_t *count, int32_t *start, int32_t *perm)
+{
+    if (!c) return LJ_EINVAL;
+    const size_t n = (size_t)c->p.n;
+    if (cell_of && n) {
+        int r = check_dev_ptr(cell_of, 4);
+        if (r) return r;
+        LJ_CK(cudaMemcpyAsync(cell_of, c->cell_of, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (perm && n) {
+        int r = check_dev_ptr(perm, 4);
+        if (r) return r;
+        LJ_CK(cudaMemcpyAsync(perm, c->perm, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (start) {
+        int r = check_dev_ptr(start, 4);
+        if (r) return r;
+        LJ_CK(cudaMemcpyAsync(start, c->start, (size_t)(c->ncell + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                              c->stream));
+    }
+    if (count) {
+        int r = check_dev_ptr(count, 4);
+        if (r) return r;
+        LJ_CK(launch_counts_from_start(c, count));
+    }
+    return LJ_OK;
+}
+
+extern "C" int lj_forces(lj_ctx *c, const double *x, void *f, double *e_pot, double *virial)
+{
+    if (!c) return LJ_EINVAL;
+    if (c->p.n > 0) {
+        int r = check_dev_ptr(x, 8);
+        if (r) return r;
+        r = check_dev_ptr(f, 16);
+        if (r) return r;
+    }
+    int r = do_bin(c, x, true);
+    if (r) return r;
+    const bool energy = e_pot || virial;
+    LJ_CK(launch_force(c, f, energy));
+    if (!energy) return LJ_OK;
+    LJ_CK(cudaMemsetAsync(c->scalars, 0, 2 * sizeof(double), c->stream));
+    if (c->p.n > 0) LJ_CK(launch_energy_reduce(c));
+    LJ_CK(cudaMemcpyAsync(c->host_scalars, c->scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    r = sync_and_check(c);
+    if (r) return r;
+    if (e_pot) *e_pot = c->host_scalars[0];
+    if (virial) *virial = c->host_scalars[1];
+    return LJ_OK;
+}
+
+extern "C" int lj_step(lj_ctx *c, double *x, double *v, void *f, int32_t nsteps)
+{
+    if (!c || nsteps < 0) return LJ_EINVAL;
+    if (c->p.n > 0 && nsteps > 0) {
+        int r = check_dev_ptr(x, 8);
+        if (r) return r;
+        r = check_dev_ptr(v, 8);
+        if (r) return r;
+        r = check_dev_ptr(f, 16);
+        if (r) return r;
+    }
+    return do_steps(c, x, v, f, nsteps);
+}
+
+extern "C" int lj_step_host(lj_ctx *c, double *x, double *v, void *f, int32_t nsteps)
+{
+    if (!c || nsteps < 0) return LJ_EINVAL;
+    const size_t n = (size_t)c->p.n;
+    if (n > 0 && (!x || !v || !f)) return LJ_EINVAL;
+    int r = ensure_staging(c);
+    if (r) return r;
+    const size_t bx = 3 * n * sizeof(double), bf = n * force_vsize(c);
+    if (n > 0) {
+        LJ_CK(cudaMemcpyAsync(c->xs, x, bx, cudaMemcpyHostToDevice, c->stream));
+        LJ_CK(cudaMemcpyAsync(c->vs, v, bx, cudaMemcpyHostToDevice, c->stream));
+        LJ_CK(cudaMemcpyAsync(c->fs, f, bf, cudaMemcpyHostToDevice, c->stream));
+    }
+    r = do_steps(c, c->xs, c->vs, c->fs, nsteps);
+    if (r) return r;
+    if (n > 0) {
+        LJ_CK(cudaMemcpyAsync(x, c->xs, bx, cudaMemcpyDeviceToHost, c->stream));
+        LJ_CK(cudaMemcpyAsync(v, c->vs, bx, cudaMemcpyDeviceToHost, c->stream));
+        LJ_CK(cudaMemcpyAsync(f, c->fs, bf, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return sync_and_check(c);
+}
+
+extern "C" int lj_energy(lj_ctx *c, const double *x, const double *v, double *out)
+{
+    if (!c || !out) return LJ_EINVAL;
+    if (c->p.n > 0) {
+        int r = check_dev_ptr(x, 8);
+        if (r) return r;
+        r = check_dev_ptr(v, 8);
+        if (r) return r;
+    }
+    int r = ensure_staging(c);
+    if (r) return r;
+    LJ_CK(cudaMemsetAsync(c->scalars, 0, 4 * sizeof(double), c->stream));
+    if (c->p.n > 0) {
+        LJ_CK(launch_ekin(c, v));
+        r = do_bin(c, x, true);
+        if (r) return r;
+        LJ_CK(launch_force(c, c->fs, true));
+        LJ_CK(launch_energy_reduce(c));
+    }
+    LJ_CK(cudaMemcpyAsync(c->host_scalars, c->scalars, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    r = sync_and_check(c);
+    if (r) return r;
+    out[0] = c->host_scalars[2];
+    out[1] = c->host_scalars[0];
+    out[2] = out[0] + out[1];
+    return LJ_OK;
+}
+
+extern "C" int lj_check(lj_ctx *c)
+{
+    if (!c) return LJ_EINVAL;
+    return sync_and_check(c);
+}
+
+extern "C" int lj_set_timing(lj_ctx *c, int32_t enable)
+{
+    if (!c) return LJ_EINVAL;
+    if (enable) {
+        if (!c->ev) {
+            c->ev = (cudaEvent_t *)calloc(kEventPool, sizeof(cudaEvent_t));
+            if (!c->ev) return LJ_ENOMEM;
+            for (int i = 0; i < kEventPool; i++) {
+                cudaError_t e = cudaEventCreate(&c->ev[i]);
+                if (e != cudaSuccess) {
+                    c->nev = i;
+                    return map_cuda(e);
+                }
+            }
+            c->nev = kEventPool;
+        }
+        LJ_CK(cudaStreamSynchronize(c->stream));
+        c->ev_used = 0;
+        c->force_ms = 0.0;
+        c->force_launches = 0;
+    }
+    c->timing = enable ? 1 : 0;
+    return LJ_OK;
+}
+
+extern "C" int lj_read_timing(lj_ctx *c, double *force_ms, int64_t *force_launches, int64_t *kernel_launches)
+{
+    if (!c) return LJ_EINVAL;
+    LJ_CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i + 1 < c->ev_used; i += 2) {
+        float ms = 0.0f;
+        LJ_CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+        c->force_ms += ms;
+        c->force_launches++;
+    }
+    c->ev_used = 0;
+    if (force_ms) *force_ms = c->force_ms;
+    if (force_launches) *force_launches = c->force_launches;
+    if (kernel_launches) *kernel_launches = c->kernel_launches;
+    return LJ_OK;
+}

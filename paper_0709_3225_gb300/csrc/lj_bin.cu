@@ -1,0 +1,195 @@
+// Cell binning as a counting sort: count (atomics), exclusive scan, scatter.
+// This rebuilds the cell lists of Section 3 from scratch at every call; the
+// sorted positions play the role of the paper's per-cell arrays of
+// placeholders (Section 3.1: particles of a cell physically together in
+// memory) without a fixed capacity.
+#include "lj_internal.cuh"
+
+namespace {
+
+// Per particle: wrapped position, cell id, rank within the cell (atomic).
+__global__ void k_bin_count(const double *__restrict__ x, int n, double L, double s, int nc,
+                            int32_t *__restrict__ cell_of, int32_t *__restrict__ rank,
+                            int32_t *__restrict__ count, int32_t *__restrict__ err)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double px = x[3 * (int64_t)i + 0], py = x[3 * (int64_t)i + 1], pz = x[3 * (int64_t)i + 2];
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
+    int cx = lj_cell1(lj_wrap(px, L), s, nc);
+    int cy = lj_cell1(lj_wrap(py, L), s, nc);
+    int cz = lj_cell1(lj_wrap(pz, L), s, nc);
+    int c = cx + nc * (cy + nc * cz);
+    cell_of[i] = c;
+    rank[i] = atomicAdd(count + c, 1);
+}
+
+// Scan phase 1: sum of each tile of kScanTile counts.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t *__restrict__ count, int64_t ncell,
+                                                             int32_t *__restrict__ tile_sum)
+{
+    __shared__ int32_t warp_sum[kScanThreads / 32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int32_t acc = 0;
+    for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+        int64_t e = base + k;
+        if (e < ncell) acc += count[e];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; w++) t += warp_sum[w];
+        tile_sum[blockIdx.x] = t;
+    }
+}
+
+// Scan phase 2: each tile adds the sum of all earlier tiles and scans its
+// own counts into start[].  Counts are reset to zero for the next binning.
+// The last tile writes start[ncell] and checks it against n.
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(int32_t *__restrict__ count, int64_t ncell,
+                                                             const int32_t *__restrict__ tile_sum,
+                                                             int32_t *__restrict__ start, int n,
+                                                             int32_t *__restrict__ err)
+{
+    __shared__ int32_t warp_tot[kScanThreads / 32];
+    __shared__ int32_t s_prefix;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+    // prefix of earlier tiles
+    int32_t pre = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += kScanThreads) pre += tile_sum[t];
+    for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+    if (lane == 0) warp_tot[wid] = pre;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; w++) t += warp_tot[w];
+        s_prefix = t;
+    }
+    __syncthreads();
+    const int32_t tile_prefix = s_prefix;
+
+    // thread-local run of kScanItems consecutive counts
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t local = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t e = base + k;
+        v[k] = e < ncell ? count[e] : 0;
+        local += v[k];
+    }
+    // block exclusive scan of the per-thread totals
+    int32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    int32_t warp_pre = 0;
+    for (int w = 0; w < wid; w++) warp_pre += warp_tot[w];
+    int32_t run = tile_prefix + warp_pre + incl - local;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t e = base + k;
+        if (e < ncell) {
+            start[e] = run;
+            count[e] = 0;
+        }
+        run += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) {
+        start[ncell] = run;
+        if (run != n) atomicOr(err, LJ_ERRBIT_SCAN);
+    }
+}
+
+// Scatter each particle to its sorted slot: perm[slot] = i and the position
+// relative to the centre of its cell (FP32 or FP64), with the particle index
+// carried in .w.
+template <typename T>
+__global__ void k_scatter(const double *__restrict__ x, int n, double L, double cw, int nc, bool wrap,
+                          const int32_t *__restrict__ cell_of, const int32_t *__restrict__ rank,
+                          const int32_t *__restrict__ start, int32_t *__restrict__ perm,
+                          typename Vec4<T>::type *__restrict__ pos)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cell_of[i];
+    int slot = start[c] + rank[i];
+    double px = x[3 * (int64_t)i + 0], py = x[3 * (int64_t)i + 1], pz = x[3 * (int64_t)i + 2];
+    if (wrap) {
+        px = lj_wrap(px, L);
+        py = lj_wrap(py, L);
+        pz = lj_wrap(pz, L);
+    }
+    int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    typename Vec4<T>::type q;
+    q.x = (T)(px - ((double)cx + 0.5) * cw);
+    q.y = (T)(py - ((double)cy + 0.5) * cw);
+    q.z = (T)(pz - ((double)cz + 0.5) * cw);
+    if constexpr (sizeof(T) == 4) {
+        q.w = __int_as_float(i);
+    } else {
+        q.w = (double)i;
+    }
+    perm[slot] = i;
+    pos[slot] = q;
+}
+
+__global__ void k_counts_from_start(const int32_t *__restrict__ start, int64_t ncell, int32_t *__restrict__ count)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) count[c] = start[c + 1] - start[c];
+}
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_bin_count(lj_ctx *c, const double *x)
+{
+    int n = (int)c->p.n;
+    if (n > 0) {
+        k_bin_count<<<blocks_for(n, 256), 256, 0, c->stream>>>(x, n, c->p.box, c->inv_cw, c->nc, c->cell_of,
+                                                                c->rank, c->count, c->err);
+        c->kernel_launches++;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(lj_ctx *c)
+{
+    k_scan_tiles<<<c->ntiles, kScanThreads, 0, c->stream>>>(c->count, c->ncell, c->tile_sum);
+    k_scan_apply<<<c->ntiles, kScanThreads, 0, c->stream>>>(c->count, c->ncell, c->tile_sum, c->start,
+                                                             (int)c->p.n, c->err);
+    c->kernel_launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(lj_ctx *c, const double *x, bool wrap)
+{
+    int n = (int)c->p.n;
+    if (n > 0) {
+        if (c->p.precision == LJ_PREC_FP64)
+            k_scatter<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(
+                x, n, c->p.box, c->cw, c->nc, wrap, c->cell_of, c->rank, c->start, c->perm, (double4_16a *)c->pos);
+        else
+            k_scatter<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(
+                x, n, c->p.box, c->cw, c->nc, wrap, c->cell_of, c->rank, c->start, c->perm, (float4 *)c->pos);
+        c->kernel_launches++;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counts_from_start(lj_ctx *c, int32_t *count)
+{
+    k_counts_from_start<<<blocks_for(c->ncell, 256), 256, 0, c->stream>>>(c->start, c->ncell, count);
+    c->kernel_launches++;
+    return cudaGetLastError();
+}

@@ -1,0 +1,108 @@
+// Internal declarations shared by the liblj.so translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lj.h"
+
+// Error bits latched in device memory by kernels, mapped to lj_status by
+// lj_check.
+enum : int32_t {
+    LJ_ERRBIT_NONFINITE = 1,
+    LJ_ERRBIT_TIMEOUT = 2,
+    LJ_ERRBIT_SCAN = 4,
+};
+
+// Force-kernel geometry: a work item is a run of up to kRunMax consecutive
+// cells along x in one (y, z) row of cells; one consumer warp per home cell.
+constexpr int kRunMax = 8;
+constexpr int kWinMax = kRunMax + 2;           // window cells per row
+constexpr int kTabMax = 9 * kWinMax;           // 9 neighbour rows
+constexpr int kConsumerWarps = kRunMax;
+constexpr int kForceThreads = (kConsumerWarps + 1) * 32;  // + 1 producer warp
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+constexpr int kReduceThreads = 256;
+
+struct lj_ctx {
+    lj_params p;
+    int nc;              // cells per side
+    int64_t ncell;       // nc^3
+    double inv_cw;       // s = nc / L (cell index scale)
+    double cw;           // cell side L / nc
+    cudaStream_t stream;
+    int device;
+    int nsm;
+
+    // device scratch
+    int32_t *cell_of, *rank, *count, *start, *perm;
+    void *pos;           // float4 or double4_16a [n], sorted, cell-centred coordinates
+    int32_t *tile_sum;
+    int ntiles;
+    double *partial;     // force-kernel per-block (energy, virial) partials
+    double *ekin_partial;
+    double *scalars;     // [0] = E_pot, [1] = virial, [2] = E_kin
+    int32_t *err;
+    double *host_scalars;   // pinned, 4 doubles
+    int32_t *host_err;      // pinned
+
+    // force kernel configuration
+    int run_len, runs, nitems, cap, force_grid, force_smem, use_tma;
+    int ekin_grid;
+
+    // lazily allocated staging for lj_step_host / lj_energy
+    double *xs, *vs;
+    void *fs;
+
+    // timing
+    int timing;
+    cudaEvent_t *ev;
+    int nev, ev_used;
+    double force_ms;
+    int64_t force_launches;
+    int64_t kernel_launches;
+};
+
+// ---------------------------------------------------------------- device --
+
+// Wrap one coordinate into [0, L): w = x - L floor(x / L), then w >= L folds
+// to w - L.  Every operation is separately rounded (no contraction) so that
+// the cell assignment is reproducible bit for bit.
+__device__ __forceinline__ double lj_wrap(double x, double L)
+{
+    double q = floor(__ddiv_rn(x, L));
+    double w = __dsub_rn(x, __dmul_rn(L, q));
+    if (w >= L) w = __dsub_rn(w, L);
+    return w;
+}
+
+// Cell coordinate trunc(w * s), clamped to [0, nc - 1].
+__device__ __forceinline__ int lj_cell1(double w, double s, int nc)
+{
+    int c = __double2int_rz(__dmul_rn(w, s));
+    c = c < nc ? c : nc - 1;
+    c = c > 0 ? c : 0;
+    return c;
+}
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_16a; };
+
+// ------------------------------------------------------------------ host --
+
+// Kernel launchers (each returns cudaGetLastError()).
+cudaError_t launch_bin_count(lj_ctx *c, const double *x);
+cudaError_t launch_scan(lj_ctx *c);
+cudaError_t launch_scatter(lj_ctx *c, const double *x, bool wrap);
+cudaError_t launch_force(lj_ctx *c, void *f, bool energy);
+cudaError_t launch_energy_reduce(lj_ctx *c);
+cudaError_t launch_kick_drift_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick);
+cudaError_t launch_kick(lj_ctx *c, double *v, const void *f);
+cudaError_t launch_ekin(lj_ctx *c, const double *v);
+cudaError_t launch_counts_from_start(lj_ctx *c, int32_t *count);
+cudaError_t force_configure(lj_ctx *c);

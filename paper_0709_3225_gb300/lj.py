@@ -1,0 +1,316 @@
+"""Thin ctypes binding of liblj.so (C ABI in include/lj.h).
+
+The functions carry the C names and do argument marshalling only: they check
+dtypes, shapes and devices of torch tensors and pass raw pointers.  Every
+step of the MD path runs in the library's CUDA kernels; there is no CPU
+fallback.  If the library has not been built, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblj.so")
+
+LJ_OK, LJ_EINVAL, LJ_EBOX, LJ_ECUDA, LJ_ENONFINITE, LJ_ETIMEOUT, LJ_EOVERFLOW, LJ_ENOMEM = range(8)
+LJ_SHIFT_NONE, LJ_SHIFT_ENERGY, LJ_SHIFT_FORCE = 0, 1, 2
+LJ_PREC_MIXED, LJ_PREC_FP64 = 0, 1
+LJ_FLAG_NO_STAGING = 1
+
+_PREC = {"mixed": LJ_PREC_MIXED, "fp64": LJ_PREC_FP64, LJ_PREC_MIXED: LJ_PREC_MIXED, LJ_PREC_FP64: LJ_PREC_FP64}
+
+
+class lj_params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("box", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("rc", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("mass", ctypes.c_double),
+        ("shift_mode", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("cell_subdiv", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
+    ]
+
+
+def make_params(n: int, box: float, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5,
+                dt: float = 0.005, mass: float = 1.0, shift_mode: int = LJ_SHIFT_ENERGY,
+                precision="mixed", cell_subdiv: int = 1, flags: int = 0) -> lj_params:
+    return lj_params(int(n), float(box), float(eps), float(sigma), float(rc), float(dt), float(mass),
+                     int(shift_mode), _PREC[precision], int(cell_subdiv), int(flags))
+
+
+class LJError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {lj_strerror(code)} (status {code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+# Every entry point of include/lj.h with its ctypes signature.
+_P = ctypes.c_void_p
+_SIGS = {
+    "lj_version": ([], ctypes.c_int),
+    "lj_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "lj_grid": ([ctypes.POINTER(lj_params), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "lj_create": ([ctypes.POINTER(_P), ctypes.POINTER(lj_params), _P], ctypes.c_int),
+    "lj_destroy": ([_P], None),
+    "lj_bin": ([_P, _P], ctypes.c_int),
+    "lj_get_cells": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "lj_forces": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "lj_step": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
+    "lj_step_host": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
+    "lj_energy": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "lj_check": ([_P], ctypes.c_int),
+    "lj_set_timing": ([_P, ctypes.c_int32], ctypes.c_int),
+    "lj_read_timing": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+}
+
+
+def load() -> ctypes.CDLL:
+    """Load liblj.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() "
+                               "(the CUDA library is required: there is no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _ck(code: int, where: str) -> None:
+    if code != LJ_OK:
+        raise LJError(code, where)
+
+
+def lj_version() -> int:
+    return load().lj_version()
+
+
+def lj_strerror(code: int) -> str:
+    return load().lj_strerror(int(code)).decode()
+
+
+def lj_grid(params: lj_params) -> int:
+    nc = ctypes.c_int32()
+    _ck(load().lj_grid(ctypes.byref(params), ctypes.byref(nc)), "lj_grid")
+    return nc.value
+
+
+def _stream_ptr(stream) -> int | None:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+def _dev(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns an lj_ctx*; ``params`` and ``nc`` are kept for marshalling."""
+
+    def __init__(self, params: lj_params, stream=None):
+        self.params = params
+        self.nc = lj_grid(params)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _ck(load().lj_create(ctypes.byref(h), ctypes.byref(params), _stream_ptr(stream)), "lj_create")
+        self.handle = h
+
+    @property
+    def n(self) -> int:
+        return int(self.params.n)
+
+    @property
+    def force_dtype(self):
+        import torch
+        return torch.float64 if self.params.precision == LJ_PREC_FP64 else torch.float32
+
+    def close(self) -> None:
+        if self.handle:
+            load().lj_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lj_create(params: lj_params, stream=None) -> Context:
+    return Context(params, stream)
+
+
+def lj_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def lj_bin(ctx: Context, x) -> None:
+    import torch
+    _ck(load().lj_bin(ctx.handle, _dev(x, torch.float64, (ctx.n, 3), "x")), "lj_bin")
+
+
+def lj_get_cells(ctx: Context, cell_of=None, count=None, start=None, perm=None) -> None:
+    import torch
+    ncell = ctx.nc ** 3
+    a = [None if cell_of is None else _dev(cell_of, torch.int32, (ctx.n,), "cell_of"),
+         None if count is None else _dev(count, torch.int32, (ncell,), "count"),
+         None if start is None else _dev(start, torch.int32, (ncell + 1,), "start"),
+         None if perm is None else _dev(perm, torch.int32, (ctx.n,), "perm")]
+    _ck(load().lj_get_cells(ctx.handle, *a), "lj_get_cells")
+
+
+def lj_forces(ctx: Context, x, f, energy: bool = False):
+    """Forces into f (n, 4); with energy=True returns (e_pot, virial)."""
+    import torch
+    xp = _dev(x, torch.float64, (ctx.n, 3), "x")
+    fp = _dev(f, ctx.force_dtype, (ctx.n, 4), "f")
+    if energy:
+        e = ctypes.c_double()
+        w = ctypes.c_double()
+        _ck(load().lj_forces(ctx.handle, xp, fp, ctypes.byref(e), ctypes.byref(w)), "lj_forces")
+        return e.value, w.value
+    _ck(load().lj_forces(ctx.handle, xp, fp, None, None), "lj_forces")
+    return None
+
+
+def lj_step(ctx: Context, x, v, f, nsteps: int) -> None:
+    import torch
+    _ck(load().lj_step(ctx.handle, _dev(x, torch.float64, (ctx.n, 3), "x"),
+                       _dev(v, torch.float64, (ctx.n, 3), "v"),
+                       _dev(f, ctx.force_dtype, (ctx.n, 4), "f"), int(nsteps)), "lj_step")
+
+
+def _host(a, dtype, shape, name):
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != dtype or tuple(a.shape) != tuple(shape) or not a.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU {dtype} tensor of shape {tuple(shape)}")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        npd = np.float64 if dtype == torch.float64 else np.float32
+        if a.dtype != npd or a.shape != tuple(shape) or not a.flags.c_contiguous:
+            raise ValueError(f"{name} must be a C-contiguous {npd.__name__} array of shape {tuple(shape)}")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"{name} must be a CPU tensor or numpy array")
+
+
+def lj_step_host(ctx: Context, x, v, f, nsteps: int) -> None:
+    """lj_step on host arrays (numpy or CPU tensors, pinned or not)."""
+    import torch
+    _ck(load().lj_step_host(ctx.handle, _host(x, torch.float64, (ctx.n, 3), "x"),
+                            _host(v, torch.float64, (ctx.n, 3), "v"),
+                            _host(f, ctx.force_dtype, (ctx.n, 4), "f"), int(nsteps)), "lj_step_host")
+
+
+def lj_energy(ctx: Context, x, v) -> tuple[float, float, float]:
+    """(kinetic, potential, total) energy, FP64."""
+    import torch
+    out = (ctypes.c_double * 3)()
+    _ck(load().lj_energy(ctx.handle, _dev(x, torch.float64, (ctx.n, 3), "x"),
+                         _dev(v, torch.float64, (ctx.n, 3), "v"), out), "lj_energy")
+    return out[0], out[1], out[2]
+
+
+def lj_check(ctx: Context) -> None:
+    _ck(load().lj_check(ctx.handle), "lj_check")
+
+
+def lj_set_timing(ctx: Context, enable: bool) -> None:
+    _ck(load().lj_set_timing(ctx.handle, 1 if enable else 0), "lj_set_timing")
+
+
+def lj_read_timing(ctx: Context) -> tuple[float, int, int]:
+    """(force-kernel ms, timed force launches, kernels launched)."""
+    ms = ctypes.c_double()
+    nf = ctypes.c_int64()
+    nk = ctypes.c_int64()
+    _ck(load().lj_read_timing(ctx.handle, ctypes.byref(ms), ctypes.byref(nf), ctypes.byref(nk)),
+        "lj_read_timing")
+    return ms.value, nf.value, nk.value
+
+
+class System:
+    """Convenience owner of a context and its device state (x, v, f).
+
+    x, v are (n, 3) float64 CUDA tensors, f is (n, 4) float32 (mixed) or
+    float64 (fp64)."""
+
+    def __init__(self, x, v, box: float, *, eps=1.0, sigma=1.0, rc=2.5, dt=0.005, mass=1.0,
+                 shift_mode=LJ_SHIFT_ENERGY, precision="mixed", flags=0, device=None, stream=None):
+        import torch
+        device = torch.device("cuda") if device is None else torch.device(device)
+        self.x = torch.as_tensor(np.asarray(x, dtype=np.float64)).to(device).contiguous()
+        n = self.x.shape[0]
+        if v is None:
+            self.v = torch.zeros((n, 3), dtype=torch.float64, device=device)
+        else:
+            self.v = torch.as_tensor(np.asarray(v, dtype=np.float64)).to(device).contiguous()
+        self.params = make_params(n, box, eps, sigma, rc, dt, mass, shift_mode, precision, 1, flags)
+        self.ctx = Context(self.params, stream)
+        self.f = torch.zeros((n, 4), dtype=self.ctx.force_dtype, device=device)
+        self._forces_valid = False
+
+    @property
+    def n(self) -> int:
+        return self.ctx.n
+
+    def forces(self, energy: bool = False):
+        r = lj_forces(self.ctx, self.x, self.f, energy)
+        self._forces_valid = True
+        return r
+
+    def step(self, nsteps: int) -> None:
+        if not self._forces_valid:
+            self.forces()
+        lj_step(self.ctx, self.x, self.v, self.f, nsteps)
+
+    def energy(self):
+        return lj_energy(self.ctx, self.x, self.v)
+
+    def cells(self):
+        import torch
+        dev = self.x.device
+        ncell = self.ctx.nc ** 3
+        cell_of = torch.empty(self.n, dtype=torch.int32, device=dev)
+        count = torch.empty(ncell, dtype=torch.int32, device=dev)
+        start = torch.empty(ncell + 1, dtype=torch.int32, device=dev)
+        perm = torch.empty(self.n, dtype=torch.int32, device=dev)
+        lj_bin(self.ctx, self.x)
+        lj_get_cells(self.ctx, cell_of, count, start, perm)
+        return cell_of, count, start, perm
+
+    def check(self) -> None:
+        lj_check(self.ctx)
+
+    def close(self) -> None:
+        self.ctx.close()

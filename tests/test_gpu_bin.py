@@ -1,0 +1,88 @@
+"""GPU binning parity: cell ids, counts and starts bit-exact against the
+oracle's serial counting sort; the order inside a cell is unspecified, so the
+permutation is compared as one set per cell."""
+import numpy as np
+import pytest
+
+from paper_0709_3225_gb300 import inputs
+
+from gpu_util import dense_cluster_state
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_cells(x, L, precision="mixed"):
+    from paper_0709_3225_gb300 import lj
+    s = lj.System(x, None, L, precision=precision)
+    out = [t.cpu().numpy() for t in s.cells()]
+    s.check()
+    nc = s.ctx.nc
+    s.close()
+    return nc, out
+
+
+def _compare(x, L, oracle_mod, precision="mixed"):
+    nc, (cell_of, count, start, perm) = _gpu_cells(x, L, precision)
+    assert nc == oracle_mod.ncells(L)
+    o_cell, o_count, o_start, o_perm = oracle_mod.bin_cells(x, L, nc)
+    assert np.array_equal(cell_of, o_cell)
+    assert np.array_equal(count, o_count)
+    assert np.array_equal(start, o_start)
+    # same set of particles in every cell
+    assert np.array_equal(np.sort(perm), np.arange(x.shape[0]))
+    key = cell_of[perm].astype(np.int64) * (x.shape[0] + 1) + perm
+    okey = o_cell[o_perm].astype(np.int64) * (x.shape[0] + 1) + o_perm
+    assert np.array_equal(np.sort(key), np.sort(okey))
+    assert np.array_equal(cell_of[perm], np.repeat(np.arange(nc ** 3), count))
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_fcc_2k(oracle_mod, precision):
+    x, _, L, _ = inputs.workload_state("fluid-2k")
+    _compare(x, L, oracle_mod, precision)
+
+
+def test_jittered_131k(oracle_mod):
+    x, L = inputs.jittered_fcc(32, 0.8442, 0.2, 5)
+    _compare(x, L, oracle_mod)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 1000, 4097])
+def test_uniform_ragged(oracle_mod, n):
+    L = 12.3
+    x = inputs.uniform(n, L, n) * 3.0 - L       # coordinates over three images
+    _compare(x, L, oracle_mod)
+
+
+def test_dense_cluster(oracle_mod):
+    x, L = dense_cluster_state()
+    _compare(x, L, oracle_mod)
+
+
+def test_edge_coordinates(oracle_mod):
+    L = 13.436769531060056
+    nc = 5
+    below = np.nextafter(L, 0.0)
+    vals = [0.0, below, L, -1e-300, -0.0, -0.1, 2.5 * L, -3.3 * L, 1e9 + 0.3, -1e9 - 0.7,
+            np.nextafter(0.0, 1.0)]
+    vals += [k * (L / nc) for k in range(1, nc)]
+    vals += [np.nextafter(k * (L / nc), 0.0) for k in range(1, nc)]
+    vals += [np.nextafter(k * (L / nc), 1e300) for k in range(1, nc)]
+    vals = np.array(vals)
+    rng = np.random.default_rng(0)
+    x = np.stack([vals, rng.permutation(vals), rng.permutation(vals)], axis=1)
+    _compare(np.ascontiguousarray(x), L, oracle_mod)
+
+
+def test_empty_system(oracle_mod):
+    nc, (cell_of, count, start, perm) = _gpu_cells(np.zeros((0, 3)), 10.0)
+    assert cell_of.size == 0 and perm.size == 0
+    assert count.sum() == 0 and np.all(start == 0)
+
+
+@pytest.mark.slow
+def test_full_size_4m(oracle_mod):
+    """Bit-exact binning at the 4,000,000-particle workload (jittered so that
+    cells are uneven)."""
+    x, L = inputs.jittered_fcc(100, 0.8442, 0.3, 11)
+    _compare(x, L, oracle_mod)

@@ -1,0 +1,90 @@
+"""Error paths through the C ABI on a GPU: latched device errors, argument
+checks.  Nothing here faults or hangs the GPU: every bad pointer is rejected
+on the host before a kernel sees it."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_0709_3225_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_nonfinite_position_is_reported():
+    from paper_0709_3225_gb300 import lj
+    x, L = inputs.jittered_fcc(6, 0.8442, 0.05, 1)
+    x[17, 1] = np.nan
+    x[40, 0] = np.inf
+    s = lj.System(x, None, L)
+    lj.lj_forces(s.ctx, s.x, s.f)        # queued; the kernel latches the error
+    with pytest.raises(lj.LJError) as ei:
+        s.check()
+    assert ei.value.code == lj.LJ_ENONFINITE
+    s.check()                             # the latch is cleared by the check
+    with pytest.raises(lj.LJError) as ei:
+        s.forces(energy=True)             # synchronizing call reports it directly
+    assert ei.value.code == lj.LJ_ENONFINITE
+    s.close()
+
+
+def test_box_too_small():
+    from paper_0709_3225_gb300 import lj
+    with pytest.raises(lj.LJError) as ei:
+        lj.System(np.zeros((4, 3)), None, 7.0)
+    assert ei.value.code == lj.LJ_EBOX
+
+
+def test_binding_rejects_bad_tensors():
+    import torch
+    from paper_0709_3225_gb300 import lj
+    x, L = inputs.jittered_fcc(6, 0.8442, 0.05, 1)
+    s = lj.System(x, None, L)
+    with pytest.raises(TypeError):
+        lj.lj_bin(s.ctx, torch.zeros((s.n, 3), dtype=torch.float64))             # CPU tensor
+    with pytest.raises(TypeError):
+        lj.lj_bin(s.ctx, torch.zeros((s.n, 3), dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        lj.lj_bin(s.ctx, torch.zeros((s.n + 1, 3), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        lj.lj_forces(s.ctx, s.x, torch.zeros((s.n, 8), dtype=torch.float32, device="cuda")[:, ::2])
+    s.close()
+
+
+def test_c_abi_rejects_host_and_misaligned_pointers():
+    import torch
+    from paper_0709_3225_gb300 import lj
+    lib = lj.load()
+    x, L = inputs.jittered_fcc(6, 0.8442, 0.05, 1)
+    s = lj.System(x, None, L)
+    host = np.zeros((s.n, 3))
+    assert lib.lj_bin(s.ctx.handle, ctypes.c_void_p(host.ctypes.data)) == lj.LJ_EINVAL
+    big = torch.zeros(3 * s.n + 8, dtype=torch.float64, device="cuda")
+    assert lib.lj_bin(s.ctx.handle, ctypes.c_void_p(big.data_ptr() + 4)) == lj.LJ_EINVAL
+    f = torch.zeros(4 * s.n + 8, dtype=torch.float32, device="cuda")
+    assert lib.lj_forces(s.ctx.handle, ctypes.c_void_p(s.x.data_ptr()), ctypes.c_void_p(f.data_ptr() + 8),
+                         None, None) == lj.LJ_EINVAL
+    assert lib.lj_step(s.ctx.handle, ctypes.c_void_p(s.x.data_ptr()), ctypes.c_void_p(s.v.data_ptr()),
+                       ctypes.c_void_p(s.f.data_ptr()), -1) == lj.LJ_EINVAL
+    out = (ctypes.c_double * 3)()
+    assert lib.lj_energy(s.ctx.handle, ctypes.c_void_p(host.ctypes.data), ctypes.c_void_p(s.v.data_ptr()),
+                         out) == lj.LJ_EINVAL
+    s.check()
+    s.close()
+
+
+def test_context_reuse_and_streams():
+    """Two contexts on two streams give identical results to one context."""
+    import torch
+    from paper_0709_3225_gb300 import lj
+    x, L = inputs.jittered_fcc(8, 0.8442, 0.08, 3)
+    ref = lj.System(x, None, L, precision="fp64")
+    ref.forces()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        other = lj.System(x, None, L, precision="fp64", stream=st)
+        other.forces()
+    st.synchronize()
+    assert torch.allclose(ref.f, other.f, rtol=0, atol=1e-12)
+    ref.close()
+    other.close()

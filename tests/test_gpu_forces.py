@@ -1,0 +1,164 @@
+"""GPU force parity against the FP64 oracle (Section 2 pair force over the
+Section 3 cell list).
+
+Tolerances (from the arithmetic, "Tolerances"):
+  mixed: relative RMS force error <= 1e-5 over all particles; per particle
+         |df| <= 2e-3 (eps/sigma) for particles with no partner within 1e-5
+         of rc; energy and virial (FP64 sums of FP32 terms) to 2e-6 relative.
+  fp64:  per particle |df| <= 1e-10 (|f| + f_rms), energy / virial to 1e-11.
+A pair whose distance is within working precision of rc may fall on either
+side of the cutoff: such particles are excluded from the per-particle bound
+(and stay in the RMS)."""
+import numpy as np
+import pytest
+
+from paper_0709_3225_gb300 import inputs
+
+from gpu_util import dense_cluster_state, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"mixed": dict(rms=1e-5, abs=2e-3, e=2e-6, band=1e-5),
+       "fp64": dict(rms=1e-12, rel=1e-10, e=1e-11, band=1e-12)}
+
+
+def _gpu_forces(x, L, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5):
+    from paper_0709_3225_gb300 import lj
+    s = lj.System(x, None, L, precision=precision, shift_mode=mode, flags=flags, eps=eps, sigma=sigma, rc=rc)
+    e, w = s.forces(energy=True)
+    f = s.f.double().cpu().numpy()
+    s.check()
+    s.close()
+    return f, e, w
+
+
+def _check(x, L, oracle_mod, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5):
+    f, e, w = _gpu_forces(x, L, precision, mode, flags, eps, sigma, rc)
+    fo, epo, eo, wo = oracle_mod.forces_cells(x, L, eps=eps, sigma=sigma, rc=rc, mode=mode)
+    t = TOL[precision]
+    near = oracle_mod.near_cutoff(x, L, rc=rc, band=t["band"])
+    assert rel_rms(f[:, :3], fo) <= t["rms"]
+    d = np.abs(f[:, :3] - fo).max(axis=1)
+    frms = np.sqrt((fo ** 2).sum(axis=1).mean()) if fo.size else 0.0
+    if precision == "mixed":
+        assert np.all(d[~near] <= t["abs"]), d[~near].max()
+    else:
+        bound = t["rel"] * (np.abs(fo).max(axis=1) + frms)
+        assert np.all(d[~near] <= bound[~near])
+    assert e == pytest.approx(eo, rel=t["e"], abs=1e-9)
+    assert w == pytest.approx(wo, rel=t["e"], abs=1e-9)
+    # per-particle energies in f[:, 3]
+    escale = np.abs(epo).max() if epo.size else 1.0
+    assert np.all(np.abs(f[~near, 3] - epo[~near]) <= (1e-4 if precision == "mixed" else 1e-10) * escale)
+    return f, fo
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_liquid_2k(oracle_mod, precision, mode):
+    x, L = inputs.jittered_fcc(8, 0.8442, 0.1, 1)
+    _check(x, L, oracle_mod, precision, mode)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("flags", [0, 1])
+def test_staging_paths(oracle_mod, precision, flags):
+    """Bulk-copy staging and direct global reads give the same forces."""
+    x, L = inputs.jittered_fcc(10, 0.8442, 0.1, 2)
+    _check(x, L, oracle_mod, precision, 1, flags)
+
+
+@pytest.mark.parametrize("n_fcc,rho", [(5, 0.8442), (6, 0.8442), (7, 0.5), (9, 0.95), (12, 0.8442)])
+def test_box_sizes(oracle_mod, n_fcc, rho):
+    """3, 4, 5 ... cells per side: run windows that wrap on both sides."""
+    x, L = inputs.jittered_fcc(n_fcc, rho, 0.08, n_fcc)
+    _check(x, L, oracle_mod, "mixed")
+    _check(x, L, oracle_mod, "fp64")
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_dense_cluster_and_overflow(oracle_mod, precision):
+    """Cells with > 32 particles (several passes) and stencil windows larger
+    than the staging capacity (global-memory fallback)."""
+    x, L = dense_cluster_state()
+    _check(x, L, oracle_mod, precision)
+
+
+def test_ragged_random_gas(oracle_mod):
+    # Uniform random gas with a minimum-distance filter: empty cells, uneven
+    # counts, particle count not a multiple of anything.
+    L = 15.1
+    x = inputs.uniform(3000, L, 9)
+    keep = [0]
+    for i in range(1, x.shape[0]):
+        d = x[keep] - x[i]
+        d -= L * np.round(d / L)
+        if (d * d).sum(axis=1).min() > 0.8 ** 2:
+            keep.append(i)
+    x = np.ascontiguousarray(x[keep])
+    _check(x, L, oracle_mod, "mixed")
+    _check(x, L, oracle_mod, "fp64")
+
+
+@pytest.mark.parametrize("eps,sigma,rc", [(0.9, 1.05, 2.5), (1.3, 0.9, 3.0)])
+def test_other_parameters(oracle_mod, eps, sigma, rc):
+    x, L = inputs.jittered_fcc(8, 0.8442, 0.08, 4)
+    for mode in (1, 2):
+        _check(x, L, oracle_mod, "mixed", mode, eps=eps, sigma=sigma, rc=rc)
+        _check(x, L, oracle_mod, "fp64", mode, eps=eps, sigma=sigma, rc=rc)
+
+
+def test_translation_invariance_gpu(oracle_mod):
+    x, L = inputs.jittered_fcc(8, 0.8442, 0.08, 6)
+    f1, _, _ = _gpu_forces(x, L, "fp64")
+    f2, _, _ = _gpu_forces(x + np.array([5.5, -100.25, 33.0]), L, "fp64")
+    assert np.abs(f1[:, :3] - f2[:, :3]).max() <= 1e-9 * np.abs(f1).max()
+
+
+def test_fcc_lattice_forces_vanish():
+    x, _, L, _ = inputs.workload_state("fluid-2k")
+    f, e, w = _gpu_forces(x, L, "fp64")
+    assert np.abs(f[:, :3]).max() < 1e-10
+    f, e, w = _gpu_forces(x, L, "mixed")
+    assert np.abs(f[:, :3]).max() < 1e-3
+
+
+@pytest.mark.slow
+def test_liquid_131k(oracle_mod):
+    x, L = inputs.jittered_fcc(32, 0.8442, 0.1, 8)
+    _check(x, L, oracle_mod, "mixed")
+    _check(x, L, oracle_mod, "fp64")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_4m_sampled(oracle_mod, precision):
+    """The 4,000,000-particle workload in the launch configuration the
+    benchmark uses: 256 sampled particles against the oracle's per-particle
+    definition, plus zero net force (Newton III) over all particles."""
+    from paper_0709_3225_gb300 import lj
+    x, L = inputs.jittered_fcc(100, 0.8442, 0.1, 12)
+    s = lj.System(x, None, L, precision=precision)
+    s.forces()
+    s.check()
+    f = s.f.double().cpu().numpy()
+    s.close()
+    idx = np.random.default_rng(0).choice(x.shape[0], 256, replace=False)
+    ref = np.array([oracle_mod.force_one(x, L, int(i))[0] for i in idx])
+    got = f[idx, :3]
+    err = np.abs(got - ref).max(axis=1)
+    bound = 2e-3 if precision == "mixed" else 1e-9 * (np.abs(ref).max() + 1)
+    bad = err > bound
+    # any sampled particle over the bound must have a pair at the cutoff
+    for i in np.flatnonzero(bad):
+        fi, _ = oracle_mod.force_one(x, L, int(idx[i]))
+        d = x - x[idx[i]]
+        d -= L * np.round(d / L)
+        r = np.sqrt((d * d).sum(axis=1))
+        assert np.any(np.abs(r - 2.5) < 1e-5), (i, err[i])
+    assert rel_rms(got, ref) <= (1e-5 if precision == "mixed" else 1e-12)
+    # Newton III: pair terms cancel up to rounding (random-walk bound).
+    frms = float(np.sqrt((ref ** 2).sum(axis=1).mean()))
+    net = np.abs(f[:, :3].sum(axis=0)).max()
+    unit = 1e-5 if precision == "mixed" else 1e-14
+    assert net <= 10 * np.sqrt(x.shape[0]) * unit * frms

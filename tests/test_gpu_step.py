@@ -1,0 +1,129 @@
+"""GPU velocity-Verlet parity against the oracle's integrator (Section 2),
+time reversibility, conservation laws and the host-buffer entry point."""
+import numpy as np
+import pytest
+
+from paper_0709_3225_gb300 import inputs
+
+from gpu_util import min_image
+
+pytestmark = pytest.mark.gpu
+
+
+def _liquid(n_fcc=8, T=0.728, seed=31):
+    x, L = inputs.jittered_fcc(n_fcc, 0.8442, 0.05, seed)
+    v = inputs.velocities(x.shape[0], T, seed)
+    return x, v, L
+
+
+@pytest.mark.parametrize("precision,xtol,vtol", [("fp64", 1e-10, 1e-9), ("mixed", 2e-6, 2e-4)])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_trajectory_matches_oracle(oracle_mod, precision, xtol, vtol, mode):
+    from paper_0709_3225_gb300 import lj
+    x, v, L = _liquid()
+    xo, vo = x.copy(), v.copy()
+    fo = oracle_mod.forces_cells(xo, L, mode=mode)[0]
+    oracle_mod.vv(xo, vo, fo, L, 20, mode=mode)
+    s = lj.System(x, v, L, precision=precision, shift_mode=mode)
+    s.step(7)
+    s.step(13)       # two calls: the closing half kick of the first is applied
+    s.check()
+    xg, vg, fg = s.x.cpu().numpy(), s.v.cpu().numpy(), s.f.double().cpu().numpy()[:, :3]
+    assert np.abs(min_image(xg - xo, L)).max() <= xtol
+    assert np.abs(vg - vo).max() <= vtol
+    assert np.all(xg >= 0.0) and np.all(xg < L)
+    scale = np.abs(fo).max()
+    assert np.abs(fg - fo).max() <= (1e-8 if precision == "fp64" else 3e-4) * scale
+    s.close()
+
+
+def test_time_reversibility_fp64():
+    from paper_0709_3225_gb300 import lj
+    x, v, L = _liquid(seed=5)
+    s = lj.System(x, v, L, precision="fp64")
+    s.step(50)
+    s.v.neg_()
+    s.step(50)
+    s.check()
+    assert np.abs(min_image(s.x.cpu().numpy() - x, L)).max() < 1e-8
+    assert np.abs(-s.v.cpu().numpy() - v).max() < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_energy_and_momentum(oracle_mod, precision):
+    from paper_0709_3225_gb300 import lj
+    x, v, L = _liquid(seed=8)
+    s = lj.System(x, v, L, precision=precision)
+    ek, ep, et = s.energy()
+    fo, _, eo, _ = oracle_mod.forces_cells(x, L, mode=1)
+    assert ek == pytest.approx(oracle_mod.ekin(v), rel=1e-13)
+    assert ep == pytest.approx(eo, rel=2e-6 if precision == "mixed" else 1e-11)
+    assert et == pytest.approx(ek + ep, rel=1e-15)
+    p0 = s.v.sum(dim=0).cpu().numpy()
+    s.step(200)
+    ek2, ep2, et2 = s.energy()
+    s.check()
+    n = x.shape[0]
+    # energy-shifted LJ at dt = 0.005: total energy stays within 1e-3 per particle
+    assert abs(et2 - et) / n < 1e-3
+    p1 = s.v.sum(dim=0).cpu().numpy()
+    assert np.abs(p1 - p0).max() < (1e-6 if precision == "mixed" else 1e-10) * n
+
+
+def test_step_host_matches_device(oracle_mod):
+    from paper_0709_3225_gb300 import lj
+    import torch
+    x, v, L = _liquid(seed=12)
+    s = lj.System(x, v, L, precision="fp64")
+    s.forces()
+    xh = s.x.cpu().numpy().copy()
+    vh = s.v.cpu().numpy().copy()
+    fh = s.f.cpu().numpy().copy()
+    s.step(10)
+    lj.lj_step_host(s.ctx, xh, vh, fh, 10)
+    assert np.abs(min_image(xh - s.x.cpu().numpy(), L)).max() < 1e-11
+    assert np.abs(vh - s.v.cpu().numpy()).max() < 1e-10
+    # pinned CPU tensors work too
+    xp = torch.from_numpy(xh.copy()).pin_memory()
+    vp = torch.from_numpy(vh.copy()).pin_memory()
+    fp = torch.from_numpy(fh.copy()).pin_memory()
+    lj.lj_step_host(s.ctx, xp, vp, fp, 3)
+    s.step(3)
+    assert np.abs(min_image(xp.numpy() - s.x.cpu().numpy(), L)).max() < 1e-11
+    s.close()
+
+
+def test_zero_steps_and_empty():
+    from paper_0709_3225_gb300 import lj
+    x, v, L = _liquid(seed=2)
+    s = lj.System(x, v, L)
+    s.forces()
+    x0 = s.x.clone()
+    s.step(0)
+    assert bool((s.x == x0).all())
+    s.close()
+    e = lj.System(np.zeros((0, 3)), np.zeros((0, 3)), 10.0)
+    e.forces(energy=True)
+    e.step(5)
+    assert e.energy() == (0.0, 0.0, 0.0)
+    e.close()
+
+
+@pytest.mark.slow
+def test_drift_131k_mixed_vs_fp64():
+    """Energy drift over 1000 steps of the 131,072-particle workload, mixed
+    vs FP64 (reported in the log; bounded loosely)."""
+    from paper_0709_3225_gb300 import lj
+    x, v, L, w = inputs.workload_state("fluid-131k")
+    out = {}
+    for precision in ("mixed", "fp64"):
+        s = lj.System(x, v, L, precision=precision)
+        e0 = s.energy()[2]
+        s.step(1000)
+        e1 = s.energy()[2]
+        s.check()
+        out[precision] = (e1 - e0) / x.shape[0]
+        s.close()
+    print("energy drift per particle over 1000 steps:", out)
+    for k, d in out.items():
+        assert abs(d) < 1e-2, (k, d)
