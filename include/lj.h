@@ -81,13 +81,19 @@ typedef struct lj_params {
     int32_t precision;   /* lj_precision */
     int32_t cell_subdiv; /* cells per rc along each axis: 1 (27-cell stencil,
                             Section 3) or 0 for the default (1) */
-    int32_t flags;       /* 0 or LJ_FLAG_NO_STAGING */
+    int32_t flags;       /* 0, LJ_FLAG_RUN_STAGED or LJ_FLAG_RUN_DIRECT */
 } lj_params;
 
-/* lj_params.flags: the force kernel reads neighbour cells straight from
- * global memory instead of staging them in shared memory with bulk copies
- * (same results; for comparison and diagnosis). */
-#define LJ_FLAG_NO_STAGING 1
+/* lj_params.flags select the force kernel (same results; for comparison).
+ * Default (0): FP32-mixed uses the warp-per-cell kernel, which stages each
+ * cell's 27-cell stencil in shared memory relative to the cell centre; FP64
+ * uses the run kernel with bulk-copy staging.
+ * LJ_FLAG_RUN_STAGED: the run kernel (a CTA per run of cells along x) with its
+ *   9 neighbour-row windows staged by bulk asynchronous copies.
+ * LJ_FLAG_RUN_DIRECT: the run kernel reading neighbour cells from global
+ *   memory. */
+#define LJ_FLAG_RUN_STAGED 1
+#define LJ_FLAG_RUN_DIRECT 2
 
 typedef struct lj_ctx lj_ctx;
 

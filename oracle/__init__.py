@@ -81,6 +81,9 @@ def _load():
         lib.or_near_cutoff.argtypes = [ctypes.c_int64, _D, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_double, _I32]
         lib.or_near_cutoff.restype = None
+        lib.or_stiffness.argtypes = [ctypes.c_int64, _D] + [ctypes.c_double] * 4 + \
+            [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, _D, _D]
+        lib.or_stiffness.restype = None
         lib.or_ekin.argtypes = [ctypes.c_int64, _D, ctypes.c_double]
         lib.or_ekin.restype = ctypes.c_double
         lib.or_vv.argtypes = [ctypes.c_int64, _D, _D, _D] + [ctypes.c_double] * 4 + \
@@ -195,6 +198,26 @@ def near_cutoff(x, L: float, rc: float = 2.5, band: float = 1e-5, k: int = 1) ->
     near = np.empty(x.shape[0], np.int32)
     _load().or_near_cutoff(x.shape[0], _dp(x), float(L), float(rc), int(k), float(band), _ip(near))
     return near.astype(bool)
+
+
+def stiffness(x, L: float, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5, mode: int = 1,
+              idx=None):
+    """Per-particle (K, S): K = sum_j |F'(r_ij)| + |F(r_ij)|/r_ij and
+    S = sum_j |F(r_ij)| over partners within rc (brute force) -- the
+    sensitivity of f_i to rounding of the pair vectors and of the sum, for
+    tolerance bounds only.  idx: optional particle subset."""
+    x = _pos(x)
+    n = x.shape[0]
+    if idx is None:
+        m, ip = n, None
+    else:
+        sel = np.ascontiguousarray(idx, dtype=np.int64)
+        m, ip = sel.shape[0], sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    K = np.empty(m)
+    S = np.empty(m)
+    _load().or_stiffness(n, _dp(x), float(L), float(eps), float(sigma), float(rc), int(mode), ip, m,
+                         _dp(K), _dp(S))
+    return K, S
 
 
 def ekin(v, mass: float = 1.0) -> float:

@@ -317,6 +317,48 @@ void or_near_cutoff(int64_t n, const double *x, double L, double rc, int k,
     free(cell_of); free(count); free(start); free(perm);
 }
 
+/* Per-particle sensitivity of the force sum to rounding of the pair
+ * vectors, for tolerance bounds in tests (not part of the method):
+ *   K_i = sum_j (|dF/dr(r_ij)| + |F(r_ij)| / r_ij),  S_i = sum_j |F(r_ij)|,
+ * over partners within rc (brute force over all j).  dF/dr of the LJ force is
+ * (24 eps / sigma^2) [7 (sigma/r)^8 - 26 (sigma/r)^14]; the force shift of
+ * mode 2 is a constant and does not change it. */
+static void stiffness_one(int64_t n, const double *x, double L, double eps, double sigma,
+                          double rc, int mode, int64_t i, double *K, double *S)
+{
+    double k = 0.0, sacc = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+        if (j == i) continue;
+        double d[3];
+        for (int q = 0; q < 3; q++) d[q] = min_image(x[3 * i + q] - x[3 * j + q], L);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (!(r2 < rc * rc)) continue;
+        double r = sqrt(r2);
+        double F, U;
+        or_pair(r, eps, sigma, rc, mode, &F, &U);
+        double s = sigma / r;
+        double s8 = s * s * s * s * s * s * s * s;
+        double s14 = s8 * s * s * s * s * s * s;
+        double dF = (24.0 * eps / (sigma * sigma)) * (7.0 * s8 - 26.0 * s14);
+        k += fabs(dF) + fabs(F) / r;
+        sacc += fabs(F);
+    }
+    *K = k;
+    *S = sacc;
+}
+
+/* For the m particles listed in idx (all particles when idx is NULL, m = n). */
+void or_stiffness(int64_t n, const double *x, double L, double eps,
+                  double sigma, double rc, int mode, const int64_t *idx, int64_t m,
+                  double *K, double *S)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = idx ? idx[q] : q;
+        stiffness_one(n, x, L, eps, sigma, rc, mode, i, &K[q], &S[q]);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Observables.                                                              */
 

@@ -35,7 +35,8 @@ int validate(const lj_params *p, int *nc_out)
     if (p->shift_mode < LJ_SHIFT_NONE || p->shift_mode > LJ_SHIFT_FORCE) return LJ_EINVAL;
     if (p->precision != LJ_PREC_MIXED && p->precision != LJ_PREC_FP64) return LJ_EINVAL;
     if (p->cell_subdiv != 0 && p->cell_subdiv != 1) return LJ_EINVAL;
-    if ((p->flags & ~LJ_FLAG_NO_STAGING) != 0) return LJ_EINVAL;
+    if ((p->flags & ~(LJ_FLAG_RUN_STAGED | LJ_FLAG_RUN_DIRECT)) != 0) return LJ_EINVAL;
+    if ((p->flags & LJ_FLAG_RUN_STAGED) && (p->flags & LJ_FLAG_RUN_DIRECT)) return LJ_EINVAL;
     const int k = 1;
     double q = floor(((double)k * p->box) / p->rc);
     if (!(q >= 2.0 * k + 1.0)) return LJ_EBOX;
@@ -180,7 +181,10 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     c->inv_cw = (double)nc / p->box;
     c->cw = p->box / (double)nc;
     c->stream = (cudaStream_t)stream;
-    c->use_tma = (p->flags & LJ_FLAG_NO_STAGING) ? 0 : 1;
+    // Kernel choice: FP32-mixed defaults to the warp-per-cell kernel, FP64
+    // to the run-staged kernel; the flags force a run kernel.
+    c->use_tma = (p->flags & LJ_FLAG_RUN_DIRECT) ? 0 : 1;
+    c->use_run_kernel = (p->precision == LJ_PREC_FP64 || (p->flags & (LJ_FLAG_RUN_STAGED | LJ_FLAG_RUN_DIRECT))) ? 1 : 0;
 
 #define LJ_CREATE_CK(call)            \
     do {                              \
@@ -203,7 +207,11 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     c->ntiles = (int)((c->ncell + kScanTile - 1) / kScanTile);
     LJ_CREATE_CK(cudaMalloc(&c->tile_sum, (size_t)c->ntiles * sizeof(int32_t)));
     LJ_CREATE_CK(force_configure(c));
-    LJ_CREATE_CK(cudaMalloc(&c->partial, 2 * (size_t)c->force_grid * sizeof(double)));
+    if (p->precision == LJ_PREC_MIXED) LJ_CREATE_CK(warp_force_configure(c));
+    {
+        int np = c->force_grid > c->wforce_grid ? c->force_grid : c->wforce_grid;
+        LJ_CREATE_CK(cudaMalloc(&c->partial, 2 * (size_t)np * sizeof(double)));
+    }
     int64_t eb = (3 * (int64_t)n1 + kReduceThreads - 1) / kReduceThreads;
     c->ekin_grid = (int)(eb < 4 * (int64_t)c->nsm ? eb : 4 * (int64_t)c->nsm);
     LJ_CREATE_CK(cudaMalloc(&c->ekin_partial, (size_t)c->ekin_grid * sizeof(double)));

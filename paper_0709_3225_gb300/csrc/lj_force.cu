@@ -583,6 +583,11 @@ cudaError_t force_configure(lj_ctx *c)
 cudaError_t launch_force(lj_ctx *c, void *f, bool energy)
 {
     if (c->p.n == 0) return cudaSuccess;
+    if (!c->use_run_kernel) {
+        c->npartial = c->wforce_grid;
+        return launch_force_warp(c, f, energy);
+    }
+    c->npartial = c->force_grid;
     ForceParams fp = make_params(c);
     const bool fp64 = c->p.precision == LJ_PREC_FP64;
     void *kern = fp64 ? pick_kernel<double>(c->p.shift_mode, energy) : pick_kernel<float>(c->p.shift_mode, energy);
@@ -605,7 +610,7 @@ cudaError_t launch_force(lj_ctx *c, void *f, bool energy)
 
 cudaError_t launch_energy_reduce(lj_ctx *c)
 {
-    k_reduce_pairs<<<1, kReduceThreads, 0, c->stream>>>(c->partial, c->force_grid, c->scalars);
+    k_reduce_pairs<<<1, kReduceThreads, 0, c->stream>>>(c->partial, c->npartial, c->scalars);
     c->kernel_launches++;
     return cudaGetLastError();
 }

@@ -1,0 +1,413 @@
+// Lennard-Jones forces over cell lists, warp-per-cell variant (FP32-mixed).
+//
+// Same method as lj_force.cu (Section 3: a particle interacts with the
+// particles of its own and the 26 neighbouring cells; Section 2 pair
+// force), organised for GB300:
+//  * Warps work independently (no CTA barriers): a persistent grid, warp w
+//    takes home cells w, w + W, w + 2W, ... in linear cell order, so warps of
+//    one CTA work on neighbouring cells and share L1 lines.
+//  * Per home cell the warp stages the 27 stencil cells into its own slice
+//    of shared memory, converting every candidate to coordinates relative to
+//    the HOME cell centre (|x| <= 1.5 cell sides, so FP32 keeps ~1e-7
+//    absolute resolution).  The compute loop is then one flat candidate list
+//    with no per-cell offset.  Lane k (< 27) copies stencil cell k.
+//  * Lanes form S = 32/G groups of G lanes (G = 8, 16 or 32, the smallest
+//    that holds the cell's particles): lane g of a group owns home particle
+//    g, group s takes candidates s, s+S, s+2S, ...  Staged data are stored
+//    SoA and interleaved so that one 8-byte shared load gives a lane its two
+//    next candidates, evaluated together with packed FP32x2 arithmetic
+//    (__ffma2_rn / __fmul2_rn).
+//  * Cells with more than 32 particles, or stencils that do not fit the
+//    warp's slice, take a plain path reading global memory per stencil cell.
+#include "lj_internal.cuh"
+
+namespace {
+
+constexpr float kFar = 1.0e4f;   // padding candidate: r^2 ~ 1e8 > rc^2
+
+struct WarpParams {
+    int n, nc, cap;              // cap: staged candidates per warp (multiple of 8)
+    int64_t ncell;
+    float cw;
+    float rc2, rc, a12, b6, c12, c6, uc, fc;
+};
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Two candidate pairs at once: d = x_i - x_j for j = a, b; see lj_force.cu
+// for the scalar form.  SELF adds the r^2 > 0 test that drops i == j.
+template <int MODE, bool ENERGY, bool SELF>
+__device__ __forceinline__ void pair2(float2 xs, float2 ys, float2 zs, float2 qx, float2 qy, float2 qz,
+                                      const WarpParams &k, float2 &fx, float2 &fy, float2 &fz, float2 &e,
+                                      float2 &w)
+{
+    const float2 m1 = f2(-1.0f);
+    const float2 dx = __ffma2_rn(qx, m1, xs);
+    const float2 dy = __ffma2_rn(qy, m1, ys);
+    const float2 dz = __ffma2_rn(qz, m1, zs);
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    bool ina = r2.x < k.rc2, inb = r2.y < k.rc2;
+    if constexpr (SELF) {
+        ina = ina && (r2.x > 0.0f);
+        inb = inb && (r2.y > 0.0f);
+    }
+    float2 ri, rinv = f2(0.0f);
+    if constexpr (MODE == 2) {
+        rinv.x = ina ? rsqrt_approx(r2.x) : 0.0f;
+        rinv.y = inb ? rsqrt_approx(r2.y) : 0.0f;
+        ri = __fmul2_rn(rinv, rinv);
+    } else {
+        ri.x = ina ? rcp_approx(r2.x) : 0.0f;
+        ri.y = inb ? rcp_approx(r2.y) : 0.0f;
+    }
+    const float2 r6 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+    const float2 t = __ffma2_rn(f2(k.a12), r6, f2(-k.b6));
+    float2 ff = __fmul2_rn(__fmul2_rn(ri, r6), t);
+    if constexpr (MODE == 2) ff = __ffma2_rn(f2(-k.fc), rinv, ff);
+    fx = __ffma2_rn(ff, dx, fx);
+    fy = __ffma2_rn(ff, dy, fy);
+    fz = __ffma2_rn(ff, dz, fz);
+    if constexpr (ENERGY) {
+        float2 u = __fmul2_rn(r6, __ffma2_rn(f2(k.c12), r6, f2(-k.c6)));
+        if constexpr (MODE >= 1) u = __fadd2_rn(u, f2(-k.uc));
+        if constexpr (MODE == 2) u = __ffma2_rn(__ffma2_rn(r2, rinv, f2(-k.rc)), f2(k.fc), u);
+        u.x = ina ? u.x : 0.0f;
+        u.y = inb ? u.y : 0.0f;
+        e = __fadd2_rn(e, u);
+        w = __ffma2_rn(ff, r2, w);
+    }
+}
+
+// Scalar pair for the plain path (per stencil cell, shifted home particle).
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void pair1(float dx, float dy, float dz, const WarpParams &k, float &fx, float &fy,
+                                      float &fz, float &e, float &w)
+{
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const bool in = (r2 < k.rc2) && (r2 > 0.0f);
+    float ri, rinv = 0.0f;
+    if constexpr (MODE == 2) {
+        rinv = in ? rsqrt_approx(r2) : 0.0f;
+        ri = rinv * rinv;
+    } else {
+        ri = in ? rcp_approx(r2) : 0.0f;
+    }
+    const float r6 = ri * ri * ri;
+    float ff = ri * r6 * (k.a12 * r6 - k.b6);
+    if constexpr (MODE == 2) ff -= k.fc * rinv;
+    fx += ff * dx;
+    fy += ff * dy;
+    fz += ff * dz;
+    if constexpr (ENERGY) {
+        float u = r6 * (k.c12 * r6 - k.c6);
+        if constexpr (MODE >= 1) u -= k.uc;
+        if constexpr (MODE == 2) u += (r2 * rinv - k.rc) * k.fc;
+        e += in ? u : 0.0f;
+        w += ff * r2;
+    }
+}
+
+// Stencil slot k = 0 is the home cell, k = 1..26 the neighbours.
+__device__ __forceinline__ void stencil_offset(int k, int &dx, int &dy, int &dz)
+{
+    const int idx = k == 0 ? 13 : (k <= 13 ? k - 1 : k);
+    dx = idx % 3 - 1;
+    dy = (idx / 3) % 3 - 1;
+    dz = idx / 9 - 1;
+}
+
+// Position of flat candidate j in the interleaved SoA layout for S streams.
+template <int S>
+__device__ __forceinline__ int slot_of(int j)
+{
+    const int m = j / (2 * S);
+    const int r = j - m * 2 * S;
+    const int s = r % S;
+    const int h = r / S;
+    return 2 * (m * S + s) + h;
+}
+
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void write_out(float4 *__restrict__ fout, int idx, int n, float fx, float fy, float fz,
+                                          float e, float w, double &eacc, double &wacc)
+{
+    if ((unsigned)idx < (unsigned)n) {
+        fout[idx] = make_float4(fx, fy, fz, ENERGY ? 0.5f * e : 0.0f);
+        if constexpr (ENERGY) {
+            eacc += 0.5 * (double)e;
+            wacc += 0.5 * (double)w;
+        }
+    }
+}
+
+// Fast path: staged flat list, G lanes per group, S = 32 / G groups.
+template <int G, int MODE, bool ENERGY>
+__device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *__restrict__ pos,
+                                            float4 *__restrict__ fout, float *X, float *Y, float *Z, int s_k,
+                                            int n_k, int P_k, float sx, float sy, float sz, int s_home, int n_home,
+                                            int T, double &eacc, double &wacc)
+{
+    constexpr int S = 32 / G;
+    const int lane = threadIdx.x & 31;
+    // stage: lane k copies stencil cell k, shifted to home-centre coordinates
+    if (lane < 27) {
+#pragma unroll 4
+        for (int e = 0; e < n_k; e++) {
+            const float4 q = __ldg(pos + s_k + e);
+            const int sl = slot_of<S>(P_k + e);
+            X[sl] = q.x + sx;
+            Y[sl] = q.y + sy;
+            Z[sl] = q.z + sz;
+        }
+    }
+    const int Tpad = (T + 2 * S - 1) / (2 * S) * (2 * S);
+    if (lane < Tpad - T) {
+        const int sl = slot_of<S>(T + lane);
+        X[sl] = kFar;
+        Y[sl] = kFar;
+        Z[sl] = kFar;
+    }
+    __syncwarp();
+
+    const int gl = lane % G;
+    const int sg = lane / G;
+    const bool vi = gl < n_home;
+    const float4 pi = __ldg(pos + s_home + (vi ? gl : 0));
+    const float2 xs = f2(pi.x), ys = f2(pi.y), zs = f2(pi.z);
+    float2 fx = f2(0.f), fy = f2(0.f), fz = f2(0.f), e = f2(0.f), w = f2(0.f);
+    const int iters = Tpad / (2 * S);
+    const int ihome = (n_home + 2 * S - 1) / (2 * S);   // iterations that may hold i itself
+    const float2 *X2 = reinterpret_cast<const float2 *>(X) + sg;
+    const float2 *Y2 = reinterpret_cast<const float2 *>(Y) + sg;
+    const float2 *Z2 = reinterpret_cast<const float2 *>(Z) + sg;
+    int m = 0;
+    for (; m < ihome; m++)
+        pair2<MODE, ENERGY, true>(xs, ys, zs, X2[m * S], Y2[m * S], Z2[m * S], k, fx, fy, fz, e, w);
+#pragma unroll 4
+    for (; m < iters; m++)
+        pair2<MODE, ENERGY, false>(xs, ys, zs, X2[m * S], Y2[m * S], Z2[m * S], k, fx, fy, fz, e, w);
+    float Fx = fx.x + fx.y, Fy = fy.x + fy.y, Fz = fz.x + fz.y, E = e.x + e.y, Wv = w.x + w.y;
+#pragma unroll
+    for (int o = G; o < 32; o <<= 1) {
+        Fx += __shfl_xor_sync(0xffffffffu, Fx, o);
+        Fy += __shfl_xor_sync(0xffffffffu, Fy, o);
+        Fz += __shfl_xor_sync(0xffffffffu, Fz, o);
+        if constexpr (ENERGY) {
+            E += __shfl_xor_sync(0xffffffffu, E, o);
+            Wv += __shfl_xor_sync(0xffffffffu, Wv, o);
+        }
+    }
+    if (sg == 0 && vi) write_out<MODE, ENERGY>(fout, __float_as_int(pi.w), k.n, Fx, Fy, Fz, E, Wv, eacc, wacc);
+    __syncwarp();   // the slice is reused by the next cell
+}
+
+// Plain path: any occupancy; each stencil cell read from global memory with
+// the home particle shifted into that cell's frame.
+template <int MODE, bool ENERGY>
+__device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, float4 *__restrict__ fout, int s_k,
+                           int n_k, float sx, float sy, float sz, int s_home, int n_home, double &eacc, double &wacc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int p0 = 0; p0 < n_home; p0 += 32) {
+        const int i = p0 + lane;
+        const bool vi = i < n_home;
+        const float4 pi = __ldg(pos + s_home + (vi ? i : 0));
+        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, w = 0.f;
+        for (int kk = 0; kk < 27; kk++) {
+            const int s = __shfl_sync(0xffffffffu, s_k, kk);
+            const int nn = __shfl_sync(0xffffffffu, n_k, kk);
+            const float xs = pi.x - __shfl_sync(0xffffffffu, sx, kk);
+            const float ys = pi.y - __shfl_sync(0xffffffffu, sy, kk);
+            const float zs = pi.z - __shfl_sync(0xffffffffu, sz, kk);
+            for (int j = 0; j < nn; j++) {
+                const float4 q = __ldg(pos + s + j);
+                pair1<MODE, ENERGY>(xs - q.x, ys - q.y, zs - q.z, k, fx, fy, fz, e, w);
+            }
+        }
+        if (vi) write_out<MODE, ENERGY>(fout, __float_as_int(pi.w), k.n, fx, fy, fz, e, w, eacc, wacc);
+    }
+}
+
+template <int MODE, bool ENERGY>
+__global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams k, const float4 *__restrict__ pos,
+                                                                  const int32_t *__restrict__ start,
+                                                                  float4 *__restrict__ fout,
+                                                                  double *__restrict__ partial)
+{
+    extern __shared__ __align__(16) float wsmem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float *X = wsmem + (size_t)warp * 3 * k.cap;
+    float *Y = X + k.cap;
+    float *Z = Y + k.cap;
+    const int nc = k.nc;
+    double eacc = 0.0, wacc = 0.0;
+    const int64_t nwarps = (int64_t)gridDim.x * (kWarpForceThreads / 32);
+    for (int64_t c = (int64_t)blockIdx.x * (kWarpForceThreads / 32) + warp; c < k.ncell; c += nwarps) {
+        const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+        // stencil table: lane kk < 27 holds cell kk
+        int s_k = 0, n_k = 0;
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        if (lane < 27) {
+            int dx, dy, dz;
+            stencil_offset(lane, dx, dy, dz);
+            int ux = cx + dx, uy = cy + dy, uz = cz + dz;
+            ux += ux < 0 ? nc : 0;
+            ux -= ux >= nc ? nc : 0;
+            uy += uy < 0 ? nc : 0;
+            uy -= uy >= nc ? nc : 0;
+            uz += uz < 0 ? nc : 0;
+            uz -= uz >= nc ? nc : 0;
+            const int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
+            s_k = start[cn];
+            n_k = start[cn + 1] - s_k;
+            sx = (float)dx * k.cw;
+            sy = (float)dy * k.cw;
+            sz = (float)dz * k.cw;
+        }
+        int P = n_k;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, P, o);
+            if (lane >= o) P += y;
+        }
+        const int T = __shfl_sync(0xffffffffu, P, 31);
+        const int P_k = P - n_k;
+        const int s_home = __shfl_sync(0xffffffffu, s_k, 0);
+        const int n_home = __shfl_sync(0xffffffffu, n_k, 0);
+        if (n_home == 0) continue;
+        if (n_home <= 32 && T + 8 <= k.cap) {
+            if (n_home <= 8)
+                cell_staged<8, MODE, ENERGY>(k, pos, fout, X, Y, Z, s_k, n_k, P_k, sx, sy, sz, s_home, n_home, T,
+                                             eacc, wacc);
+            else if (n_home <= 16)
+                cell_staged<16, MODE, ENERGY>(k, pos, fout, X, Y, Z, s_k, n_k, P_k, sx, sy, sz, s_home, n_home, T,
+                                              eacc, wacc);
+            else
+                cell_staged<32, MODE, ENERGY>(k, pos, fout, X, Y, Z, s_k, n_k, P_k, sx, sy, sz, s_home, n_home, T,
+                                              eacc, wacc);
+        } else {
+            cell_plain<MODE, ENERGY>(k, pos, fout, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
+        }
+    }
+    if constexpr (ENERGY) {
+        __shared__ double red[2 * (kWarpForceThreads / 32)];
+        for (int o = 16; o > 0; o >>= 1) {
+            eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+            wacc += __shfl_xor_sync(0xffffffffu, wacc, o);
+        }
+        if (lane == 0) {
+            red[2 * warp] = eacc;
+            red[2 * warp + 1] = wacc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double es = 0.0, ws = 0.0;
+            for (int q = 0; q < kWarpForceThreads / 32; q++) {
+                es += red[2 * q];
+                ws += red[2 * q + 1];
+            }
+            partial[2 * blockIdx.x] = es;
+            partial[2 * blockIdx.x + 1] = ws;
+        }
+    }
+}
+
+void *warp_kernel(int mode, bool energy)
+{
+    switch (mode * 2 + (energy ? 1 : 0)) {
+        case 0: return (void *)k_force_warp<0, false>;
+        case 1: return (void *)k_force_warp<0, true>;
+        case 2: return (void *)k_force_warp<1, false>;
+        case 3: return (void *)k_force_warp<1, true>;
+        case 4: return (void *)k_force_warp<2, false>;
+        default: return (void *)k_force_warp<2, true>;
+    }
+}
+
+}  // namespace
+
+cudaError_t warp_force_configure(lj_ctx *c)
+{
+    // Staged candidates per warp: 1.5x the mean stencil population + 64,
+    // multiple of 8, capped so that 4 CTAs (32 warps, the register limit)
+    // fit in an SM's 227 KB of shared memory.
+    double mean = c->ncell > 0 ? (double)c->p.n / (double)c->ncell : 0.0;
+    int cap = (int)(1.5 * 27.0 * mean) + 64;
+    cap = (cap + 7) & ~7;
+    const int cap_max = ((227 * 1024 / 4 - 1152) / ((kWarpForceThreads / 32) * 3 * (int)sizeof(float))) & ~7;
+    cap = cap > cap_max ? cap_max : cap;
+    c->wcap = cap;
+    c->wforce_smem = (kWarpForceThreads / 32) * 3 * cap * (int)sizeof(float);
+    int minblk = 1 << 30;
+    for (int mode = 0; mode < 3; mode++)
+        for (int en = 0; en < 2; en++) {
+            void *kern = warp_kernel(mode, en != 0);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->wforce_smem);
+            if (e != cudaSuccess) return e;
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kWarpForceThreads, c->wforce_smem);
+            if (e != cudaSuccess) return e;
+            if (nb < minblk) minblk = nb;
+        }
+    if (minblk < 1) minblk = 1;
+    int64_t cells_per_block = kWarpForceThreads / 32;
+    int64_t need = (c->ncell + cells_per_block - 1) / cells_per_block;
+    int64_t grid = (int64_t)minblk * c->nsm;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    c->wforce_grid = (int)grid;
+    return cudaSuccess;
+}
+
+cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
+{
+    WarpParams k;
+    k.n = (int)c->p.n;
+    k.nc = c->nc;
+    k.cap = c->wcap;
+    k.ncell = c->ncell;
+    k.cw = (float)c->cw;
+    const double eps = c->p.eps, sg = c->p.sigma, rc = c->p.rc;
+    const double s6 = sg * sg * sg * sg * sg * sg, s12 = s6 * s6;
+    const double rci2 = 1.0 / (rc * rc), rci6 = rci2 * rci2 * rci2;
+    k.rc2 = (float)(rc * rc);
+    k.rc = (float)rc;
+    k.a12 = (float)(48.0 * eps * s12);
+    k.b6 = (float)(24.0 * eps * s6);
+    k.c12 = (float)(4.0 * eps * s12);
+    k.c6 = (float)(4.0 * eps * s6);
+    k.uc = (float)(rci6 * (4.0 * eps * s12 * rci6 - 4.0 * eps * s6));
+    k.fc = (float)(rc * rci2 * rci6 * (48.0 * eps * s12 * rci6 - 24.0 * eps * s6));
+    void *kern = warp_kernel(c->p.shift_mode, energy);
+    const float4 *pos = (const float4 *)c->pos;
+    const int32_t *start = c->start;
+    double *partial = c->partial;
+    void *args[] = {&k, (void *)&pos, (void *)&start, &f, &partial};
+    if (c->timing && c->ev_used + 2 <= c->nev) cudaEventRecord(c->ev[c->ev_used], c->stream);
+    cudaError_t e = cudaLaunchKernel(kern, dim3(c->wforce_grid), dim3(kWarpForceThreads), args, c->wforce_smem,
+                                     c->stream);
+    if (c->timing && c->ev_used + 2 <= c->nev) {
+        cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+        c->ev_used += 2;
+    }
+    c->kernel_launches++;
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}

@@ -28,6 +28,8 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 constexpr int kReduceThreads = 256;
 
+constexpr int kWarpForceThreads = 256;         // warp-per-cell force kernel
+
 struct lj_ctx {
     lj_params p;
     int nc;              // cells per side
@@ -50,8 +52,11 @@ struct lj_ctx {
     double *host_scalars;   // pinned, 4 doubles
     int32_t *host_err;      // pinned
 
-    // force kernel configuration
-    int run_len, runs, nitems, cap, force_grid, force_smem, use_tma;
+    // force kernel configuration: run-staged kernel (lj_force.cu) ...
+    int run_len, runs, nitems, cap, force_grid, force_smem, use_tma, use_run_kernel;
+    // ... and warp-per-cell kernel (lj_force_warp.cu, FP32-mixed)
+    int wcap, wforce_smem, wforce_grid;
+    int npartial;        // partials written by the last energy launch
     int ekin_grid;
 
     // lazily allocated staging for lj_step_host / lj_energy
@@ -106,3 +111,5 @@ cudaError_t launch_kick(lj_ctx *c, double *v, const void *f);
 cudaError_t launch_ekin(lj_ctx *c, const double *v);
 cudaError_t launch_counts_from_start(lj_ctx *c, int32_t *count);
 cudaError_t force_configure(lj_ctx *c);
+cudaError_t warp_force_configure(lj_ctx *c);
+cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);

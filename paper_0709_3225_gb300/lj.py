@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "liblj.so")
 LJ_OK, LJ_EINVAL, LJ_EBOX, LJ_ECUDA, LJ_ENONFINITE, LJ_ETIMEOUT, LJ_EOVERFLOW, LJ_ENOMEM = range(8)
 LJ_SHIFT_NONE, LJ_SHIFT_ENERGY, LJ_SHIFT_FORCE = 0, 1, 2
 LJ_PREC_MIXED, LJ_PREC_FP64 = 0, 1
-LJ_FLAG_NO_STAGING = 1
+LJ_FLAG_RUN_STAGED = 1
+LJ_FLAG_RUN_DIRECT = 2
 
 _PREC = {"mixed": LJ_PREC_MIXED, "fp64": LJ_PREC_FP64, LJ_PREC_MIXED: LJ_PREC_MIXED, LJ_PREC_FP64: LJ_PREC_FP64}
 

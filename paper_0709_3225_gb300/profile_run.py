@@ -1,0 +1,52 @@
+"""Run one library operation on a synthetic LJ liquid, for profilers.
+
+  python -m paper_0709_3225_gb300.profile_run --op force --n-fcc 80 --reps 3
+
+Builds a jittered FCC liquid of 4 n^3 particles at rho = 0.8442, then runs
+``--reps`` force evaluations (``--op force``) or velocity-Verlet steps
+(``--op step``) through the C ABI after one untimed warm-up, and prints the
+CUDA-event time per call.  It reports no benchmark figures; use bench.py for
+those.
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+from . import inputs, lj
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", choices=["force", "step"], default="force")
+    ap.add_argument("--n-fcc", type=int, default=80)
+    ap.add_argument("--rho", type=float, default=0.8442)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--flags", type=int, default=0)
+    args = ap.parse_args(argv)
+    x, L = inputs.jittered_fcc(args.n_fcc, args.rho, 0.1, 1)
+    v = inputs.velocities(x.shape[0], 1.0, 1)
+    s = lj.System(x, v, L, precision=args.precision, flags=args.flags)
+    s.forces()
+    if args.op == "step":
+        s.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        if args.op == "force":
+            s.forces()
+        else:
+            s.step(1)
+    e1.record()
+    torch.cuda.synchronize()
+    s.check()
+    print(f"{args.op} n={s.n} nc={s.ctx.nc} {e0.elapsed_time(e1) / args.reps:.3f} ms per call")
+    s.close()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -71,7 +71,7 @@ def test_grid_agrees_with_oracle(lib, oracle_mod):
 @pytest.mark.parametrize("field,value,code", [
     ("box", 7.4, 2), ("box", 0.0, 1), ("box", float("nan"), 1), ("sigma", 0.0, 1), ("rc", -1.0, 1),
     ("mass", 0.0, 1), ("eps", -1.0, 1), ("shift_mode", 3, 1), ("precision", 2, 1),
-    ("cell_subdiv", 2, 1), ("flags", 8, 1), ("n", -1, 1), ("n", 2 ** 31, 6), ("box", 1e6, 6),
+    ("cell_subdiv", 2, 1), ("flags", 8, 1), ("flags", 3, 1), ("n", -1, 1), ("n", 2 ** 31, 6), ("box", 1e6, 6),
 ])
 def test_bad_parameters_rejected(lib, field, value, code):
     from paper_0709_3225_gb300 import lj
