@@ -21,6 +21,16 @@ int map_cuda(cudaError_t e)
         if (lj_ck_e_ != cudaSuccess) return map_cuda(lj_ck_e_); \
     } while (0)
 
+// Smallest double t >= 0 with trunc(t * s) >= k (IEEE double multiply, the
+// same operation the kernels use): the lower edge of cell k.
+double cell_threshold(int k, double s)
+{
+    double t = (double)k / s;
+    while (t > 0.0 && nextafter(t, 0.0) * s >= (double)k) t = nextafter(t, 0.0);
+    while (!(t * s >= (double)k)) t = nextafter(t, INFINITY);
+    return t;
+}
+
 int validate(const lj_params *p, int *nc_out)
 {
     if (!p) return LJ_EINVAL;
@@ -75,6 +85,8 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->perm);
     cudaFree(c->pos);
     cudaFree(c->tile_sum);
+    cudaFree(c->centre);
+    cudaFree(c->thb);
     cudaFree(c->partial);
     cudaFree(c->ekin_partial);
     cudaFree(c->scalars);
@@ -180,6 +192,8 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     c->ncell = (int64_t)nc * nc * nc;
     c->inv_cw = (double)nc / p->box;
     c->cw = p->box / (double)nc;
+    c->wrap_hi = p->box * (1.0 - ldexp(1.0, -50));
+    c->wrap_lo = p->box * ldexp(1.0, -50);
     c->stream = (cudaStream_t)stream;
     // Kernel choice: FP32-mixed defaults to the warp-per-cell kernel, FP64
     // to the run-staged kernel; the flags force a run kernel.
@@ -204,6 +218,35 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     LJ_CREATE_CK(cudaMalloc(&c->count, (size_t)c->ncell * sizeof(int32_t)));
     LJ_CREATE_CK(cudaMalloc(&c->start, (size_t)(c->ncell + 1) * sizeof(int32_t)));
     LJ_CREATE_CK(cudaMalloc(&c->pos, n1 * force_vsize(c)));
+    {
+        double *h = (double *)malloc(sizeof(double) * (size_t)nc);
+        if (!h) {
+            free_ctx(c);
+            return LJ_ENOMEM;
+        }
+        for (int k = 0; k < nc; k++) h[k] = ((double)k + 0.5) * c->cw;
+        cudaError_t e = cudaMalloc(&c->centre, sizeof(double) * (size_t)nc);
+        if (e == cudaSuccess) e = cudaMemcpy(c->centre, h, sizeof(double) * (size_t)nc, cudaMemcpyHostToDevice);
+        free(h);
+        long long *tb = (long long *)malloc(sizeof(long long) * (size_t)(nc + 1));
+        if (!tb && e == cudaSuccess) e = cudaErrorMemoryAllocation;
+        if (tb) {
+            tb[0] = 0;
+            for (int k = 1; k < nc; k++) {
+                double t = cell_threshold(k, c->inv_cw);
+                memcpy(&tb[k], &t, sizeof(double));
+            }
+            tb[nc] = INT64_MAX;
+            if (e == cudaSuccess) e = cudaMalloc(&c->thb, sizeof(long long) * (size_t)(nc + 1));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(c->thb, tb, sizeof(long long) * (size_t)(nc + 1), cudaMemcpyHostToDevice);
+            free(tb);
+        }
+        if (e != cudaSuccess) {
+            free_ctx(c);
+            return map_cuda(e);
+        }
+    }
     c->ntiles = (int)((c->ncell + kScanTile - 1) / kScanTile);
     LJ_CREATE_CK(cudaMalloc(&c->tile_sum, (size_t)c->ntiles * sizeof(int32_t)));
     LJ_CREATE_CK(force_configure(c));
@@ -220,6 +263,7 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     LJ_CREATE_CK(cudaMallocHost(&c->host_scalars, 4 * sizeof(double)));
     LJ_CREATE_CK(cudaMallocHost(&c->host_err, sizeof(int32_t)));
     LJ_CREATE_CK(cudaMemsetAsync(c->count, 0, (size_t)c->ncell * sizeof(int32_t), c->stream));
+    LJ_CREATE_CK(cudaMemsetAsync(c->cell_of, 0, n1 * sizeof(int32_t), c->stream));
     LJ_CREATE_CK(cudaMemsetAsync(c->start, 0, (size_t)(c->ncell + 1) * sizeof(int32_t), c->stream));
     LJ_CREATE_CK(cudaMemsetAsync(c->scalars, 0, 4 * sizeof(double), c->stream));
     LJ_CREATE_CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));

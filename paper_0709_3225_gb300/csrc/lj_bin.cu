@@ -7,21 +7,28 @@
 
 namespace {
 
-// Per particle: wrapped position, cell id, rank within the cell (atomic).
-__global__ void k_bin_count(const double *__restrict__ x, int n, double L, double s, int nc,
+// Per particle: wrapped position, cell id, rank within the cell (one
+// atomic per distinct cell per warp).  Launched with whole warps.
+__global__ void k_bin_count(const double *__restrict__ x, int n, double L, double whi, double wlo, double s, int nc,
                             int32_t *__restrict__ cell_of, int32_t *__restrict__ rank,
                             int32_t *__restrict__ count, int32_t *__restrict__ err)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double px = x[3 * (int64_t)i + 0], py = x[3 * (int64_t)i + 1], pz = x[3 * (int64_t)i + 2];
-    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
-    int cx = lj_cell1(lj_wrap(px, L), s, nc);
-    int cy = lj_cell1(lj_wrap(py, L), s, nc);
-    int cz = lj_cell1(lj_wrap(pz, L), s, nc);
-    int c = cx + nc * (cy + nc * cz);
-    cell_of[i] = c;
-    rank[i] = atomicAdd(count + c, 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    int c = 0;
+    if (valid) {
+        double px = x[3 * (int64_t)i + 0], py = x[3 * (int64_t)i + 1], pz = x[3 * (int64_t)i + 2];
+        if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
+        int cx = lj_cell1(lj_wrap_fast(px, L, whi, wlo), s, nc);
+        int cy = lj_cell1(lj_wrap_fast(py, L, whi, wlo), s, nc);
+        int cz = lj_cell1(lj_wrap_fast(pz, L, whi, wlo), s, nc);
+        c = cx + nc * (cy + nc * cz);
+    }
+    const int r = lj_warp_rank(count, c, valid);
+    if (valid) {
+        cell_of[i] = c;
+        rank[i] = r;
+    }
 }
 
 // Scan phase 1: sum of each tile of kScanTile counts.
@@ -111,10 +118,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int32_t *__restrict
 
 // Scatter each particle to its sorted slot: perm[slot] = i and the position
 // relative to the centre of its cell (FP32 or FP64), with the particle index
-// carried in .w.
+// carried in .w.  centre[k] = (k + 1/2) L / nc, one FP64 subtraction per
+// coordinate.
 template <typename T>
-__global__ void k_scatter(const double *__restrict__ x, int n, double L, double cw, int nc, bool wrap,
-                          const int32_t *__restrict__ cell_of, const int32_t *__restrict__ rank,
+__global__ void k_scatter(const double *__restrict__ x, int n, double L, double whi, double wlo,
+                          const double *__restrict__ centre, int nc, bool wrap, const int32_t *__restrict__ cell_of, const int32_t *__restrict__ rank,
                           const int32_t *__restrict__ start, int32_t *__restrict__ perm,
                           typename Vec4<T>::type *__restrict__ pos)
 {
@@ -124,15 +132,15 @@ __global__ void k_scatter(const double *__restrict__ x, int n, double L, double 
     int slot = start[c] + rank[i];
     double px = x[3 * (int64_t)i + 0], py = x[3 * (int64_t)i + 1], pz = x[3 * (int64_t)i + 2];
     if (wrap) {
-        px = lj_wrap(px, L);
-        py = lj_wrap(py, L);
-        pz = lj_wrap(pz, L);
+        px = lj_wrap_fast(px, L, whi, wlo);
+        py = lj_wrap_fast(py, L, whi, wlo);
+        pz = lj_wrap_fast(pz, L, whi, wlo);
     }
     int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
     typename Vec4<T>::type q;
-    q.x = (T)(px - ((double)cx + 0.5) * cw);
-    q.y = (T)(py - ((double)cy + 0.5) * cw);
-    q.z = (T)(pz - ((double)cz + 0.5) * cw);
+    q.x = (T)(px - __ldg(centre + cx));
+    q.y = (T)(py - __ldg(centre + cy));
+    q.z = (T)(pz - __ldg(centre + cz));
     if constexpr (sizeof(T) == 4) {
         q.w = __int_as_float(i);
     } else {
@@ -156,7 +164,7 @@ cudaError_t launch_bin_count(lj_ctx *c, const double *x)
 {
     int n = (int)c->p.n;
     if (n > 0) {
-        k_bin_count<<<blocks_for(n, 256), 256, 0, c->stream>>>(x, n, c->p.box, c->inv_cw, c->nc, c->cell_of,
+        k_bin_count<<<blocks_for(n, 256), 256, 0, c->stream>>>(x, n, c->p.box, c->wrap_hi, c->wrap_lo, c->inv_cw, c->nc, c->cell_of,
                                                                 c->rank, c->count, c->err);
         c->kernel_launches++;
     }
@@ -178,10 +186,10 @@ cudaError_t launch_scatter(lj_ctx *c, const double *x, bool wrap)
     if (n > 0) {
         if (c->p.precision == LJ_PREC_FP64)
             k_scatter<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(
-                x, n, c->p.box, c->cw, c->nc, wrap, c->cell_of, c->rank, c->start, c->perm, (double4_16a *)c->pos);
+                x, n, c->p.box, c->wrap_hi, c->wrap_lo, c->centre, c->nc, wrap, c->cell_of, c->rank, c->start, c->perm, (double4_16a *)c->pos);
         else
             k_scatter<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(
-                x, n, c->p.box, c->cw, c->nc, wrap, c->cell_of, c->rank, c->start, c->perm, (float4 *)c->pos);
+                x, n, c->p.box, c->wrap_hi, c->wrap_lo, c->centre, c->nc, wrap, c->cell_of, c->rank, c->start, c->perm, (float4 *)c->pos);
         c->kernel_launches++;
     }
     return cudaGetLastError();

@@ -19,36 +19,48 @@ __device__ __forceinline__ void load_f(const F4 *__restrict__ f, int i, double &
 // nkick half kicks v += h f (1 on the first step of a call, 2 when the
 // closing half kick of the previous step is fused in), drift x += dt v, wrap
 // into [0, L), cell id and rank (atomic count) of the new position.
+// nkick half kicks v += h f (1 on the first step of a call, 2 when the
+// closing half kick of the previous step is fused in, applied as one FP64
+// FMA with nkick*h), drift x += dt v (FP64 FMA), wrap into [0, L), cell id
+// (exact, from the previous cell as a guess) and rank of the new position
+// (one atomic per distinct cell per warp).  No FP64 division or multiply
+// in the common path: this GPU's FP64 rate is a small fraction of FP32.
 template <typename F4>
 __global__ void k_kick_drift_bin(double *__restrict__ x, double *__restrict__ v, const F4 *__restrict__ f, int n,
-                                 double h, double dt, int nkick, double L, double s, int nc,
-                                 int32_t *__restrict__ cell_of, int32_t *__restrict__ rank,
-                                 int32_t *__restrict__ count, int32_t *__restrict__ err)
+                                 double hk, double dt, double L, double whi, double wlo, double s, int nc,
+                                 const long long *__restrict__ thb, int32_t *__restrict__ cell_of,
+                                 int32_t *__restrict__ rank, int32_t *__restrict__ count, int32_t *__restrict__ err)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t b = 3 * (int64_t)i;
-    double fx, fy, fz;
-    load_f(f, i, fx, fy, fz);
-    double vx = v[b], vy = v[b + 1], vz = v[b + 2];
-    for (int k = 0; k < nkick; k++) {
-        vx = __dadd_rn(vx, __dmul_rn(h, fx));
-        vy = __dadd_rn(vy, __dmul_rn(h, fy));
-        vz = __dadd_rn(vz, __dmul_rn(h, fz));
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    int c = 0;
+    if (valid) {
+        const int64_t b = 3 * (int64_t)i;
+        double fx, fy, fz;
+        load_f(f, i, fx, fy, fz);
+        const double vx = __fma_rn(hk, fx, v[b]);
+        const double vy = __fma_rn(hk, fy, v[b + 1]);
+        const double vz = __fma_rn(hk, fz, v[b + 2]);
+        const double px = lj_wrap_fast(__fma_rn(dt, vx, x[b]), L, whi, wlo);
+        const double py = lj_wrap_fast(__fma_rn(dt, vy, x[b + 1]), L, whi, wlo);
+        const double pz = lj_wrap_fast(__fma_rn(dt, vz, x[b + 2]), L, whi, wlo);
+        if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
+        v[b] = vx;
+        v[b + 1] = vy;
+        v[b + 2] = vz;
+        x[b] = px;
+        x[b + 1] = py;
+        x[b + 2] = pz;
+        const int old = cell_of[i];
+        const int ox = old % nc, oy = (old / nc) % nc, oz = old / (nc * nc);
+        c = lj_cell_from_guess(px, ox, thb, s, nc) +
+            nc * (lj_cell_from_guess(py, oy, thb, s, nc) + nc * lj_cell_from_guess(pz, oz, thb, s, nc));
     }
-    double px = lj_wrap(__dadd_rn(x[b], __dmul_rn(dt, vx)), L);
-    double py = lj_wrap(__dadd_rn(x[b + 1], __dmul_rn(dt, vy)), L);
-    double pz = lj_wrap(__dadd_rn(x[b + 2], __dmul_rn(dt, vz)), L);
-    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
-    v[b] = vx;
-    v[b + 1] = vy;
-    v[b + 2] = vz;
-    x[b] = px;
-    x[b + 1] = py;
-    x[b + 2] = pz;
-    int c = lj_cell1(px, s, nc) + nc * (lj_cell1(py, s, nc) + nc * lj_cell1(pz, s, nc));
-    cell_of[i] = c;
-    rank[i] = atomicAdd(count + c, 1);
+    const int r = lj_warp_rank(count, c, valid);
+    if (valid) {
+        cell_of[i] = c;
+        rank[i] = r;
+    }
 }
 
 template <typename F4>
@@ -59,9 +71,9 @@ __global__ void k_kick(double *__restrict__ v, const F4 *__restrict__ f, int n, 
     const int64_t b = 3 * (int64_t)i;
     double fx, fy, fz;
     load_f(f, i, fx, fy, fz);
-    v[b] = __dadd_rn(v[b], __dmul_rn(h, fx));
-    v[b + 1] = __dadd_rn(v[b + 1], __dmul_rn(h, fy));
-    v[b + 2] = __dadd_rn(v[b + 2], __dmul_rn(h, fz));
+    v[b] = __fma_rn(h, fx, v[b]);
+    v[b + 1] = __fma_rn(h, fy, v[b + 1]);
+    v[b + 2] = __fma_rn(h, fz, v[b + 2]);
 }
 
 // Per-block partial sums of v.v (grid-stride, fixed grid), then one block
@@ -106,15 +118,15 @@ cudaError_t launch_kick_drift_bin(lj_ctx *c, double *x, double *v, const void *f
 {
     int n = (int)c->p.n;
     if (n == 0) return cudaSuccess;
-    const double h = 0.5 * c->p.dt / c->p.mass;
+    const double hk = nkick * (0.5 * c->p.dt / c->p.mass);
     if (c->p.precision == LJ_PREC_FP64)
         k_kick_drift_bin<double4_16a><<<blocks_for(n, 256), 256, 0, c->stream>>>(
-            x, v, (const double4_16a *)f, n, h, c->p.dt, nkick, c->p.box, c->inv_cw, c->nc, c->cell_of, c->rank,
-            c->count, c->err);
+            x, v, (const double4_16a *)f, n, hk, c->p.dt, c->p.box, c->wrap_hi, c->wrap_lo, c->inv_cw, c->nc, c->thb,
+            c->cell_of, c->rank, c->count, c->err);
     else
         k_kick_drift_bin<float4><<<blocks_for(n, 256), 256, 0, c->stream>>>(
-            x, v, (const float4 *)f, n, h, c->p.dt, nkick, c->p.box, c->inv_cw, c->nc, c->cell_of, c->rank,
-            c->count, c->err);
+            x, v, (const float4 *)f, n, hk, c->p.dt, c->p.box, c->wrap_hi, c->wrap_lo, c->inv_cw, c->nc, c->thb,
+            c->cell_of, c->rank, c->count, c->err);
     c->kernel_launches++;
     return cudaGetLastError();
 }

@@ -43,6 +43,9 @@ struct lj_ctx {
     // device scratch
     int32_t *cell_of, *rank, *count, *start, *perm;
     void *pos;           // float4 or double4_16a [n], sorted, cell-centred coordinates
+    double *centre;      // [nc] cell-centre coordinate (k + 1/2) L / nc
+    long long *thb;      // [nc + 1] bits of the cell thresholds (lj_cell_from_guess)
+    double wrap_hi, wrap_lo;  // lj_wrap_fast bounds
     int32_t *tile_sum;
     int ntiles;
     double *partial;     // force-kernel per-block (energy, virial) partials
@@ -85,6 +88,25 @@ __device__ __forceinline__ double lj_wrap(double x, double L)
     return w;
 }
 
+// lj_wrap without the division in the common cases: for x in [0, L - L/2^50)
+// the quotient floor(x / L) is exactly 0, in [L + L/2^50, 2L - L/2^49) it is
+// exactly 1 and in (-L + L/2^50, -L/2^50] exactly -1, so the result is bit
+// for bit that of lj_wrap; other inputs take lj_wrap itself.  The first test
+// runs on the integer pipe (non-negative doubles order like their bits).
+// hi = L (1 - 2^-50), lo = L 2^-50.
+__device__ __forceinline__ double lj_wrap_fast(double x, double L, double hi, double lo)
+{
+    const long long b = __double_as_longlong(x);
+    if (b >= 0 && b < __double_as_longlong(hi)) return x;
+    double q;
+    if (x >= L + lo && x < 2.0 * L - 2.0 * lo) q = 1.0;
+    else if (x <= -lo && x > -hi) q = -1.0;
+    else return lj_wrap(x, L);
+    double w = __dsub_rn(x, __dmul_rn(L, q));
+    if (w >= L) w = __dsub_rn(w, L);
+    return w;
+}
+
 // Cell coordinate trunc(w * s), clamped to [0, nc - 1].
 __device__ __forceinline__ int lj_cell1(double w, double s, int nc)
 {
@@ -92,6 +114,43 @@ __device__ __forceinline__ int lj_cell1(double w, double s, int nc)
     c = c < nc ? c : nc - 1;
     c = c > 0 ? c : 0;
     return c;
+}
+
+// Rank of a particle within its cell by one atomicAdd per distinct cell in
+// the warp: lanes holding the same cell id are grouped with match.any, the
+// lowest lane adds the group size, and ranks follow lane order inside the
+// group.  All 32 lanes must call it (valid = false lanes get no rank).
+__device__ __forceinline__ int lj_warp_rank(int32_t *count, int c, bool valid)
+{
+    const unsigned key = valid ? (unsigned)c : 0xffffffffu;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (valid && lane == leader) base = atomicAdd(count + c, __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+// Exact cell coordinate of a wrapped w from a guess g: thb[k] holds the bits
+// of the smallest double t with trunc(t * s) >= k (thb[0] = 0, thb[nc] =
+// INT64_MAX), so the cell is the largest k with w >= t_k -- the same value
+// lj_cell1 returns.  Checks g - 1, g, g + 1 with integer compares and falls
+// back to lj_cell1 when the guess is further off.
+__device__ __forceinline__ int lj_cell_from_guess(double w, int g, const long long *__restrict__ thb, double s,
+                                                  int nc)
+{
+    long long b = __double_as_longlong(w);
+    b = b < 0 ? 0 : b;                  // -0 and negative values bin like 0
+    g = g < 0 ? 0 : (g >= nc ? nc - 1 : g);
+    if (b < __ldg(thb + g)) {
+        g -= 1;
+        if (g < 0 || b < __ldg(thb + g)) return lj_cell1(w, s, nc);
+    } else if (b >= __ldg(thb + g + 1)) {
+        g += 1;
+        if (g >= nc || b >= __ldg(thb + g + 1)) return lj_cell1(w, s, nc);
+    }
+    return g;
 }
 
 template <typename T> struct Vec4;
