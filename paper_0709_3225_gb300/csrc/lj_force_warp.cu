@@ -160,21 +160,62 @@ __device__ __forceinline__ void write_out(float4 *__restrict__ fout, int idx, in
 template <int G, int MODE, bool ENERGY>
 __device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *__restrict__ pos,
                                             float4 *__restrict__ fout, float *X, float *Y, float *Z, int s_k,
-                                            int n_k, int P_k, float sx, float sy, float sz, int s_home, int n_home,
-                                            int T, double &eacc, double &wacc)
+                                            int n_k, float sx, float sy, float sz, int s_home, int n_home,
+                                            double &eacc, double &wacc)
 {
     constexpr int S = 32 / G;
     const int lane = threadIdx.x & 31;
-    // stage: lane k copies stencil cell k, shifted to home-centre coordinates
-    if (lane < 27) {
-#pragma unroll 4
-        for (int e = 0; e < n_k; e++) {
+    // Home particles (lane e holds home particle e) and their bounding box in
+    // the home-centre frame.  Stencil candidates farther than rc from the box
+    // cannot interact with any home particle and are not staged (the margin
+    // covers FP32 rounding of the box test).
+    const bool hl = lane < n_home;
+    const float4 ph = __ldg(pos + s_home + (hl ? lane : 0));
+    float bxl = hl ? ph.x : 3.4e38f, byl = hl ? ph.y : 3.4e38f, bzl = hl ? ph.z : 3.4e38f;
+    float bxh = hl ? ph.x : -3.4e38f, byh = hl ? ph.y : -3.4e38f, bzh = hl ? ph.z : -3.4e38f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
+        byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
+        bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
+        bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
+        byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
+        bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
+    }
+    // stage the home cell first (candidates 0 .. n_home-1, all kept)
+    if (hl) {
+        const int sl = slot_of<S>(lane);
+        X[sl] = ph.x;
+        Y[sl] = ph.y;
+        Z[sl] = ph.z;
+    }
+    // then lane k = 1..26 walks stencil cell k; kept candidates are appended
+    // in ballot order
+    const float rcut2 = k.rc2 * 1.0001f;
+    const int my_n = (lane >= 1 && lane < 27) ? n_k : 0;
+    const unsigned lt = (1u << lane) - 1u;
+    int T = n_home;
+    for (int e = 0; __any_sync(0xffffffffu, e < my_n); e++) {
+        bool keep = false;
+        float cx = 0.f, cy = 0.f, cz = 0.f;
+        if (e < my_n) {
             const float4 q = __ldg(pos + s_k + e);
-            const int sl = slot_of<S>(P_k + e);
-            X[sl] = q.x + sx;
-            Y[sl] = q.y + sy;
-            Z[sl] = q.z + sz;
+            cx = q.x + sx;
+            cy = q.y + sy;
+            cz = q.z + sz;
+            const float dx = fmaxf(fmaxf(bxl - cx, cx - bxh), 0.f);
+            const float dy = fmaxf(fmaxf(byl - cy, cy - byh), 0.f);
+            const float dz = fmaxf(fmaxf(bzl - cz, cz - bzh), 0.f);
+            keep = dx * dx + dy * dy + dz * dz < rcut2;
         }
+        const unsigned kept = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int sl = slot_of<S>(T + __popc(kept & lt));
+            X[sl] = cx;
+            Y[sl] = cy;
+            Z[sl] = cz;
+        }
+        T += __popc(kept);
     }
     const int Tpad = (T + 2 * S - 1) / (2 * S) * (2 * S);
     if (lane < Tpad - T) {
@@ -188,7 +229,8 @@ __device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *_
     const int gl = lane % G;
     const int sg = lane / G;
     const bool vi = gl < n_home;
-    const float4 pi = __ldg(pos + s_home + (vi ? gl : 0));
+    const float4 pi = make_float4(__shfl_sync(0xffffffffu, ph.x, gl), __shfl_sync(0xffffffffu, ph.y, gl),
+                                  __shfl_sync(0xffffffffu, ph.z, gl), __shfl_sync(0xffffffffu, ph.w, gl));
     const float2 xs = f2(pi.x), ys = f2(pi.y), zs = f2(pi.z);
     float2 fx = f2(0.f), fy = f2(0.f), fz = f2(0.f), e = f2(0.f), w = f2(0.f);
     const int iters = Tpad / (2 * S);
@@ -288,19 +330,18 @@ __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams 
             if (lane >= o) P += y;
         }
         const int T = __shfl_sync(0xffffffffu, P, 31);
-        const int P_k = P - n_k;
         const int s_home = __shfl_sync(0xffffffffu, s_k, 0);
         const int n_home = __shfl_sync(0xffffffffu, n_k, 0);
         if (n_home == 0) continue;
         if (n_home <= 32 && T + 8 <= k.cap) {
             if (n_home <= 8)
-                cell_staged<8, MODE, ENERGY>(k, pos, fout, X, Y, Z, s_k, n_k, P_k, sx, sy, sz, s_home, n_home, T,
+                cell_staged<8, MODE, ENERGY>(k, pos, fout, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home,
                                              eacc, wacc);
             else if (n_home <= 16)
-                cell_staged<16, MODE, ENERGY>(k, pos, fout, X, Y, Z, s_k, n_k, P_k, sx, sy, sz, s_home, n_home, T,
+                cell_staged<16, MODE, ENERGY>(k, pos, fout, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home,
                                               eacc, wacc);
             else
-                cell_staged<32, MODE, ENERGY>(k, pos, fout, X, Y, Z, s_k, n_k, P_k, sx, sy, sz, s_home, n_home, T,
+                cell_staged<32, MODE, ENERGY>(k, pos, fout, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home,
                                               eacc, wacc);
         } else {
             cell_plain<MODE, ENERGY>(k, pos, fout, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
