@@ -162,6 +162,32 @@ int lj_energy(lj_ctx *ctx, const double *x, const double *v, double *out);
  * kernel since the last check. */
 int lj_check(lj_ctx *ctx);
 
+/* Limits of lj_forces_static's fixed scratch buffer. */
+#define LJ_STATIC_MAX_N 32768      /* particles */
+#define LJ_STATIC_MAX_CELLS 32768  /* n_x^3, i.e. n_x <= 32 */
+
+/* Forces without any device allocation.  The paper has no counterpart: this
+ * is lj_forces for callers that cannot call cudaMalloc -- code that runs on
+ * a fixed device-memory budget, inside another runtime's memory pool, or at
+ * points where allocating (and the synchronization it can imply) is not
+ * allowed.  It computes what lj_create + lj_forces(x, f, NULL, NULL) +
+ * lj_destroy compute (same kernels, same precision modes), but needs no
+ * context: the cell arrays and sorted positions live in one fixed buffer of
+ * about 1.8 MB inside liblj.so, which every GPU that loads the library holds
+ * until the process exits.  x (n, 3) double and f (n, 4) float or double are
+ * caller-owned DEVICE arrays; p is validated as by lj_grid.
+ * Limits: p->n <= LJ_STATIC_MAX_N and n_x^3 <= LJ_STATIC_MAX_CELLS; larger
+ * sizes return LJ_EOVERFLOW before any work is queued.
+ * Set-up: the first call on a device (with that device current) looks up
+ * the buffer's device address and keeps it; make that first call before any
+ * stream capture.
+ * All calls share the one buffer, which keeps the previous call's contents
+ * (the kernels clear what must start at zero).  Calls whose work overlaps on
+ * the GPU -- two streams, two host threads -- race on it: serialize them.
+ * Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * and not synchronized; non-finite coordinates are not reported here. */
+int lj_forces_static(const lj_params *p, const double *x, void *f, void *stream);
+
 /* Enable (1) or disable (0) CUDA-event timing of the force kernel on the
  * context's stream; enabling resets the counters. */
 int lj_set_timing(lj_ctx *ctx, int32_t enable);

@@ -72,6 +72,7 @@ _SIGS = {
     "lj_step_host": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "lj_energy": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lj_check": ([_P], ctypes.c_int),
+    "lj_forces_static": ([ctypes.POINTER(lj_params), _P, _P, _P], ctypes.c_int),
     "lj_set_timing": ([_P, ctypes.c_int32], ctypes.c_int),
     "lj_read_timing": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                         ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -240,6 +241,21 @@ def lj_energy(ctx: Context, x, v) -> tuple[float, float, float]:
     _ck(load().lj_energy(ctx.handle, _dev(x, torch.float64, (ctx.n, 3), "x"),
                          _dev(v, torch.float64, (ctx.n, 3), "v"), out), "lj_energy")
     return out[0], out[1], out[2]
+
+
+LJ_STATIC_MAX_N = 32768
+LJ_STATIC_MAX_CELLS = 32768
+
+
+def lj_forces_static(params: lj_params, x, f, stream=None) -> None:
+    """Forces into f with no device allocation (fixed static scratch inside
+    the library; see include/lj.h): for callers that cannot allocate.  n and
+    cells per side are limited (LJ_STATIC_MAX_N, LJ_STATIC_MAX_CELLS)."""
+    import torch
+    n = int(params.n)
+    fdt = torch.float64 if params.precision == LJ_PREC_FP64 else torch.float32
+    _ck(load().lj_forces_static(ctypes.byref(params), _dev(x, torch.float64, (n, 3), "x"),
+                                _dev(f, fdt, (n, 4), "f"), _stream_ptr(stream)), "lj_forces_static")
 
 
 def lj_check(ctx: Context) -> None:
