@@ -283,13 +283,7 @@ def run_gpu(args):
         return 0
 
     peaks = read_peaks()
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "force_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as fh:
-            t = json.load(fh)
-        if t.get("kernel_rev") == FORCE_KERNEL_REV:
-            traffic = t.get("bytes_per_launch")
+    traffic = force_traffic()
 
     line = {
         "metric": METRIC,
@@ -334,9 +328,31 @@ def run_gpu(args):
     return 0
 
 
-# Revision tag of the force kernel the committed ncu traffic figure belongs
-# to; bump when the kernel changes so a stale figure is reported as null.
-FORCE_KERNEL_REV = "v1"
+FORCE_SOURCE = os.path.join(ROOT, "paper_0709_3225_gb300", "csrc", "lj_force_warp.cu")
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_force_warp_traffic_fluid-4m.md")
+
+
+def force_traffic():
+    """DRAM bytes per force launch from the committed ncu summary, or None
+    when the summary is missing or was taken on a different kernel source."""
+    import hashlib
+    try:
+        with open(FORCE_SOURCE, "rb") as fh:
+            sha = hashlib.sha1(fh.read()).hexdigest()
+        fields = {}
+        with open(TRAFFIC_SUMMARY) as fh:
+            for line in fh:
+                if ":" in line and line.strip().startswith(("kernel_source_sha1", "dram_bytes_per_launch")):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+    except OSError:
+        return None
+    if fields.get("kernel_source_sha1") != sha:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def main(argv=None):
