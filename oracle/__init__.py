@@ -84,6 +84,14 @@ def _load():
         lib.or_stiffness.argtypes = [ctypes.c_int64, _D] + [ctypes.c_double] * 4 + \
             [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, _D, _D]
         lib.or_stiffness.restype = None
+        lib.or_pair_deriv.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, _D, _D, _D, _D]
+        lib.or_pair_deriv.restype = None
+        lib.or_forces_vjp.argtypes = [ctypes.c_int64, _D] + [ctypes.c_double] * 4 + \
+            [ctypes.c_int, ctypes.c_int, _D, _D, _D]
+        lib.or_forces_vjp.restype = ctypes.c_int
+        lib.or_vv_adjoint.argtypes = [ctypes.c_int64, _D, _D] + [ctypes.c_double] * 4 + \
+            [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D, _D, _D]
+        lib.or_vv_adjoint.restype = ctypes.c_int
         lib.or_ekin.argtypes = [ctypes.c_int64, _D, ctypes.c_double]
         lib.or_ekin.restype = ctypes.c_double
         lib.or_vv.argtypes = [ctypes.c_int64, _D, _D, _D] + [ctypes.c_double] * 4 + \
@@ -218,6 +226,44 @@ def stiffness(x, L: float, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5
     _load().or_stiffness(n, _dp(x), float(L), float(eps), float(sigma), float(rc), int(mode), ip, m,
                          _dp(K), _dp(S))
     return K, S
+
+
+def pair_deriv(r: float, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5, mode: int = 1):
+    """(F, dF/dr, dF/dsigma, dF/deps) of one pair (rc held fixed)."""
+    out = [ctypes.c_double() for _ in range(4)]
+    _load().or_pair_deriv(float(r), float(eps), float(sigma), float(rc), int(mode), *[ctypes.byref(o) for o in out])
+    return tuple(o.value for o in out)
+
+
+def forces_vjp(x, L: float, g, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5, mode: int = 1,
+               k: int = 1):
+    """Vector-Jacobian product of the cell-list forces with g = dL/dF:
+    returns (dL/dx (n, 3), dL/deps, dL/dsigma)."""
+    x = _pos(x)
+    g = _pos(g)
+    dx = np.empty_like(x)
+    dp = np.zeros(2)
+    r = _load().or_forces_vjp(x.shape[0], _dp(x), float(L), float(eps), float(sigma), float(rc), int(mode),
+                              int(k), _dp(g), _dp(dx), _dp(dp))
+    if r != 0:
+        raise ValueError("box too small for the cell stencil")
+    return dx, float(dp[0]), float(dp[1])
+
+
+def vv_adjoint(x0, v0, L: float, nsteps: int, gx, gv, dt: float = 0.005, eps: float = 1.0,
+               sigma: float = 1.0, rc: float = 2.5, mode: int = 1, k: int = 1, mass: float = 1.0):
+    """Adjoint of nsteps velocity-Verlet steps from (x0, v0): given dL/dx and
+    dL/dv at the end, returns (dL/dx0, dL/dv0, dL/deps, dL/dsigma)."""
+    x0 = _pos(x0)
+    v0 = _pos(v0)
+    ax = np.array(_pos(gx), copy=True)
+    av = np.array(_pos(gv), copy=True)
+    dp = np.zeros(2)
+    r = _load().or_vv_adjoint(x0.shape[0], _dp(x0), _dp(v0), float(L), float(eps), float(sigma), float(rc),
+                              int(mode), int(k), float(dt), float(mass), int(nsteps), _dp(ax), _dp(av), _dp(dp))
+    if r != 0:
+        raise ValueError("box too small for the cell stencil")
+    return ax, av, float(dp[0]), float(dp[1])
 
 
 def ekin(v, mass: float = 1.0) -> float:

@@ -360,6 +360,137 @@ void or_stiffness(int64_t n, const double *x, double L, double eps,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Derivatives for the adjoint (not in the paper: the derivative of Eq.
+ * (n2_force) with the Section 2 pair force, used for force matching).       */
+
+/* Pair force F(r) of or_pair and its derivatives dF/dr, dF/dsigma, dF/deps
+ * (rc fixed).  F_LJ = 24 eps (2 sigma^12 r^-13 - sigma^6 r^-7);
+ * dF_LJ/dr = 24 eps (-26 sigma^12 r^-14 + 7 sigma^6 r^-8);
+ * dF_LJ/dsigma = 24 eps (24 sigma^11 r^-13 - 6 sigma^5 r^-7);
+ * dF/deps = F / eps (computed without dividing).  Mode 2 subtracts the same
+ * expressions at rc (except dF/dr).  Zero for r >= rc. */
+void or_pair_deriv(double r, double eps, double sigma, double rc, int mode,
+                   double *F, double *dFdr, double *dFds, double *dFde)
+{
+    if (!(r < rc)) { *F = *dFdr = *dFds = *dFde = 0.0; return; }
+    double s6 = pow(sigma, 6.0), s12 = s6 * s6;
+    double f1 = 24.0 * (2.0 * s12 * pow(r, -13.0) - s6 * pow(r, -7.0));
+    double d1 = 24.0 * (-26.0 * s12 * pow(r, -14.0) + 7.0 * s6 * pow(r, -8.0));
+    double g1 = 24.0 * (24.0 * s12 / sigma * pow(r, -13.0) - 6.0 * s6 / sigma * pow(r, -7.0));
+    if (mode == 2) {
+        f1 -= 24.0 * (2.0 * s12 * pow(rc, -13.0) - s6 * pow(rc, -7.0));
+        g1 -= 24.0 * (24.0 * s12 / sigma * pow(rc, -13.0) - 6.0 * s6 / sigma * pow(rc, -7.0));
+    }
+    *F = eps * f1;
+    *dFdr = eps * d1;
+    *dFds = eps * g1;
+    *dFde = f1;
+}
+
+/* Vector-Jacobian product of the cell-list forces: with g_i = dL/dF_i,
+ *   dx_i  = sum_j J_ij (g_i - g_j),  J_ij = phi I + (phi'(r)/r) d d^T,
+ *           phi = F(r)/r, d = x_i - x_j (minimum image), r = |d|;
+ *   d_eps = sum_i g_i . dF_i/deps,   d_sigma = sum_i g_i . dF_i/dsigma,
+ * over pairs within rc found through the cell list (as or_forces_cells).
+ * dx is overwritten; dparam[0] = d_eps, dparam[1] = d_sigma.  Returns -1 on
+ * a bad box. */
+int or_forces_vjp(int64_t n, const double *x, double L, double eps, double sigma,
+                  double rc, int mode, int k, const double *g, double *dx,
+                  double *dparam)
+{
+    int nc = or_ncells(L, rc, k);
+    if (nc < 2 * k + 1) return -1;
+    int64_t ncell = (int64_t)nc * nc * nc;
+    int32_t *cell_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *count = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncell);
+    int32_t *start = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncell + 1));
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    or_bin(n, x, L, nc, cell_of, count, start, perm);
+    double de = 0.0, ds = 0.0, rc2 = rc * rc;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : de, ds)
+    for (int64_t i = 0; i < n; i++) {
+        int32_t c = cell_of[i];
+        int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int dz = -k; dz <= k; dz++)
+            for (int dy = -k; dy <= k; dy++)
+                for (int dxc = -k; dxc <= k; dxc++) {
+                    int64_t cn = (cx + dxc + nc) % nc + (int64_t)nc * ((cy + dy + nc) % nc + (int64_t)nc * ((cz + dz + nc) % nc));
+                    for (int32_t s = start[cn]; s < start[cn + 1]; s++) {
+                        int32_t j = perm[s];
+                        if (j == i) continue;
+                        double d[3], dg[3];
+                        for (int q = 0; q < 3; q++) {
+                            d[q] = min_image(x[3 * i + q] - x[3 * (int64_t)j + q], L);
+                            dg[q] = g[3 * i + q] - g[3 * (int64_t)j + q];
+                        }
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (!(r2 < rc2)) continue;
+                        double r = sqrt(r2);
+                        double F, dFdr, dFds, dFde;
+                        or_pair_deriv(r, eps, sigma, rc, mode, &F, &dFdr, &dFds, &dFde);
+                        double phi = F / r;
+                        double dphi_r = (dFdr / r - F / r2) / r;   /* phi'(r) / r */
+                        double ddg = d[0] * dg[0] + d[1] * dg[1] + d[2] * dg[2];
+                        double gid = g[3 * i] * d[0] + g[3 * i + 1] * d[1] + g[3 * i + 2] * d[2];
+                        for (int q = 0; q < 3; q++) acc[q] += phi * dg[q] + dphi_r * ddg * d[q];
+                        de += dFde / r * gid;
+                        ds += dFds / r * gid;
+                    }
+                }
+        for (int q = 0; q < 3; q++) dx[3 * i + q] = acc[q];
+    }
+    dparam[0] = de;
+    dparam[1] = ds;
+    free(cell_of); free(count); free(start); free(perm);
+    return 0;
+}
+
+/* Adjoint of nsteps velocity-Verlet steps (the or_vv scheme) from (x0, v0):
+ * given gx = dL/dx(T), gv = dL/dv(T) at the end, returns dL/dx0, dL/dv0 and
+ * adds dL/d(eps, sigma) to dparam.  The forward states are kept (no
+ * checkpointing).  Per step, backwards (h = dt / 2m):
+ *   lambda_v += (nothing);  lambda_x += h VJP(x_{n+1}, lambda_v)
+ *   lambda_v += dt lambda_x
+ *   lambda_x += h VJP(x_n, lambda_v)
+ * with the parameter parts of both VJPs (times h) added to dparam.  The wrap
+ * of positions has derivative 1.  gx / gv are overwritten with dL/dx0,
+ * dL/dv0.  Returns -1 on a bad box. */
+int or_vv_adjoint(int64_t n, const double *x0, const double *v0, double L,
+                  double eps, double sigma, double rc, int mode, int k, double dt,
+                  double mass, int nsteps, double *gx, double *gv, double *dparam)
+{
+    size_t m = (size_t)(3 * n);
+    double *xs = (double *)malloc(sizeof(double) * m * (size_t)(nsteps + 1));
+    double *v = (double *)malloc(sizeof(double) * (m > 0 ? m : 1));
+    double *f = (double *)malloc(sizeof(double) * (m > 0 ? m : 1));
+    double *tmp = (double *)malloc(sizeof(double) * (m > 0 ? m : 1));
+    double E, W, dp[2];
+    memcpy(xs, x0, sizeof(double) * m);
+    memcpy(v, v0, sizeof(double) * m);
+    if (or_forces_cells(n, xs, L, eps, sigma, rc, mode, k, f, NULL, &E, &W) != 0) return -1;
+    for (int s = 0; s < nsteps; s++) {
+        double *xn1 = xs + m * (size_t)(s + 1);
+        memcpy(xn1, xs + m * (size_t)s, sizeof(double) * m);
+        or_vv(n, xn1, v, f, L, eps, sigma, rc, mode, k, dt, mass, 1, NULL, NULL);
+    }
+    double h = 0.5 * dt / mass;
+    for (int s = nsteps - 1; s >= 0; s--) {
+        or_forces_vjp(n, xs + m * (size_t)(s + 1), L, eps, sigma, rc, mode, k, gv, tmp, dp);
+        for (size_t q = 0; q < m; q++) gx[q] += h * tmp[q];
+        dparam[0] += h * dp[0];
+        dparam[1] += h * dp[1];
+        for (size_t q = 0; q < m; q++) gv[q] += dt * gx[q];
+        or_forces_vjp(n, xs + m * (size_t)s, L, eps, sigma, rc, mode, k, gv, tmp, dp);
+        for (size_t q = 0; q < m; q++) gx[q] += h * tmp[q];
+        dparam[0] += h * dp[0];
+        dparam[1] += h * dp[1];
+    }
+    free(xs); free(v); free(f); free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Observables.                                                              */
 
 /* Kinetic energy (1/2) m sum v^2 in FP64. */
