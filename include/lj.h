@@ -162,6 +162,33 @@ int lj_energy(lj_ctx *ctx, const double *x, const double *v, double *out);
  * kernel since the last check. */
 int lj_check(lj_ctx *ctx);
 
+/* Change eps and sigma of an existing context (rc, the box and the cell grid
+ * stay).  Later launches on the context's stream use the new values.
+ * LJ_EINVAL unless sigma > 0 and eps >= 0, both finite. */
+int lj_set_params(lj_ctx *ctx, double eps, double sigma);
+
+/* Vector-Jacobian product of the forces (the derivative of Eq. n2_force with
+ * the Section 2 pair force, rc held fixed; the paper has no adjoint).  With
+ * g = dL/dF (device (n, 3) double) at positions x (device (n, 3) double):
+ *   dx     += scale * dL/dx,  dL/dx_i = sum_j J_ij (g_i - g_j),
+ *             J = phi I + (phi'(r)/r) d d^T, phi = F(r)/r  (a Hessian-vector
+ *             product of the potential energy; device (n, 3) double);
+ *   dparam += scale * (dL/deps, dL/dsigma)  (device double[2]).
+ * The cell list is piecewise constant in x and contributes nothing.  Pair
+ * arithmetic in the context's precision, parameter sums in FP64.  Allocates
+ * an (n)-element cotangent buffer on first use.  Asynchronous. */
+int lj_forces_vjp(lj_ctx *ctx, const double *x, const double *g, double scale, double *dx, double *dparam);
+
+/* One step of the adjoint of lj_step's velocity Verlet (Section 2), from the
+ * positions before (x_n) and after (x_n1) the step (device (n, 3) double).
+ * With h = dt / 2m, in place on the device (n, 3) adjoints:
+ *   lam_x += h VJP(x_n1, lam_v);  lam_v += dt lam_x;  lam_x += h VJP(x_n, lam_v),
+ * and dparam += the matching parameter parts.  Running it for steps
+ * n = N-1 .. 0 with lam = (dL/dx_N, dL/dv_N) leaves (dL/dx_0, dL/dv_0) in
+ * lam and adds dL/d(eps, sigma) to dparam.  Asynchronous. */
+int lj_vv_adjoint_step(lj_ctx *ctx, const double *x_n, const double *x_n1, double *lam_x, double *lam_v,
+                       double *dparam);
+
 /* Limits of lj_forces_static's fixed scratch buffer. */
 #define LJ_STATIC_MAX_N 32768      /* particles */
 #define LJ_STATIC_MAX_CELLS 32768  /* n_x^3, i.e. n_x <= 32 */

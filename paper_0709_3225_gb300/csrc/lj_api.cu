@@ -94,6 +94,7 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->xs);
     cudaFree(c->vs);
     cudaFree(c->fs);
+    cudaFree(c->g4);
     if (c->host_scalars) cudaFreeHost(c->host_scalars);
     if (c->host_err) cudaFreeHost(c->host_err);
     if (c->ev) {
@@ -253,6 +254,8 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     if (p->precision == LJ_PREC_MIXED) LJ_CREATE_CK(warp_force_configure(c));
     {
         int np = c->force_grid > c->wforce_grid ? c->force_grid : c->wforce_grid;
+        if (np < 32 * c->nsm) np = 32 * c->nsm;   // room for the adjoint kernel's grid
+        c->npartial_cap = np;
         LJ_CREATE_CK(cudaMalloc(&c->partial, 2 * (size_t)np * sizeof(double)));
     }
     int64_t eb = (3 * (int64_t)n1 + kReduceThreads - 1) / kReduceThreads;
@@ -411,6 +414,53 @@ extern "C" int lj_check(lj_ctx *c)
 {
     if (!c) return LJ_EINVAL;
     return sync_and_check(c);
+}
+
+extern "C" int lj_set_params(lj_ctx *c, double eps, double sigma)
+{
+    if (!c || !(sigma > 0.0) || !isfinite(sigma) || !(eps >= 0.0) || !isfinite(eps)) return LJ_EINVAL;
+    c->p.eps = eps;
+    c->p.sigma = sigma;
+    return LJ_OK;
+}
+
+extern "C" int lj_forces_vjp(lj_ctx *c, const double *x, const double *g, double scale, double *dx, double *dparam)
+{
+    if (!c || !isfinite(scale)) return LJ_EINVAL;
+    int r;
+    if ((r = check_dev_ptr(dparam, 8)) != LJ_OK) return r;
+    if (c->p.n == 0) return LJ_OK;
+    if ((r = check_dev_ptr(x, 8)) != LJ_OK) return r;
+    if ((r = check_dev_ptr(g, 8)) != LJ_OK) return r;
+    if ((r = check_dev_ptr(dx, 8)) != LJ_OK) return r;
+    if (!c->g4) LJ_CK(cudaMalloc(&c->g4, (size_t)c->p.n * force_vsize(c)));
+    if ((r = do_bin(c, x, true)) != LJ_OK) return r;
+    LJ_CK(launch_vjp(c, g, scale, dx, dparam));
+    return LJ_OK;
+}
+
+extern "C" int lj_vv_adjoint_step(lj_ctx *c, const double *x_n, const double *x_n1, double *lam_x, double *lam_v,
+                                  double *dparam)
+{
+    if (!c) return LJ_EINVAL;
+    int r;
+    if ((r = check_dev_ptr(dparam, 8)) != LJ_OK) return r;
+    if (c->p.n == 0) return LJ_OK;
+    if ((r = check_dev_ptr(x_n, 8)) != LJ_OK) return r;
+    if ((r = check_dev_ptr(x_n1, 8)) != LJ_OK) return r;
+    if ((r = check_dev_ptr(lam_x, 8)) != LJ_OK) return r;
+    if ((r = check_dev_ptr(lam_v, 8)) != LJ_OK) return r;
+    if (!c->g4) LJ_CK(cudaMalloc(&c->g4, (size_t)c->p.n * force_vsize(c)));
+    const double h = 0.5 * c->p.dt / c->p.mass;
+    // v_{n+1} = v_half + h F(x_{n+1})
+    if ((r = do_bin(c, x_n1, true)) != LJ_OK) return r;
+    LJ_CK(launch_vjp(c, lam_v, h, lam_x, dparam));
+    // x_{n+1} = x_n + dt v_half
+    LJ_CK(launch_axpy(c, lam_v, lam_x, c->p.dt));
+    // v_half = v_n + h F(x_n)
+    if ((r = do_bin(c, x_n, true)) != LJ_OK) return r;
+    LJ_CK(launch_vjp(c, lam_v, h, lam_x, dparam));
+    return LJ_OK;
 }
 
 extern "C" int lj_set_timing(lj_ctx *c, int32_t enable)

@@ -60,6 +60,8 @@ struct lj_ctx {
     // ... and warp-per-cell kernel (lj_force_warp.cu, FP32-mixed)
     int wcap, wforce_smem, wforce_grid;
     int npartial;        // partials written by the last energy launch
+    int npartial_cap;    // capacity of `partial` in (energy, virial) pairs
+    void *g4;            // sorted cotangents for the adjoint (lazily allocated)
     int ekin_grid;
 
     // lazily allocated staging for lj_step_host / lj_energy
@@ -171,4 +173,6 @@ cudaError_t launch_ekin(lj_ctx *c, const double *v);
 cudaError_t launch_counts_from_start(lj_ctx *c, int32_t *count);
 cudaError_t force_configure(lj_ctx *c);
 cudaError_t warp_force_configure(lj_ctx *c);
+cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, double *dparam);
+cudaError_t launch_axpy(lj_ctx *c, double *y, const double *x, double a);
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);

@@ -72,6 +72,9 @@ _SIGS = {
     "lj_step_host": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "lj_energy": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lj_check": ([_P], ctypes.c_int),
+    "lj_set_params": ([_P, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "lj_forces_vjp": ([_P, _P, _P, ctypes.c_double, _P, _P], ctypes.c_int),
+    "lj_vv_adjoint_step": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "lj_forces_static": ([ctypes.POINTER(lj_params), _P, _P, _P], ctypes.c_int),
     "lj_set_timing": ([_P, ctypes.c_int32], ctypes.c_int),
     "lj_read_timing": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
@@ -241,6 +244,31 @@ def lj_energy(ctx: Context, x, v) -> tuple[float, float, float]:
     _ck(load().lj_energy(ctx.handle, _dev(x, torch.float64, (ctx.n, 3), "x"),
                          _dev(v, torch.float64, (ctx.n, 3), "v"), out), "lj_energy")
     return out[0], out[1], out[2]
+
+
+def lj_set_params(ctx: Context, eps: float, sigma: float) -> None:
+    _ck(load().lj_set_params(ctx.handle, float(eps), float(sigma)), "lj_set_params")
+    ctx.params.eps = float(eps)
+    ctx.params.sigma = float(sigma)
+
+
+def lj_forces_vjp(ctx: Context, x, g, scale: float, dx, dparam) -> None:
+    """dx += scale dL/dx and dparam += scale (dL/deps, dL/dsigma) for g = dL/dF."""
+    import torch
+    _ck(load().lj_forces_vjp(ctx.handle, _dev(x, torch.float64, (ctx.n, 3), "x"),
+                             _dev(g, torch.float64, (ctx.n, 3), "g"), float(scale),
+                             _dev(dx, torch.float64, (ctx.n, 3), "dx"),
+                             _dev(dparam, torch.float64, (2,), "dparam")), "lj_forces_vjp")
+
+
+def lj_vv_adjoint_step(ctx: Context, x_n, x_n1, lam_x, lam_v, dparam) -> None:
+    """One velocity-Verlet adjoint step (see include/lj.h), in place."""
+    import torch
+    _ck(load().lj_vv_adjoint_step(ctx.handle, _dev(x_n, torch.float64, (ctx.n, 3), "x_n"),
+                                  _dev(x_n1, torch.float64, (ctx.n, 3), "x_n1"),
+                                  _dev(lam_x, torch.float64, (ctx.n, 3), "lam_x"),
+                                  _dev(lam_v, torch.float64, (ctx.n, 3), "lam_v"),
+                                  _dev(dparam, torch.float64, (2,), "dparam")), "lj_vv_adjoint_step")
 
 
 LJ_STATIC_MAX_N = 32768

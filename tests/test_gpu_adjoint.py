@@ -1,0 +1,187 @@
+"""GPU adjoint parity: the force VJP (Hessian-vector product and parameter
+gradients) and the checkpointed velocity-Verlet adjoint against the FP64
+oracle's independent implementations and against finite differences.
+
+Force-matching workload (N = 32,000, 4*20^3 FCC at rho 0.8442, T = 1.0):
+the perfect lattice has zero force for every (eps, sigma), so the starting
+configuration is the lattice jittered by +-0.1 sigma.  Targets come from the
+oracle at (eps, sigma) = (1, 1); parameters start at (0.9, 1.05).
+loss = (1/N) sum_i |F_i(theta) - F_i^t|^2 + (1/N) sum_i |x_i(50) - x_i^t(50)|^2
+(minimum image), 50 steps, checkpoints every 10, force-shifted potential
+(continuous force, so the trajectory is differentiable)."""
+import numpy as np
+import pytest
+
+from paper_0709_3225_gb300 import inputs
+
+from gpu_util import min_image, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+
+def _vjp_gpu(x, L, g, precision, mode, eps, sigma, scale=1.0, calls=1):
+    import torch
+    from paper_0709_3225_gb300 import lj
+    s = lj.System(x, None, L, precision=precision, shift_mode=mode, eps=eps, sigma=sigma)
+    gt = torch.as_tensor(g, device="cuda")
+    dx = torch.zeros_like(s.x)
+    dp = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for _ in range(calls):
+        lj.lj_forces_vjp(s.ctx, s.x, gt, scale, dx, dp)
+    s.check()
+    out = dx.cpu().numpy(), dp.cpu().numpy()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_vjp_matches_oracle(oracle_mod, precision, mode):
+    x, L = inputs.jittered_fcc(8, 0.8442, 0.1, 41)
+    g = np.random.default_rng(3).standard_normal(x.shape)
+    eps, sigma = 0.9, 1.05
+    dx, dp = _vjp_gpu(x, L, g, precision, mode, eps, sigma)
+    odx, ode, ods = oracle_mod.forces_vjp(x, L, g, eps=eps, sigma=sigma, mode=mode)
+    near = oracle_mod.near_cutoff(x, L, band=1e-5 if precision == "mixed" else 1e-12)
+    err_dx = rel_rms(dx, odx)
+    err_e = abs(dp[0] - ode) / abs(ode)
+    err_s = abs(dp[1] - ods) / abs(ods)
+    print(f"{precision} mode {mode}: dx rel RMS {err_dx:.2e}, d_eps rel {err_e:.2e}, d_sigma rel {err_s:.2e}")
+    if precision == "fp64":
+        assert err_dx <= 1e-11
+        scale = np.abs(odx).max(axis=1) + np.sqrt((odx ** 2).sum(axis=1).mean())
+        assert np.all(np.abs(dx - odx).max(axis=1)[~near] <= 1e-10 * scale[~near])
+        assert err_e <= 1e-11 and err_s <= 1e-11
+    else:
+        # target for the FP32 adjoint: parameter gradients within 1e-6 of FP64
+        assert err_dx <= 1e-5
+        assert err_e <= 1e-6 and err_s <= 1e-6
+
+
+def test_vjp_accumulates_with_scale(oracle_mod):
+    x, L = inputs.jittered_fcc(6, 0.8442, 0.1, 43)
+    g = np.random.default_rng(4).standard_normal(x.shape)
+    dx1, dp1 = _vjp_gpu(x, L, g, "fp64", 2, 1.0, 1.0, scale=1.0, calls=1)
+    dx2, dp2 = _vjp_gpu(x, L, g, "fp64", 2, 1.0, 1.0, scale=0.25, calls=4)
+    np.testing.assert_allclose(dx2, dx1, rtol=1e-12, atol=1e-12 * np.abs(dx1).max())
+    np.testing.assert_allclose(dp2, dp1, rtol=1e-12)
+
+
+def test_autograd_forces_against_finite_differences():
+    import torch
+    from paper_0709_3225_gb300 import autograd, lj
+    x, L = inputs.jittered_fcc(6, 0.8442, 0.1, 45)
+    w = torch.as_tensor(np.random.default_rng(5).standard_normal(x.shape), device="cuda")
+    s = lj.System(x, None, L, precision="fp64", shift_mode=2)
+    xt = s.x.clone().requires_grad_(True)
+    theta = torch.tensor([0.95, 1.03], dtype=torch.float64, device="cuda", requires_grad=True)
+    (w * autograd.forces(xt, theta, s.ctx)).sum().backward()
+
+    def loss(xx, th):
+        with torch.no_grad():
+            return float((w * autograd.forces(xx, th, s.ctx)).sum())
+
+    h = 1e-6
+    for k in range(2):
+        e = torch.zeros(2, dtype=torch.float64, device="cuda")
+        e[k] = h
+        fd = (loss(s.x, theta.detach() + e) - loss(s.x, theta.detach() - e)) / (2 * h)
+        assert float(theta.grad[k]) == pytest.approx(fd, rel=1e-6)
+    for i, q in ((3, 0), (100, 2), (700, 1)):
+        xp = s.x.clone(); xp[i, q] += h
+        xm = s.x.clone(); xm[i, q] -= h
+        fd = (loss(xp, theta.detach()) - loss(xm, theta.detach())) / (2 * h)
+        assert float(xt.grad[i, q]) == pytest.approx(fd, rel=1e-5, abs=1e-6)
+    s.close()
+
+
+def _force_matching_setup(oracle_mod):
+    w = inputs.WORKLOADS["fm-32k"]
+    x0, L = inputs.jittered_fcc(w.n_fcc, w.rho, 0.1, w.seed)
+    v0 = inputs.velocities(w.n, w.temperature, w.seed)
+    f_t = oracle_mod.forces_cells(x0, L, 1.0, 1.0, mode=2)[0]
+    xt, vt, ft = x0.copy(), v0.copy(), f_t.copy()
+    oracle_mod.vv(xt, vt, ft, L, 50, eps=1.0, sigma=1.0, mode=2)
+    return x0, v0, L, f_t, xt
+
+
+def _oracle_gradient(oracle_mod, x0, v0, L, f_t, xt, eps, sigma, nsteps=50):
+    n = x0.shape[0]
+    F = oracle_mod.forces_cells(x0, L, eps, sigma, mode=2)[0]
+    dxF, deF, dsF = oracle_mod.forces_vjp(x0, L, 2.0 / n * (F - f_t), eps=eps, sigma=sigma, mode=2)
+    xo, vo, fo = x0.copy(), v0.copy(), F.copy()
+    oracle_mod.vv(xo, vo, fo, L, nsteps, eps=eps, sigma=sigma, mode=2)
+    gx = 2.0 / n * min_image(xo - xt, L)
+    gx0, gv0, deT, dsT = oracle_mod.vv_adjoint(x0, v0, L, nsteps, gx, np.zeros_like(gx), eps=eps,
+                                               sigma=sigma, mode=2)
+    loss = ((F - f_t) ** 2).sum() / n + (min_image(xo - xt, L) ** 2).sum() / n
+    return loss, np.array([deF + deT, dsF + dsT]), dxF + gx0
+
+
+def _gpu_gradient(x0, v0, L, f_t, xt, theta0, precision, nsteps=50, every=10):
+    import torch
+    from paper_0709_3225_gb300 import autograd, lj
+    n = x0.shape[0]
+    s = lj.System(x0, v0, L, precision=precision, shift_mode=2)
+    x = s.x.clone().requires_grad_(True)
+    theta = torch.tensor(theta0, dtype=torch.float64, device="cuda", requires_grad=True)
+    ft = torch.as_tensor(f_t, device="cuda")
+    xtt = torch.as_tensor(xt, device="cuda")
+    F = autograd.forces(x, theta, s.ctx)
+    xT, vT = autograd.trajectory(x, s.v, theta, s.ctx, nsteps, every)
+    d = xT - xtt
+    d = d - L * torch.round(d / L)
+    loss = ((F - ft) ** 2).sum() / n + (d ** 2).sum() / n
+    loss.backward()
+    s.check()
+    out = float(loss.detach()), theta.grad.cpu().numpy(), x.grad.cpu().numpy(), s
+    return out
+
+
+@pytest.mark.slow
+def test_force_matching_gradient_fp64_vs_oracle_and_fd(oracle_mod):
+    import torch
+    from paper_0709_3225_gb300 import autograd
+    x0, v0, L, f_t, xt = _force_matching_setup(oracle_mod)
+    theta0 = (0.9, 1.05)
+    lo, go, gxo = _oracle_gradient(oracle_mod, x0, v0, L, f_t, xt, *theta0)
+    lg, gg, gxg, s = _gpu_gradient(x0, v0, L, f_t, xt, theta0, "fp64")
+    print("oracle dL/dtheta", go, "gpu fp64", gg)
+    assert lg == pytest.approx(lo, rel=1e-9)
+    np.testing.assert_allclose(gg, go, rtol=1e-7)
+    assert rel_rms(gxg, gxo) <= 1e-7
+    # finite differences of the GPU FP64 loss in eps and sigma
+    n = x0.shape[0]
+    ft = torch.as_tensor(f_t, device="cuda")
+    xtt = torch.as_tensor(xt, device="cuda")
+
+    def loss(th):
+        with torch.no_grad():
+            t = torch.tensor(th, dtype=torch.float64, device="cuda")
+            F = autograd.forces(s.x, t, s.ctx)
+            xT, _ = autograd.trajectory(s.x, s.v, t, s.ctx, 50, 10)
+            d = xT - xtt
+            d = d - L * torch.round(d / L)
+            return float(((F - ft) ** 2).sum() / n + (d ** 2).sum() / n)
+
+    h = 1e-6
+    fd = [(loss((theta0[0] + h, theta0[1])) - loss((theta0[0] - h, theta0[1]))) / (2 * h),
+          (loss((theta0[0], theta0[1] + h)) - loss((theta0[0], theta0[1] - h))) / (2 * h)]
+    print("finite differences", fd)
+    np.testing.assert_allclose(gg, fd, rtol=1e-6)
+    s.close()
+
+
+@pytest.mark.slow
+def test_force_matching_gradient_mixed_vs_fp64(oracle_mod):
+    x0, v0, L, f_t, xt = _force_matching_setup(oracle_mod)
+    theta0 = (0.9, 1.05)
+    _, g64, gx64, s64 = _gpu_gradient(x0, v0, L, f_t, xt, theta0, "fp64")
+    _, g32, gx32, s32 = _gpu_gradient(x0, v0, L, f_t, xt, theta0, "mixed")
+    rel = np.abs(g32 - g64) / np.abs(g64)
+    print(f"mixed vs fp64: dL/deps rel {rel[0]:.2e}, dL/dsigma rel {rel[1]:.2e}, "
+          f"dL/dx rel RMS {rel_rms(gx32, gx64):.2e}")
+    assert np.all(rel <= 1e-6)              # the FP32 adjoint's target
+    assert rel_rms(gx32, gx64) <= 1e-5      # reported; per-particle FP32 sums
+    s64.close()
+    s32.close()
