@@ -189,6 +189,67 @@ int lj_forces_vjp(lj_ctx *ctx, const double *x, const double *g, double scale, d
 int lj_vv_adjoint_step(lj_ctx *ctx, const double *x_n, const double *x_n1, double *lam_x, double *lam_v,
                        double *dparam);
 
+/* Choose the force kernel of a context (same results; for autotuning):
+ * kernel 0 = warp-per-cell kernel (FP32-mixed only), 1 = run kernel with
+ * bulk-copy staging, 2 = run kernel reading global memory.  gmin is the
+ * smallest lane-group width of the warp kernel (0 = smallest that holds a
+ * cell, or 8, 16, 32).  LJ_EINVAL for other values. */
+int lj_set_tuning(lj_ctx *ctx, int32_t kernel, int32_t gmin);
+
+/* ---------------------------------------------------------------------- */
+/* Batched ensembles.  nrep independent periodic systems ("replicas") of
+ * possibly different N and box, each the method above (Sections 2 and 3),
+ * stored back to back: replica r owns particles [o_r, o_r + n[r]) of the
+ * concatenated (sum n, 3) / (sum n, 4) arrays, o_r = n[0] + ... + n[r-1].
+ * One velocity-Verlet step of every replica is ONE cooperative persistent
+ * kernel launch (binning, scan, scatter and forces separated by bounded grid
+ * barriers), captured once in a CUDA graph and replayed.  FP32-mixed only.
+ * Batching is not in the paper; it serves many small systems at once.    */
+
+typedef struct lj_batch lj_batch;
+
+/* Create a batch: n[r] particles in a cubic box of side box[r] for
+ * r < nrep; common supplies eps, sigma, rc, dt, mass, shift_mode, flags and
+ * precision (must be LJ_PREC_MIXED); common->n and common->box are ignored.
+ * Each replica is validated as by lj_grid.  stream: cudaStream_t (NULL =
+ * legacy default stream; graph capture then uses a private stream). */
+int lj_batch_create(lj_batch **out, int32_t nrep, const int64_t *n, const double *box, const lj_params *common,
+                    void *stream);
+void lj_batch_destroy(lj_batch *b);
+
+/* Totals and launch geometry: particles, cells, cooperative grid size and
+ * staging capacity per warp.  Host only. */
+int lj_batch_info(const lj_batch *b, int64_t *ntot, int64_t *ncell, int32_t *grid, int32_t *cap);
+
+/* Tuning: cells a warp takes per pull from the work counter (1..1024),
+ * whether steps are graph-replayed (1) or launched directly (0), and the
+ * smallest lane-group width (0, 8, 16, 32). */
+int lj_batch_set_tuning(lj_batch *b, int32_t cells_per_grab, int32_t use_graph, int32_t gmin);
+
+/* Forces of every replica at x into f (device arrays as above); with
+ * energy != 0, f[:, 3] holds per-particle energies.  Asynchronous. */
+int lj_batch_forces(lj_batch *b, const double *x, void *f, int32_t energy);
+
+/* nsteps velocity-Verlet steps of every replica (as lj_step: f must hold
+ * F(x) on entry and holds F at the final positions on return). */
+int lj_batch_step(lj_batch *b, double *x, double *v, void *f, int32_t nsteps);
+
+/* Per-replica energies into the HOST array out[3 * nrep]: (kinetic,
+ * potential, total) of replica r at out[3r .. 3r+2]; f is overwritten with
+ * forces and per-particle energies.  Synchronizes. */
+int lj_batch_energy(lj_batch *b, const double *x, const double *v, void *f, double *out);
+
+/* nsteps capped steepest-descent moves x += alpha F (the move of a particle
+ * scaled down to length max_disp when longer), then wrapped; f holds F at
+ * the final positions.  For relaxing random starting configurations. */
+int lj_batch_relax(lj_batch *b, double *x, void *f, int32_t nsteps, double alpha, double max_disp);
+
+/* Synchronize and return latched kernel errors (as lj_check). */
+int lj_batch_check(lj_batch *b);
+
+/* Kernel launches issued so far and whether steps are graph-replayed. */
+int lj_batch_launches(const lj_batch *b, int64_t *launches, int32_t *graph);
+
 /* Limits of lj_forces_static's fixed scratch buffer. */
 #define LJ_STATIC_MAX_N 32768      /* particles */
 #define LJ_STATIC_MAX_CELLS 32768  /* n_x^3, i.e. n_x <= 32 */

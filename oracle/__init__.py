@@ -92,6 +92,9 @@ def _load():
         lib.or_vv_adjoint.argtypes = [ctypes.c_int64, _D, _D] + [ctypes.c_double] * 4 + \
             [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D, _D, _D]
         lib.or_vv_adjoint.restype = ctypes.c_int
+        lib.or_relax.argtypes = [ctypes.c_int64, _D, _D] + [ctypes.c_double] * 4 + \
+            [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        lib.or_relax.restype = ctypes.c_int
         lib.or_ekin.argtypes = [ctypes.c_int64, _D, ctypes.c_double]
         lib.or_ekin.restype = ctypes.c_double
         lib.or_vv.argtypes = [ctypes.c_int64, _D, _D, _D] + [ctypes.c_double] * 4 + \
@@ -264,6 +267,19 @@ def vv_adjoint(x0, v0, L: float, nsteps: int, gx, gv, dt: float = 0.005, eps: fl
     if r != 0:
         raise ValueError("box too small for the cell stencil")
     return ax, av, float(dp[0]), float(dp[1])
+
+
+def relax(x, L: float, nsteps: int, alpha: float = 1e-3, dmax: float = 0.05, eps: float = 1.0,
+          sigma: float = 1.0, rc: float = 2.5, mode: int = 1, k: int = 1):
+    """Capped steepest descent (x += alpha F per particle, move length capped
+    at dmax, wrapped).  Returns (relaxed x, forces there)."""
+    x = np.array(_pos(x), copy=True)
+    f = np.empty_like(x)
+    r = _load().or_relax(x.shape[0], _dp(x), _dp(f), float(L), float(eps), float(sigma), float(rc), int(mode),
+                         int(k), int(nsteps), float(alpha), float(dmax))
+    if r != 0:
+        raise ValueError("box too small for the cell stencil")
+    return x, f
 
 
 def ekin(v, mass: float = 1.0) -> float:

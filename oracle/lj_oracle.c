@@ -529,6 +529,31 @@ int or_vv(int64_t n, double *x, double *v, double *f, double L, double eps,
     return 0;
 }
 
+/* Capped steepest descent for relaxing random starting configurations:
+ * nsteps times, forces F at x, each particle moved by d = alpha F_i, scaled
+ * down to length dmax when longer, then wrapped (the initial relaxation of
+ * the batched-ensemble workload; not in the paper).  x updated in place;
+ * f receives the forces at the final positions.  Returns -1 on a bad box. */
+int or_relax(int64_t n, double *x, double *f, double L, double eps, double sigma,
+             double rc, int mode, int k, int nsteps, double alpha, double dmax)
+{
+    double E, W;
+    for (int s = 0; s < nsteps; s++) {
+        if (or_forces_cells(n, x, L, eps, sigma, rc, mode, k, f, NULL, &E, &W) != 0) return -1;
+        for (int64_t i = 0; i < n; i++) {
+            double d[3], len = 0.0;
+            for (int q = 0; q < 3; q++) {
+                d[q] = alpha * f[3 * i + q];
+                len += d[q] * d[q];
+            }
+            len = sqrt(len);
+            double sc = len > dmax ? dmax / len : 1.0;
+            for (int q = 0; q < 3; q++) x[3 * i + q] = wrap1(x[3 * i + q] + sc * d[q], L);
+        }
+    }
+    return or_forces_cells(n, x, L, eps, sigma, rc, mode, k, f, NULL, &E, &W);
+}
+
 /* Threads the OpenMP loops may use (no-op without OpenMP); returns the
  * number in effect. */
 int or_set_threads(int nthreads)

@@ -463,6 +463,18 @@ extern "C" int lj_vv_adjoint_step(lj_ctx *c, const double *x_n, const double *x_
     return LJ_OK;
 }
 
+extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t gmin)
+{
+    if (!c || kernel < 0 || kernel > 2) return LJ_EINVAL;
+    if (gmin != 0 && gmin != 8 && gmin != 16 && gmin != 32) return LJ_EINVAL;
+    if (kernel == 0 && c->p.precision == LJ_PREC_FP64) return LJ_EINVAL;   // warp kernel is FP32-mixed
+    if (kernel == 0 && c->wforce_grid == 0) LJ_CK(warp_force_configure(c));
+    c->use_run_kernel = kernel != 0;
+    c->use_tma = kernel == 2 ? 0 : 1;
+    c->gmin = gmin;
+    return LJ_OK;
+}
+
 extern "C" int lj_set_timing(lj_ctx *c, int32_t enable)
 {
     if (!c) return LJ_EINVAL;

@@ -59,6 +59,7 @@ struct lj_ctx {
     int run_len, runs, nitems, cap, force_grid, force_smem, use_tma, use_run_kernel;
     // ... and warp-per-cell kernel (lj_force_warp.cu, FP32-mixed)
     int wcap, wforce_smem, wforce_grid;
+    int gmin;            // tuning: smallest lane-group width in the warp kernel
     int npartial;        // partials written by the last energy launch
     int npartial_cap;    // capacity of `partial` in (energy, virial) pairs
     void *g4;            // sorted cotangents for the adjoint (lazily allocated)

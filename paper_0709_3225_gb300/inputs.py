@@ -95,6 +95,54 @@ def jittered_fcc(n_fcc: int, rho: float, amplitude: float, seed: int) -> tuple[n
     return np.ascontiguousarray(x), L
 
 
+def lattice_gas(n: int, rho: float, seed: int, jitter: float = 0.1) -> tuple[np.ndarray, float]:
+    """n random positions without overlaps at density rho: the smallest FCC
+    lattice of 4 m^3 >= n sites in the box L = (n/rho)^(1/3), with n sites
+    kept at random (random vacancies), each coordinate displaced uniformly
+    by +-jitter lattice constants."""
+    L = box_side(n, rho)
+    m = 1
+    while 4 * m ** 3 < n:
+        m += 1
+    a = L / m
+    sites, _ = fcc(m, 4 * m ** 3 / L ** 3)
+    rng = np.random.default_rng(seed)
+    keep = np.sort(rng.choice(sites.shape[0], n, replace=False))
+    x = sites[keep] + (rng.random((n, 3)) * 2.0 - 1.0) * jitter * a
+    return np.ascontiguousarray(x), L
+
+
+@dataclass(frozen=True)
+class Ensemble:
+    """Independent replicas: N_r uniform in [n_lo, n_hi], rho_r uniform in
+    [rho_lo, rho_hi], T_r uniform in [t_lo, t_hi], all drawn from one seed."""
+    n: np.ndarray
+    rho: np.ndarray
+    temperature: np.ndarray
+    box: np.ndarray
+    seed: int
+
+
+def ensemble(nrep: int = 256, seed: int = 2024, n_lo: int = 500, n_hi: int = 50000, rho_lo: float = 0.7,
+             rho_hi: float = 0.9, t_lo: float = 0.7, t_hi: float = 1.5) -> Ensemble:
+    rng = np.random.default_rng(seed)
+    n = rng.integers(n_lo, n_hi + 1, nrep)
+    rho = rng.uniform(rho_lo, rho_hi, nrep)
+    temp = rng.uniform(t_lo, t_hi, nrep)
+    box = np.array([box_side(int(a), float(b)) for a, b in zip(n, rho)])
+    return Ensemble(n, rho, temp, box, seed)
+
+
+def ensemble_state(ens: Ensemble):
+    """Per-replica starting positions (lattice_gas) and velocities."""
+    xs, vs = [], []
+    for r in range(len(ens.n)):
+        x, _ = lattice_gas(int(ens.n[r]), float(ens.rho[r]), ens.seed + 7919 * r)
+        xs.append(x)
+        vs.append(velocities(int(ens.n[r]), float(ens.temperature[r]), ens.seed + 104729 * r))
+    return xs, vs
+
+
 def workload_state(name: str) -> tuple[np.ndarray, np.ndarray, float, Workload]:
     """(x, v, L, workload) of a named workload's starting state."""
     w = WORKLOADS[name]

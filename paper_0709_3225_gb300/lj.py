@@ -73,6 +73,19 @@ _SIGS = {
     "lj_energy": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lj_check": ([_P], ctypes.c_int),
     "lj_set_params": ([_P, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "lj_set_tuning": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "lj_batch_create": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(lj_params), _P], ctypes.c_int),
+    "lj_batch_destroy": ([_P], None),
+    "lj_batch_info": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "lj_batch_set_tuning": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "lj_batch_forces": ([_P, _P, _P, ctypes.c_int32], ctypes.c_int),
+    "lj_batch_step": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
+    "lj_batch_energy": ([_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "lj_batch_relax": ([_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "lj_batch_check": ([_P], ctypes.c_int),
+    "lj_batch_launches": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "lj_forces_vjp": ([_P, _P, _P, ctypes.c_double, _P, _P], ctypes.c_int),
     "lj_vv_adjoint_step": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "lj_forces_static": ([ctypes.POINTER(lj_params), _P, _P, _P], ctypes.c_int),
@@ -269,6 +282,104 @@ def lj_vv_adjoint_step(ctx: Context, x_n, x_n1, lam_x, lam_v, dparam) -> None:
                                   _dev(lam_x, torch.float64, (ctx.n, 3), "lam_x"),
                                   _dev(lam_v, torch.float64, (ctx.n, 3), "lam_v"),
                                   _dev(dparam, torch.float64, (2,), "dparam")), "lj_vv_adjoint_step")
+
+
+def lj_set_tuning(ctx: Context, kernel: int, gmin: int = 0) -> None:
+    """Force kernel of a context: 0 warp-per-cell (mixed), 1 run-staged, 2 run-direct."""
+    _ck(load().lj_set_tuning(ctx.handle, int(kernel), int(gmin)), "lj_set_tuning")
+
+
+class Batch:
+    """Owns an lj_batch* (see include/lj.h) and its device state.
+
+    ``xs``, ``vs``: lists of per-replica (n_r, 3) arrays; ``boxes``: per-replica
+    box sides.  State is concatenated: x, v (sum n, 3) float64, f (sum n, 4)
+    float32 CUDA tensors; ``offsets[r]:offsets[r+1]`` is replica r."""
+
+    def __init__(self, xs, vs, boxes, *, eps=1.0, sigma=1.0, rc=2.5, dt=0.005, mass=1.0,
+                 shift_mode=LJ_SHIFT_ENERGY, stream=None):
+        import torch
+        ns = [int(np.asarray(a).shape[0]) for a in xs]
+        self.nrep = len(ns)
+        self.offsets = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        self.boxes = [float(b) for b in boxes]
+        self.x = torch.as_tensor(np.concatenate([np.asarray(a, np.float64) for a in xs])).cuda().contiguous()
+        if vs is None:
+            self.v = torch.zeros_like(self.x)
+        else:
+            self.v = torch.as_tensor(np.concatenate([np.asarray(a, np.float64) for a in vs])).cuda().contiguous()
+        self.f = torch.zeros((self.x.shape[0], 4), dtype=torch.float32, device="cuda")
+        self.params = make_params(0, 1.0, eps, sigma, rc, dt, mass, shift_mode, "mixed")
+        n_arr = (ctypes.c_int64 * self.nrep)(*ns)
+        b_arr = (ctypes.c_double * self.nrep)(*self.boxes)
+        h = ctypes.c_void_p()
+        _ck(load().lj_batch_create(ctypes.byref(h), self.nrep, n_arr, b_arr, ctypes.byref(self.params),
+                                   _stream_ptr(stream)), "lj_batch_create")
+        self.handle = h
+        self._forces_valid = False
+
+    @property
+    def ntot(self) -> int:
+        return int(self.offsets[-1])
+
+    def info(self):
+        nt, nc = ctypes.c_int64(), ctypes.c_int64()
+        g, cap = ctypes.c_int32(), ctypes.c_int32()
+        _ck(load().lj_batch_info(self.handle, ctypes.byref(nt), ctypes.byref(nc), ctypes.byref(g),
+                                 ctypes.byref(cap)), "lj_batch_info")
+        return {"ntot": nt.value, "ncell": nc.value, "grid": g.value, "cap": cap.value}
+
+    def set_tuning(self, cells_per_grab: int = 4, use_graph: bool = True, gmin: int = 0) -> None:
+        _ck(load().lj_batch_set_tuning(self.handle, int(cells_per_grab), 1 if use_graph else 0, int(gmin)),
+            "lj_batch_set_tuning")
+
+    def forces(self, energy: bool = False) -> None:
+        _ck(load().lj_batch_forces(self.handle, ctypes.c_void_p(self.x.data_ptr()),
+                                   ctypes.c_void_p(self.f.data_ptr()), 1 if energy else 0), "lj_batch_forces")
+        self._forces_valid = True
+
+    def step(self, nsteps: int) -> None:
+        if not self._forces_valid:
+            self.forces()
+        _ck(load().lj_batch_step(self.handle, ctypes.c_void_p(self.x.data_ptr()),
+                                 ctypes.c_void_p(self.v.data_ptr()), ctypes.c_void_p(self.f.data_ptr()),
+                                 int(nsteps)), "lj_batch_step")
+
+    def energy(self) -> np.ndarray:
+        out = (ctypes.c_double * (3 * self.nrep))()
+        _ck(load().lj_batch_energy(self.handle, ctypes.c_void_p(self.x.data_ptr()),
+                                   ctypes.c_void_p(self.v.data_ptr()), ctypes.c_void_p(self.f.data_ptr()), out),
+            "lj_batch_energy")
+        self._forces_valid = True
+        return np.array(out).reshape(self.nrep, 3)
+
+    def relax(self, nsteps: int, alpha: float, max_disp: float) -> None:
+        _ck(load().lj_batch_relax(self.handle, ctypes.c_void_p(self.x.data_ptr()),
+                                  ctypes.c_void_p(self.f.data_ptr()), int(nsteps), float(alpha),
+                                  float(max_disp)), "lj_batch_relax")
+        self._forces_valid = True
+
+    def check(self) -> None:
+        _ck(load().lj_batch_check(self.handle), "lj_batch_check")
+
+    def launches(self):
+        n, g = ctypes.c_int64(), ctypes.c_int32()
+        _ck(load().lj_batch_launches(self.handle, ctypes.byref(n), ctypes.byref(g)), "lj_batch_launches")
+        return n.value, bool(g.value)
+
+    def replica(self, t, r: int):
+        return t[int(self.offsets[r]):int(self.offsets[r + 1])]
+
+    def close(self) -> None:
+        if self.handle:
+            load().lj_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 LJ_STATIC_MAX_N = 32768

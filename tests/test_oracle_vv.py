@@ -82,3 +82,32 @@ def test_input_state_pins():
     v = inputs.velocities(256, 0.728, 1)
     assert np.abs(v.sum(axis=0)).max() < 1e-12
     assert (v ** 2).sum() / (3 * 256 - 3) == pytest.approx(0.728, rel=1e-12)
+
+
+def test_relaxation_pins(oracle_mod):
+    """Capped steepest descent: every move is at most dmax, the energy does
+    not increase for a small step, and a force-free lattice stays put."""
+    x0, L = inputs.lattice_gas(864, 0.85, 3, jitter=0.2)
+    E0 = oracle_mod.forces_cells(x0, L, mode=1)[2]
+    x1, _ = oracle_mod.relax(x0, L, 1, alpha=1e-3, dmax=0.05)
+    d = x1 - x0
+    d -= L * np.round(d / L)
+    assert np.sqrt((d ** 2).sum(axis=1)).max() <= 0.05 + 1e-12
+    energies = [E0]
+    x = x0
+    for _ in range(10):
+        x, _ = oracle_mod.relax(x, L, 1, alpha=1e-3, dmax=0.05)
+        energies.append(oracle_mod.forces_cells(x, L, mode=1)[2])
+    assert np.all(np.diff(energies) <= 1e-9 * abs(E0))
+    xl, Ll = inputs.fcc(5, 0.8442)
+    xr, _ = oracle_mod.relax(xl, Ll, 5)
+    np.testing.assert_allclose(xr, xl, rtol=0, atol=1e-11)
+
+
+def test_lattice_gas_inputs():
+    x, L = inputs.lattice_gas(5071, 0.726, 9)
+    assert x.shape == (5071, 3)
+    assert L == pytest.approx((5071 / 0.726) ** (1 / 3))
+    e = inputs.ensemble(8, seed=1)
+    assert len(e.n) == 8 and np.all((e.n >= 500) & (e.n <= 50000))
+    assert np.all((e.rho >= 0.7) & (e.rho <= 0.9)) and np.all((e.temperature >= 0.7) & (e.temperature <= 1.5))
