@@ -132,6 +132,45 @@ def max_over_ranks(world, value: float) -> float:
     return float(t.item())
 
 
+def run_ensemble(args, stream, world):
+    """The batched workload: 256 replicas, N_r uniform in [500, 50000], rho_r
+    in [0.7, 0.9], T_r in [0.7, 1.5]; 50 capped steepest-descent steps and
+    autotuning (untimed), then steps timed with CUDA events, one cooperative
+    launch per step (graph-replayed)."""
+    import torch
+    from paper_0709_3225_gb300 import autotune, inputs, lj
+    e = inputs.ensemble()
+    xs, vs = inputs.ensemble_state(e)
+    b = lj.Batch(xs, vs, e.box)
+    b.relax(50, 1e-3, 0.05)
+    b.forces()
+    tuning = autotune.tune_batch(b, float(np.mean(e.rho)))
+    tuning.pop("trials", None)
+    b.step(args.warmup)
+    b.check()
+    k = max(10, min(args.steps, 200))
+    n0, _ = b.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    b.step(k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    b.check()
+    n1, graph = b.launches()
+    ms = max_over_ranks(world, ev0.elapsed_time(ev1)) / k
+    pairs = float(sum(unique_pairs(int(n), float(r), 2.5) for n, r in zip(e.n, e.rho)))
+    info = b.info()
+    b.close()
+    return {"workload": "ensemble-256", "replicas": int(b.nrep), "n_total": int(info["ntot"]),
+            "cells_total": int(info["ncell"]), "steps": k, "ms_per_step": ms,
+            "value": world * 1e3 / ms, "unit": "ensemble steps/s",
+            "replica_steps_per_s": world * b.nrep * 1e3 / ms,
+            "pair_interactions_per_s": world * pairs * 1e3 / ms,
+            "launches_per_step": (n1 - n0 - 1) / k, "graph": graph, "tuning": tuning}
+
+
 def cpu_baseline(x, v, L, w, max_seconds: float = 20.0, max_steps: int = 3):
     """The FP64 oracle as it stands, on this host's cores: full velocity-Verlet
     steps of the same workload until ~max_seconds of work, scaled to steps/s."""
@@ -210,8 +249,11 @@ def run_gpu(args):
     pairs = unique_pairs(n, w.rho, w.rc)
 
     # ---- FP32-mixed, device-resident (the headline `value`) --------------
+    from paper_0709_3225_gb300 import autotune
     s = lj.System(x, v, L, precision="mixed", dt=w.dt, rc=w.rc)
     s.forces()
+    tuning = autotune.tune_system(s, w.rho)
+    tuning.pop("trials", None)
     s.step(args.warmup)
     s.check()
     lj.lj_set_timing(s.ctx, True)
@@ -276,6 +318,8 @@ def run_gpu(args):
     s64.close()
     del s64
 
+    ensemble = None if args.no_ensemble else run_ensemble(args, stream, world)
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -310,6 +354,8 @@ def run_gpu(args):
                      "flops_per_launch": FLOPS_PER_PAIR * pairs,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
         "other_kernels_ms_per_step": other_ms,
+        "tuning": tuning,
+        "ensemble": ensemble,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64},
@@ -328,7 +374,8 @@ def run_gpu(args):
     return 0
 
 
-FORCE_SOURCE = os.path.join(ROOT, "paper_0709_3225_gb300", "csrc", "lj_force_warp.cu")
+FORCE_SOURCES = [os.path.join(ROOT, "paper_0709_3225_gb300", "csrc", f)
+                 for f in ("lj_force_warp.cu", "lj_force_cell.cuh")]
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_force_warp_traffic_fluid-4m.md")
 
 
@@ -337,8 +384,11 @@ def force_traffic():
     when the summary is missing or was taken on a different kernel source."""
     import hashlib
     try:
-        with open(FORCE_SOURCE, "rb") as fh:
-            sha = hashlib.sha1(fh.read()).hexdigest()
+        h = hashlib.sha1()
+        for path in FORCE_SOURCES:
+            with open(path, "rb") as fh:
+                h.update(fh.read())
+        sha = h.hexdigest()
         fields = {}
         with open(TRAFFIC_SUMMARY) as fh:
             for line in fh:
@@ -362,6 +412,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
