@@ -171,6 +171,66 @@ def run_ensemble(args, stream, world):
             "launches_per_step": (n1 - n0 - 1) / k, "graph": graph, "tuning": tuning}
 
 
+def run_adjoint(x4m, L4m, stream):
+    """The adjoint workload: the force-matching gradient (loss = mean |F -
+    F_target|^2 + mean |x(50) - x_target(50)|^2, theta = (0.9, 1.05)) of the
+    32,000-particle jittered lattice, forward + checkpointed backward through
+    50 force-shifted steps, FP32-mixed; plus one VJP launch at N = 4M.
+    Targets come from the same library at theta = (1, 1) (this times the
+    path; parity is established in the tests)."""
+    import torch
+    from paper_0709_3225_gb300 import autograd, inputs, lj
+    w = inputs.WORKLOADS["fm-32k"]
+    x0, L = inputs.jittered_fcc(w.n_fcc, w.rho, 0.1, w.seed)
+    v0 = inputs.velocities(w.n, w.temperature, w.seed)
+    s = lj.System(x0, v0, L, shift_mode=2)
+    with torch.no_grad():
+        star = torch.tensor([1.0, 1.0], dtype=torch.float64, device="cuda")
+        f_t = autograd.forces(s.x, star, s.ctx).clone()
+        x_t, _ = autograd.trajectory(s.x, s.v, star, s.ctx, 50, 10)
+    n = w.n
+
+    def grad():
+        theta = torch.tensor([0.9, 1.05], dtype=torch.float64, device="cuda", requires_grad=True)
+        F = autograd.forces(s.x, theta, s.ctx)
+        xT, _ = autograd.trajectory(s.x, s.v, theta, s.ctx, 50, 10)
+        d = xT - x_t
+        d = d - L * torch.round(d / L)
+        loss = ((F - f_t) ** 2).sum() / n + (d ** 2).sum() / n
+        loss.backward()
+        return theta.grad
+
+    grad()
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g = grad()
+    torch.cuda.synchronize()
+    t_grad = (time.perf_counter() - t0) / reps
+    s.close()
+    # one VJP of the 4M system
+    s4 = lj.System(x4m, None, L4m)
+    g4 = torch.randn((s4.n, 3), dtype=torch.float64, device="cuda")
+    dx = torch.zeros_like(s4.x)
+    dp = torch.zeros(2, dtype=torch.float64, device="cuda")
+    lj.lj_forces_vjp(s4.ctx, s4.x, g4, 1.0, dx, dp)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(3):
+        lj.lj_forces_vjp(s4.ctx, s4.x, g4, 1.0, dx, dp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    s4.check()
+    vjp_ms = ev0.elapsed_time(ev1) / 3
+    s4.close()
+    return {"workload": "fm-32k force matching, 50 steps, checkpoints every 10", "n": n,
+            "gradient_s": t_grad, "gradients_per_s": 1.0 / t_grad,
+            "dL_dtheta": [float(g[0]), float(g[1])],
+            "vjp_4m_ms": vjp_ms, "vjp_4m_pairs_per_s": unique_pairs(4_000_000, 0.8442, 2.5) / (vjp_ms / 1e3)}
+
+
 def cpu_baseline(x, v, L, w, max_seconds: float = 20.0, max_steps: int = 3):
     """The FP64 oracle as it stands, on this host's cores: full velocity-Verlet
     steps of the same workload until ~max_seconds of work, scaled to steps/s."""
@@ -319,6 +379,7 @@ def run_gpu(args):
     del s64
 
     ensemble = None if args.no_ensemble else run_ensemble(args, stream, world)
+    adjoint = None if (args.no_ensemble or rank != 0) else run_adjoint(x, L, stream)
 
     if rank != 0:
         if world > 1:
@@ -356,6 +417,7 @@ def run_gpu(args):
         "other_kernels_ms_per_step": other_ms,
         "tuning": tuning,
         "ensemble": ensemble,
+        "adjoint": adjoint,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64},
@@ -412,7 +474,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the batched-ensemble and adjoint measurements")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -190,8 +190,10 @@ int lj_vv_adjoint_step(lj_ctx *ctx, const double *x_n, const double *x_n1, doubl
                        double *dparam);
 
 /* Choose the force kernel of a context (same results; for autotuning):
- * kernel 0 = warp-per-cell kernel (FP32-mixed only), 1 = run kernel with
- * bulk-copy staging, 2 = run kernel reading global memory.  gmin is the
+ * kernel 0 = warp-per-cell kernel (FP32-mixed only) with the velocity-Verlet
+ * update of lj_step fused into it, 1 = run kernel with bulk-copy staging,
+ * 2 = run kernel reading global memory, 3 = warp-per-cell kernel with the
+ * update in a separate kernel (the FP32-mixed default).  gmin is the
  * smallest lane-group width of the warp kernel (0 = smallest that holds a
  * cell, or 8, 16, 32).  LJ_EINVAL for other values. */
 int lj_set_tuning(lj_ctx *ctx, int32_t kernel, int32_t gmin);

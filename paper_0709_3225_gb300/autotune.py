@@ -1,8 +1,9 @@
 """Autotuner for the force kernels' launch choices.
 
 It picks, by timing velocity-Verlet steps on a copy of the state:
-  single systems  -- force kernel (warp-per-cell, run kernel with bulk-copy
-                     staging, run kernel reading global memory) and the
+  single systems  -- force kernel (warp-per-cell with the velocity-Verlet
+                     update separate or fused into it, run kernel with
+                     bulk-copy staging, run kernel reading global memory) and the
                      smallest lane-group width of the warp kernel (threads
                      per cell: the group of lanes that owns a cell's
                      particles);
@@ -81,8 +82,8 @@ def _time_steps(run, steps: int, warmup: int) -> float:
 def system_candidates(precision: str) -> list[dict]:
     if precision == "fp64":
         return [{"kernel": 1, "gmin": 0}, {"kernel": 2, "gmin": 0}]
-    return ([{"kernel": 0, "gmin": g} for g in (0, 16, 32)] +
-            [{"kernel": 1, "gmin": 0}, {"kernel": 2, "gmin": 0}])
+    return ([{"kernel": 3, "gmin": g} for g in (0, 16, 32)] +
+            [{"kernel": 0, "gmin": 0}, {"kernel": 1, "gmin": 0}, {"kernel": 2, "gmin": 0}])
 
 
 def tune_system(system: lj.System, rho: float, steps: int = 10, warmup: int = 3, use_cache: bool = True,

@@ -264,7 +264,8 @@ __device__ void phase_force(const BatchDev &b, const WarpParams &k, float4 *__re
             const int nc = b.ncs[r];
             int cx, cy, cz;
             decode_cell((int)(c - b.coff[r]), nc, cx, cy, cz);
-            process_home_cell<MODE, ENERGY, false>(k, b.pos, b.start, f, X, Y, Z, cx, cy, cz, nc, b.coff[r],
+            const StoreForce<MODE, ENERGY> out{f, k.n};
+            process_home_cell<MODE, ENERGY, false>(k, b.pos, b.start, out, X, Y, Z, cx, cy, cz, nc, b.coff[r],
                                                    (float)b.cw[r], eacc, wacc);
         }
     }

@@ -141,23 +141,89 @@ __device__ __forceinline__ int slot_of(int j)
     return 2 * (m * S + s) + h;
 }
 
+// Output of one home particle's result, called by all 32 lanes of the warp
+// (valid = this lane holds a particle's final sums).  StoreForce writes the
+// force (and its energy share); KickDriftBin applies the velocity-Verlet
+// update of that particle instead (see k_force_warp).
 template <int MODE, bool ENERGY>
-__device__ __forceinline__ void write_out(float4 *__restrict__ fout, int idx, int n, float fx, float fy, float fz,
-                                          float e, float w, double &eacc, double &wacc)
-{
-    if ((unsigned)idx < (unsigned)n) {
-        fout[idx] = make_float4(fx, fy, fz, ENERGY ? 0.5f * e : 0.0f);
-        if constexpr (ENERGY) {
-            eacc += 0.5 * (double)e;
-            wacc += 0.5 * (double)w;
+struct StoreForce {
+    float4 *fout;
+    int n;
+    __device__ __forceinline__ void set_home(int, int, int) {}
+    __device__ __forceinline__ void operator()(int idx, bool valid, float fx, float fy, float fz, float e, float w,
+                                               double &eacc, double &wacc) const
+    {
+        if (valid && (unsigned)idx < (unsigned)n) {
+            fout[idx] = make_float4(fx, fy, fz, ENERGY ? 0.5f * e : 0.0f);
+            if constexpr (ENERGY) {
+                eacc += 0.5 * (double)e;
+                wacc += 0.5 * (double)w;
+            }
         }
     }
-}
+};
+
+// Velocity-Verlet update fused behind the force (FP64 state):
+//   last == 0: v += hk f (the closing half kick of this step and the opening
+//              half kick of the next, hk = dt/m), x += dt v, wrap, new cell
+//              (the home cell is the guess) and rank for the next binning;
+//   last != 0: v += hk f (hk = dt/2m) and f is stored (the end of lj_step).
+struct KickDriftBin {
+    float4 *fout;
+    int n;
+    double *x, *v;
+    double hk, dt, L, whi, wlo, s;
+    int nc, last;
+    const long long *thb;
+    int32_t *cell_of, *rank, *count, *err;
+    int hx, hy, hz;
+    __device__ __forceinline__ void set_home(int cx, int cy, int cz)
+    {
+        hx = cx;
+        hy = cy;
+        hz = cz;
+    }
+    __device__ __forceinline__ void operator()(int idx, bool valid, float fx, float fy, float fz, float, float,
+                                               double &, double &) const
+    {
+        valid = valid && (unsigned)idx < (unsigned)n;
+        int c = 0;
+        if (valid) {
+            const int64_t b = 3 * (int64_t)idx;
+            const double vx = __fma_rn(hk, (double)fx, v[b]);
+            const double vy = __fma_rn(hk, (double)fy, v[b + 1]);
+            const double vz = __fma_rn(hk, (double)fz, v[b + 2]);
+            v[b] = vx;
+            v[b + 1] = vy;
+            v[b + 2] = vz;
+            if (last) {
+                fout[idx] = make_float4(fx, fy, fz, 0.0f);
+            } else {
+                const double px = lj_wrap_fast(__fma_rn(dt, vx, x[b]), L, whi, wlo);
+                const double py = lj_wrap_fast(__fma_rn(dt, vy, x[b + 1]), L, whi, wlo);
+                const double pz = lj_wrap_fast(__fma_rn(dt, vz, x[b + 2]), L, whi, wlo);
+                if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
+                x[b] = px;
+                x[b + 1] = py;
+                x[b + 2] = pz;
+                c = lj_cell_from_guess(px, hx, thb, s, nc) +
+                    nc * (lj_cell_from_guess(py, hy, thb, s, nc) + nc * lj_cell_from_guess(pz, hz, thb, s, nc));
+            }
+        }
+        if (!last) {
+            const int r = lj_warp_rank(count, c, valid);
+            if (valid) {
+                cell_of[idx] = c;
+                rank[idx] = r;
+            }
+        }
+    }
+};
 
 // Fast path: staged flat list, G lanes per group, S = 32 / G groups.
-template <int G, int MODE, bool ENERGY, bool NC>
-__device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *__restrict__ pos,
-                                            float4 *__restrict__ fout, float *X, float *Y, float *Z, int s_k,
+template <int G, int MODE, bool ENERGY, bool NC, class Out>
+__device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *__restrict__ pos, const Out &out,
+                                            float *X, float *Y, float *Z, int s_k,
                                             int n_k, float sx, float sy, float sz, int s_home, int n_home,
                                             double &eacc, double &wacc)
 {
@@ -253,14 +319,14 @@ __device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *_
             Wv += __shfl_xor_sync(0xffffffffu, Wv, o);
         }
     }
-    if (sg == 0 && vi) write_out<MODE, ENERGY>(fout, __float_as_int(pi.w), k.n, Fx, Fy, Fz, E, Wv, eacc, wacc);
+    out(__float_as_int(pi.w), sg == 0 && vi, Fx, Fy, Fz, E, Wv, eacc, wacc);
     __syncwarp();   // the slice is reused by the next cell
 }
 
 // Plain path: any occupancy; each stencil cell read from global memory with
 // the home particle shifted into that cell's frame.
-template <int MODE, bool ENERGY, bool NC>
-__device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, float4 *__restrict__ fout, int s_k,
+template <int MODE, bool ENERGY, bool NC, class Out>
+__device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, const Out &out, int s_k,
                            int n_k, float sx, float sy, float sz, int s_home, int n_home, double &eacc, double &wacc)
 {
     const int lane = threadIdx.x & 31;
@@ -280,7 +346,7 @@ __device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, 
                 pair1<MODE, ENERGY>(xs - q.x, ys - q.y, zs - q.z, k, fx, fy, fz, e, w);
             }
         }
-        if (vi) write_out<MODE, ENERGY>(fout, __float_as_int(pi.w), k.n, fx, fy, fz, e, w, eacc, wacc);
+        out(__float_as_int(pi.w), vi, fx, fy, fz, e, w, eacc, wacc);
     }
 }
 
@@ -288,12 +354,14 @@ __device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, 
 // whose linear ids start at cell_base in start[] (0 for a single system),
 // cell side cw.  Builds the 27-cell stencil table in lanes 0..26 and runs
 // the staged or the plain path.
-template <int MODE, bool ENERGY, bool NC>
+template <int MODE, bool ENERGY, bool NC, class Out>
 __device__ __forceinline__ void process_home_cell(const WarpParams &k, const float4 *__restrict__ pos,
-                                                  const int32_t *__restrict__ start, float4 *__restrict__ fout,
+                                                  const int32_t *__restrict__ start, const Out &out_in,
                                                   float *X, float *Y, float *Z, int cx, int cy, int cz, int nc,
                                                   int64_t cell_base, float cw, double &eacc, double &wacc)
 {
+    Out out = out_in;
+    out.set_home(cx, cy, cz);
     const int lane = threadIdx.x & 31;
     int s_k = 0, n_k = 0;
     float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -327,13 +395,13 @@ __device__ __forceinline__ void process_home_cell(const WarpParams &k, const flo
     if (n_home <= 32 && T + 8 <= k.cap) {
         const int need = n_home > k.gmin ? n_home : k.gmin;
         if (need <= 8)
-            cell_staged<8, MODE, ENERGY, NC>(k, pos, fout, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
+            cell_staged<8, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
         else if (need <= 16)
-            cell_staged<16, MODE, ENERGY, NC>(k, pos, fout, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
+            cell_staged<16, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
         else
-            cell_staged<32, MODE, ENERGY, NC>(k, pos, fout, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
+            cell_staged<32, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
     } else {
-        cell_plain<MODE, ENERGY, NC>(k, pos, fout, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
+        cell_plain<MODE, ENERGY, NC>(k, pos, out, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
     }
 }
 

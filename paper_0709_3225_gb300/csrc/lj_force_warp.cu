@@ -19,15 +19,19 @@
 //    (__ffma2_rn / __fmul2_rn).
 //  * Cells with more than 32 particles, or stencils that do not fit the
 //    warp's slice, take a plain path reading global memory per stencil cell.
+#include <string.h>
+
 #include "lj_force_cell.cuh"
 
 namespace {
 
-template <int MODE, bool ENERGY>
+// EPI 0: store forces (and energies); EPI 1: apply the fused velocity-Verlet
+// update (KickDriftBin) to each particle instead.
+template <int MODE, bool ENERGY, int EPI>
 __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams k, const float4 *__restrict__ pos,
                                                                   const int32_t *__restrict__ start,
                                                                   float4 *__restrict__ fout,
-                                                                  double *__restrict__ partial)
+                                                                  double *__restrict__ partial, KickDriftBin kd)
 {
     extern __shared__ __align__(16) float wsmem[];
     const int lane = threadIdx.x & 31;
@@ -40,7 +44,12 @@ __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams 
     const int64_t nwarps = (int64_t)gridDim.x * (kWarpForceThreads / 32);
     for (int64_t c = (int64_t)blockIdx.x * (kWarpForceThreads / 32) + warp; c < k.ncell; c += nwarps) {
         const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
-        process_home_cell<MODE, ENERGY, true>(k, pos, start, fout, X, Y, Z, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
+        if constexpr (EPI == 0) {
+            const StoreForce<MODE, ENERGY> out{fout, k.n};
+            process_home_cell<MODE, ENERGY, true>(k, pos, start, out, X, Y, Z, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
+        } else {
+            process_home_cell<MODE, ENERGY, true>(k, pos, start, kd, X, Y, Z, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
+        }
     }
     if constexpr (ENERGY) {
         __shared__ double red[2 * (kWarpForceThreads / 32)];
@@ -65,15 +74,22 @@ __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams 
     }
 }
 
-void *warp_kernel(int mode, bool energy)
+void *warp_kernel(int mode, bool energy, bool fused = false)
 {
+    if (fused) {
+        switch (mode) {
+            case 0: return (void *)k_force_warp<0, false, 1>;
+            case 1: return (void *)k_force_warp<1, false, 1>;
+            default: return (void *)k_force_warp<2, false, 1>;
+        }
+    }
     switch (mode * 2 + (energy ? 1 : 0)) {
-        case 0: return (void *)k_force_warp<0, false>;
-        case 1: return (void *)k_force_warp<0, true>;
-        case 2: return (void *)k_force_warp<1, false>;
-        case 3: return (void *)k_force_warp<1, true>;
-        case 4: return (void *)k_force_warp<2, false>;
-        default: return (void *)k_force_warp<2, true>;
+        case 0: return (void *)k_force_warp<0, false, 0>;
+        case 1: return (void *)k_force_warp<0, true, 0>;
+        case 2: return (void *)k_force_warp<1, false, 0>;
+        case 3: return (void *)k_force_warp<1, true, 0>;
+        case 4: return (void *)k_force_warp<2, false, 0>;
+        default: return (void *)k_force_warp<2, true, 0>;
     }
 }
 
@@ -93,8 +109,8 @@ cudaError_t warp_force_configure(lj_ctx *c)
     c->wforce_smem = (kWarpForceThreads / 32) * 3 * cap * (int)sizeof(float);
     int minblk = 1 << 30;
     for (int mode = 0; mode < 3; mode++)
-        for (int en = 0; en < 2; en++) {
-            void *kern = warp_kernel(mode, en != 0);
+        for (int en = 0; en < 3; en++) {
+            void *kern = warp_kernel(mode, en == 1, en == 2);
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->wforce_smem);
             if (e != cudaSuccess) return e;
             int nb = 0;
@@ -112,7 +128,9 @@ cudaError_t warp_force_configure(lj_ctx *c)
     return cudaSuccess;
 }
 
-cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
+namespace {
+
+WarpParams warp_params(const lj_ctx *c)
 {
     WarpParams k;
     k.gmin = c->gmin;
@@ -132,11 +150,15 @@ cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
     k.c6 = (float)(4.0 * eps * s6);
     k.uc = (float)(rci6 * (4.0 * eps * s12 * rci6 - 4.0 * eps * s6));
     k.fc = (float)(rc * rci2 * rci6 * (48.0 * eps * s12 * rci6 - 24.0 * eps * s6));
-    void *kern = warp_kernel(c->p.shift_mode, energy);
+    return k;
+}
+
+cudaError_t launch_warp(lj_ctx *c, void *kern, WarpParams k, void *f, KickDriftBin kd)
+{
     const float4 *pos = (const float4 *)c->pos;
     const int32_t *start = c->start;
     double *partial = c->partial;
-    void *args[] = {&k, (void *)&pos, (void *)&start, &f, &partial};
+    void *args[] = {&k, (void *)&pos, (void *)&start, &f, &partial, &kd};
     if (c->timing && c->ev_used + 2 <= c->nev) cudaEventRecord(c->ev[c->ev_used], c->stream);
     cudaError_t e = cudaLaunchKernel(kern, dim3(c->wforce_grid), dim3(kWarpForceThreads), args, c->wforce_smem,
                                      c->stream);
@@ -147,4 +169,37 @@ cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
     c->kernel_launches++;
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
+{
+    KickDriftBin kd;
+    memset(&kd, 0, sizeof(kd));
+    return launch_warp(c, warp_kernel(c->p.shift_mode, energy), warp_params(c), f, kd);
+}
+
+cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bool last)
+{
+    KickDriftBin kd;
+    memset(&kd, 0, sizeof(kd));
+    kd.fout = (float4 *)f;
+    kd.n = (int)c->p.n;
+    kd.x = x;
+    kd.v = v;
+    kd.last = last ? 1 : 0;
+    kd.hk = (last ? 0.5 : 1.0) * c->p.dt / c->p.mass;
+    kd.dt = c->p.dt;
+    kd.L = c->p.box;
+    kd.whi = c->wrap_hi;
+    kd.wlo = c->wrap_lo;
+    kd.s = c->inv_cw;
+    kd.nc = c->nc;
+    kd.thb = c->thb;
+    kd.cell_of = c->cell_of;
+    kd.rank = c->rank;
+    kd.count = c->count;
+    kd.err = c->err;
+    return launch_warp(c, warp_kernel(c->p.shift_mode, false, true), warp_params(c), f, kd);
 }

@@ -60,6 +60,7 @@ struct lj_ctx {
     // ... and warp-per-cell kernel (lj_force_warp.cu, FP32-mixed)
     int wcap, wforce_smem, wforce_grid;
     int gmin;            // tuning: smallest lane-group width in the warp kernel
+    int fuse_update;     // warp kernel applies the velocity-Verlet update (lj_step)
     int npartial;        // partials written by the last energy launch
     int npartial_cap;    // capacity of `partial` in (energy, virial) pairs
     void *g4;            // sorted cotangents for the adjoint (lazily allocated)
@@ -177,3 +178,4 @@ cudaError_t warp_force_configure(lj_ctx *c);
 cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, double *dparam);
 cudaError_t launch_axpy(lj_ctx *c, double *y, const double *x, double a);
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);
+cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bool last);

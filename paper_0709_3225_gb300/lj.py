@@ -285,7 +285,8 @@ def lj_vv_adjoint_step(ctx: Context, x_n, x_n1, lam_x, lam_v, dparam) -> None:
 
 
 def lj_set_tuning(ctx: Context, kernel: int, gmin: int = 0) -> None:
-    """Force kernel of a context: 0 warp-per-cell (mixed), 1 run-staged, 2 run-direct."""
+    """Force kernel of a context: 0 warp-per-cell with fused update (mixed),
+    1 run-staged, 2 run-direct, 3 warp-per-cell with separate update (mixed)."""
     _ck(load().lj_set_tuning(ctx.handle, int(kernel), int(gmin)), "lj_set_tuning")
 
 

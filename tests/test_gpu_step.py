@@ -37,6 +37,26 @@ def test_trajectory_matches_oracle(oracle_mod, precision, xtol, vtol, mode):
     s.close()
 
 
+@pytest.mark.parametrize("kernel", [0, 3, 1])
+def test_update_paths_agree(oracle_mod, kernel):
+    """The fused update (kernel 0), the separate update (3) and the run kernel
+    (1) integrate the same trajectory (force-shifted, FP32 rounding only)."""
+    from paper_0709_3225_gb300 import lj
+    x, v, L = _liquid(seed=17)
+    xo, vo = x.copy(), v.copy()
+    fo = oracle_mod.forces_cells(xo, L, mode=2)[0]
+    oracle_mod.vv(xo, vo, fo, L, 15, mode=2)
+    s = lj.System(x, v, L, shift_mode=2)
+    lj.lj_set_tuning(s.ctx, kernel, 0)
+    s.step(1)
+    s.step(14)
+    s.check()
+    assert np.abs(min_image(s.x.cpu().numpy() - xo, L)).max() <= 2e-6
+    assert np.abs(s.v.cpu().numpy() - vo).max() <= 2e-4
+    assert np.abs(s.f.double().cpu().numpy()[:, :3] - fo).max() <= 3e-4 * np.abs(fo).max()
+    s.close()
+
+
 def test_time_reversibility_fp64():
     from paper_0709_3225_gb300 import lj
     x, v, L = _liquid(seed=5)
