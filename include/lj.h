@@ -195,8 +195,11 @@ int lj_vv_adjoint_step(lj_ctx *ctx, const double *x_n, const double *x_n1, doubl
  * 2 = run kernel reading global memory, 3 = warp-per-cell kernel with the
  * update in a separate kernel (the FP32-mixed default).  gmin is the
  * smallest lane-group width of the warp kernel (0 = smallest that holds a
- * cell, or 8, 16, 32).  LJ_EINVAL for other values. */
-int lj_set_tuning(lj_ctx *ctx, int32_t kernel, int32_t gmin);
+ * cell, or 8, 16, 32).  cells_per_grab: 0 = the warp kernel's warps take
+ * cells by static striding, 1..1024 = they pull that many cells at a time
+ * from an atomic work counter (a new context uses 4).  LJ_EINVAL for other
+ * values. */
+int lj_set_tuning(lj_ctx *ctx, int32_t kernel, int32_t gmin, int32_t cells_per_grab);
 
 /* ---------------------------------------------------------------------- */
 /* Batched ensembles.  nrep independent periodic systems ("replicas") of

@@ -81,9 +81,10 @@ def _time_steps(run, steps: int, warmup: int) -> float:
 
 def system_candidates(precision: str) -> list[dict]:
     if precision == "fp64":
-        return [{"kernel": 1, "gmin": 0}, {"kernel": 2, "gmin": 0}]
-    return ([{"kernel": 3, "gmin": g} for g in (0, 16, 32)] +
-            [{"kernel": 0, "gmin": 0}, {"kernel": 1, "gmin": 0}, {"kernel": 2, "gmin": 0}])
+        return [{"kernel": 1, "gmin": 0, "grab": 0}, {"kernel": 2, "gmin": 0, "grab": 0}]
+    warp = [{"kernel": 3, "gmin": g, "grab": c} for g in (0, 16) for c in (0, 1, 4)]
+    return warp + [{"kernel": 3, "gmin": 32, "grab": 0}, {"kernel": 0, "gmin": 0, "grab": 1},
+                   {"kernel": 1, "gmin": 0, "grab": 0}, {"kernel": 2, "gmin": 0, "grab": 0}]
 
 
 def tune_system(system: lj.System, rho: float, steps: int = 10, warmup: int = 3, use_cache: bool = True,
@@ -94,19 +95,20 @@ def tune_system(system: lj.System, rho: float, steps: int = 10, warmup: int = 3,
     if use_cache:
         hit = load_cache(path).get(key)
         if hit:
-            lj.lj_set_tuning(system.ctx, hit["kernel"], hit["gmin"])
+            lj.lj_set_tuning(system.ctx, hit["kernel"], hit["gmin"], hit.get("grab", 0))
             return dict(hit, cached=True)
     x, v, f = system.x.clone(), system.v.clone(), system.f.clone()
     lj.lj_forces(system.ctx, x, f)
     results = []
     for cand in system_candidates(precision):
-        lj.lj_set_tuning(system.ctx, cand["kernel"], cand["gmin"])
+        lj.lj_set_tuning(system.ctx, cand["kernel"], cand["gmin"], cand["grab"])
         ms = _time_steps(lambda k: lj.lj_step(system.ctx, x, v, f, k), steps, warmup)
         results.append(dict(cand, ms_per_step=ms))
     lj.lj_check(system.ctx)
     best = min(results, key=lambda r: r["ms_per_step"])
-    lj.lj_set_tuning(system.ctx, best["kernel"], best["gmin"])
-    choice = {"kernel": best["kernel"], "gmin": best["gmin"], "ms_per_step": best["ms_per_step"]}
+    lj.lj_set_tuning(system.ctx, best["kernel"], best["gmin"], best["grab"])
+    choice = {"kernel": best["kernel"], "gmin": best["gmin"], "grab": best["grab"],
+              "ms_per_step": best["ms_per_step"]}
     store_cache(key, choice, path)
     return dict(choice, cached=False, trials=results)
 

@@ -127,8 +127,12 @@ __device__ void phase_bin(const BatchDev &b, int op, double *__restrict__ x, dou
                 cy = lj_cell1(py, s, nc);
                 cz = lj_cell1(pz, s, nc);
             }
-            if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(b.err, LJ_ERRBIT_NONFINITE);
-            gc = b.coff[r] + cx + nc * (cy + nc * cz);
+            if (isfinite(px) && isfinite(py) && isfinite(pz)) {
+                gc = b.coff[r] + cx + nc * (cy + nc * cz);
+            } else {   // the extra cell after all replicas' grids
+                atomicOr(b.err, LJ_ERRBIT_NONFINITE);
+                gc = (int)b.ncell;
+            }
         }
         const int rk = lj_warp_rank(b.count, gc, valid);
         if (valid) {
@@ -146,7 +150,7 @@ __device__ void phase_tiles(const BatchDev &b)
         int32_t acc = 0;
         for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
             const int64_t e = (int64_t)t * kScanTile + k;
-            if (e < b.ncell) acc += b.count[e];
+            if (e <= b.ncell) acc += b.count[e];
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
@@ -187,7 +191,7 @@ __device__ void phase_scan(const BatchDev &b)
 #pragma unroll
         for (int k = 0; k < items; k++) {
             const int64_t e = base + k;
-            vals[k] = e < b.ncell ? b.count[e] : 0;
+            vals[k] = e <= b.ncell ? b.count[e] : 0;
             local += vals[k];
         }
         int32_t incl = local;
@@ -205,14 +209,14 @@ __device__ void phase_scan(const BatchDev &b)
 #pragma unroll
         for (int k = 0; k < items; k++) {
             const int64_t e = base + k;
-            if (e < b.ncell) {
+            if (e <= b.ncell) {
                 b.start[e] = run;
                 b.count[e] = 0;
             }
             run += vals[k];
         }
         if (t == b.ntiles - 1 && threadIdx.x == blockDim.x - 1) {
-            b.start[b.ncell] = run;
+            b.start[b.ncell + 1] = run;
             if ((int64_t)run != b.ntot) atomicOr(b.err, LJ_ERRBIT_SCAN);
         }
         __syncthreads();
@@ -227,9 +231,13 @@ __device__ void phase_scatter(const BatchDev &b, int op, const double *__restric
         const int r = b.rep_of[i];
         const int c = b.cell_of[i];
         const int nc = b.ncs[r];
+        double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+        if (c >= b.ncell) {   // non-finite particle in the extra cell
+            b.pos[b.start[c] + b.rank[i]] = make_float4((float)px, (float)px, (float)px, __int_as_float((int)i));
+            continue;
+        }
         int cx, cy, cz;
         decode_cell(c - b.coff[r], nc, cx, cy, cz);
-        double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
         if (op != 0) {
             const double L = b.L[r], whi = b.whi[r], wlo = b.wlo[r];
             px = lj_wrap_fast(px, L, whi, wlo);
@@ -573,7 +581,7 @@ extern "C" int lj_batch_create(lj_batch **out, int32_t nrep, const int64_t *n, c
     d.ntot = ntot;
     d.ncell = ncell;
     d.nrep = nrep;
-    d.ntiles = (int)((ncell + kScanTile - 1) / kScanTile);
+    d.ntiles = (int)((ncell + 1 + kScanTile - 1) / kScanTile);   // grid cells + the extra cell
     d.cells_per_grab = 4;
     d.h = 0.5 * common->dt / common->mass;
     d.dt = common->dt;
@@ -626,8 +634,8 @@ extern "C" int lj_batch_create(lj_batch **out, int32_t nrep, const int64_t *n, c
     d.thb = thb_d;
     LJ_BCK(balloc(b, &d.cell_of, n1));
     LJ_BCK(balloc(b, &d.rank, n1));
-    LJ_BCK(balloc(b, &d.count, (size_t)ncell));
-    LJ_BCK(balloc(b, &d.start, (size_t)ncell + 1));
+    LJ_BCK(balloc(b, &d.count, (size_t)ncell + 1));
+    LJ_BCK(balloc(b, &d.start, (size_t)ncell + 2));
     LJ_BCK(balloc(b, &d.tile_sum, (size_t)d.ntiles));
     LJ_BCK(balloc(b, &d.err, 1));
     LJ_BCK(balloc(b, &d.pos, n1));
@@ -638,7 +646,7 @@ extern "C" int lj_batch_create(lj_batch **out, int32_t nrep, const int64_t *n, c
     LJ_BCK(balloc(b, &b->rep_out, 3 * (size_t)nrep));
     LJ_BCK(cudaMallocHost(&b->host_out, sizeof(double) * 3 * (size_t)nrep));
     LJ_BCK(cudaMallocHost(&b->host_err, sizeof(int32_t)));
-    LJ_BCK(cudaMemset(d.count, 0, sizeof(int32_t) * (size_t)ncell));
+    LJ_BCK(cudaMemset(d.count, 0, sizeof(int32_t) * ((size_t)ncell + 1)));
     LJ_BCK(cudaMemset(d.cell_of, 0, sizeof(int32_t) * n1));
     LJ_BCK(cudaMemset(d.err, 0, sizeof(int32_t)));
     LJ_BCK(cudaMemset(d.bar_count, 0, sizeof(unsigned)));

@@ -18,11 +18,15 @@ __global__ void k_bin_count(const double *__restrict__ x, int n, double L, doubl
     int c = 0;
     if (valid) {
         double px = x[3 * (int64_t)i + 0], py = x[3 * (int64_t)i + 1], pz = x[3 * (int64_t)i + 2];
-        if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
-        int cx = lj_cell1(lj_wrap_fast(px, L, whi, wlo), s, nc);
-        int cy = lj_cell1(lj_wrap_fast(py, L, whi, wlo), s, nc);
-        int cz = lj_cell1(lj_wrap_fast(pz, L, whi, wlo), s, nc);
-        c = cx + nc * (cy + nc * cz);
+        if (isfinite(px) && isfinite(py) && isfinite(pz)) {
+            int cx = lj_cell1(lj_wrap_fast(px, L, whi, wlo), s, nc);
+            int cy = lj_cell1(lj_wrap_fast(py, L, whi, wlo), s, nc);
+            int cz = lj_cell1(lj_wrap_fast(pz, L, whi, wlo), s, nc);
+            c = cx + nc * (cy + nc * cz);
+        } else {
+            atomicOr(err, LJ_ERRBIT_NONFINITE);
+            c = nc * nc * nc;   // the extra cell
+        }
     }
     const int r = lj_warp_rank(count, c, valid);
     if (valid) {
@@ -33,8 +37,9 @@ __global__ void k_bin_count(const double *__restrict__ x, int n, double L, doubl
 
 // Scan phase 1: sum of each tile of kScanTile counts.
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t *__restrict__ count, int64_t ncell,
-                                                             int32_t *__restrict__ tile_sum)
+                                                             int32_t *__restrict__ tile_sum, unsigned *work)
 {
+    if (work && blockIdx.x == 0 && threadIdx.x == 0) *work = 0u;   // the force kernel's work counter
     __shared__ int32_t warp_sum[kScanThreads / 32];
     int64_t base = (int64_t)blockIdx.x * kScanTile;
     int32_t acc = 0;
@@ -136,11 +141,15 @@ __global__ void k_scatter(const double *__restrict__ x, int n, double L, double 
         py = lj_wrap_fast(py, L, whi, wlo);
         pz = lj_wrap_fast(pz, L, whi, wlo);
     }
-    int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
     typename Vec4<T>::type q;
-    q.x = (T)(px - __ldg(centre + cx));
-    q.y = (T)(py - __ldg(centre + cy));
-    q.z = (T)(pz - __ldg(centre + cz));
+    if (c < nc * nc * nc) {
+        int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+        q.x = (T)(px - __ldg(centre + cx));
+        q.y = (T)(py - __ldg(centre + cy));
+        q.z = (T)(pz - __ldg(centre + cz));
+    } else {   // the extra cell of non-finite particles (never read as a neighbour)
+        q.x = q.y = q.z = (T)px;
+    }
     if constexpr (sizeof(T) == 4) {
         q.w = __int_as_float(i);
     } else {
@@ -173,8 +182,9 @@ cudaError_t launch_bin_count(lj_ctx *c, const double *x)
 
 cudaError_t launch_scan(lj_ctx *c)
 {
-    k_scan_tiles<<<c->ntiles, kScanThreads, 0, c->stream>>>(c->count, c->ncell, c->tile_sum);
-    k_scan_apply<<<c->ntiles, kScanThreads, 0, c->stream>>>(c->count, c->ncell, c->tile_sum, c->start,
+    // ncell + 1 cells: the grid and the extra cell of non-finite particles
+    k_scan_tiles<<<c->ntiles, kScanThreads, 0, c->stream>>>(c->count, c->ncell + 1, c->tile_sum, c->work);
+    k_scan_apply<<<c->ntiles, kScanThreads, 0, c->stream>>>(c->count, c->ncell + 1, c->tile_sum, c->start,
                                                              (int)c->p.n, c->err);
     c->kernel_launches += 2;
     return cudaGetLastError();

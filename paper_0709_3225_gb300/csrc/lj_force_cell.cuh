@@ -12,6 +12,8 @@ constexpr float kFar = 1.0e4f;   // padding candidate: r^2 ~ 1e8 > rc^2
 struct WarpParams {
     int n, nc, cap;              // cap: staged candidates per warp (multiple of 8)
     int gmin;                    // smallest lane-group width to use (0, 8, 16 or 32)
+    int grab;                    // cells per pull from *work (0 = static striding)
+    unsigned *work;              // work counter, zero at launch
     int64_t ncell;
     float cw;
     float rc2, rc, a12, b6, c12, c6, uc, fc;
@@ -202,12 +204,16 @@ struct KickDriftBin {
                 const double px = lj_wrap_fast(__fma_rn(dt, vx, x[b]), L, whi, wlo);
                 const double py = lj_wrap_fast(__fma_rn(dt, vy, x[b + 1]), L, whi, wlo);
                 const double pz = lj_wrap_fast(__fma_rn(dt, vz, x[b + 2]), L, whi, wlo);
-                if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
                 x[b] = px;
                 x[b + 1] = py;
                 x[b + 2] = pz;
-                c = lj_cell_from_guess(px, hx, thb, s, nc) +
-                    nc * (lj_cell_from_guess(py, hy, thb, s, nc) + nc * lj_cell_from_guess(pz, hz, thb, s, nc));
+                if (isfinite(px) && isfinite(py) && isfinite(pz)) {
+                    c = lj_cell_from_guess(px, hx, thb, s, nc) +
+                        nc * (lj_cell_from_guess(py, hy, thb, s, nc) + nc * lj_cell_from_guess(pz, hz, thb, s, nc));
+                } else {
+                    atomicOr(err, LJ_ERRBIT_NONFINITE);
+                    c = nc * nc * nc;   // the extra cell
+                }
             }
         }
         if (!last) {

@@ -41,8 +41,7 @@ __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams 
     float *Z = Y + k.cap;
     const int nc = k.nc;
     double eacc = 0.0, wacc = 0.0;
-    const int64_t nwarps = (int64_t)gridDim.x * (kWarpForceThreads / 32);
-    for (int64_t c = (int64_t)blockIdx.x * (kWarpForceThreads / 32) + warp; c < k.ncell; c += nwarps) {
+    auto one_cell = [&](int64_t c) {
         const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
         if constexpr (EPI == 0) {
             const StoreForce<MODE, ENERGY> out{fout, k.n};
@@ -50,6 +49,20 @@ __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams 
         } else {
             process_home_cell<MODE, ENERGY, true>(k, pos, start, kd, X, Y, Z, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
         }
+    };
+    if (k.grab > 0) {
+        // dynamic: warps pull chunks of `grab` consecutive cells
+        for (;;) {
+            unsigned c0 = 0;
+            if (lane == 0) c0 = atomicAdd(k.work, (unsigned)k.grab);
+            c0 = __shfl_sync(0xffffffffu, c0, 0);
+            if ((int64_t)c0 >= k.ncell) break;
+            const int64_t c1 = min((int64_t)c0 + k.grab, k.ncell);
+            for (int64_t c = c0; c < c1; c++) one_cell(c);
+        }
+    } else {
+        const int64_t nwarps = (int64_t)gridDim.x * (kWarpForceThreads / 32);
+        for (int64_t c = (int64_t)blockIdx.x * (kWarpForceThreads / 32) + warp; c < k.ncell; c += nwarps) one_cell(c);
     }
     if constexpr (ENERGY) {
         __shared__ double red[2 * (kWarpForceThreads / 32)];
@@ -134,6 +147,8 @@ WarpParams warp_params(const lj_ctx *c)
 {
     WarpParams k;
     k.gmin = c->gmin;
+    k.grab = c->grab;
+    k.work = c->work;
     k.n = (int)c->p.n;
     k.nc = c->nc;
     k.cap = c->wcap;

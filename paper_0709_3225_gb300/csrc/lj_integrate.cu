@@ -44,17 +44,21 @@ __global__ void k_kick_drift_bin(double *__restrict__ x, double *__restrict__ v,
         const double px = lj_wrap_fast(__fma_rn(dt, vx, x[b]), L, whi, wlo);
         const double py = lj_wrap_fast(__fma_rn(dt, vy, x[b + 1]), L, whi, wlo);
         const double pz = lj_wrap_fast(__fma_rn(dt, vz, x[b + 2]), L, whi, wlo);
-        if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
         v[b] = vx;
         v[b + 1] = vy;
         v[b + 2] = vz;
         x[b] = px;
         x[b + 1] = py;
         x[b + 2] = pz;
-        const int old = cell_of[i];
-        const int ox = old % nc, oy = (old / nc) % nc, oz = old / (nc * nc);
-        c = lj_cell_from_guess(px, ox, thb, s, nc) +
-            nc * (lj_cell_from_guess(py, oy, thb, s, nc) + nc * lj_cell_from_guess(pz, oz, thb, s, nc));
+        if (isfinite(px) && isfinite(py) && isfinite(pz)) {
+            const int old = cell_of[i];
+            const int ox = old % nc, oy = (old / nc) % nc, oz = old / (nc * nc);
+            c = lj_cell_from_guess(px, ox, thb, s, nc) +
+                nc * (lj_cell_from_guess(py, oy, thb, s, nc) + nc * lj_cell_from_guess(pz, oz, thb, s, nc));
+        } else {
+            atomicOr(err, LJ_ERRBIT_NONFINITE);
+            c = nc * nc * nc;   // the extra cell
+        }
     }
     const int r = lj_warp_rank(count, c, valid);
     if (valid) {

@@ -6,6 +6,11 @@
 
 #include "../../include/lj.h"
 
+// Particles with a non-finite coordinate are binned into one extra cell
+// with id ncell, after the grid: no stencil visits it, so they cannot pile
+// into a real cell and make its force work quadratic.  count[] and start[]
+// hold ncell + 1 and ncell + 2 entries.
+//
 // Error bits latched in device memory by kernels, mapped to lj_status by
 // lj_check.
 enum : int32_t {
@@ -61,6 +66,8 @@ struct lj_ctx {
     int wcap, wforce_smem, wforce_grid;
     int gmin;            // tuning: smallest lane-group width in the warp kernel
     int fuse_update;     // warp kernel applies the velocity-Verlet update (lj_step)
+    int grab;            // tuning: cells per work pull in the warp kernel (0 = static)
+    unsigned *work;      // work counter of the warp kernel, zeroed by k_scan_tiles
     int npartial;        // partials written by the last energy launch
     int npartial_cap;    // capacity of `partial` in (energy, virial) pairs
     void *g4;            // sorted cotangents for the adjoint (lazily allocated)

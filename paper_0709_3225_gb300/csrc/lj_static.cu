@@ -31,10 +31,10 @@ constexpr size_t kOffRank = kOffCellOf + align256(4 * kMaxN);
 constexpr size_t kOffPerm = kOffRank + align256(4 * kMaxN);
 constexpr size_t kOffPos = kOffPerm + align256(4 * kMaxN);
 constexpr size_t kOffCount = kOffPos + align256(32 * kMaxN);          // double4 in FP64 mode
-constexpr size_t kOffStart = kOffCount + align256(4 * kMaxCells);
-constexpr size_t kOffCentre = kOffStart + align256(4 * (kMaxCells + 1));
+constexpr size_t kOffStart = kOffCount + align256(4 * (kMaxCells + 1));
+constexpr size_t kOffCentre = kOffStart + align256(4 * (kMaxCells + 2));
 constexpr size_t kOffTiles = kOffCentre + align256(8 * kMaxNc);
-constexpr size_t kOffPartial = kOffTiles + align256(4 * ((kMaxCells + kScanTile - 1) / kScanTile));
+constexpr size_t kOffPartial = kOffTiles + align256(4 * ((kMaxCells + 1 + kScanTile - 1) / kScanTile));
 constexpr size_t kOffScalars = kOffPartial + align256(16 * kMaxPartials);
 constexpr size_t kOffErr = kOffScalars + align256(4 * sizeof(double));
 constexpr size_t kScratchBytes = kOffErr + 256;
@@ -123,7 +123,7 @@ extern "C" int lj_forces_static(const lj_params *p, const double *x, void *f, vo
     c.start = (int32_t *)(base + kOffStart);
     c.centre = (double *)(base + kOffCentre);
     c.tile_sum = (int32_t *)(base + kOffTiles);
-    c.ntiles = (int)((ncell + kScanTile - 1) / kScanTile);
+    c.ntiles = (int)((ncell + 1 + kScanTile - 1) / kScanTile);
     c.partial = (double *)(base + kOffPartial);
     c.scalars = (double *)(base + kOffScalars);
     c.err = (int32_t *)(base + kOffErr);
@@ -134,7 +134,7 @@ extern "C" int lj_forces_static(const lj_params *p, const double *x, void *f, vo
     if (p->n == 0) return LJ_OK;
 
     // The buffer keeps the previous call's contents: clear what must start at 0.
-    if ((e = cudaMemsetAsync(c.count, 0, (size_t)ncell * sizeof(int32_t), c.stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(c.count, 0, (size_t)(ncell + 1) * sizeof(int32_t), c.stream)) != cudaSuccess)
         return map_err(e);
     if ((e = cudaMemsetAsync(c.err, 0, sizeof(int32_t), c.stream)) != cudaSuccess) return map_err(e);
     k_static_centres<<<1, kMaxNc, 0, c.stream>>>(c.centre, nc, c.cw);

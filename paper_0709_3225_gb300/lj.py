@@ -73,7 +73,7 @@ _SIGS = {
     "lj_energy": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lj_check": ([_P], ctypes.c_int),
     "lj_set_params": ([_P, ctypes.c_double, ctypes.c_double], ctypes.c_int),
-    "lj_set_tuning": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "lj_set_tuning": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "lj_batch_create": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(lj_params), _P], ctypes.c_int),
     "lj_batch_destroy": ([_P], None),
@@ -284,10 +284,10 @@ def lj_vv_adjoint_step(ctx: Context, x_n, x_n1, lam_x, lam_v, dparam) -> None:
                                   _dev(dparam, torch.float64, (2,), "dparam")), "lj_vv_adjoint_step")
 
 
-def lj_set_tuning(ctx: Context, kernel: int, gmin: int = 0) -> None:
+def lj_set_tuning(ctx: Context, kernel: int, gmin: int = 0, cells_per_grab: int = 0) -> None:
     """Force kernel of a context: 0 warp-per-cell with fused update (mixed),
     1 run-staged, 2 run-direct, 3 warp-per-cell with separate update (mixed)."""
-    _ck(load().lj_set_tuning(ctx.handle, int(kernel), int(gmin)), "lj_set_tuning")
+    _ck(load().lj_set_tuning(ctx.handle, int(kernel), int(gmin), int(cells_per_grab)), "lj_set_tuning")
 
 
 class Batch:

@@ -32,7 +32,7 @@ def test_tune_system_and_batch(tmp_path):
     ref = s.f.clone()
     x_before = s.x.clone()
     r = autotune.tune_system(s, 0.8442, steps=4, warmup=3, path=path)
-    assert not r["cached"] and len(r["trials"]) == 6
+    assert not r["cached"] and len(r["trials"]) == 10
     assert torch.equal(s.x, x_before)                 # tuning works on a copy
     s.forces()
     assert float((s.f[:, :3] - ref[:, :3]).abs().max()) <= 1e-4 * float(ref[:, :3].abs().max())

@@ -88,3 +88,55 @@ def test_context_reuse_and_streams():
     assert torch.allclose(ref.f, other.f, rtol=0, atol=1e-12)
     ref.close()
     other.close()
+
+
+@pytest.mark.parametrize("kernel,grab", [(3, 0), (3, 4), (1, 0)])
+def test_nonfinite_particles_go_to_the_extra_cell(oracle_mod, kernel, grab):
+    """Non-finite particles are binned past the grid: the finite ones keep
+    their exact cells and forces, and the error is still reported."""
+    from paper_0709_3225_gb300 import lj
+    from gpu_util import rel_rms
+    x, L = inputs.jittered_fcc(8, 0.8442, 0.05, 3)
+    bad = [5, 300, 1999]
+    x[bad[0], 0] = np.nan
+    x[bad[1], 2] = -np.inf
+    x[bad[2], 1] = np.inf
+    good = np.setdiff1d(np.arange(x.shape[0]), bad)
+    s = lj.System(x, None, L)
+    lj.lj_set_tuning(s.ctx, kernel, 0, grab)
+    lj.lj_forces(s.ctx, s.x, s.f)
+    with pytest.raises(lj.LJError) as ei:
+        s.check()
+    assert ei.value.code == lj.LJ_ENONFINITE
+    cell_of, count, start, perm = (t.cpu().numpy() for t in s.cells())
+    with pytest.raises(lj.LJError):
+        s.check()
+    ncell = s.ctx.nc ** 3
+    assert np.all(cell_of[bad] == ncell)
+    assert int(start[ncell]) == len(good) and int(count.sum()) == len(good)
+    assert sorted(perm[len(good):].tolist()) == bad
+    want = oracle_mod.bin_cells(np.ascontiguousarray(x[good]), L, s.ctx.nc)[0]
+    assert np.array_equal(cell_of[good], want)
+    fo = oracle_mod.forces_cells(np.ascontiguousarray(x[good]), L, mode=1)[0]
+    fg = s.f.double().cpu().numpy()[good, :3]
+    assert rel_rms(fg, fo) <= 1e-5
+    s.close()
+
+
+def test_nonfinite_replica_particle_is_isolated(oracle_mod):
+    from paper_0709_3225_gb300 import lj
+    from gpu_util import rel_rms
+    e = inputs.ensemble(3, seed=9, n_lo=600, n_hi=1500)
+    xs, vs = inputs.ensemble_state(e)
+    xs[1] = xs[1].copy()
+    xs[1][7, 0] = np.nan
+    b = lj.Batch(xs, vs, e.box)
+    b.forces()
+    with pytest.raises(lj.LJError) as ei:
+        b.check()
+    assert ei.value.code == lj.LJ_ENONFINITE
+    f = b.f.double().cpu().numpy()[:, :3]
+    for r in (0, 2):
+        fo = oracle_mod.forces_cells(xs[r], e.box[r], mode=1)[0]
+        assert rel_rms(b.replica(f, r), fo) <= 1e-5, r
+    b.close()

@@ -37,8 +37,8 @@ def test_trajectory_matches_oracle(oracle_mod, precision, xtol, vtol, mode):
     s.close()
 
 
-@pytest.mark.parametrize("kernel", [0, 3, 1])
-def test_update_paths_agree(oracle_mod, kernel):
+@pytest.mark.parametrize("kernel,grab", [(0, 0), (3, 0), (3, 1), (3, 8), (1, 0)])
+def test_update_paths_agree(oracle_mod, kernel, grab):
     """The fused update (kernel 0), the separate update (3) and the run kernel
     (1) integrate the same trajectory (force-shifted, FP32 rounding only)."""
     from paper_0709_3225_gb300 import lj
@@ -47,7 +47,7 @@ def test_update_paths_agree(oracle_mod, kernel):
     fo = oracle_mod.forces_cells(xo, L, mode=2)[0]
     oracle_mod.vv(xo, vo, fo, L, 15, mode=2)
     s = lj.System(x, v, L, shift_mode=2)
-    lj.lj_set_tuning(s.ctx, kernel, 0)
+    lj.lj_set_tuning(s.ctx, kernel, 0, grab)
     s.step(1)
     s.step(14)
     s.check()
