@@ -79,8 +79,11 @@ typedef struct lj_params {
     double mass;         /* particle mass, > 0 */
     int32_t shift_mode;  /* lj_shift */
     int32_t precision;   /* lj_precision */
-    int32_t cell_subdiv; /* cells per rc along each axis: 1 (27-cell stencil,
-                            Section 3) or 0 for the default (1) */
+    int32_t cell_subdiv; /* cells per rc along each axis, k: 1 (cell side
+                            >= rc, 27-cell stencil, Section 3), 2 (side >= rc/2,
+                            125-cell stencil; FP32-mixed and flags 0 only) or
+                            0 for the default (1).  n = floor(k L / rc) cells
+                            per axis, n >= 2k + 1 required (LJ_EBOX). */
     int32_t flags;       /* 0, LJ_FLAG_RUN_STAGED or LJ_FLAG_RUN_DIRECT */
 } lj_params;
 
@@ -193,13 +196,14 @@ int lj_vv_adjoint_step(lj_ctx *ctx, const double *x_n, const double *x_n1, doubl
  * kernel 0 = warp-per-cell kernel (FP32-mixed only) with the velocity-Verlet
  * update of lj_step fused into it, 1 = run kernel with bulk-copy staging,
  * 2 = run kernel reading global memory, 3 = warp-per-cell kernel with the
- * update in a separate kernel (the FP32-mixed default).  gmin is the
- * smallest lane-group width of the warp kernel (0 = smallest that holds a
- * cell, or 8, 16, 32).  cells_per_grab: 0 = the warp kernel's warps take
- * cells by static striding, 1..1024 = they pull that many cells at a time
- * from an atomic work counter (a new context uses 4).  LJ_EINVAL for other
- * values. */
-int lj_set_tuning(lj_ctx *ctx, int32_t kernel, int32_t gmin, int32_t cells_per_grab);
+ * update in a separate kernel (the FP32-mixed default); kernels 1 and 2
+ * need cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
+ * in chunks of this many lanes, the other 32 / group_width lane groups
+ * splitting the candidates; 0 = chosen per cell to minimise idle lanes, or
+ * 2, 4, 8, 16, 32.  cells_per_grab: 0 = the warp kernel's warps take cells
+ * by static striding, 1..1024 = they pull that many cells at a time from an
+ * atomic work counter (a new context uses 4).  LJ_EINVAL for other values. */
+int lj_set_tuning(lj_ctx *ctx, int32_t kernel, int32_t group_width, int32_t cells_per_grab);
 
 /* ---------------------------------------------------------------------- */
 /* Batched ensembles.  nrep independent periodic systems ("replicas") of
@@ -228,8 +232,9 @@ int lj_batch_info(const lj_batch *b, int64_t *ntot, int64_t *ncell, int32_t *gri
 
 /* Tuning: cells a warp takes per pull from the work counter (1..1024),
  * whether steps are graph-replayed (1) or launched directly (0), and the
- * smallest lane-group width (0, 8, 16, 32). */
-int lj_batch_set_tuning(lj_batch *b, int32_t cells_per_grab, int32_t use_graph, int32_t gmin);
+ * lane-group width of the warp kernel (0 = per cell, 2, 4, 8, 16, 32; as in
+ * lj_set_tuning). */
+int lj_batch_set_tuning(lj_batch *b, int32_t cells_per_grab, int32_t use_graph, int32_t group_width);
 
 /* Forces of every replica at x into f (device arrays as above); with
  * energy != 0, f[:, 3] holds per-particle energies.  Asynchronous. */

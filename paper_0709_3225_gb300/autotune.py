@@ -1,12 +1,14 @@
 """Autotuner for the force kernels' launch choices.
 
 It picks, by timing velocity-Verlet steps on a copy of the state:
-  single systems  -- force kernel (warp-per-cell with the velocity-Verlet
+  single systems  -- cell subdivision k (cell side >= rc / k: 1, the 27-cell
+                     stencil, or 2, the 125-cell stencil of half-size cells),
+                     force kernel (warp-per-cell with the velocity-Verlet
                      update separate or fused into it, run kernel with
-                     bulk-copy staging, run kernel reading global memory) and the
-                     smallest lane-group width of the warp kernel (threads
-                     per cell: the group of lanes that owns a cell's
-                     particles);
+                     bulk-copy staging, run kernel reading global memory),
+                     the lane-group width of the warp kernel (home particles
+                     per chunk; 0 = chosen per cell) and the cells per pull
+                     from its work counter (0 = static striding);
   batches         -- cells per pull from the work counter, lane-group width,
                      graph replay or direct launches.
 Choices are cached in a JSON file keyed by (GPU name, kind, N bucket, density
@@ -81,41 +83,94 @@ def _time_steps(run, steps: int, warmup: int) -> float:
 
 def system_candidates(precision: str) -> list[dict]:
     if precision == "fp64":
-        return [{"kernel": 1, "gmin": 0, "grab": 0}, {"kernel": 2, "gmin": 0, "grab": 0}]
-    warp = [{"kernel": 3, "gmin": g, "grab": c} for g in (0, 16) for c in (0, 1, 4)]
-    return warp + [{"kernel": 3, "gmin": 32, "grab": 0}, {"kernel": 0, "gmin": 0, "grab": 1},
-                   {"kernel": 1, "gmin": 0, "grab": 0}, {"kernel": 2, "gmin": 0, "grab": 0}]
+        return [{"subdiv": 1, "kernel": k, "gw": 0, "grab": 0} for k in (1, 2)]
+    warp = [{"subdiv": 1, "kernel": 3, "gw": g, "grab": c} for g in (0, 4, 8, 16) for c in (0, 4)]
+    return warp + [{"subdiv": 1, "kernel": 0, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 1, "gw": 0, "grab": 0},
+                   {"subdiv": 1, "kernel": 2, "gw": 0, "grab": 0}, {"subdiv": 2, "kernel": 3, "gw": 0, "grab": 4},
+                   {"subdiv": 2, "kernel": 3, "gw": 2, "grab": 4}]
+
+
+def _apply(system: lj.System, choice: dict) -> None:
+    lj.lj_set_tuning(system.ctx, choice["kernel"], choice["gw"], choice["grab"])
+
+
+def _clone_system(system: lj.System, subdiv: int) -> lj.System:
+    p = system.params
+    prec = "fp64" if p.precision == lj.LJ_PREC_FP64 else "mixed"
+    return lj.System(system.x.cpu().numpy(), system.v.cpu().numpy(), p.box, eps=p.eps, sigma=p.sigma, rc=p.rc,
+                     dt=p.dt, mass=p.mass, shift_mode=p.shift_mode, precision=prec, flags=p.flags,
+                     cell_subdiv=subdiv, device=system.x.device)
 
 
 def tune_system(system: lj.System, rho: float, steps: int = 10, warmup: int = 3, use_cache: bool = True,
                 path: str | None = None) -> dict:
-    """Choose and apply the fastest force-kernel setting for ``system``."""
+    """Time every candidate setting and apply the fastest one that ``system``
+    can take.  A subdivision other than the system's is timed on a temporary
+    copy; when it wins, the returned choice names it (``make_system`` then
+    builds the system with it) and ``system`` gets the best setting of its own
+    subdivision."""
     precision = "fp64" if system.params.precision == lj.LJ_PREC_FP64 else "mixed"
     key = bucket_key(f"system-{precision}", system.n, rho)
+    own = system.params.cell_subdiv or 1
     if use_cache:
         hit = load_cache(path).get(key)
-        if hit:
-            lj.lj_set_tuning(system.ctx, hit["kernel"], hit["gmin"], hit.get("grab", 0))
+        if hit and hit.get("subdiv", 1) == own:
+            _apply(system, hit)
             return dict(hit, cached=True)
-    x, v, f = system.x.clone(), system.v.clone(), system.f.clone()
-    lj.lj_forces(system.ctx, x, f)
     results = []
-    for cand in system_candidates(precision):
-        lj.lj_set_tuning(system.ctx, cand["kernel"], cand["gmin"], cand["grab"])
-        ms = _time_steps(lambda k: lj.lj_step(system.ctx, x, v, f, k), steps, warmup)
-        results.append(dict(cand, ms_per_step=ms))
-    lj.lj_check(system.ctx)
+    copies = {own: system}
+    try:
+        for cand in system_candidates(precision):
+            sub = cand["subdiv"]
+            if sub not in copies:
+                try:
+                    copies[sub] = _clone_system(system, sub)
+                except lj.LJError:      # box too small for that subdivision
+                    copies[sub] = None
+            target = copies[sub]
+            if target is None:
+                continue
+            x, v, f = target.x.clone(), target.v.clone(), target.f.clone()
+            _apply(target, cand)
+            lj.lj_forces(target.ctx, x, f)
+            ms = _time_steps(lambda k: lj.lj_step(target.ctx, x, v, f, k), steps, warmup)
+            lj.lj_check(target.ctx)
+            results.append(dict(cand, ms_per_step=ms))
+    finally:
+        for sub, t in copies.items():
+            if sub != own and t is not None:
+                t.close()
     best = min(results, key=lambda r: r["ms_per_step"])
-    lj.lj_set_tuning(system.ctx, best["kernel"], best["gmin"], best["grab"])
-    choice = {"kernel": best["kernel"], "gmin": best["gmin"], "grab": best["grab"],
-              "ms_per_step": best["ms_per_step"]}
+    best_own = min((r for r in results if r["subdiv"] == own), key=lambda r: r["ms_per_step"])
+    _apply(system, best_own)
+    choice = {k: best[k] for k in ("subdiv", "kernel", "gw", "grab", "ms_per_step")}
     store_cache(key, choice, path)
     return dict(choice, cached=False, trials=results)
 
 
+def make_system(x, v, box: float, rho: float, *, use_cache: bool = True, path: str | None = None, **kw):
+    """A tuned lj.System for (x, v, box): built with the subdivision the
+    tuner chose (timing once if the cache has no entry), tuning applied.
+    Returns (system, choice)."""
+    precision = kw.get("precision", "mixed")
+    if use_cache:
+        hit = load_cache(path).get(bucket_key(f"system-{precision}", int(len(x)), rho))
+        if hit:
+            s = lj.System(x, v, box, cell_subdiv=hit.get("subdiv", 1), **kw)
+            _apply(s, hit)
+            return s, dict(hit, cached=True)
+    s = lj.System(x, v, box, **kw)
+    choice = tune_system(s, rho, use_cache=False, path=path)
+    if choice.get("subdiv", 1) != (s.params.cell_subdiv or 1):
+        s.close()
+        s = lj.System(x, v, box, cell_subdiv=choice["subdiv"], **kw)
+        _apply(s, choice)
+    return s, choice
+
+
 def batch_candidates() -> list[dict]:
-    out = [{"cells_per_grab": c, "gmin": g, "graph": True} for c in (1, 2, 4, 8, 16) for g in (0, 16)]
-    out.append({"cells_per_grab": 4, "gmin": 0, "graph": False})
+    out = [{"cells_per_grab": c, "gw": g, "graph": True} for c in (1, 2, 4, 8, 16) for g in (0, 8)]
+    out.append({"cells_per_grab": 4, "gw": 0, "graph": False})
     return out
 
 
@@ -126,12 +181,12 @@ def tune_batch(batch: lj.Batch, rho: float, steps: int = 10, warmup: int = 3, us
     if use_cache:
         hit = load_cache(path).get(key)
         if hit:
-            batch.set_tuning(hit["cells_per_grab"], hit["graph"], hit["gmin"])
+            batch.set_tuning(hit["cells_per_grab"], hit["graph"], hit["gw"])
             return dict(hit, cached=True)
     saved = (batch.x.clone(), batch.v.clone(), batch.f.clone(), batch._forces_valid)
     results = []
     for cand in batch_candidates():
-        batch.set_tuning(cand["cells_per_grab"], cand["graph"], cand["gmin"])
+        batch.set_tuning(cand["cells_per_grab"], cand["graph"], cand["gw"])
         ms = _time_steps(batch.step, steps, warmup)
         results.append(dict(cand, ms_per_step=ms))
     batch.check()
@@ -140,7 +195,7 @@ def tune_batch(batch: lj.Batch, rho: float, steps: int = 10, warmup: int = 3, us
     batch.f.copy_(saved[2])
     batch._forces_valid = saved[3]
     best = min(results, key=lambda r: r["ms_per_step"])
-    batch.set_tuning(best["cells_per_grab"], best["graph"], best["gmin"])
-    choice = {k: best[k] for k in ("cells_per_grab", "gmin", "graph", "ms_per_step")}
+    batch.set_tuning(best["cells_per_grab"], best["graph"], best["gw"])
+    choice = {k: best[k] for k in ("cells_per_grab", "gw", "graph", "ms_per_step")}
     store_cache(key, choice, path)
     return dict(choice, cached=False, trials=results)

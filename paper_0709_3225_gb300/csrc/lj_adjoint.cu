@@ -54,7 +54,7 @@ __global__ void k_gather_cotangent(const double *__restrict__ g, const int32_t *
     g4[s] = q;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int R>
 __global__ void __launch_bounds__(kVjpThreads) k_vjp(int n, int nc, int64_t ncell, double cw_d, VjpCoef kd,
                                                      const typename Vec4<T>::type *__restrict__ pos,
                                                      const typename Vec4<T>::type *__restrict__ g4,
@@ -62,44 +62,50 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp(int n, int nc, int64_t ncel
                                                      double *__restrict__ dx, double *__restrict__ partial)
 {
     using V = typename Vec4<T>::type;
+    constexpr int NS = Stencil<R>::NS;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const T cw = (T)cw_d, rc2 = (T)kd.rc2, a1 = (T)kd.a1, b1 = (T)kd.b1, fc1 = (T)kd.fc1, dfc1 = (T)kd.dfc1;
     const T eps = (T)kd.eps, isg = (T)kd.inv_sigma;
     double acc_e = 0.0, acc_s = 0.0;
     const int64_t nwarps = (int64_t)gridDim.x * (kVjpThreads / 32);
+    // stencil entry kk of home cell (cx, cy, cz): first particle, count, shift
+    auto entry = [&](int kk, int cx, int cy, int cz, int &s, int &nn, T &shx, T &shy, T &shz) {
+        int ddx, ddy, ddz;
+        stencil_delta<R>(kk, ddx, ddy, ddz);
+        int ux = cx + ddx, uy = cy + ddy, uz = cz + ddz;
+        ux += ux < 0 ? nc : 0;
+        ux -= ux >= nc ? nc : 0;
+        uy += uy < 0 ? nc : 0;
+        uy -= uy >= nc ? nc : 0;
+        uz += uz < 0 ? nc : 0;
+        uz -= uz >= nc ? nc : 0;
+        const int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
+        s = start[cn];
+        nn = start[cn + 1] - s;
+        shx = (T)ddx * cw;
+        shy = (T)ddy * cw;
+        shz = (T)ddz * cw;
+    };
     for (int64_t c = (int64_t)blockIdx.x * (kVjpThreads / 32) + warp; c < ncell; c += nwarps) {
         const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
-        int s_k = 0, n_k = 0, dxk = 0, dyk = 0, dzk = 0;
-        if (lane < 27) {
-            dxk = lane % 3 - 1;
-            dyk = (lane / 3) % 3 - 1;
-            dzk = lane / 9 - 1;
-            int ux = cx + dxk, uy = cy + dyk, uz = cz + dzk;
-            ux += ux < 0 ? nc : 0;
-            ux -= ux >= nc ? nc : 0;
-            uy += uy < 0 ? nc : 0;
-            uy -= uy >= nc ? nc : 0;
-            uz += uz < 0 ? nc : 0;
-            uz -= uz >= nc ? nc : 0;
-            const int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
-            s_k = start[cn];
-            n_k = start[cn + 1] - s_k;
-        }
-        const int s_home = __shfl_sync(0xffffffffu, s_k, 13);
-        const int n_home = __shfl_sync(0xffffffffu, n_k, 13);
+        int s_home, n_home;
+        T h0, h1, h2;
+        entry(0, cx, cy, cz, s_home, n_home, h0, h1, h2);
         for (int p0 = 0; p0 < n_home; p0 += 32) {
             const int i = p0 + lane;
             const bool vi = i < n_home;
             const V pi = pos[s_home + (vi ? i : 0)];
             const V gi = g4[s_home + (vi ? i : 0)];
-            T ax = 0, ay = 0, az = 0, ae = 0, as = 0;
-            for (int kk = 0; kk < 27; kk++) {
-                const int s = __shfl_sync(0xffffffffu, s_k, kk);
-                const int nn = __shfl_sync(0xffffffffu, n_k, kk);
-                const T xs = pi.x - (T)__shfl_sync(0xffffffffu, dxk, kk) * cw;
-                const T ys = pi.y - (T)__shfl_sync(0xffffffffu, dyk, kk) * cw;
-                const T zs = pi.z - (T)__shfl_sync(0xffffffffu, dzk, kk) * cw;
+            T ax = 0, ay = 0, az = 0;
+            double ae = 0.0, as = 0.0;   // parameter sums over pairs: FP64 (cancelling sums of FP32 terms)
+            for (int kk = 0; kk < NS; kk++) {
+                int s, nn;
+                T shx, shy, shz;
+                entry(kk, cx, cy, cz, s, nn, shx, shy, shz);
+                const T xs = pi.x - shx;
+                const T ys = pi.y - shy;
+                const T zs = pi.z - shz;
                 for (int j = 0; j < nn; j++) {
                     const V qj = pos[s + j];
                     const V gj = g4[s + j];
@@ -130,8 +136,8 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp(int n, int nc, int64_t ncel
                     ax += phi * gx + dphi * dot * dx_;
                     ay += phi * gy + dphi * dot * dy_;
                     az += phi * gz + dphi * dot * dz_;
-                    ae += phi1 * gid;
-                    as += eps * dsig1 * gid;
+                    ae += (double)(phi1 * gid);
+                    as += (double)(eps * dsig1 * gid);
                 }
             }
             if (vi) {
@@ -145,8 +151,8 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp(int n, int nc, int64_t ncel
                     dx[3 * (int64_t)idx] += scale * (double)ax;
                     dx[3 * (int64_t)idx + 1] += scale * (double)ay;
                     dx[3 * (int64_t)idx + 2] += scale * (double)az;
-                    acc_e += (double)ae;
-                    acc_s += (double)as;
+                    acc_e += ae;
+                    acc_s += as;
                 }
             }
         }
@@ -205,10 +211,11 @@ __global__ void k_axpy(double *__restrict__ y, const double *__restrict__ x, dou
 }
 
 template <typename T>
-void *vjp_kernel(int mode)
+void *vjp_kernel(int mode, int subdiv)
 {
-    if (mode == 2) return (void *)k_vjp<T, 2>;
-    return (void *)k_vjp<T, 0>;   // modes 0 and 1 have the same force
+    // modes 0 and 1 have the same force
+    if (subdiv == 2) return mode == 2 ? (void *)k_vjp<T, 2, 2> : (void *)k_vjp<T, 0, 2>;
+    return mode == 2 ? (void *)k_vjp<T, 2, 1> : (void *)k_vjp<T, 0, 1>;
 }
 
 }  // namespace
@@ -216,8 +223,8 @@ void *vjp_kernel(int mode)
 int vjp_grid(lj_ctx *c)
 {
     int nb = 0;
-    void *kern = c->p.precision == LJ_PREC_FP64 ? vjp_kernel<double>(c->p.shift_mode)
-                                                : vjp_kernel<float>(c->p.shift_mode);
+    void *kern = c->p.precision == LJ_PREC_FP64 ? vjp_kernel<double>(c->p.shift_mode, c->p.cell_subdiv)
+                                                : vjp_kernel<float>(c->p.shift_mode, c->p.cell_subdiv);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kVjpThreads, 0) != cudaSuccess || nb < 1) nb = 1;
     int64_t need = (c->ncell + kVjpThreads / 32 - 1) / (kVjpThreads / 32);
     int64_t grid = (int64_t)nb * c->nsm;
@@ -248,27 +255,18 @@ cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, dou
     k.inv_sigma = 1.0 / sg;
     const int grid = vjp_grid(c);
     if (grid > c->npartial_cap) return cudaErrorInvalidValue;
-    if (fp64) {
-        if (c->p.shift_mode == 2)
-            k_vjp<double, 2><<<grid, kVjpThreads, 0, c->stream>>>(n, c->nc, c->ncell, c->cw, k,
-                                                                  (const double4_16a *)c->pos,
-                                                                  (const double4_16a *)c->g4, c->start, scale, dx,
-                                                                  c->partial);
-        else
-            k_vjp<double, 0><<<grid, kVjpThreads, 0, c->stream>>>(n, c->nc, c->ncell, c->cw, k,
-                                                                  (const double4_16a *)c->pos,
-                                                                  (const double4_16a *)c->g4, c->start, scale, dx,
-                                                                  c->partial);
-    } else {
-        if (c->p.shift_mode == 2)
-            k_vjp<float, 2><<<grid, kVjpThreads, 0, c->stream>>>(n, c->nc, c->ncell, c->cw, k, (const float4 *)c->pos,
-                                                                 (const float4 *)c->g4, c->start, scale, dx,
-                                                                 c->partial);
-        else
-            k_vjp<float, 0><<<grid, kVjpThreads, 0, c->stream>>>(n, c->nc, c->ncell, c->cw, k, (const float4 *)c->pos,
-                                                                 (const float4 *)c->g4, c->start, scale, dx,
-                                                                 c->partial);
-    }
+    void *kern = fp64 ? vjp_kernel<double>(c->p.shift_mode, c->p.cell_subdiv)
+                      : vjp_kernel<float>(c->p.shift_mode, c->p.cell_subdiv);
+    int nc = c->nc;
+    int64_t ncell = c->ncell;
+    double cw = c->cw;
+    const void *pos = c->pos;
+    const void *g4 = c->g4;
+    const int32_t *start = c->start;
+    double *partial = c->partial;
+    void *args[] = {(void *)&n, &nc, &ncell, &cw, &k, (void *)&pos, (void *)&g4, (void *)&start, &scale, &dx, &partial};
+    cudaError_t e = cudaLaunchKernel(kern, dim3(grid), dim3(kVjpThreads), args, 0, c->stream);
+    if (e != cudaSuccess) return e;
     k_accum_params<<<1, kReduceThreads, 0, c->stream>>>(c->partial, grid, scale, dparam);
     c->kernel_launches += 2;
     return cudaGetLastError();

@@ -44,10 +44,12 @@ int validate(const lj_params *p, int *nc_out)
     if (!isfinite(p->dt)) return LJ_EINVAL;
     if (p->shift_mode < LJ_SHIFT_NONE || p->shift_mode > LJ_SHIFT_FORCE) return LJ_EINVAL;
     if (p->precision != LJ_PREC_MIXED && p->precision != LJ_PREC_FP64) return LJ_EINVAL;
-    if (p->cell_subdiv != 0 && p->cell_subdiv != 1) return LJ_EINVAL;
+    if (p->cell_subdiv < 0 || p->cell_subdiv > 2) return LJ_EINVAL;
+    // subdivision 2 runs on the warp kernel only (FP32-mixed, no run-kernel flag)
+    if (p->cell_subdiv == 2 && (p->precision != LJ_PREC_MIXED || p->flags != 0)) return LJ_EINVAL;
     if ((p->flags & ~(LJ_FLAG_RUN_STAGED | LJ_FLAG_RUN_DIRECT)) != 0) return LJ_EINVAL;
     if ((p->flags & LJ_FLAG_RUN_STAGED) && (p->flags & LJ_FLAG_RUN_DIRECT)) return LJ_EINVAL;
-    const int k = 1;
+    const int k = p->cell_subdiv == 2 ? 2 : 1;
     double q = floor(((double)k * p->box) / p->rc);
     if (!(q >= 2.0 * k + 1.0)) return LJ_EBOX;
     if (q > 1290.0) return LJ_EOVERFLOW;   // nc^3 + 1 must fit in int32
@@ -483,18 +485,21 @@ extern "C" int lj_vv_adjoint_step(lj_ctx *c, const double *x_n, const double *x_
     return LJ_OK;
 }
 
-extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t gmin, int32_t cells_per_grab)
+extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int32_t cells_per_grab)
 {
     if (!c || kernel < 0 || kernel > 3 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
-    if (gmin != 0 && gmin != 8 && gmin != 16 && gmin != 32) return LJ_EINVAL;
+    if (group_width != 0 && group_width != 2 && group_width != 4 && group_width != 8 && group_width != 16 &&
+        group_width != 32)
+        return LJ_EINVAL;
     const bool warp = kernel == 0 || kernel == 3;
     if (warp && c->p.precision == LJ_PREC_FP64) return LJ_EINVAL;   // warp kernel is FP32-mixed
+    if (!warp && c->p.cell_subdiv == 2) return LJ_EINVAL;            // run kernels: 27-cell stencil only
     if (warp && c->wforce_grid == 0) LJ_CK(warp_force_configure(c));
     c->use_run_kernel = warp ? 0 : 1;
     c->fuse_update = kernel == 0 ? 1 : 0;
     c->grab = cells_per_grab;
     c->use_tma = kernel == 2 ? 0 : 1;
-    c->gmin = gmin;
+    c->gw = group_width;
     return LJ_OK;
 }
 

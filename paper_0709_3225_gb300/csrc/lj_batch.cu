@@ -257,9 +257,7 @@ __device__ void phase_force(const BatchDev &b, const WarpParams &k, float4 *__re
     extern __shared__ __align__(16) float bsmem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float *X = bsmem + (size_t)warp * 3 * k.cap;
-    float *Y = X + k.cap;
-    float *Z = Y + k.cap;
+    float *slice = bsmem + (size_t)warp * warp_slice_words(k.cap, 1);
     double eacc = 0.0, wacc = 0.0;
     for (;;) {
         unsigned c0 = 0;
@@ -273,8 +271,8 @@ __device__ void phase_force(const BatchDev &b, const WarpParams &k, float4 *__re
             int cx, cy, cz;
             decode_cell((int)(c - b.coff[r]), nc, cx, cy, cz);
             const StoreForce<MODE, ENERGY> out{f, k.n};
-            process_home_cell<MODE, ENERGY, false>(k, b.pos, b.start, out, X, Y, Z, cx, cy, cz, nc, b.coff[r],
-                                                   (float)b.cw[r], eacc, wacc);
+            process_home_cell<1, MODE, ENERGY, false>(k, b.pos, b.start, out, slice, cx, cy, cz, nc, b.coff[r],
+                                                      (float)b.cw[r], eacc, wacc);
         }
     }
 }
@@ -440,13 +438,11 @@ void batch_free(lj_batch *b)
 
 cudaError_t configure(lj_batch *b)
 {
-    // Staging capacity for the densest replica, capped so that 4 CTAs fit.
-    int cap = (int)(1.5 * 27.0 * b->max_mean_occ) + 64;
-    cap = (cap + 7) & ~7;
-    const int cap_max = ((227 * 1024 / 4 - 2048) / ((kBatchThreads / 32) * 3 * (int)sizeof(float))) & ~7;
-    cap = cap > cap_max ? cap_max : cap;
+    // Staging capacity for the densest replica (static shared memory of the
+    // scan phases: at most 2 KB).
+    const int cap = warp_stencil_cap(b->max_mean_occ, 1, kBatchThreads, 2048);
     b->k.cap = cap;
-    b->smem = (kBatchThreads / 32) * 3 * cap * (int)sizeof(float);
+    b->smem = (kBatchThreads / 32) * warp_slice_words(cap, 1) * (int)sizeof(float);
     int minblk = 1 << 30;
     for (int mode = 0; mode < 3; mode++)
         for (int en = 0; en < 2; en++) {
@@ -654,7 +650,7 @@ extern "C" int lj_batch_create(lj_batch **out, int32_t nrep, const int64_t *n, c
     LJ_BCK(cudaMemset(d.first, 1, 1));
 
     WarpParams &k = b->k;
-    k.gmin = 0;
+    k.gw = 0;
     k.n = (int)ntot;
     k.nc = 0;
     k.ncell = ncell;
@@ -693,12 +689,14 @@ extern "C" int lj_batch_info(const lj_batch *b, int64_t *ntot, int64_t *ncell, i
     return LJ_OK;
 }
 
-extern "C" int lj_batch_set_tuning(lj_batch *b, int32_t cells_per_grab, int32_t use_graph, int32_t gmin)
+extern "C" int lj_batch_set_tuning(lj_batch *b, int32_t cells_per_grab, int32_t use_graph, int32_t group_width)
 {
     if (!b || cells_per_grab < 1 || cells_per_grab > 1024) return LJ_EINVAL;
-    if (gmin != 0 && gmin != 8 && gmin != 16 && gmin != 32) return LJ_EINVAL;
+    if (group_width != 0 && group_width != 2 && group_width != 4 && group_width != 8 && group_width != 16 &&
+        group_width != 32)
+        return LJ_EINVAL;
     b->d.cells_per_grab = cells_per_grab;
-    b->k.gmin = gmin;
+    b->k.gw = group_width;
     b->use_graph = use_graph ? 1 : 0;
     if (b->gexec) {
         cudaGraphExecDestroy(b->gexec);

@@ -1,6 +1,7 @@
 // Device code shared by the single-system and batched warp-per-cell force
 // kernels (see lj_force_warp.cu for the design): the packed pair math, the
-// staging of one home cell's stencil and the plain fallback path.
+// stencil table, the staging of one home cell's stencil, the chunked
+// compute phase and the plain fallback path.
 #pragma once
 
 #include "lj_internal.cuh"
@@ -8,10 +9,11 @@
 namespace {
 
 constexpr float kFar = 1.0e4f;   // padding candidate: r^2 ~ 1e8 > rc^2
+constexpr int kStageBatch = 4;   // staging rounds whose loads are in flight together
 
 struct WarpParams {
-    int n, nc, cap;              // cap: staged candidates per warp (multiple of 8)
-    int gmin;                    // smallest lane-group width to use (0, 8, 16 or 32)
+    int n, nc, cap;              // cap: staged candidates per warp (multiple of 8, >= 40)
+    int gw;                      // lane-group width of the compute phase (0 = per-cell choice, 2 .. 32)
     int grab;                    // cells per pull from *work (0 = static striding)
     unsigned *work;              // work counter, zero at launch
     int64_t ncell;
@@ -123,26 +125,6 @@ __device__ __forceinline__ void pair1(float dx, float dy, float dz, const WarpPa
     }
 }
 
-// Stencil slot k = 0 is the home cell, k = 1..26 the neighbours.
-__device__ __forceinline__ void stencil_offset(int k, int &dx, int &dy, int &dz)
-{
-    const int idx = k == 0 ? 13 : (k <= 13 ? k - 1 : k);
-    dx = idx % 3 - 1;
-    dy = (idx / 3) % 3 - 1;
-    dz = idx / 9 - 1;
-}
-
-// Position of flat candidate j in the interleaved SoA layout for S streams.
-template <int S>
-__device__ __forceinline__ int slot_of(int j)
-{
-    const int m = j / (2 * S);
-    const int r = j - m * 2 * S;
-    const int s = r % S;
-    const int h = r / S;
-    return 2 * (m * S + s) + h;
-}
-
 // Output of one home particle's result, called by all 32 lanes of the warp
 // (valid = this lane holds a particle's final sums).  StoreForce writes the
 // force (and its energy share); KickDriftBin applies the velocity-Verlet
@@ -226,23 +208,113 @@ struct KickDriftBin {
     }
 };
 
-// Fast path: staged flat list, G lanes per group, S = 32 / G groups.
+// 32-bit words of one warp's shared-memory slice: staged X, Y, Z (cap each),
+// the stencil table (float4 per entry: shift xyz, start index) and the
+// stencil prefix sums (NS + 1 ints, padded to 4).
+__host__ __device__ constexpr int warp_slice_words(int cap, int R)
+{
+    return 3 * cap + 4 * (2 * R + 1) * (2 * R + 1) * (2 * R + 1) +
+           (((2 * R + 1) * (2 * R + 1) * (2 * R + 1) + 1 + 3) & ~3);
+}
+
+// Lane-group width of the compute phase: the warp takes the home particles
+// in chunks of G; lane g of a group owns particle g of the chunk and the
+// S = 32 / G groups split the candidates (group s takes candidate pairs
+// s, s + S, s + 2S, ...).  Automatic choice: the G in {2, 4, 8, 16} with the
+// fewest candidate-pair iterations (a chunk's stream reduction and set-up
+// count as about one iteration).
+__device__ __forceinline__ int choose_group(int n_home, int T, int fixed)
+{
+    if (fixed) return fixed;
+    int best = 4, best_cost = 1 << 30;
+#pragma unroll
+    for (int lg = 1; lg <= 4; lg++) {
+        const int G = 1 << lg;
+        const int chunks = (n_home + G - 1) / G;
+        const int cost = chunks * ((T * G + 63) / 64 + 1);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = G;
+        }
+    }
+    return best;
+}
+
+// Compute phase over the staged list: candidates 0 .. T-1 (home particles
+// first, 0 .. n_home-1), padded with far points to a multiple of 2S.
+// Home particle p sits at staged position p (coordinates in shared memory);
+// its particle index is in lane p's hid for p < 32, else read from pos.
 template <int G, int MODE, bool ENERGY, bool NC, class Out>
-__device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *__restrict__ pos, const Out &out,
-                                            float *X, float *Y, float *Z, int s_k,
-                                            int n_k, float sx, float sy, float sz, int s_home, int n_home,
-                                            double &eacc, double &wacc)
+__device__ __forceinline__ void compute_chunks(const WarpParams &k, const float4 *__restrict__ pos, const Out &out,
+                                               const float *X, const float *Y, const float *Z, int T, int s_home,
+                                               int n_home, int hid, double &eacc, double &wacc)
 {
     constexpr int S = 32 / G;
     const int lane = threadIdx.x & 31;
-    // Home particles (lane e holds home particle e) and their bounding box in
-    // the home-centre frame.  Stencil candidates farther than rc from the box
-    // cannot interact with any home particle and are not staged (the margin
-    // covers FP32 rounding of the box test).
-    const bool hl = lane < n_home;
-    const float4 ph = load_pos<NC>(pos + s_home + (hl ? lane : 0));
-    float bxl = hl ? ph.x : 3.4e38f, byl = hl ? ph.y : 3.4e38f, bzl = hl ? ph.z : 3.4e38f;
-    float bxh = hl ? ph.x : -3.4e38f, byh = hl ? ph.y : -3.4e38f, bzh = hl ? ph.z : -3.4e38f;
+    const int gl = lane % G;
+    const int sg = lane / G;
+    const int iters = (T + 2 * S - 1) / (2 * S);
+    const int ihome = (n_home + 2 * S - 1) / (2 * S);   // iterations that may hold i itself
+    const float2 *X2 = reinterpret_cast<const float2 *>(X) + sg;
+    const float2 *Y2 = reinterpret_cast<const float2 *>(Y) + sg;
+    const float2 *Z2 = reinterpret_cast<const float2 *>(Z) + sg;
+    for (int c0 = 0; c0 < n_home; c0 += G) {
+        const int p = c0 + gl;
+        const bool vi = p < n_home;
+        const int pp = vi ? p : 0;
+        const float2 xs = f2(X[pp]), ys = f2(Y[pp]), zs = f2(Z[pp]);
+        int idx = __shfl_sync(0xffffffffu, hid, pp & 31);
+        if (pp >= 32) idx = __float_as_int(load_pos<NC>(pos + s_home + pp).w);
+        float2 fx = f2(0.f), fy = f2(0.f), fz = f2(0.f), e = f2(0.f), w = f2(0.f);
+        int m = 0;
+        for (; m < ihome; m++)
+            pair2<MODE, ENERGY, true>(xs, ys, zs, X2[m * S], Y2[m * S], Z2[m * S], k, fx, fy, fz, e, w);
+#pragma unroll 4
+        for (; m < iters; m++)
+            pair2<MODE, ENERGY, false>(xs, ys, zs, X2[m * S], Y2[m * S], Z2[m * S], k, fx, fy, fz, e, w);
+        float Fx = fx.x + fx.y, Fy = fy.x + fy.y, Fz = fz.x + fz.y, E = e.x + e.y, Wv = w.x + w.y;
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) {
+            Fx += __shfl_xor_sync(0xffffffffu, Fx, o);
+            Fy += __shfl_xor_sync(0xffffffffu, Fy, o);
+            Fz += __shfl_xor_sync(0xffffffffu, Fz, o);
+            if constexpr (ENERGY) {
+                E += __shfl_xor_sync(0xffffffffu, E, o);
+                Wv += __shfl_xor_sync(0xffffffffu, Wv, o);
+            }
+        }
+        out(idx, sg == 0 && vi, Fx, Fy, Fz, E, Wv, eacc, wacc);
+    }
+}
+
+// Staged path.  The stencil's candidates are taken as one flat index space
+// t = 0 .. Ttot-1 (lane l takes t = l, l + 32, ...; the stencil entry of t is
+// found by binary search in the prefix sums), converted to the home-cell
+// frame and kept only if within rc of the home particles' bounding box (the
+// margin covers FP32 rounding of the box test).  Kept candidates are
+// appended in ballot order, so the home particles (entry 0, all inside the
+// box) occupy 0 .. n_home-1.
+template <int R, int MODE, bool ENERGY, bool NC, class Out>
+__device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *__restrict__ pos, const Out &out,
+                                            float *X, float *Y, float *Z, const float4 *stab, const int *spre,
+                                            int Ttot, int s_home, int n_home, double &eacc, double &wacc)
+{
+    constexpr int NS = Stencil<R>::NS, P2 = Stencil<R>::P2;
+    const int lane = threadIdx.x & 31;
+    float bxl = 3.4e38f, byl = 3.4e38f, bzl = 3.4e38f, bxh = -3.4e38f, byh = -3.4e38f, bzh = -3.4e38f;
+    int hid = 0;   // particle index of home particle `lane`
+    for (int p0 = 0; p0 < n_home; p0 += 32) {
+        if (p0 + lane < n_home) {
+            const float4 q = load_pos<NC>(pos + s_home + p0 + lane);
+            if (p0 == 0) hid = __float_as_int(q.w);
+            bxl = fminf(bxl, q.x);
+            byl = fminf(byl, q.y);
+            bzl = fminf(bzl, q.z);
+            bxh = fmaxf(bxh, q.x);
+            byh = fmaxf(byh, q.y);
+            bzh = fmaxf(bzh, q.z);
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
@@ -252,101 +324,89 @@ __device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *_
         byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
         bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
     }
-    // stage the home cell first (candidates 0 .. n_home-1, all kept)
-    if (hl) {
-        const int sl = slot_of<S>(lane);
-        X[sl] = ph.x;
-        Y[sl] = ph.y;
-        Z[sl] = ph.z;
-    }
-    // then lane k = 1..26 walks stencil cell k; kept candidates are appended
-    // in ballot order
     const float rcut2 = k.rc2 * 1.0001f;
-    const int my_n = (lane >= 1 && lane < 27) ? n_k : 0;
     const unsigned lt = (1u << lane) - 1u;
-    int T = n_home;
-    for (int e = 0; __any_sync(0xffffffffu, e < my_n); e++) {
-        bool keep = false;
-        float cx = 0.f, cy = 0.f, cz = 0.f;
-        if (e < my_n) {
-            const float4 q = load_pos<NC>(pos + s_k + e);
-            cx = q.x + sx;
-            cy = q.y + sy;
-            cz = q.z + sz;
+    int T = 0;
+    // Batches of kStageBatch rounds: the stencil-entry searches and the
+    // position loads of a batch are issued before any of them is used,
+    // so their latencies overlap.
+    for (int t0 = 0; t0 < Ttot; t0 += 32 * kStageBatch) {
+        float4 q[kStageBatch], sh[kStageBatch];
+#pragma unroll
+        for (int u = 0; u < kStageBatch; u++) {
+            const int t = t0 + 32 * u + lane;
+            q[u] = make_float4(kFar, kFar, kFar, 0.f);
+            sh[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < Ttot) {
+                int kc = 0, kb = 0;   // stencil entry of t and its prefix
+#pragma unroll
+                for (int step = P2 / 2; step > 0; step >>= 1) {
+                    const int m = kc + step;
+                    if (m < NS) {
+                        const int v = spre[m];
+                        if (v <= t) {
+                            kc = m;
+                            kb = v;
+                        }
+                    }
+                }
+                sh[u] = stab[kc];
+                q[u] = load_pos<NC>(pos + __float_as_int(sh[u].w) + (t - kb));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStageBatch; u++) {
+            const int t = t0 + 32 * u + lane;
+            const float cx = q[u].x + sh[u].x;
+            const float cy = q[u].y + sh[u].y;
+            const float cz = q[u].z + sh[u].z;
             const float dx = fmaxf(fmaxf(bxl - cx, cx - bxh), 0.f);
             const float dy = fmaxf(fmaxf(byl - cy, cy - byh), 0.f);
             const float dz = fmaxf(fmaxf(bzl - cz, cz - bzh), 0.f);
-            keep = dx * dx + dy * dy + dz * dz < rcut2;
+            const bool keep = t < Ttot && dx * dx + dy * dy + dz * dz < rcut2;
+            const unsigned kept = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int sl = T + __popc(kept & lt);
+                X[sl] = cx;
+                Y[sl] = cy;
+                Z[sl] = cz;
+            }
+            T += __popc(kept);
         }
-        const unsigned kept = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            const int sl = slot_of<S>(T + __popc(kept & lt));
-            X[sl] = cx;
-            Y[sl] = cy;
-            Z[sl] = cz;
-        }
-        T += __popc(kept);
     }
-    const int Tpad = (T + 2 * S - 1) / (2 * S) * (2 * S);
-    if (lane < Tpad - T) {
-        const int sl = slot_of<S>(T + lane);
-        X[sl] = kFar;
-        Y[sl] = kFar;
-        Z[sl] = kFar;
-    }
+    X[T + lane] = kFar;   // padding up to the next multiple of 2S (T + 32 <= cap)
+    Y[T + lane] = kFar;
+    Z[T + lane] = kFar;
     __syncwarp();
-
-    const int gl = lane % G;
-    const int sg = lane / G;
-    const bool vi = gl < n_home;
-    const float4 pi = make_float4(__shfl_sync(0xffffffffu, ph.x, gl), __shfl_sync(0xffffffffu, ph.y, gl),
-                                  __shfl_sync(0xffffffffu, ph.z, gl), __shfl_sync(0xffffffffu, ph.w, gl));
-    const float2 xs = f2(pi.x), ys = f2(pi.y), zs = f2(pi.z);
-    float2 fx = f2(0.f), fy = f2(0.f), fz = f2(0.f), e = f2(0.f), w = f2(0.f);
-    const int iters = Tpad / (2 * S);
-    const int ihome = (n_home + 2 * S - 1) / (2 * S);   // iterations that may hold i itself
-    const float2 *X2 = reinterpret_cast<const float2 *>(X) + sg;
-    const float2 *Y2 = reinterpret_cast<const float2 *>(Y) + sg;
-    const float2 *Z2 = reinterpret_cast<const float2 *>(Z) + sg;
-    int m = 0;
-    for (; m < ihome; m++)
-        pair2<MODE, ENERGY, true>(xs, ys, zs, X2[m * S], Y2[m * S], Z2[m * S], k, fx, fy, fz, e, w);
-#pragma unroll 4
-    for (; m < iters; m++)
-        pair2<MODE, ENERGY, false>(xs, ys, zs, X2[m * S], Y2[m * S], Z2[m * S], k, fx, fy, fz, e, w);
-    float Fx = fx.x + fx.y, Fy = fy.x + fy.y, Fz = fz.x + fz.y, E = e.x + e.y, Wv = w.x + w.y;
-#pragma unroll
-    for (int o = G; o < 32; o <<= 1) {
-        Fx += __shfl_xor_sync(0xffffffffu, Fx, o);
-        Fy += __shfl_xor_sync(0xffffffffu, Fy, o);
-        Fz += __shfl_xor_sync(0xffffffffu, Fz, o);
-        if constexpr (ENERGY) {
-            E += __shfl_xor_sync(0xffffffffu, E, o);
-            Wv += __shfl_xor_sync(0xffffffffu, Wv, o);
-        }
+    switch (choose_group(n_home, T, k.gw)) {
+        case 2: compute_chunks<2, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+        case 4: compute_chunks<4, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+        case 8: compute_chunks<8, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+        case 16: compute_chunks<16, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+        default: compute_chunks<32, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
     }
-    out(__float_as_int(pi.w), sg == 0 && vi, Fx, Fy, Fz, E, Wv, eacc, wacc);
-    __syncwarp();   // the slice is reused by the next cell
 }
 
 // Plain path: any occupancy; each stencil cell read from global memory with
 // the home particle shifted into that cell's frame.
-template <int MODE, bool ENERGY, bool NC, class Out>
-__device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, const Out &out, int s_k,
-                           int n_k, float sx, float sy, float sz, int s_home, int n_home, double &eacc, double &wacc)
+template <int R, int MODE, bool ENERGY, bool NC, class Out>
+__device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, const Out &out, const float4 *stab,
+                           const int *spre, int s_home, int n_home, double &eacc, double &wacc)
 {
+    constexpr int NS = Stencil<R>::NS;
     const int lane = threadIdx.x & 31;
     for (int p0 = 0; p0 < n_home; p0 += 32) {
         const int i = p0 + lane;
         const bool vi = i < n_home;
         const float4 pi = load_pos<NC>(pos + s_home + (vi ? i : 0));
         float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, w = 0.f;
-        for (int kk = 0; kk < 27; kk++) {
-            const int s = __shfl_sync(0xffffffffu, s_k, kk);
-            const int nn = __shfl_sync(0xffffffffu, n_k, kk);
-            const float xs = pi.x - __shfl_sync(0xffffffffu, sx, kk);
-            const float ys = pi.y - __shfl_sync(0xffffffffu, sy, kk);
-            const float zs = pi.z - __shfl_sync(0xffffffffu, sz, kk);
+        for (int kk = 0; kk < NS; kk++) {
+            const float4 sh = stab[kk];
+            const int s = __float_as_int(sh.w);
+            const int nn = spre[kk + 1] - spre[kk];
+            const float xs = pi.x - sh.x;
+            const float ys = pi.y - sh.y;
+            const float zs = pi.z - sh.z;
             for (int j = 0; j < nn; j++) {
                 const float4 q = load_pos<NC>(pos + s + j);
                 pair1<MODE, ENERGY>(xs - q.x, ys - q.y, zs - q.z, k, fx, fy, fz, e, w);
@@ -358,57 +418,62 @@ __device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, 
 
 // One home cell at cell coordinates (cx, cy, cz) of a grid of nc^3 cells
 // whose linear ids start at cell_base in start[] (0 for a single system),
-// cell side cw.  Builds the 27-cell stencil table in lanes 0..26 and runs
-// the staged or the plain path.
-template <int MODE, bool ENERGY, bool NC, class Out>
+// cell side cw.  Builds the stencil table in the warp's slice and runs the
+// staged path, or the plain path when the stencil does not fit the slice.
+template <int R, int MODE, bool ENERGY, bool NC, class Out>
 __device__ __forceinline__ void process_home_cell(const WarpParams &k, const float4 *__restrict__ pos,
                                                   const int32_t *__restrict__ start, const Out &out_in,
-                                                  float *X, float *Y, float *Z, int cx, int cy, int cz, int nc,
-                                                  int64_t cell_base, float cw, double &eacc, double &wacc)
+                                                  float *slice, int cx, int cy, int cz, int nc, int64_t cell_base,
+                                                  float cw, double &eacc, double &wacc)
 {
+    constexpr int NS = Stencil<R>::NS;
     Out out = out_in;
     out.set_home(cx, cy, cz);
     const int lane = threadIdx.x & 31;
-    int s_k = 0, n_k = 0;
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-    if (lane < 27) {
-        int dx, dy, dz;
-        stencil_offset(lane, dx, dy, dz);
-        int ux = cx + dx, uy = cy + dy, uz = cz + dz;
-        ux += ux < 0 ? nc : 0;
-        ux -= ux >= nc ? nc : 0;
-        uy += uy < 0 ? nc : 0;
-        uy -= uy >= nc ? nc : 0;
-        uz += uz < 0 ? nc : 0;
-        uz -= uz >= nc ? nc : 0;
-        const int64_t cn = cell_base + ux + (int64_t)nc * (uy + (int64_t)nc * uz);
-        s_k = start[cn];
-        n_k = start[cn + 1] - s_k;
-        sx = (float)dx * cw;
-        sy = (float)dy * cw;
-        sz = (float)dz * cw;
-    }
-    int P = n_k;
+    float *X = slice;
+    float *Y = X + k.cap;
+    float *Z = Y + k.cap;
+    float4 *stab = reinterpret_cast<float4 *>(Z + k.cap);
+    int *spre = reinterpret_cast<int *>(stab + NS);
+    __syncwarp();   // the slice still holds the previous cell's data
+    int carry = 0;
+#pragma unroll 1
+    for (int b0 = 0; b0 < NS; b0 += 32) {
+        const int kk = b0 + lane;
+        int nn = 0;
+        if (kk < NS) {
+            int dx, dy, dz;
+            stencil_delta<R>(kk, dx, dy, dz);
+            int ux = cx + dx, uy = cy + dy, uz = cz + dz;
+            ux += ux < 0 ? nc : 0;
+            ux -= ux >= nc ? nc : 0;
+            uy += uy < 0 ? nc : 0;
+            uy -= uy >= nc ? nc : 0;
+            uz += uz < 0 ? nc : 0;
+            uz -= uz >= nc ? nc : 0;
+            const int64_t cn = cell_base + ux + (int64_t)nc * (uy + (int64_t)nc * uz);
+            const int s = start[cn];
+            nn = start[cn + 1] - s;
+            stab[kk] = make_float4((float)dx * cw, (float)dy * cw, (float)dz * cw, __int_as_float(s));
+        }
+        int P = nn;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, P, o);
-        if (lane >= o) P += y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, P, o);
+            if (lane >= o) P += y;
+        }
+        if (kk < NS) spre[kk] = carry + P - nn;
+        carry += __shfl_sync(0xffffffffu, P, 31);
     }
-    const int T = __shfl_sync(0xffffffffu, P, 31);
-    const int s_home = __shfl_sync(0xffffffffu, s_k, 0);
-    const int n_home = __shfl_sync(0xffffffffu, n_k, 0);
+    if (lane == 0) spre[NS] = carry;
+    __syncwarp();
+    const int n_home = spre[1];
     if (n_home == 0) return;
-    if (n_home <= 32 && T + 8 <= k.cap) {
-        const int need = n_home > k.gmin ? n_home : k.gmin;
-        if (need <= 8)
-            cell_staged<8, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
-        else if (need <= 16)
-            cell_staged<16, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
-        else
-            cell_staged<32, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
-    } else {
-        cell_plain<MODE, ENERGY, NC>(k, pos, out, s_k, n_k, sx, sy, sz, s_home, n_home, eacc, wacc);
-    }
+    const int s_home = __float_as_int(stab[0].w);
+    if (carry + 32 <= k.cap)
+        cell_staged<R, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, stab, spre, carry, s_home, n_home, eacc, wacc);
+    else
+        cell_plain<R, MODE, ENERGY, NC>(k, pos, out, stab, spre, s_home, n_home, eacc, wacc);
 }
 
 }  // namespace

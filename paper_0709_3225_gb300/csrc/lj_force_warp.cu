@@ -1,24 +1,29 @@
 // Lennard-Jones forces over cell lists, warp-per-cell variant (FP32-mixed).
 //
 // Same method as lj_force.cu (Section 3: a particle interacts with the
-// particles of its own and the 26 neighbouring cells; Section 2 pair
-// force), organised for GB300:
-//  * Warps work independently (no CTA barriers): a persistent grid, warp w
-//    takes home cells w, w + W, w + 2W, ... in linear cell order, so warps of
-//    one CTA work on neighbouring cells and share L1 lines.
-//  * Per home cell the warp stages the 27 stencil cells into its own slice
-//    of shared memory, converting every candidate to coordinates relative to
-//    the HOME cell centre (|x| <= 1.5 cell sides, so FP32 keeps ~1e-7
-//    absolute resolution).  The compute loop is then one flat candidate list
-//    with no per-cell offset.  Lane k (< 27) copies stencil cell k.
-//  * Lanes form S = 32/G groups of G lanes (G = 8, 16 or 32, the smallest
-//    that holds the cell's particles): lane g of a group owns home particle
-//    g, group s takes candidates s, s+S, s+2S, ...  Staged data are stored
-//    SoA and interleaved so that one 8-byte shared load gives a lane its two
-//    next candidates, evaluated together with packed FP32x2 arithmetic
-//    (__ffma2_rn / __fmul2_rn).
-//  * Cells with more than 32 particles, or stencils that do not fit the
-//    warp's slice, take a plain path reading global memory per stencil cell.
+// particles of its own and the neighbouring cells; Section 2 pair force),
+// organised for GB300:
+//  * Warps work independently (no CTA barriers): a persistent grid whose
+//    warps pull runs of consecutive home cells from an atomic counter (or
+//    take cells w, w + W, ... by static striding), so warps of one CTA work
+//    on neighbouring cells and share L1 lines.
+//  * Cell side >= rc / k for subdivision k = 1 (the paper's 27-cell stencil)
+//    or k = 2 (125-cell stencil of half-size cells); the stencil radius is
+//    the template parameter R = k.
+//  * Per home cell the warp writes the stencil table (start, count, shift)
+//    to its own slice of shared memory, then stages the stencil's particles
+//    as one flat list, converting every candidate to coordinates relative to
+//    the HOME cell centre (|x| <= (R + 1/2) cell sides, so FP32 keeps ~1e-7
+//    absolute resolution) and dropping candidates farther than rc from the
+//    home particles' bounding box.
+//  * The compute phase takes the home particles in chunks of G lanes
+//    (G = 2 .. 32, chosen per cell to minimise idle lanes): lane g of a
+//    group owns particle g of the chunk, the S = 32/G groups split the
+//    candidates.  Staged data are SoA, so one 8-byte shared load gives a
+//    lane its next two candidates, evaluated together with packed FP32x2
+//    arithmetic (__ffma2_rn / __fmul2_rn).
+//  * Stencils that do not fit the warp's slice take a plain path reading
+//    global memory per stencil cell.
 #include <string.h>
 
 #include "lj_force_cell.cuh"
@@ -27,7 +32,7 @@ namespace {
 
 // EPI 0: store forces (and energies); EPI 1: apply the fused velocity-Verlet
 // update (KickDriftBin) to each particle instead.
-template <int MODE, bool ENERGY, int EPI>
+template <int R, int MODE, bool ENERGY, int EPI>
 __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams k, const float4 *__restrict__ pos,
                                                                   const int32_t *__restrict__ start,
                                                                   float4 *__restrict__ fout,
@@ -36,18 +41,16 @@ __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams 
     extern __shared__ __align__(16) float wsmem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float *X = wsmem + (size_t)warp * 3 * k.cap;
-    float *Y = X + k.cap;
-    float *Z = Y + k.cap;
+    float *slice = wsmem + (size_t)warp * warp_slice_words(k.cap, R);
     const int nc = k.nc;
     double eacc = 0.0, wacc = 0.0;
     auto one_cell = [&](int64_t c) {
         const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
         if constexpr (EPI == 0) {
             const StoreForce<MODE, ENERGY> out{fout, k.n};
-            process_home_cell<MODE, ENERGY, true>(k, pos, start, out, X, Y, Z, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
+            process_home_cell<R, MODE, ENERGY, true>(k, pos, start, out, slice, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
         } else {
-            process_home_cell<MODE, ENERGY, true>(k, pos, start, kd, X, Y, Z, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
+            process_home_cell<R, MODE, ENERGY, true>(k, pos, start, kd, slice, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
         }
     };
     if (k.grab > 0) {
@@ -87,43 +90,64 @@ __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams 
     }
 }
 
-void *warp_kernel(int mode, bool energy, bool fused = false)
+template <int R>
+void *warp_kernel_r(int mode, bool energy, bool fused)
 {
     if (fused) {
         switch (mode) {
-            case 0: return (void *)k_force_warp<0, false, 1>;
-            case 1: return (void *)k_force_warp<1, false, 1>;
-            default: return (void *)k_force_warp<2, false, 1>;
+            case 0: return (void *)k_force_warp<R, 0, false, 1>;
+            case 1: return (void *)k_force_warp<R, 1, false, 1>;
+            default: return (void *)k_force_warp<R, 2, false, 1>;
         }
     }
     switch (mode * 2 + (energy ? 1 : 0)) {
-        case 0: return (void *)k_force_warp<0, false, 0>;
-        case 1: return (void *)k_force_warp<0, true, 0>;
-        case 2: return (void *)k_force_warp<1, false, 0>;
-        case 3: return (void *)k_force_warp<1, true, 0>;
-        case 4: return (void *)k_force_warp<2, false, 0>;
-        default: return (void *)k_force_warp<2, true, 0>;
+        case 0: return (void *)k_force_warp<R, 0, false, 0>;
+        case 1: return (void *)k_force_warp<R, 0, true, 0>;
+        case 2: return (void *)k_force_warp<R, 1, false, 0>;
+        case 3: return (void *)k_force_warp<R, 1, true, 0>;
+        case 4: return (void *)k_force_warp<R, 2, false, 0>;
+        default: return (void *)k_force_warp<R, 2, true, 0>;
     }
+}
+
+void *warp_kernel(int subdiv, int mode, bool energy, bool fused = false)
+{
+    return subdiv == 2 ? warp_kernel_r<2>(mode, energy, fused) : warp_kernel_r<1>(mode, energy, fused);
 }
 
 }  // namespace
 
+int warp_stencil_cap(double mean_occupancy, int subdiv, int threads, int static_bytes)
+{
+    // Staged candidates per warp: the largest slice with which 4 CTAs fit in
+    // an SM's shared memory (228 KB, 1 KB reserved per CTA), raised up to
+    // 1.25x the mean stencil population + 64 for dense systems (then fewer
+    // CTAs fit).  Multiple of 8, at least 40 (the 32-entry padding).
+    const int R = subdiv == 2 ? 2 : 1;
+    const int warps = threads / 32;
+    const int ns = (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
+    auto cap_for = [&](int bytes_per_cta) {
+        const int words = (bytes_per_cta - static_bytes) / (4 * warps);
+        return ((words - warp_slice_words(0, R)) / 3) & ~7;
+    };
+    const int cap4 = cap_for(228 * 1024 / 4 - 1024);
+    const int cap1 = cap_for(227 * 1024);
+    int need = (int)(1.25 * (double)ns * mean_occupancy) + 64;
+    need = (need + 7) & ~7;
+    int cap = need > cap4 ? (need < cap1 ? need : cap1) : cap4;
+    return cap < 40 ? 40 : cap;
+}
+
 cudaError_t warp_force_configure(lj_ctx *c)
 {
-    // Staged candidates per warp: 1.5x the mean stencil population + 64,
-    // multiple of 8, capped so that 4 CTAs (32 warps, the register limit)
-    // fit in an SM's 227 KB of shared memory.
+    const int subdiv = c->p.cell_subdiv == 2 ? 2 : 1;
     double mean = c->ncell > 0 ? (double)c->p.n / (double)c->ncell : 0.0;
-    int cap = (int)(1.5 * 27.0 * mean) + 64;
-    cap = (cap + 7) & ~7;
-    const int cap_max = ((227 * 1024 / 4 - 1152) / ((kWarpForceThreads / 32) * 3 * (int)sizeof(float))) & ~7;
-    cap = cap > cap_max ? cap_max : cap;
-    c->wcap = cap;
-    c->wforce_smem = (kWarpForceThreads / 32) * 3 * cap * (int)sizeof(float);
+    c->wcap = warp_stencil_cap(mean, subdiv, kWarpForceThreads, 2 * (kWarpForceThreads / 32) * (int)sizeof(double));
+    c->wforce_smem = (kWarpForceThreads / 32) * warp_slice_words(c->wcap, subdiv) * (int)sizeof(float);
     int minblk = 1 << 30;
     for (int mode = 0; mode < 3; mode++)
         for (int en = 0; en < 3; en++) {
-            void *kern = warp_kernel(mode, en == 1, en == 2);
+            void *kern = warp_kernel(subdiv, mode, en == 1, en == 2);
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->wforce_smem);
             if (e != cudaSuccess) return e;
             int nb = 0;
@@ -146,7 +170,7 @@ namespace {
 WarpParams warp_params(const lj_ctx *c)
 {
     WarpParams k;
-    k.gmin = c->gmin;
+    k.gw = c->gw;
     k.grab = c->grab;
     k.work = c->work;
     k.n = (int)c->p.n;
@@ -192,7 +216,7 @@ cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
 {
     KickDriftBin kd;
     memset(&kd, 0, sizeof(kd));
-    return launch_warp(c, warp_kernel(c->p.shift_mode, energy), warp_params(c), f, kd);
+    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, energy), warp_params(c), f, kd);
 }
 
 cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bool last)
@@ -216,5 +240,5 @@ cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bo
     kd.rank = c->rank;
     kd.count = c->count;
     kd.err = c->err;
-    return launch_warp(c, warp_kernel(c->p.shift_mode, false, true), warp_params(c), f, kd);
+    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, false, true), warp_params(c), f, kd);
 }

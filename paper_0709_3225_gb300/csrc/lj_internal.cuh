@@ -64,7 +64,7 @@ struct lj_ctx {
     int run_len, runs, nitems, cap, force_grid, force_smem, use_tma, use_run_kernel;
     // ... and warp-per-cell kernel (lj_force_warp.cu, FP32-mixed)
     int wcap, wforce_smem, wforce_grid;
-    int gmin;            // tuning: smallest lane-group width in the warp kernel
+    int gw;              // tuning: lane-group width of the warp kernel (0 = per-cell choice)
     int fuse_update;     // warp kernel applies the velocity-Verlet update (lj_step)
     int grab;            // tuning: cells per work pull in the warp kernel (0 = static)
     unsigned *work;      // work counter of the warp kernel, zeroed by k_scan_tiles
@@ -143,6 +143,26 @@ __device__ __forceinline__ int lj_warp_rank(int32_t *count, int c, bool valid)
     return base + __popc(peers & ((1u << lane) - 1u));
 }
 
+// Stencil of radius R (cell subdivision k = R, Section 3): W^3 cells with
+// W = 2R + 1.  Entry 0 is the home cell, entries 1 .. NS-1 the neighbours in
+// x-fastest order with the centre skipped.
+template <int R>
+struct Stencil {
+    static constexpr int W = 2 * R + 1;
+    static constexpr int NS = W * W * W;
+    static constexpr int P2 = NS <= 32 ? 32 : (NS <= 64 ? 64 : 128);   // power of two >= NS
+};
+
+template <int R>
+__device__ __forceinline__ void stencil_delta(int k, int &dx, int &dy, int &dz)
+{
+    constexpr int W = Stencil<R>::W, C = Stencil<R>::NS / 2;
+    const int idx = k == 0 ? C : (k <= C ? k - 1 : k);
+    dx = idx % W - R;
+    dy = (idx / W) % W - R;
+    dz = idx / (W * W) - R;
+}
+
 // Exact cell coordinate of a wrapped w from a guess g: thb[k] holds the bits
 // of the smallest double t with trunc(t * s) >= k (thb[0] = 0, thb[nc] =
 // INT64_MAX), so the cell is the largest k with w >= t_k -- the same value
@@ -182,6 +202,8 @@ cudaError_t launch_ekin(lj_ctx *c, const double *v);
 cudaError_t launch_counts_from_start(lj_ctx *c, int32_t *count);
 cudaError_t force_configure(lj_ctx *c);
 cudaError_t warp_force_configure(lj_ctx *c);
+// Staged-candidate capacity per warp of the warp kernels (lj_force_warp.cu).
+int warp_stencil_cap(double mean_occupancy, int subdiv, int threads, int static_bytes);
 cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, double *dparam);
 cudaError_t launch_axpy(lj_ctx *c, double *y, const double *x, double a);
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);

@@ -284,10 +284,12 @@ def lj_vv_adjoint_step(ctx: Context, x_n, x_n1, lam_x, lam_v, dparam) -> None:
                                   _dev(dparam, torch.float64, (2,), "dparam")), "lj_vv_adjoint_step")
 
 
-def lj_set_tuning(ctx: Context, kernel: int, gmin: int = 0, cells_per_grab: int = 0) -> None:
+def lj_set_tuning(ctx: Context, kernel: int, group_width: int = 0, cells_per_grab: int = 4) -> None:
     """Force kernel of a context: 0 warp-per-cell with fused update (mixed),
-    1 run-staged, 2 run-direct, 3 warp-per-cell with separate update (mixed)."""
-    _ck(load().lj_set_tuning(ctx.handle, int(kernel), int(gmin), int(cells_per_grab)), "lj_set_tuning")
+    1 run-staged, 2 run-direct, 3 warp-per-cell with separate update (mixed);
+    group_width 0 (per cell), 2, 4, 8, 16 or 32; cells_per_grab 0 (static
+    striding) or 1..1024."""
+    _ck(load().lj_set_tuning(ctx.handle, int(kernel), int(group_width), int(cells_per_grab)), "lj_set_tuning")
 
 
 class Batch:
@@ -330,8 +332,8 @@ class Batch:
                                  ctypes.byref(cap)), "lj_batch_info")
         return {"ntot": nt.value, "ncell": nc.value, "grid": g.value, "cap": cap.value}
 
-    def set_tuning(self, cells_per_grab: int = 4, use_graph: bool = True, gmin: int = 0) -> None:
-        _ck(load().lj_batch_set_tuning(self.handle, int(cells_per_grab), 1 if use_graph else 0, int(gmin)),
+    def set_tuning(self, cells_per_grab: int = 4, use_graph: bool = True, group_width: int = 0) -> None:
+        _ck(load().lj_batch_set_tuning(self.handle, int(cells_per_grab), 1 if use_graph else 0, int(group_width)),
             "lj_batch_set_tuning")
 
     def forces(self, energy: bool = False) -> None:
@@ -423,7 +425,7 @@ class System:
     float64 (fp64)."""
 
     def __init__(self, x, v, box: float, *, eps=1.0, sigma=1.0, rc=2.5, dt=0.005, mass=1.0,
-                 shift_mode=LJ_SHIFT_ENERGY, precision="mixed", flags=0, device=None, stream=None):
+                 shift_mode=LJ_SHIFT_ENERGY, precision="mixed", flags=0, cell_subdiv=1, device=None, stream=None):
         import torch
         device = torch.device("cuda") if device is None else torch.device(device)
         self.x = torch.as_tensor(np.asarray(x, dtype=np.float64)).to(device).contiguous()
@@ -432,7 +434,7 @@ class System:
             self.v = torch.zeros((n, 3), dtype=torch.float64, device=device)
         else:
             self.v = torch.as_tensor(np.asarray(v, dtype=np.float64)).to(device).contiguous()
-        self.params = make_params(n, box, eps, sigma, rc, dt, mass, shift_mode, precision, 1, flags)
+        self.params = make_params(n, box, eps, sigma, rc, dt, mass, shift_mode, precision, cell_subdiv, flags)
         self.ctx = Context(self.params, stream)
         self.f = torch.zeros((n, 4), dtype=self.ctx.force_dtype, device=device)
         self._forces_valid = False

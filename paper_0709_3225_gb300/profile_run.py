@@ -25,10 +25,14 @@ def main(argv=None) -> int:
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--flags", type=int, default=0)
+    ap.add_argument("--subdiv", type=int, default=1, help="cell subdivision k (1 or 2)")
+    ap.add_argument("--group-width", type=int, default=None, help="warp-kernel lane-group width (0 = per cell)")
     args = ap.parse_args(argv)
     x, L = inputs.jittered_fcc(args.n_fcc, args.rho, 0.1, 1)
     v = inputs.velocities(x.shape[0], 1.0, 1)
-    s = lj.System(x, v, L, precision=args.precision, flags=args.flags)
+    s = lj.System(x, v, L, precision=args.precision, flags=args.flags, cell_subdiv=args.subdiv)
+    if args.group_width is not None:
+        lj.lj_set_tuning(s.ctx, 3, args.group_width, 4)
     s.forces()
     if args.op == "step":
         s.step(1)

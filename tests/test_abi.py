@@ -66,12 +66,17 @@ def test_grid_agrees_with_oracle(lib, oracle_mod):
     from paper_0709_3225_gb300 import lj
     for L in (7.5, 7.6, 8.4, 11.0, 13.43677, 53.74708, 167.95962, 321.0):
         assert lj.lj_grid(lj.make_params(10, L)) == oracle_mod.ncells(L, 2.5)
+        # subdivision k = 2: n = floor(2L / rc) >= 5 half-size cells per side
+        assert lj.lj_grid(lj.make_params(10, L, cell_subdiv=2)) == oracle_mod.ncells(L, 2.5, k=2)
+    assert lj.lj_grid(lj.make_params(10, 6.25, cell_subdiv=2)) == 5
+    with pytest.raises(lj.LJError):
+        lj.lj_grid(lj.make_params(10, 6.2, cell_subdiv=2))      # 4 cells < 2k + 1
 
 
 @pytest.mark.parametrize("field,value,code", [
     ("box", 7.4, 2), ("box", 0.0, 1), ("box", float("nan"), 1), ("sigma", 0.0, 1), ("rc", -1.0, 1),
     ("mass", 0.0, 1), ("eps", -1.0, 1), ("shift_mode", 3, 1), ("precision", 2, 1),
-    ("cell_subdiv", 2, 1), ("flags", 8, 1), ("flags", 3, 1), ("n", -1, 1), ("n", 2 ** 31, 6), ("box", 1e6, 6),
+    ("cell_subdiv", 3, 1), ("cell_subdiv", -1, 1), ("flags", 8, 1), ("flags", 3, 1), ("n", -1, 1), ("n", 2 ** 31, 6), ("box", 1e6, 6),
 ])
 def test_bad_parameters_rejected(lib, field, value, code):
     from paper_0709_3225_gb300 import lj
@@ -83,6 +88,14 @@ def test_bad_parameters_rejected(lib, field, value, code):
     h = ctypes.c_void_p()
     assert lib.lj_create(ctypes.byref(h), ctypes.byref(p), None) == code
     assert not h.value
+
+
+@pytest.mark.parametrize("precision,flags", [("fp64", 0), ("mixed", 1), ("mixed", 2)])
+def test_subdivision_two_needs_the_warp_kernel(lib, precision, flags):
+    from paper_0709_3225_gb300 import lj
+    p = lj.make_params(1000, 20.0, precision=precision, cell_subdiv=2, flags=flags)
+    nc = ctypes.c_int32()
+    assert lib.lj_grid(ctypes.byref(p), ctypes.byref(nc)) == 1
 
 
 def test_null_arguments_rejected(lib):

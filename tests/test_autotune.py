@@ -14,10 +14,10 @@ def test_bucket_key_and_cache_round_trip(tmp_path):
     assert k1 == k2 and k1 != k3
     assert k1 == "GB300|system-mixed|N2^22|rho0.85"
     path = str(tmp_path / "cache.json")
-    autotune.store_cache(k1, {"kernel": 0, "gmin": 16}, path)
-    autotune.store_cache(k3, {"kernel": 1, "gmin": 0}, path)
+    autotune.store_cache(k1, {"kernel": 0, "gw": 16}, path)
+    autotune.store_cache(k3, {"kernel": 1, "gw": 0}, path)
     data = autotune.load_cache(path)
-    assert data[k1] == {"kernel": 0, "gmin": 16} and data[k3]["kernel"] == 1
+    assert data[k1] == {"kernel": 0, "gw": 16} and data[k3]["kernel"] == 1
     assert autotune.load_cache(str(tmp_path / "missing.json")) == {}
 
 
@@ -32,7 +32,8 @@ def test_tune_system_and_batch(tmp_path):
     ref = s.f.clone()
     x_before = s.x.clone()
     r = autotune.tune_system(s, 0.8442, steps=4, warmup=3, path=path)
-    assert not r["cached"] and len(r["trials"]) == 10
+    assert not r["cached"] and len(r["trials"]) == 13
+    assert {t["subdiv"] for t in r["trials"]} == {1, 2}
     assert torch.equal(s.x, x_before)                 # tuning works on a copy
     s.forces()
     assert float((s.f[:, :3] - ref[:, :3]).abs().max()) <= 1e-4 * float(ref[:, :3].abs().max())

@@ -102,8 +102,8 @@ def test_tuning_knobs_give_same_forces():
     b.forces()
     ref = b.f.clone()
     rms = float(ref[:, :3].double().pow(2).sum(dim=1).mean().sqrt())
-    for cpg, gmin in ((1, 0), (16, 32), (3, 16)):
-        b.set_tuning(cells_per_grab=cpg, use_graph=True, gmin=gmin)
+    for cpg, gw in ((1, 0), (16, 32), (3, 16), (2, 2), (5, 4)):
+        b.set_tuning(cells_per_grab=cpg, use_graph=True, group_width=gw)
         b.forces()
         # same arithmetic up to the order of FP32 sums
         diff = (b.f[:, :3] - ref[:, :3]).double().abs()

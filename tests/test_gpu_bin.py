@@ -11,9 +11,9 @@ from gpu_util import dense_cluster_state
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_cells(x, L, precision="mixed"):
+def _gpu_cells(x, L, precision="mixed", subdiv=1):
     from paper_0709_3225_gb300 import lj
-    s = lj.System(x, None, L, precision=precision)
+    s = lj.System(x, None, L, precision=precision, cell_subdiv=subdiv)
     out = [t.cpu().numpy() for t in s.cells()]
     s.check()
     nc = s.ctx.nc
@@ -21,9 +21,9 @@ def _gpu_cells(x, L, precision="mixed"):
     return nc, out
 
 
-def _compare(x, L, oracle_mod, precision="mixed"):
-    nc, (cell_of, count, start, perm) = _gpu_cells(x, L, precision)
-    assert nc == oracle_mod.ncells(L)
+def _compare(x, L, oracle_mod, precision="mixed", subdiv=1):
+    nc, (cell_of, count, start, perm) = _gpu_cells(x, L, precision, subdiv)
+    assert nc == oracle_mod.ncells(L, k=subdiv)
     o_cell, o_count, o_start, o_perm = oracle_mod.bin_cells(x, L, nc)
     assert np.array_equal(cell_of, o_cell)
     assert np.array_equal(count, o_count)
@@ -34,6 +34,13 @@ def _compare(x, L, oracle_mod, precision="mixed"):
     okey = o_cell[o_perm].astype(np.int64) * (x.shape[0] + 1) + o_perm
     assert np.array_equal(np.sort(key), np.sort(okey))
     assert np.array_equal(cell_of[perm], np.repeat(np.arange(nc ** 3), count))
+
+
+def test_subdivision_two(oracle_mod):
+    """Half-size cells (k = 2): the same exact binning rule with n = floor(2L/rc)."""
+    x, L = inputs.jittered_fcc(9, 0.8442, 0.2, 5)
+    _compare(x, L, oracle_mod, subdiv=2)
+    _compare(inputs.uniform(1001, 7.0, 3), 7.0, oracle_mod, subdiv=2)
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])

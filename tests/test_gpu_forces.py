@@ -25,9 +25,12 @@ TOL = {"mixed": dict(rms=1e-5, dr=6e-7, ds=1e-5, e=2e-6, band=1e-5),
        "fp64": dict(rms=1e-12, rel=1e-10, e=1e-11, band=1e-12)}
 
 
-def _gpu_forces(x, L, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5):
+def _gpu_forces(x, L, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5, subdiv=1, gw=None):
     from paper_0709_3225_gb300 import lj
-    s = lj.System(x, None, L, precision=precision, shift_mode=mode, flags=flags, eps=eps, sigma=sigma, rc=rc)
+    s = lj.System(x, None, L, precision=precision, shift_mode=mode, flags=flags, eps=eps, sigma=sigma, rc=rc,
+                  cell_subdiv=subdiv)
+    if gw is not None:
+        lj.lj_set_tuning(s.ctx, 3, gw, 4)
     e, w = s.forces(energy=True)
     f = s.f.double().cpu().numpy()
     s.check()
@@ -35,9 +38,9 @@ def _gpu_forces(x, L, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5):
     return f, e, w
 
 
-def _check(x, L, oracle_mod, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5):
-    f, e, w = _gpu_forces(x, L, precision, mode, flags, eps, sigma, rc)
-    fo, epo, eo, wo = oracle_mod.forces_cells(x, L, eps=eps, sigma=sigma, rc=rc, mode=mode)
+def _check(x, L, oracle_mod, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5, subdiv=1, gw=None):
+    f, e, w = _gpu_forces(x, L, precision, mode, flags, eps, sigma, rc, subdiv, gw)
+    fo, epo, eo, wo = oracle_mod.forces_cells(x, L, eps=eps, sigma=sigma, rc=rc, mode=mode, k=subdiv)
     t = TOL[precision]
     near = oracle_mod.near_cutoff(x, L, rc=rc, band=t["band"])
     assert rel_rms(f[:, :3], fo) <= t["rms"]
@@ -76,6 +79,31 @@ def test_kernel_variants(oracle_mod, precision, flags):
     _check(x, L, oracle_mod, precision, 1, flags)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_subdivision_two(oracle_mod, mode):
+    """Cell subdivision k = 2: half-size cells, 125-cell stencil, same forces
+    as the oracle's k = 2 cell list (itself equal to k = 1)."""
+    x, L = inputs.jittered_fcc(8, 0.8442, 0.1, 21)
+    _check(x, L, oracle_mod, "mixed", mode, subdiv=2)
+
+
+@pytest.mark.parametrize("subdiv", [1, 2])
+@pytest.mark.parametrize("gw", [2, 4, 8, 16, 32])
+def test_group_widths(oracle_mod, subdiv, gw):
+    """Every fixed lane-group width (chunks of gw home particles, 32 / gw
+    candidate streams) gives the oracle's forces."""
+    x, L = inputs.jittered_fcc(7, 0.8442, 0.12, 30 + gw)
+    _check(x, L, oracle_mod, "mixed", 1, subdiv=subdiv, gw=gw)
+
+
+@pytest.mark.parametrize("n_fcc,rho", [(4, 0.8442), (5, 0.8442), (4, 0.3), (9, 0.95)])
+def test_subdivision_two_box_sizes(oracle_mod, n_fcc, rho):
+    """5, 6, 7 ... half-size cells per side: stencil windows that wrap onto
+    themselves (5 cells), sparse and dense cells."""
+    x, L = inputs.jittered_fcc(n_fcc, rho, 0.08, n_fcc + 40)
+    _check(x, L, oracle_mod, "mixed", subdiv=2)
+
+
 @pytest.mark.parametrize("n_fcc,rho", [(5, 0.8442), (6, 0.8442), (7, 0.5), (9, 0.95), (12, 0.8442), (4, 0.3)])
 def test_box_sizes(oracle_mod, n_fcc, rho):
     """3, 4, 5 ... cells per side: windows that wrap on both sides; sparse
@@ -93,6 +121,10 @@ def test_dense_cluster_and_overflow(oracle_mod, precision, flags):
     windows larger than the staging capacity (global-memory fallback)."""
     x, L = dense_cluster_state()
     _check(x, L, oracle_mod, precision, flags=flags)
+    if precision == "mixed" and flags == 0:
+        _check(x, L, oracle_mod, precision, subdiv=2)
+        for gw in (2, 32):
+            _check(x, L, oracle_mod, precision, gw=gw)
 
 
 def test_ragged_random_gas(oracle_mod):
@@ -142,14 +174,14 @@ def test_liquid_131k(oracle_mod):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_full_size_4m_sampled(oracle_mod, precision):
+@pytest.mark.parametrize("precision,subdiv", [("mixed", 1), ("fp64", 1), ("mixed", 2)])
+def test_full_size_4m_sampled(oracle_mod, precision, subdiv):
     """The 4,000,000-particle workload in the launch configuration the
     benchmark uses: 256 sampled particles against the oracle's per-particle
     definition, plus zero net force (Newton III) over all particles."""
     from paper_0709_3225_gb300 import lj
     x, L = inputs.jittered_fcc(100, 0.8442, 0.1, 12)
-    s = lj.System(x, None, L, precision=precision)
+    s = lj.System(x, None, L, precision=precision, cell_subdiv=subdiv)
     s.forces()
     s.check()
     f = s.f.double().cpu().numpy()

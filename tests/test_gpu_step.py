@@ -37,16 +37,18 @@ def test_trajectory_matches_oracle(oracle_mod, precision, xtol, vtol, mode):
     s.close()
 
 
-@pytest.mark.parametrize("kernel,grab", [(0, 0), (3, 0), (3, 1), (3, 8), (1, 0)])
-def test_update_paths_agree(oracle_mod, kernel, grab):
+@pytest.mark.parametrize("kernel,grab,subdiv", [(0, 0, 1), (3, 0, 1), (3, 1, 1), (3, 8, 1), (1, 0, 1),
+                                                (3, 4, 2), (0, 4, 2)])
+def test_update_paths_agree(oracle_mod, kernel, grab, subdiv):
     """The fused update (kernel 0), the separate update (3) and the run kernel
-    (1) integrate the same trajectory (force-shifted, FP32 rounding only)."""
+    (1), with cell subdivision 1 or 2, integrate the same trajectory
+    (force-shifted, FP32 rounding only)."""
     from paper_0709_3225_gb300 import lj
     x, v, L = _liquid(seed=17)
     xo, vo = x.copy(), v.copy()
     fo = oracle_mod.forces_cells(xo, L, mode=2)[0]
     oracle_mod.vv(xo, vo, fo, L, 15, mode=2)
-    s = lj.System(x, v, L, shift_mode=2)
+    s = lj.System(x, v, L, shift_mode=2, cell_subdiv=subdiv)
     lj.lj_set_tuning(s.ctx, kernel, 0, grab)
     s.step(1)
     s.step(14)
