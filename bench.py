@@ -310,9 +310,8 @@ def run_gpu(args):
 
     # ---- FP32-mixed, device-resident (the headline `value`) --------------
     from paper_0709_3225_gb300 import autotune
-    s = lj.System(x, v, L, precision="mixed", dt=w.dt, rc=w.rc)
+    s, tuning = autotune.make_system(x, v, L, w.rho, precision="mixed", dt=w.dt, rc=w.rc)
     s.forces()
-    tuning = autotune.tune_system(s, w.rho)
     tuning.pop("trials", None)
     s.step(args.warmup)
     s.check()
@@ -437,7 +436,7 @@ def run_gpu(args):
 
 
 FORCE_SOURCES = [os.path.join(ROOT, "paper_0709_3225_gb300", "csrc", f)
-                 for f in ("lj_force_warp.cu", "lj_force_cell.cuh")]
+                 for f in ("lj_force_warp.cu", "lj_force_cell.cuh", "lj_internal.cuh")]
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_force_warp_traffic_fluid-4m.md")
 
 

@@ -438,9 +438,11 @@ void batch_free(lj_batch *b)
 
 cudaError_t configure(lj_batch *b)
 {
-    // Staging capacity for the densest replica (static shared memory of the
-    // scan phases: at most 2 KB).
-    const int cap = warp_stencil_cap(b->max_mean_occ, 1, kBatchThreads, 2048);
+    // Staging capacity from the mean occupancy over all replicas (cells of
+    // denser replicas that overflow take the plain path); static shared
+    // memory of the scan phases: at most 2 KB.
+    const double mean_occ = b->ncell > 0 ? (double)b->ntot / (double)b->ncell : 0.0;
+    const int cap = warp_stencil_cap(mean_occ, 1, kBatchThreads, 2048);
     b->k.cap = cap;
     b->smem = (kBatchThreads / 32) * warp_slice_words(cap, 1) * (int)sizeof(float);
     int minblk = 1 << 30;

@@ -24,6 +24,7 @@
 //    arithmetic (__ffma2_rn / __fmul2_rn).
 //  * Stencils that do not fit the warp's slice take a plain path reading
 //    global memory per stencil cell.
+#include <math.h>
 #include <string.h>
 
 #include "lj_force_cell.cuh"
@@ -120,9 +121,10 @@ void *warp_kernel(int subdiv, int mode, bool energy, bool fused = false)
 int warp_stencil_cap(double mean_occupancy, int subdiv, int threads, int static_bytes)
 {
     // Staged candidates per warp: the largest slice with which 4 CTAs fit in
-    // an SM's shared memory (228 KB, 1 KB reserved per CTA), raised up to
-    // 1.25x the mean stencil population + 64 for dense systems (then fewer
-    // CTAs fit).  Multiple of 8, at least 40 (the 32-entry padding).
+    // an SM's shared memory (228 KB, 1 KB reserved per CTA).  Raised (then
+    // fewer CTAs fit) only when the mean stencil population m plus 4 sqrt(m)
+    // (a Poisson spread) plus the 32-entry padding exceeds it: dense systems.
+    // Multiple of 8, at least 40.
     const int R = subdiv == 2 ? 2 : 1;
     const int warps = threads / 32;
     const int ns = (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
@@ -132,7 +134,8 @@ int warp_stencil_cap(double mean_occupancy, int subdiv, int threads, int static_
     };
     const int cap4 = cap_for(228 * 1024 / 4 - 1024);
     const int cap1 = cap_for(227 * 1024);
-    int need = (int)(1.25 * (double)ns * mean_occupancy) + 64;
+    const double m = (double)ns * mean_occupancy;
+    int need = (int)(m + 4.0 * sqrt(m)) + 32;
     need = (need + 7) & ~7;
     int cap = need > cap4 ? (need < cap1 ? need : cap1) : cap4;
     return cap < 40 ? 40 : cap;
