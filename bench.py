@@ -171,6 +171,34 @@ def run_ensemble(args, stream, world):
             "launches_per_step": (n1 - n0 - 1) / k, "graph": graph, "tuning": tuning}
 
 
+def run_n2_breakeven(stream):
+    """All-pairs (lj_forces_n2) against cell-list (lj_forces) force time,
+    FP32-mixed, liquid-density lattice gases of growing N: where the cell
+    list overtakes the paper's N^2 algorithm on this GPU."""
+    import torch
+    from paper_0709_3225_gb300 import inputs, lj
+    out = []
+    for n in (500, 2048, 8788, 32000, 131072):
+        x, L = inputs.lattice_gas(n, 0.8442, 5)
+        s = lj.System(x, None, L)
+        row = {"n": n}
+        for name, fn in (("cells_ms", lj.lj_forces), ("n2_ms", lj.lj_forces_n2)):
+            reps = 3 if (name == "n2_ms" and n > 30000) else 20
+            fn(s.ctx, s.x, s.f)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn(s.ctx, s.x, s.f)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[name] = e0.elapsed_time(e1) / reps
+        s.check()
+        s.close()
+        out.append(row)
+    return out
+
+
 def run_adjoint(x4m, L4m, stream):
     """The adjoint workload: the force-matching gradient (loss = mean |F -
     F_target|^2 + mean |x(50) - x_target(50)|^2, theta = (0.9, 1.05)) of the
@@ -379,6 +407,7 @@ def run_gpu(args):
 
     ensemble = None if args.no_ensemble else run_ensemble(args, stream, world)
     adjoint = None if (args.no_ensemble or rank != 0) else run_adjoint(x, L, stream)
+    n2 = None if (args.no_ensemble or rank != 0) else run_n2_breakeven(stream)
 
     if rank != 0:
         if world > 1:
@@ -417,6 +446,7 @@ def run_gpu(args):
         "tuning": tuning,
         "ensemble": ensemble,
         "adjoint": adjoint,
+        "n2_vs_cells": n2,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64},

@@ -145,6 +145,18 @@ int lj_get_cells(lj_ctx *ctx, int32_t *cell_of, int32_t *count, int32_t *start, 
  * energies. */
 int lj_forces(lj_ctx *ctx, const double *x, void *f, double *e_pot, double *virial);
 
+/* All-pairs forces (Section 2, Eq. n2_force with the cutoff): the same
+ * forces as lj_forces computed without cells, every pair at the minimum
+ * image, O(n^2) work.  For small systems, as a GPU brute-force cross-check,
+ * and for the all-pairs versus cell-list break-even study.  Arguments,
+ * layout, precision, energy semantics and error behaviour as lj_forces.
+ * Positions are taken relative to the box centre (absolute coordinates,
+ * as the paper's N^2 code), so in FP32-mixed the pair vectors carry
+ * rounding of order 2^-24 L rather than 2^-24 rc.  The cell arrays are not
+ * touched.  Scratch of n x 16 B (32 B in FP64) times (1 + j-splits) is
+ * allocated on the first call and kept. */
+int lj_forces_n2(lj_ctx *ctx, const double *x, void *f, double *e_pot, double *virial);
+
 /* nsteps velocity-Verlet steps (Section 2): v += dt/(2m) f; x += dt v;
  * x wrapped into [0, L); cells rebuilt; f = F(x); v += dt/(2m) f.
  * x, v: device (n, 3) double, updated in place.  f: device (n, 4), must hold

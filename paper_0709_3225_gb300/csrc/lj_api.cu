@@ -98,6 +98,7 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->vs);
     cudaFree(c->fs);
     cudaFree(c->g4);
+    cudaFree(c->n2_scratch);
     if (c->host_scalars) cudaFreeHost(c->host_scalars);
     if (c->host_err) cudaFreeHost(c->host_err);
     if (c->ev) {
@@ -361,6 +362,27 @@ extern "C" int lj_forces(lj_ctx *c, const double *x, void *f, double *e_pot, dou
     if (c->p.n > 0) LJ_CK(launch_energy_reduce(c));
     LJ_CK(cudaMemcpyAsync(c->host_scalars, c->scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     r = sync_and_check(c);
+    if (r) return r;
+    if (e_pot) *e_pot = c->host_scalars[0];
+    if (virial) *virial = c->host_scalars[1];
+    return LJ_OK;
+}
+
+extern "C" int lj_forces_n2(lj_ctx *c, const double *x, void *f, double *e_pot, double *virial)
+{
+    if (!c) return LJ_EINVAL;
+    if (c->p.n > 0) {
+        int r = check_dev_ptr(x, 8);
+        if (r) return r;
+        r = check_dev_ptr(f, 16);
+        if (r) return r;
+    }
+    const bool energy = e_pot || virial;
+    if (energy) LJ_CK(cudaMemsetAsync(c->scalars, 0, 2 * sizeof(double), c->stream));
+    LJ_CK(launch_forces_n2(c, x, f, energy));
+    if (!energy) return LJ_OK;
+    LJ_CK(cudaMemcpyAsync(c->host_scalars, c->scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    int r = sync_and_check(c);
     if (r) return r;
     if (e_pot) *e_pot = c->host_scalars[0];
     if (virial) *virial = c->host_scalars[1];

@@ -71,6 +71,8 @@ struct lj_ctx {
     int npartial;        // partials written by the last energy launch
     int npartial_cap;    // capacity of `partial` in (energy, virial) pairs
     void *g4;            // sorted cotangents for the adjoint (lazily allocated)
+    void *n2_scratch;    // all-pairs kernel scratch (lazily allocated)
+    size_t n2_bytes;
     int ekin_grid;
 
     // lazily allocated staging for lj_step_host / lj_energy
@@ -207,4 +209,6 @@ int warp_stencil_cap(double mean_occupancy, int subdiv, int threads, int static_
 cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, double *dparam);
 cudaError_t launch_axpy(lj_ctx *c, double *y, const double *x, double a);
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);
+// All-pairs forces (lj_n2.cu); energies into c->scalars[0..1] when energy.
+cudaError_t launch_forces_n2(lj_ctx *c, const double *x, void *f, bool energy);
 cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bool last);

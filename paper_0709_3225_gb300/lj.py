@@ -67,6 +67,7 @@ _SIGS = {
     "lj_destroy": ([_P], None),
     "lj_bin": ([_P, _P], ctypes.c_int),
     "lj_get_cells": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "lj_forces_n2": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "lj_forces": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lj_step": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "lj_step_host": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
@@ -218,6 +219,21 @@ def lj_forces(ctx: Context, x, f, energy: bool = False):
         _ck(load().lj_forces(ctx.handle, xp, fp, ctypes.byref(e), ctypes.byref(w)), "lj_forces")
         return e.value, w.value
     _ck(load().lj_forces(ctx.handle, xp, fp, None, None), "lj_forces")
+    return None
+
+
+def lj_forces_n2(ctx: Context, x, f, energy: bool = False):
+    """All-pairs forces (no cells) into f (n, 4); with energy=True returns
+    (e_pot, virial)."""
+    import torch
+    xp = _dev(x, torch.float64, (ctx.n, 3), "x")
+    fp = _dev(f, ctx.force_dtype, (ctx.n, 4), "f")
+    if energy:
+        e = ctypes.c_double()
+        w = ctypes.c_double()
+        _ck(load().lj_forces_n2(ctx.handle, xp, fp, ctypes.byref(e), ctypes.byref(w)), "lj_forces_n2")
+        return e.value, w.value
+    _ck(load().lj_forces_n2(ctx.handle, xp, fp, None, None), "lj_forces_n2")
     return None
 
 
