@@ -20,6 +20,11 @@ Parity status of each function (what pins it, in tests/test_oracle_*.py):
   forces_cells  -- equals forces_brute; invariance under subdivision,
                    translation and axis permutation (pinned)
   vv            -- time reversibility, second-order energy error (pinned)
+  rand48_series -- glibc's srand48 / lrand48 / drand48 sequences (pinned)
+  rand48_jump   -- equals the serial series m steps ahead (pinned through
+                   rand48_series)
+  langevin      -- gamma = 0 is velocity Verlet; the ideal gas thermalises
+                   to kT; Box-Muller normals have unit variance (pinned)
 """
 from __future__ import annotations
 
@@ -102,6 +107,16 @@ def _load():
         lib.or_vv.restype = ctypes.c_int
         lib.or_set_threads.argtypes = [ctypes.c_int]
         lib.or_set_threads.restype = ctypes.c_int
+        _U64 = ctypes.POINTER(ctypes.c_uint64)
+        lib.or_srand48_state.argtypes = [ctypes.c_int64]
+        lib.or_srand48_state.restype = ctypes.c_uint64
+        lib.or_rand48_series.argtypes = [ctypes.c_uint64, ctypes.c_int64, _U64]
+        lib.or_rand48_series.restype = None
+        lib.or_rand48_jump.argtypes = [ctypes.c_int64, _U64, _U64]
+        lib.or_rand48_jump.restype = None
+        lib.or_langevin.argtypes = [ctypes.c_int64, _D, _D, _D] + [ctypes.c_double] * 4 + \
+            [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [ctypes.c_int, _U64, _D, _D]
+        lib.or_langevin.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -301,6 +316,50 @@ def vv(x, v, f, L: float, nsteps: int, dt: float = 0.005, eps: float = 1.0,
     r = _load().or_vv(x.shape[0], _dp(x), _dp(v), _dp(f), float(L), float(eps), float(sigma),
                       float(rc), int(mode), int(k), float(dt), float(mass), int(nsteps),
                       ctypes.byref(E), ctypes.byref(W))
+    if r != 0:
+        raise ValueError("box too small for the cell stencil")
+    return E.value, W.value
+
+
+def srand48_state(seed: int) -> int:
+    """x_0 of srand48(seed): (seed << 16) | 0x330E (low 32 bits of the seed)."""
+    return int(_load().or_srand48_state(int(seed)))
+
+
+def rand48_series(x0: int, n: int) -> np.ndarray:
+    """x_1 .. x_n of the rand48 series (Section 4, Eq. lrand48) from x_0,
+    serially, as uint64 (48-bit values).  lrand48 = x >> 17, drand48 = x 2^-48."""
+    out = np.empty(int(n), np.uint64)
+    _load().or_rand48_series(ctypes.c_uint64(int(x0)), int(n), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    return out
+
+
+def rand48_jump(m: int) -> tuple[int, int]:
+    """(A, C) with x_{n+m} = (A x_n + C) mod 2^48 (Section 4, Eqs. lrand48m, AC)."""
+    A = ctypes.c_uint64()
+    C = ctypes.c_uint64()
+    _load().or_rand48_jump(int(m), ctypes.byref(A), ctypes.byref(C))
+    return int(A.value), int(C.value)
+
+
+def langevin(x, v, f, L: float, nsteps: int, seed: int, gamma: float, kT: float, dt: float = 0.005,
+             eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5, mode: int = 1, k: int = 1, mass: float = 1.0):
+    """nsteps BAOAB Langevin steps (the stochastic thermostat of Section 1;
+    scheme and random-number use documented in lj_oracle.c), normals from the
+    rand48 series of srand48(seed).  x, v, f updated IN PLACE (f = F(x) on
+    entry).  Returns (e_pot, virial) at the end."""
+    for a in (x, v, f):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                and a.ndim == 2 and a.shape[1] == 3):
+            raise ValueError("x, v, f must be C-contiguous float64 arrays of shape (n, 3)")
+    n = x.shape[0]
+    series = rand48_series(srand48_state(seed), 4 * n * int(nsteps))
+    E = ctypes.c_double()
+    W = ctypes.c_double()
+    r = _load().or_langevin(n, _dp(x), _dp(v), _dp(f), float(L), float(eps), float(sigma), float(rc), int(mode),
+                            int(k), float(dt), float(mass), float(gamma), float(kT), int(nsteps),
+                            series.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(E),
+                            ctypes.byref(W))
     if r != 0:
         raise ValueError("box too small for the cell stencil")
     return E.value, W.value

@@ -554,6 +554,107 @@ int or_relax(int64_t n, double *x, double *f, double L, double eps, double sigma
     return or_forces_cells(n, x, L, eps, sigma, rc, mode, k, f, NULL, &E, &W);
 }
 
+/* ------------------------------------------------------------------------ */
+/* rand48 linear congruential generator (Section 4, Eq. lrand48):
+ *   x_{n+1} = (a x_n + c) mod 2^48,  a = 0x5DEECE66D, c = 0xB
+ * (the constants of the POSIX/glibc rand48 family).  The 31-bit nonnegative
+ * output of lrand48 is the 31 most significant bits, x >> 17 (Section 4: the
+ * d most significant bits for a d-bit type); drand48 is x 2^-48 in [0, 1).
+ * srand48(s) starts from x_0 = (s << 16) | 0x330E.
+ * or_rand48_series writes x_1 .. x_n from x_0, one serial step at a time:
+ * the plain definition that the parallel generator must reproduce. */
+#define OR_R48_A 0x5DEECE66DULL
+#define OR_R48_C 0xBULL
+#define OR_R48_MASK ((1ULL << 48) - 1ULL)
+
+uint64_t or_srand48_state(int64_t seed)
+{
+    return ((((uint64_t)seed) & 0xFFFFFFFFULL) << 16) | 0x330EULL;
+}
+
+void or_rand48_series(uint64_t x0, int64_t n, uint64_t *out)
+{
+    uint64_t x = x0 & OR_R48_MASK;
+    for (int64_t i = 0; i < n; i++) {
+        x = (OR_R48_A * x + OR_R48_C) & OR_R48_MASK;
+        out[i] = x;
+    }
+}
+
+/* Jump constants of Eq. lrand48m: x_{n+m} = (A x_n + C) mod 2^48 with
+ * A = a^m and C = c (a^{m-1} + ... + a + 1), both mod 2^48.  (The paper's
+ * Eq. AC prints the sum up to i = m; m terms, i = 0 .. m-1, are what
+ * composing the serial step m times gives.)  Computed here by m-fold
+ * composition of the affine map, O(m): plain, not fast. */
+void or_rand48_jump(int64_t m, uint64_t *A, uint64_t *C)
+{
+    uint64_t a = 1, c = 0;
+    for (int64_t i = 0; i < m; i++) {
+        a = (a * OR_R48_A) & OR_R48_MASK;
+        c = (c * OR_R48_A + OR_R48_C) & OR_R48_MASK;
+    }
+    *A = a;
+    *C = c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Langevin thermostat (the stochastic thermostat that Section 1 names as
+ * the setting where single precision suffices; the paper gives no scheme).
+ * Reading: the BAOAB splitting of Leimkuhler and Matthews, one step
+ *   B: v += (dt/2m) f;   A: x += (dt/2) v;
+ *   O: v = c1 v + c2 sqrt(kT/m) xi,  c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2);
+ *   A: x += (dt/2) v, wrap;   f = F(x);   B: v += (dt/2m) f,
+ * with xi standard normal.  The normals come from the rand48 series u = x 2^-48
+ * (drand48): for step s and particle i, with N particles, the four uniforms
+ * u_k = drand48 number (4 s + k) N + i + 1 of the series (k = 0 .. 3) give,
+ * by the Box-Muller transform,
+ *   r1 = sqrt(-2 ln(1 - u0)), t1 = 2 pi u1:  xi_x = r1 cos t1, xi_y = r1 sin t1,
+ *   r2 = sqrt(-2 ln(1 - u2)), t2 = 2 pi u3:  xi_z = r2 cos t2
+ * (1 - u in (0, 1], so the logarithm is finite).  The series starts at x0
+ * (or_srand48_state of the seed); series[] holds x_1 .. x_{4 N nsteps}.
+ * On entry f holds F(x); on exit the forces at the final positions.
+ * Returns -1 on a bad box. */
+int or_langevin(int64_t n, double *x, double *v, double *f, double L, double eps,
+                double sigma, double rc, int mode, int k, double dt, double mass,
+                double gamma, double kT, int nsteps, const uint64_t *series,
+                double *e_pot, double *virial)
+{
+    const double h = 0.5 * dt / mass;
+    const double c1 = exp(-gamma * dt);
+    const double c2 = sqrt(1.0 - c1 * c1);
+    const double sd = sqrt(kT / mass);
+    const double two_pi = 6.283185307179586476925286766559;
+    double E = 0.0, W = 0.0;
+    for (int s = 0; s < nsteps; s++) {
+        const uint64_t *u = series + (int64_t)4 * n * s;
+        for (int64_t i = 0; i < n; i++) {
+            double xi[3];
+            const double u0 = (double)u[i] * 0x1p-48, u1 = (double)u[n + i] * 0x1p-48;
+            const double u2 = (double)u[2 * n + i] * 0x1p-48, u3 = (double)u[3 * n + i] * 0x1p-48;
+            const double r1 = sqrt(-2.0 * log(1.0 - u0)), t1 = two_pi * u1;
+            const double r2 = sqrt(-2.0 * log(1.0 - u2)), t2 = two_pi * u3;
+            xi[0] = r1 * cos(t1);
+            xi[1] = r1 * sin(t1);
+            xi[2] = r2 * cos(t2);
+            for (int q = 0; q < 3; q++) {
+                const int64_t j = 3 * i + q;
+                double vv = v[j] + h * f[j];
+                double xx = x[j] + 0.5 * dt * vv;
+                vv = c1 * vv + c2 * sd * xi[q];
+                xx = xx + 0.5 * dt * vv;
+                x[j] = wrap1(xx, L);
+                v[j] = vv;
+            }
+        }
+        if (or_forces_cells(n, x, L, eps, sigma, rc, mode, k, f, NULL, &E, &W) != 0)
+            return -1;
+        for (int64_t q = 0; q < 3 * n; q++) v[q] = v[q] + h * f[q];
+    }
+    if (e_pot) *e_pot = E;
+    if (virial) *virial = W;
+    return 0;
+}
+
 /* Threads the OpenMP loops may use (no-op without OpenMP); returns the
  * number in effect. */
 int or_set_threads(int nthreads)
