@@ -199,6 +199,57 @@ def run_n2_breakeven(stream):
     return out
 
 
+def run_rand48(stream, hbm_gbs):
+    """Section 4's generator: the first R S numbers of the lrand48 series from
+    S parallel streams (device-resident output, as the paper stored it),
+    against the measured HBM copy bandwidth (4 bytes written per number)."""
+    import torch
+    from paper_0709_3225_gb300 import lj
+    S, R = 152 * 4096, 512
+    st = torch.empty(S, dtype=torch.int64, device="cuda")
+    out = torch.empty(S * R, dtype=torch.int32, device="cuda")
+    outd = torch.empty(S * R, dtype=torch.float64, device="cuda")
+    lj.lj_rand48_seed(st, lj.lj_srand48_state(12345))
+    lj.lj_rand48_lrand(st, R, out)
+    res = {"streams": S, "per_stream": R, "numbers": S * R}
+    for name, fn, buf, nb in (("lrand48", lj.lj_rand48_lrand, out, 4), ("drand48", lj.lj_rand48_drand, outd, 8)):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            fn(st, R, buf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        gbs = S * R * nb / ms / 1e6
+        res[name] = {"ms": ms, "numbers_per_s": S * R / ms * 1e3, "GB_per_s": gbs,
+                     "frac_of_hbm": gbs / hbm_gbs if hbm_gbs else None}
+    del out, outd
+    return res
+
+
+def run_langevin(x, v, L, w, stream):
+    """The Langevin-thermostatted step (BAOAB, rand48 normals) on the 4M
+    workload: ms per step beside the plain velocity-Verlet step."""
+    import torch
+    from paper_0709_3225_gb300 import lj
+    s = lj.System(x, v, L, precision="mixed", dt=w.dt, rc=w.rc)
+    s.forces()
+    lj.lj_langevin_seed(s.ctx, 7)
+    lj.lj_langevin_step(s.ctx, s.x, s.v, s.f, 3, 1.0, w.temperature)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = 20
+    e0.record(stream)
+    lj.lj_langevin_step(s.ctx, s.x, s.v, s.f, k, 1.0, w.temperature)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s.check()
+    s.close()
+    return {"ms_per_step": e0.elapsed_time(e1) / k, "steps": k, "gamma": 1.0, "kT": w.temperature,
+            "scheme": "BAOAB, Box-Muller normals from the rand48 series (one stream per particle)"}
+
+
 def run_adjoint(x4m, L4m, stream):
     """The adjoint workload: the force-matching gradient (loss = mean |F -
     F_target|^2 + mean |x(50) - x_target(50)|^2, theta = (0.9, 1.05)) of the
@@ -408,6 +459,8 @@ def run_gpu(args):
     ensemble = None if args.no_ensemble else run_ensemble(args, stream, world)
     adjoint = None if (args.no_ensemble or rank != 0) else run_adjoint(x, L, stream)
     n2 = None if (args.no_ensemble or rank != 0) else run_n2_breakeven(stream)
+    rng = None if (args.no_ensemble or rank != 0) else run_rand48(stream, (read_peaks() or {}).get("hbm_gbs"))
+    langevin = None if (args.no_ensemble or rank != 0) else run_langevin(x, v, L, w, stream)
 
     if rank != 0:
         if world > 1:
@@ -447,6 +500,8 @@ def run_gpu(args):
         "ensemble": ensemble,
         "adjoint": adjoint,
         "n2_vs_cells": n2,
+        "rand48": rng,
+        "langevin": langevin,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64},

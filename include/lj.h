@@ -145,6 +145,50 @@ int lj_get_cells(lj_ctx *ctx, int32_t *cell_of, int32_t *count, int32_t *start, 
  * energies. */
 int lj_forces(lj_ctx *ctx, const double *x, void *f, double *e_pot, double *virial);
 
+/* ---- rand48 random numbers (Section 4) ---------------------------------
+ * The series x_{n+1} = (a x_n + c) mod 2^48, a = 0x5DEECE66D, c = 0xB (Eq.
+ * lrand48; the POSIX rand48 constants), generated by S parallel streams with
+ * the leap-frog rule x_{n+S} = (A x_n + C) mod 2^48 (Eq. lrand48m).
+ * `state` is a caller-owned device array of S uint64 (one 48-bit value per
+ * stream).  Stream i holds the series element it outputs next; output round
+ * r writes element r S + i of the call's range, so a call's output is the
+ * serial series in order and consecutive calls continue it.  Calls on one
+ * state array must not overlap.  Errors: LJ_EINVAL (negative sizes, host or
+ * misaligned pointers), LJ_EOVERFLOW (S R >= 2^40), LJ_ECUDA. */
+
+/* x_0 of srand48(seed): (low 32 bits of seed) << 16 | 0x330E.  Host. */
+uint64_t lj_srand48_state(int64_t seed);
+
+/* Jump constants A = a^m, C = c (1 + a + ... + a^{m-1}) mod 2^48 (Eq. AC,
+ * with m terms in the sum).  Host; LJ_EINVAL for m < 0 or NULL outputs. */
+int lj_rand48_jump(int64_t m, uint64_t *A, uint64_t *C);
+
+/* state[i] = x_{i+1} for i < S: the first S elements after x0.  Async. */
+int lj_rand48_seed(uint64_t *state, int64_t S, uint64_t x0, void *stream);
+
+/* R rounds: out[r S + i] = x >> 17 (lrand48, 31 bits) of stream i's
+ * element, then the stream jumps by S.  out: device int32[R S].  Async. */
+int lj_rand48_lrand(uint64_t *state, int64_t S, int64_t R, int32_t *out, void *stream);
+
+/* As lj_rand48_lrand with out[r S + i] = x 2^-48 (drand48, [0, 1)): device
+ * double[R S]. */
+int lj_rand48_drand(uint64_t *state, int64_t S, int64_t R, double *out, void *stream);
+
+/* ---- Langevin thermostat ------------------------------------------------
+ * The stochastic thermostat Section 1 names (single precision suffices for
+ * systems held in equilibrium by one); the paper gives no scheme, read here
+ * as BAOAB: v += (dt/2m) f; x += (dt/2) v; v = c1 v + c2 sqrt(kT/m) xi with
+ * c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2); x += (dt/2) v, wrap, rebin;
+ * f = F(x); v += (dt/2m) f.  xi: Box-Muller normals from the context's
+ * rand48 series, one stream per particle: step s of particle i uses series
+ * elements (4 s + k) n + i + 1, k = 0..3 (xi_x, xi_y from k = 0, 1; xi_z
+ * from k = 2, 3).  In FP32-mixed the normals are formed in FP32.
+ * lj_langevin_seed starts the series at srand48(seed) (allocates n uint64
+ * on first use); lj_langevin_step runs nsteps steps (x, v, f as lj_step;
+ * gamma, kT >= 0); it returns LJ_EINVAL before the first seed.  Async. */
+int lj_langevin_seed(lj_ctx *ctx, int64_t seed);
+int lj_langevin_step(lj_ctx *ctx, double *x, double *v, void *f, int32_t nsteps, double gamma, double kT);
+
 /* All-pairs forces (Section 2, Eq. n2_force with the cutoff): the same
  * forces as lj_forces computed without cells, every pair at the minimum
  * image, O(n^2) work.  For small systems, as a GPU brute-force cross-check,

@@ -6,6 +6,21 @@
 
 #include "lj_internal.cuh"
 
+// Device (or managed) memory check for caller arrays.
+int check_dev_ptr(const void *ptr, size_t align)
+{
+    if (!ptr) return LJ_EINVAL;
+    if (((uintptr_t)ptr) % align != 0) return LJ_EINVAL;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LJ_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return LJ_EINVAL;
+    return LJ_OK;
+}
+
 namespace {
 
 constexpr int kEventPool = 2 * 8192;
@@ -57,21 +72,6 @@ int validate(const lj_params *p, int *nc_out)
     return LJ_OK;
 }
 
-// Device (or managed) memory check for caller arrays.
-int check_dev_ptr(const void *ptr, size_t align)
-{
-    if (!ptr) return LJ_EINVAL;
-    if (((uintptr_t)ptr) % align != 0) return LJ_EINVAL;
-    cudaPointerAttributes a;
-    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return LJ_EINVAL;
-    }
-    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return LJ_EINVAL;
-    return LJ_OK;
-}
-
 size_t force_vsize(const lj_ctx *c)
 {
     return c->p.precision == LJ_PREC_FP64 ? sizeof(double4_16a) : sizeof(float4);
@@ -99,6 +99,7 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->fs);
     cudaFree(c->g4);
     cudaFree(c->n2_scratch);
+    cudaFree(c->r48_state);
     if (c->host_scalars) cudaFreeHost(c->host_scalars);
     if (c->host_err) cudaFreeHost(c->host_err);
     if (c->ev) {
@@ -365,6 +366,37 @@ extern "C" int lj_forces(lj_ctx *c, const double *x, void *f, double *e_pot, dou
     if (r) return r;
     if (e_pot) *e_pot = c->host_scalars[0];
     if (virial) *virial = c->host_scalars[1];
+    return LJ_OK;
+}
+
+extern "C" int lj_langevin_seed(lj_ctx *c, int64_t seed)
+{
+    if (!c) return LJ_EINVAL;
+    if (c->p.n == 0) return LJ_OK;
+    if (!c->r48_state) LJ_CK(cudaMalloc(&c->r48_state, (size_t)c->p.n * sizeof(uint64_t)));
+    LJ_CK(launch_r48_seed(c->r48_state, c->p.n, lj_srand48_state(seed), c->stream));
+    c->kernel_launches++;
+    return LJ_OK;
+}
+
+extern "C" int lj_langevin_step(lj_ctx *c, double *x, double *v, void *f, int32_t nsteps, double gamma, double kT)
+{
+    if (!c || nsteps < 0 || !(gamma >= 0.0) || !isfinite(gamma) || !(kT >= 0.0) || !isfinite(kT)) return LJ_EINVAL;
+    if (c->p.n == 0 || nsteps == 0) return LJ_OK;
+    if (!c->r48_state) return LJ_EINVAL;   // lj_langevin_seed first
+    int r = check_dev_ptr(x, 8);
+    if (r) return r;
+    r = check_dev_ptr(v, 8);
+    if (r) return r;
+    r = check_dev_ptr(f, 16);
+    if (r) return r;
+    for (int s = 0; s < nsteps; s++) {
+        LJ_CK(launch_langevin_bin(c, x, v, f, s == 0 ? 1 : 2, gamma, kT));
+        LJ_CK(launch_scan(c));
+        LJ_CK(launch_scatter(c, x, false));
+        LJ_CK(launch_force(c, f, false));
+    }
+    LJ_CK(launch_kick(c, v, f));
     return LJ_OK;
 }
 

@@ -72,6 +72,7 @@ struct lj_ctx {
     int npartial_cap;    // capacity of `partial` in (energy, virial) pairs
     void *g4;            // sorted cotangents for the adjoint (lazily allocated)
     void *n2_scratch;    // all-pairs kernel scratch (lazily allocated)
+    uint64_t *r48_state; // Langevin thermostat: one rand48 stream per particle (lazily allocated)
     size_t n2_bytes;
     int ekin_grid;
 
@@ -203,12 +204,20 @@ cudaError_t launch_kick(lj_ctx *c, double *v, const void *f);
 cudaError_t launch_ekin(lj_ctx *c, const double *v);
 cudaError_t launch_counts_from_start(lj_ctx *c, int32_t *count);
 cudaError_t force_configure(lj_ctx *c);
+// LJ_OK if ptr is device (or managed) memory aligned to `align` bytes, else
+// LJ_EINVAL (lj_api.cu).
+int check_dev_ptr(const void *ptr, size_t align);
+
 cudaError_t warp_force_configure(lj_ctx *c);
 // Staged-candidate capacity per warp of the warp kernels (lj_force_warp.cu).
 int warp_stencil_cap(double mean_occupancy, int subdiv, int threads, int static_bytes);
 cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, double *dparam);
 cudaError_t launch_axpy(lj_ctx *c, double *y, const double *x, double a);
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);
+// rand48 streams and the Langevin update (lj_rand48.cu).
+cudaError_t launch_r48_seed(uint64_t *state, int64_t S, uint64_t x0, cudaStream_t stream);
+cudaError_t launch_langevin_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick, double gamma, double kT);
+
 // All-pairs forces (lj_n2.cu); energies into c->scalars[0..1] when energy.
 cudaError_t launch_forces_n2(lj_ctx *c, const double *x, void *f, bool energy);
 cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bool last);

@@ -68,6 +68,13 @@ _SIGS = {
     "lj_bin": ([_P, _P], ctypes.c_int),
     "lj_get_cells": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "lj_forces_n2": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "lj_srand48_state": ([ctypes.c_int64], ctypes.c_uint64),
+    "lj_rand48_jump": ([ctypes.c_int64, _P, _P], ctypes.c_int),
+    "lj_rand48_seed": ([_P, ctypes.c_int64, ctypes.c_uint64, _P], ctypes.c_int),
+    "lj_rand48_lrand": ([_P, ctypes.c_int64, ctypes.c_int64, _P, _P], ctypes.c_int),
+    "lj_rand48_drand": ([_P, ctypes.c_int64, ctypes.c_int64, _P, _P], ctypes.c_int),
+    "lj_langevin_seed": ([_P, ctypes.c_int64], ctypes.c_int),
+    "lj_langevin_step": ([_P, _P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double], ctypes.c_int),
     "lj_forces": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lj_step": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "lj_step_host": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
@@ -235,6 +242,64 @@ def lj_forces_n2(ctx: Context, x, f, energy: bool = False):
         return e.value, w.value
     _ck(load().lj_forces_n2(ctx.handle, xp, fp, None, None), "lj_forces_n2")
     return None
+
+
+def lj_srand48_state(seed: int) -> int:
+    return int(load().lj_srand48_state(int(seed)))
+
+
+def lj_rand48_jump(m: int) -> tuple[int, int]:
+    A = ctypes.c_uint64()
+    C = ctypes.c_uint64()
+    _ck(load().lj_rand48_jump(int(m), ctypes.byref(A), ctypes.byref(C)), "lj_rand48_jump")
+    return int(A.value), int(C.value)
+
+
+def _state(state):
+    import torch
+    if not (isinstance(state, torch.Tensor) and state.is_cuda and state.dtype == torch.int64
+            and state.is_contiguous() and state.dim() == 1):
+        raise TypeError("state must be a contiguous 1-D CUDA int64 tensor (uint64 bit patterns)")
+    return ctypes.c_void_p(state.data_ptr()), state.numel()
+
+
+def lj_rand48_seed(state, x0: int, stream=None) -> None:
+    """state[i] = x_{i+1} of the series from x0 (state: CUDA int64 tensor)."""
+    p, S = _state(state)
+    _ck(load().lj_rand48_seed(p, S, ctypes.c_uint64(int(x0)), _stream_ptr(stream)), "lj_rand48_seed")
+
+
+def lj_rand48_lrand(state, R: int, out=None, stream=None):
+    """R rounds of lrand48 values from every stream: out (R * S,) int32."""
+    import torch
+    p, S = _state(state)
+    if out is None:
+        out = torch.empty(int(R) * S, dtype=torch.int32, device=state.device)
+    o = _dev(out, torch.int32, (int(R) * S,), "out")
+    _ck(load().lj_rand48_lrand(p, S, int(R), o, _stream_ptr(stream)), "lj_rand48_lrand")
+    return out
+
+
+def lj_rand48_drand(state, R: int, out=None, stream=None):
+    """R rounds of drand48 values from every stream: out (R * S,) float64."""
+    import torch
+    p, S = _state(state)
+    if out is None:
+        out = torch.empty(int(R) * S, dtype=torch.float64, device=state.device)
+    o = _dev(out, torch.float64, (int(R) * S,), "out")
+    _ck(load().lj_rand48_drand(p, S, int(R), o, _stream_ptr(stream)), "lj_rand48_drand")
+    return out
+
+
+def lj_langevin_seed(ctx: Context, seed: int) -> None:
+    _ck(load().lj_langevin_seed(ctx.handle, int(seed)), "lj_langevin_seed")
+
+
+def lj_langevin_step(ctx: Context, x, v, f, nsteps: int, gamma: float, kT: float) -> None:
+    import torch
+    _ck(load().lj_langevin_step(ctx.handle, _dev(x, torch.float64, (ctx.n, 3), "x"),
+                                _dev(v, torch.float64, (ctx.n, 3), "v"), _dev(f, ctx.force_dtype, (ctx.n, 4), "f"),
+                                int(nsteps), float(gamma), float(kT)), "lj_langevin_step")
 
 
 def lj_step(ctx: Context, x, v, f, nsteps: int) -> None:
