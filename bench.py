@@ -250,6 +250,33 @@ def run_langevin(x, v, L, w, stream):
             "scheme": "BAOAB, Box-Muller normals from the rand48 series (one stream per particle)"}
 
 
+def run_skin(x, v, L, w, stream, steps=60):
+    """Cell lists with a skin on the 4M workload: ms per step and rebuilds
+    for a few skins, beside the per-step rebuild (skin 0)."""
+    import torch
+    from paper_0709_3225_gb300 import lj
+    out = []
+    for skin in (0.0, 0.3, 0.6):
+        s = lj.System(x, v, L, precision="mixed", dt=w.dt, rc=w.rc)
+        if skin > 0:
+            lj.lj_set_skin(s.ctx, skin)
+        s.forces()
+        s.step(5)
+        torch.cuda.synchronize()
+        r0, n0 = lj.lj_skin_stats(s.ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        r1, n1 = lj.lj_skin_stats(s.ctx)
+        s.check()
+        out.append({"skin": skin, "cells_per_axis": s.ctx.nc, "ms_per_step": e0.elapsed_time(e1) / steps,
+                    "rebuilds": (r1 - r0) if skin > 0 else steps, "steps": steps})
+        s.close()
+    return out
+
+
 def run_adjoint(x4m, L4m, stream):
     """The adjoint workload: the force-matching gradient (loss = mean |F -
     F_target|^2 + mean |x(50) - x_target(50)|^2, theta = (0.9, 1.05)) of the
@@ -461,6 +488,7 @@ def run_gpu(args):
     n2 = None if (args.no_ensemble or rank != 0) else run_n2_breakeven(stream)
     rng = None if (args.no_ensemble or rank != 0) else run_rand48(stream, (read_peaks() or {}).get("hbm_gbs"))
     langevin = None if (args.no_ensemble or rank != 0) else run_langevin(x, v, L, w, stream)
+    skin = None if (args.no_ensemble or rank != 0) else run_skin(x, v, L, w, stream)
 
     if rank != 0:
         if world > 1:
@@ -502,6 +530,7 @@ def run_gpu(args):
         "n2_vs_cells": n2,
         "rand48": rng,
         "langevin": langevin,
+        "skin": skin,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64},

@@ -248,6 +248,29 @@ int lj_forces_vjp(lj_ctx *ctx, const double *x, const double *g, double scale, d
 int lj_vv_adjoint_step(lj_ctx *ctx, const double *x_n, const double *x_n1, double *lam_x, double *lam_v,
                        double *dparam);
 
+/* Cell lists with a skin (Section 3.1: cells wider than the interaction
+ * range plus a skin lambda stay valid while particles move, so they need not
+ * be rebuilt every step; the paper's one-step-lagged update is the case of a
+ * skin covering one step's motion, and it notes that a larger skin with
+ * rebuilds every few steps is common practice).  skin = lambda >= 0:
+ * cells of side >= (rc + skin) / k, i.e. n = int[k L / (rc + skin)] per
+ * axis (LJ_EBOX if n < 2k + 1); skin = 0 restores rebuilding every step.
+ * With skin > 0, lj_step rebuilds the cell lists only when some particle
+ * has moved more than skin/2 since the last rebuild -- then two particles
+ * within rc may have drifted out of each other's stencil -- or every
+ * max_interval steps if max_interval > 0.  The decision is made on the
+ * device from FP32 displacement sums, without host synchronization;
+ * between rebuilds the sorted positions are refreshed from x in the old
+ * cell order.  Forces are those of the exact cell list.  lj_forces,
+ * lj_energy and the adjoint always rebuild.  Reallocates the cell arrays
+ * when n changes; LJ_EINVAL with the fused update (lj_set_tuning kernel 0)
+ * or skin < 0.  Synchronizes. */
+int lj_set_skin(lj_ctx *ctx, double skin, int32_t max_interval);
+
+/* Rebuilds and steps counted in skin mode since lj_set_skin (a full
+ * rebuild by lj_forces is not counted).  Host pointers; synchronizes. */
+int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);
+
 /* Choose the force kernel of a context (same results; for autotuning):
  * kernel 0 = warp-per-cell kernel (FP32-mixed only) with the velocity-Verlet
  * update of lj_step fused into it, 1 = run kernel with bulk-copy staging,

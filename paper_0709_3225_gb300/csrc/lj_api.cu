@@ -100,6 +100,9 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->g4);
     cudaFree(c->n2_scratch);
     cudaFree(c->r48_state);
+    cudaFree(c->disp);
+    cudaFree(c->skin_flags);
+    cudaFree(c->skin_counts);
     if (c->host_scalars) cudaFreeHost(c->host_scalars);
     if (c->host_err) cudaFreeHost(c->host_err);
     if (c->ev) {
@@ -126,16 +129,50 @@ int sync_and_check(lj_ctx *c)
     return LJ_OK;
 }
 
+// Restart the skin bookkeeping after a full rebuild (the ungated count
+// kernel has cleared the displacements).
+int skin_restart(lj_ctx *c)
+{
+    if (c->skin > 0.0) {
+        LJ_CK(cudaMemsetAsync(c->skin_flags, 0, sizeof(int32_t), c->stream));
+        LJ_CK(cudaMemsetAsync(c->skin_flags + 2, 0, sizeof(int32_t), c->stream));
+        c->skin_dirty = 0;
+    }
+    return LJ_OK;
+}
+
 int do_bin(lj_ctx *c, const double *x, bool wrap_in_scatter)
 {
     LJ_CK(launch_bin_count(c, x));
     LJ_CK(launch_scan(c));
     LJ_CK(launch_scatter(c, x, wrap_in_scatter));
+    return skin_restart(c);
+}
+
+// Cell lists with a skin: the cells are rebuilt only when the device-side
+// decision (k_skin_decide) asks for it; otherwise the sorted positions are
+// refreshed from x in the old cell order (the scatter with the old ranks).
+int do_steps_skin(lj_ctx *c, double *x, double *v, void *f, int nsteps)
+{
+    for (int s = 0; s < nsteps; s++) {
+        LJ_CK(launch_kick_drift_skin(c, x, v, f, s == 0 ? 1 : 2));
+        const bool gated = !c->skin_dirty;
+        LJ_CK(launch_bin_count(c, x, gated));
+        LJ_CK(launch_scan(c, gated));
+        LJ_CK(launch_scatter(c, x, false));
+        if (!gated) {
+            int r = skin_restart(c);
+            if (r) return r;
+        }
+        LJ_CK(launch_force(c, f, false));
+    }
+    if (nsteps > 0) LJ_CK(launch_kick(c, v, f));
     return LJ_OK;
 }
 
 int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps)
 {
+    if (c->skin > 0.0) return do_steps_skin(c, x, v, f, nsteps);
     if (!c->use_run_kernel && c->fuse_update && nsteps > 0) {
         // FP32-mixed warp kernel: the first kick + drift + bin runs alone; every
         // force launch then applies the next step's update to the particles it
@@ -195,6 +232,71 @@ extern "C" int lj_grid(const lj_params *p, int32_t *nc_out)
     return LJ_OK;
 }
 
+// (Re)build the cell grid of a context for n cells per axis: cell geometry,
+// count / start / scan arrays, cell-centre and threshold tables, kernel
+// configurations and the energy partials.  Frees what an earlier grid held.
+int setup_grid(lj_ctx *c, int nc)
+{
+    cudaFree(c->count);
+    cudaFree(c->start);
+    cudaFree(c->centre);
+    cudaFree(c->thb);
+    cudaFree(c->tile_sum);
+    cudaFree(c->partial);
+    c->count = c->start = c->tile_sum = nullptr;
+    c->centre = nullptr;
+    c->thb = nullptr;
+    c->partial = nullptr;
+    c->nc = nc;
+    c->ncell = (int64_t)nc * nc * nc;
+    c->inv_cw = (double)nc / c->p.box;
+    c->cw = c->p.box / (double)nc;
+#define LJ_GRID_CK(call)             \
+    do {                             \
+        cudaError_t e_ = (call);     \
+        if (e_ != cudaSuccess) return map_cuda(e_); \
+    } while (0)
+    LJ_GRID_CK(cudaMalloc(&c->count, (size_t)(c->ncell + 1) * sizeof(int32_t)));
+    LJ_GRID_CK(cudaMalloc(&c->start, (size_t)(c->ncell + 2) * sizeof(int32_t)));
+    {
+        double *h = (double *)malloc(sizeof(double) * (size_t)nc);
+        if (!h) return LJ_ENOMEM;
+        for (int k = 0; k < nc; k++) h[k] = ((double)k + 0.5) * c->cw;
+        cudaError_t e = cudaMalloc(&c->centre, sizeof(double) * (size_t)nc);
+        if (e == cudaSuccess) e = cudaMemcpy(c->centre, h, sizeof(double) * (size_t)nc, cudaMemcpyHostToDevice);
+        free(h);
+        long long *tb = (long long *)malloc(sizeof(long long) * (size_t)(nc + 1));
+        if (!tb && e == cudaSuccess) e = cudaErrorMemoryAllocation;
+        if (tb) {
+            tb[0] = 0;
+            for (int k = 1; k < nc; k++) {
+                double t = cell_threshold(k, c->inv_cw);
+                memcpy(&tb[k], &t, sizeof(double));
+            }
+            tb[nc] = INT64_MAX;
+            if (e == cudaSuccess) e = cudaMalloc(&c->thb, sizeof(long long) * (size_t)(nc + 1));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(c->thb, tb, sizeof(long long) * (size_t)(nc + 1), cudaMemcpyHostToDevice);
+            free(tb);
+        }
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    c->ntiles = (int)((c->ncell + 1 + kScanTile - 1) / kScanTile);
+    LJ_GRID_CK(cudaMalloc(&c->tile_sum, (size_t)c->ntiles * sizeof(int32_t)));
+    LJ_GRID_CK(force_configure(c));
+    if (c->p.precision == LJ_PREC_MIXED) LJ_GRID_CK(warp_force_configure(c));
+    {
+        int np = c->force_grid > c->wforce_grid ? c->force_grid : c->wforce_grid;
+        if (np < 32 * c->nsm) np = 32 * c->nsm;   // room for the adjoint kernel's grid
+        c->npartial_cap = np;
+        LJ_GRID_CK(cudaMalloc(&c->partial, 2 * (size_t)np * sizeof(double)));
+    }
+    LJ_GRID_CK(cudaMemsetAsync(c->count, 0, (size_t)(c->ncell + 1) * sizeof(int32_t), c->stream));
+    LJ_GRID_CK(cudaMemsetAsync(c->start, 0, (size_t)(c->ncell + 2) * sizeof(int32_t), c->stream));
+#undef LJ_GRID_CK
+    return LJ_OK;
+}
+
 extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
 {
     if (!out) return LJ_EINVAL;
@@ -206,10 +308,6 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     if (!c) return LJ_ENOMEM;
     c->p = *p;
     if (c->p.cell_subdiv == 0) c->p.cell_subdiv = 1;
-    c->nc = nc;
-    c->ncell = (int64_t)nc * nc * nc;
-    c->inv_cw = (double)nc / p->box;
-    c->cw = p->box / (double)nc;
     c->wrap_hi = p->box * (1.0 - ldexp(1.0, -50));
     c->wrap_lo = p->box * ldexp(1.0, -50);
     c->stream = (cudaStream_t)stream;
@@ -237,47 +335,13 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     LJ_CREATE_CK(cudaMalloc(&c->cell_of, n1 * sizeof(int32_t)));
     LJ_CREATE_CK(cudaMalloc(&c->rank, n1 * sizeof(int32_t)));
     LJ_CREATE_CK(cudaMalloc(&c->perm, n1 * sizeof(int32_t)));
-    LJ_CREATE_CK(cudaMalloc(&c->count, (size_t)(c->ncell + 1) * sizeof(int32_t)));
-    LJ_CREATE_CK(cudaMalloc(&c->start, (size_t)(c->ncell + 2) * sizeof(int32_t)));
     LJ_CREATE_CK(cudaMalloc(&c->pos, n1 * force_vsize(c)));
     {
-        double *h = (double *)malloc(sizeof(double) * (size_t)nc);
-        if (!h) {
+        const int gr = setup_grid(c, nc);
+        if (gr != LJ_OK) {
             free_ctx(c);
-            return LJ_ENOMEM;
+            return gr;
         }
-        for (int k = 0; k < nc; k++) h[k] = ((double)k + 0.5) * c->cw;
-        cudaError_t e = cudaMalloc(&c->centre, sizeof(double) * (size_t)nc);
-        if (e == cudaSuccess) e = cudaMemcpy(c->centre, h, sizeof(double) * (size_t)nc, cudaMemcpyHostToDevice);
-        free(h);
-        long long *tb = (long long *)malloc(sizeof(long long) * (size_t)(nc + 1));
-        if (!tb && e == cudaSuccess) e = cudaErrorMemoryAllocation;
-        if (tb) {
-            tb[0] = 0;
-            for (int k = 1; k < nc; k++) {
-                double t = cell_threshold(k, c->inv_cw);
-                memcpy(&tb[k], &t, sizeof(double));
-            }
-            tb[nc] = INT64_MAX;
-            if (e == cudaSuccess) e = cudaMalloc(&c->thb, sizeof(long long) * (size_t)(nc + 1));
-            if (e == cudaSuccess)
-                e = cudaMemcpy(c->thb, tb, sizeof(long long) * (size_t)(nc + 1), cudaMemcpyHostToDevice);
-            free(tb);
-        }
-        if (e != cudaSuccess) {
-            free_ctx(c);
-            return map_cuda(e);
-        }
-    }
-    c->ntiles = (int)((c->ncell + 1 + kScanTile - 1) / kScanTile);
-    LJ_CREATE_CK(cudaMalloc(&c->tile_sum, (size_t)c->ntiles * sizeof(int32_t)));
-    LJ_CREATE_CK(force_configure(c));
-    if (p->precision == LJ_PREC_MIXED) LJ_CREATE_CK(warp_force_configure(c));
-    {
-        int np = c->force_grid > c->wforce_grid ? c->force_grid : c->wforce_grid;
-        if (np < 32 * c->nsm) np = 32 * c->nsm;   // room for the adjoint kernel's grid
-        c->npartial_cap = np;
-        LJ_CREATE_CK(cudaMalloc(&c->partial, 2 * (size_t)np * sizeof(double)));
     }
     int64_t eb = (3 * (int64_t)n1 + kReduceThreads - 1) / kReduceThreads;
     c->ekin_grid = (int)(eb < 4 * (int64_t)c->nsm ? eb : 4 * (int64_t)c->nsm);
@@ -289,9 +353,7 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     c->grab = 4;   // dynamic pulls of 4 cells: measured fastest at 4M (static striding 5% slower)
     LJ_CREATE_CK(cudaMallocHost(&c->host_scalars, 4 * sizeof(double)));
     LJ_CREATE_CK(cudaMallocHost(&c->host_err, sizeof(int32_t)));
-    LJ_CREATE_CK(cudaMemsetAsync(c->count, 0, (size_t)(c->ncell + 1) * sizeof(int32_t), c->stream));
     LJ_CREATE_CK(cudaMemsetAsync(c->cell_of, 0, n1 * sizeof(int32_t), c->stream));
-    LJ_CREATE_CK(cudaMemsetAsync(c->start, 0, (size_t)(c->ncell + 2) * sizeof(int32_t), c->stream));
     LJ_CREATE_CK(cudaMemsetAsync(c->scalars, 0, 4 * sizeof(double), c->stream));
     LJ_CREATE_CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
     LJ_CREATE_CK(cudaStreamSynchronize(c->stream));
@@ -539,6 +601,48 @@ extern "C" int lj_vv_adjoint_step(lj_ctx *c, const double *x_n, const double *x_
     return LJ_OK;
 }
 
+extern "C" int lj_set_skin(lj_ctx *c, double skin, int32_t max_interval)
+{
+    if (!c || !(skin >= 0.0) || !isfinite(skin) || max_interval < 0) return LJ_EINVAL;
+    if (skin > 0.0 && c->fuse_update) return LJ_EINVAL;   // the fused update bins in the force kernel
+    const int k = c->p.cell_subdiv == 2 ? 2 : 1;
+    const double q = floor(((double)k * c->p.box) / (c->p.rc + skin));
+    if (!(q >= 2.0 * k + 1.0)) return LJ_EBOX;
+    const int nc = (int)q;
+    if (nc != c->nc) {
+        LJ_CK(cudaStreamSynchronize(c->stream));
+        int r = setup_grid(c, nc);
+        if (r) return r;
+    }
+    if (skin > 0.0) {
+        const size_t n1 = (size_t)(c->p.n > 0 ? c->p.n : 1);
+        if (!c->disp) LJ_CK(cudaMalloc(&c->disp, n1 * sizeof(float4)));
+        if (!c->skin_flags) LJ_CK(cudaMalloc(&c->skin_flags, 4 * sizeof(int32_t)));
+        if (!c->skin_counts) LJ_CK(cudaMalloc(&c->skin_counts, 2 * sizeof(long long)));
+        LJ_CK(cudaMemsetAsync(c->disp, 0, n1 * sizeof(float4), c->stream));
+        LJ_CK(cudaMemsetAsync(c->skin_flags, 0, 4 * sizeof(int32_t), c->stream));
+        LJ_CK(cudaMemsetAsync(c->skin_counts, 0, 2 * sizeof(long long), c->stream));
+    }
+    c->skin = skin;
+    c->skin_max_interval = max_interval;
+    c->skin_dirty = 1;
+    LJ_CK(cudaStreamSynchronize(c->stream));
+    return LJ_OK;
+}
+
+extern "C" int lj_skin_stats(lj_ctx *c, int64_t *rebuilds, int64_t *steps)
+{
+    if (!c) return LJ_EINVAL;
+    long long h[2] = {0, 0};
+    if (c->skin_counts) {
+        LJ_CK(cudaStreamSynchronize(c->stream));
+        LJ_CK(cudaMemcpy(h, c->skin_counts, sizeof(h), cudaMemcpyDeviceToHost));
+    }
+    if (rebuilds) *rebuilds = h[0];
+    if (steps) *steps = h[1];
+    return LJ_OK;
+}
+
 extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int32_t cells_per_grab)
 {
     if (!c || kernel < 0 || kernel > 3 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
@@ -548,6 +652,7 @@ extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int
     const bool warp = kernel == 0 || kernel == 3;
     if (warp && c->p.precision == LJ_PREC_FP64) return LJ_EINVAL;   // warp kernel is FP32-mixed
     if (!warp && c->p.cell_subdiv == 2) return LJ_EINVAL;            // run kernels: 27-cell stencil only
+    if (kernel == 0 && c->skin > 0.0) return LJ_EINVAL;              // fused update bins every step
     if (warp && c->wforce_grid == 0) LJ_CK(warp_force_configure(c));
     c->use_run_kernel = warp ? 0 : 1;
     c->fuse_update = kernel == 0 ? 1 : 0;

@@ -8,12 +8,17 @@
 namespace {
 
 // Per particle: wrapped position, cell id, rank within the cell (one
-// atomic per distinct cell per warp).  Launched with whole warps.
+// atomic per distinct cell per warp).  Launched with whole warps.  With a
+// gate (cell lists with a skin), nothing happens unless *gate is set, and
+// then the particle's displacement accumulator is cleared too.
 __global__ void k_bin_count(const double *__restrict__ x, int n, double L, double whi, double wlo, double s, int nc,
                             int32_t *__restrict__ cell_of, int32_t *__restrict__ rank,
-                            int32_t *__restrict__ count, int32_t *__restrict__ err)
+                            int32_t *__restrict__ count, int32_t *__restrict__ err, const int32_t *gate,
+                            float4 *__restrict__ disp)
 {
+    if (gate && !*gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (disp && i < n) disp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     const bool valid = i < n;
     int c = 0;
     if (valid) {
@@ -37,9 +42,11 @@ __global__ void k_bin_count(const double *__restrict__ x, int n, double L, doubl
 
 // Scan phase 1: sum of each tile of kScanTile counts.
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t *__restrict__ count, int64_t ncell,
-                                                             int32_t *__restrict__ tile_sum, unsigned *work)
+                                                             int32_t *__restrict__ tile_sum, unsigned *work,
+                                                             const int32_t *gate)
 {
     if (work && blockIdx.x == 0 && threadIdx.x == 0) *work = 0u;   // the force kernel's work counter
+    if (gate && !*gate) return;
     __shared__ int32_t warp_sum[kScanThreads / 32];
     int64_t base = (int64_t)blockIdx.x * kScanTile;
     int32_t acc = 0;
@@ -63,8 +70,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t *__re
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int32_t *__restrict__ count, int64_t ncell,
                                                              const int32_t *__restrict__ tile_sum,
                                                              int32_t *__restrict__ start, int n,
-                                                             int32_t *__restrict__ err)
+                                                             int32_t *__restrict__ err, const int32_t *gate)
 {
+    if (gate && !*gate) return;
     __shared__ int32_t warp_tot[kScanThreads / 32];
     __shared__ int32_t s_prefix;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -169,23 +177,27 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 
 }  // namespace
 
-cudaError_t launch_bin_count(lj_ctx *c, const double *x)
+cudaError_t launch_bin_count(lj_ctx *c, const double *x, bool gated)
 {
     int n = (int)c->p.n;
     if (n > 0) {
+        // an ungated binning in skin mode also restarts the displacement count
+        float4 *disp = c->skin > 0.0 ? c->disp : nullptr;
         k_bin_count<<<blocks_for(n, 256), 256, 0, c->stream>>>(x, n, c->p.box, c->wrap_hi, c->wrap_lo, c->inv_cw, c->nc, c->cell_of,
-                                                                c->rank, c->count, c->err);
+                                                                c->rank, c->count, c->err,
+                                                                gated ? c->skin_flags + 1 : nullptr, disp);
         c->kernel_launches++;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(lj_ctx *c)
+cudaError_t launch_scan(lj_ctx *c, bool gated)
 {
     // ncell + 1 cells: the grid and the extra cell of non-finite particles
-    k_scan_tiles<<<c->ntiles, kScanThreads, 0, c->stream>>>(c->count, c->ncell + 1, c->tile_sum, c->work);
+    const int32_t *gate = gated ? c->skin_flags + 1 : nullptr;
+    k_scan_tiles<<<c->ntiles, kScanThreads, 0, c->stream>>>(c->count, c->ncell + 1, c->tile_sum, c->work, gate);
     k_scan_apply<<<c->ntiles, kScanThreads, 0, c->stream>>>(c->count, c->ncell + 1, c->tile_sum, c->start,
-                                                             (int)c->p.n, c->err);
+                                                             (int)c->p.n, c->err, gate);
     c->kernel_launches += 2;
     return cudaGetLastError();
 }

@@ -67,6 +67,64 @@ __global__ void k_kick_drift_bin(double *__restrict__ x, double *__restrict__ v,
     }
 }
 
+// Skin mode (cell lists rebuilt only when needed): kick and drift as
+// k_kick_drift_bin without binning; each particle's displacement since the
+// last rebuild accumulates in FP32, and the largest |displacement|^2 goes
+// to *maxd2 (float bits: non-negative floats order as their bit patterns).
+template <typename F4>
+__global__ void k_kick_drift_skin(double *__restrict__ x, double *__restrict__ v, const F4 *__restrict__ f, int n,
+                                  double hk, double dt, double L, double whi, double wlo,
+                                  float4 *__restrict__ disp, int32_t *maxd2, int32_t *__restrict__ err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float d2 = 0.f;
+    if (i < n) {
+        const int64_t b = 3 * (int64_t)i;
+        double fx, fy, fz;
+        load_f(f, i, fx, fy, fz);
+        const double vx = __fma_rn(hk, fx, v[b]);
+        const double vy = __fma_rn(hk, fy, v[b + 1]);
+        const double vz = __fma_rn(hk, fz, v[b + 2]);
+        const double px = lj_wrap_fast(__fma_rn(dt, vx, x[b]), L, whi, wlo);
+        const double py = lj_wrap_fast(__fma_rn(dt, vy, x[b + 1]), L, whi, wlo);
+        const double pz = lj_wrap_fast(__fma_rn(dt, vz, x[b + 2]), L, whi, wlo);
+        v[b] = vx;
+        v[b + 1] = vy;
+        v[b + 2] = vz;
+        x[b] = px;
+        x[b + 1] = py;
+        x[b + 2] = pz;
+        if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(err, LJ_ERRBIT_NONFINITE);
+        float4 d = disp[i];
+        d.x += (float)(dt * vx);
+        d.y += (float)(dt * vy);
+        d.z += (float)(dt * vz);
+        disp[i] = d;
+        d2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        if (!(d2 <= 3.0e38f)) d2 = 3.0e38f;   // non-finite: force a rebuild
+    }
+    for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    if ((threadIdx.x & 31) == 0 && d2 > 0.f) atomicMax(maxd2, __float_as_int(d2));
+}
+
+// One thread: decide whether this step rebuilds the cell lists (largest
+// displacement past thr2, or max_interval steps since the last rebuild) and
+// count.  flags: [0] max |disp|^2 bits, [1] rebuild, [2] steps since.
+__global__ void k_skin_decide(int32_t *flags, long long *counts, float thr2, int max_interval)
+{
+    const int since = flags[2] + 1;
+    const bool rebuild = __int_as_float(flags[0]) > thr2 || (max_interval > 0 && since >= max_interval);
+    flags[1] = rebuild ? 1 : 0;
+    if (rebuild) {
+        flags[0] = 0;
+        flags[2] = 0;
+        counts[0] += 1;
+    } else {
+        flags[2] = since;
+    }
+    counts[1] += 1;
+}
+
 template <typename F4>
 __global__ void k_kick(double *__restrict__ v, const F4 *__restrict__ f, int n, double h)
 {
@@ -132,6 +190,28 @@ cudaError_t launch_kick_drift_bin(lj_ctx *c, double *x, double *v, const void *f
             x, v, (const float4 *)f, n, hk, c->p.dt, c->p.box, c->wrap_hi, c->wrap_lo, c->inv_cw, c->nc, c->thb,
             c->cell_of, c->rank, c->count, c->err);
     c->kernel_launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick_drift_skin(lj_ctx *c, double *x, double *v, const void *f, int nkick)
+{
+    int n = (int)c->p.n;
+    if (n == 0) return cudaSuccess;
+    const double hk = nkick * (0.5 * c->p.dt / c->p.mass);
+    if (c->p.precision == LJ_PREC_FP64)
+        k_kick_drift_skin<double4_16a><<<blocks_for(n, 256), 256, 0, c->stream>>>(
+            x, v, (const double4_16a *)f, n, hk, c->p.dt, c->p.box, c->wrap_hi, c->wrap_lo, c->disp,
+            c->skin_flags, c->err);
+    else
+        k_kick_drift_skin<float4><<<blocks_for(n, 256), 256, 0, c->stream>>>(
+            x, v, (const float4 *)f, n, hk, c->p.dt, c->p.box, c->wrap_hi, c->wrap_lo, c->disp, c->skin_flags,
+            c->err);
+    // rebuild once some particle has moved half the skin (slightly less, for
+    // the FP32 displacement sums): then no pair within rc can have left the
+    // stencil, whose cells are at least rc + skin wide
+    const float thr = (float)(0.5 * c->skin * 0.999);
+    k_skin_decide<<<1, 1, 0, c->stream>>>(c->skin_flags, c->skin_counts, thr * thr, c->skin_max_interval);
+    c->kernel_launches += 2;
     return cudaGetLastError();
 }
 

@@ -73,6 +73,13 @@ struct lj_ctx {
     void *g4;            // sorted cotangents for the adjoint (lazily allocated)
     void *n2_scratch;    // all-pairs kernel scratch (lazily allocated)
     uint64_t *r48_state; // Langevin thermostat: one rand48 stream per particle (lazily allocated)
+    // cell lists with a skin (lj_set_skin): 0 = rebuilt every step
+    double skin;
+    int skin_max_interval;
+    float4 *disp;        // displacement of each particle since the last rebuild (FP32)
+    int32_t *skin_flags; // [0] max |disp|^2 (float bits), [1] rebuild now, [2] steps since rebuild
+    long long *skin_counts;  // [0] rebuilds, [1] steps (skin mode)
+    int skin_dirty;      // the grid changed: the next step rebuilds unconditionally
     size_t n2_bytes;
     int ekin_grid;
 
@@ -194,13 +201,16 @@ template <> struct Vec4<double> { using type = double4_16a; };
 // ------------------------------------------------------------------ host --
 
 // Kernel launchers (each returns cudaGetLastError()).
-cudaError_t launch_bin_count(lj_ctx *c, const double *x);
-cudaError_t launch_scan(lj_ctx *c);
+// gated: skin mode, run only when the device-side rebuild flag is set
+cudaError_t launch_bin_count(lj_ctx *c, const double *x, bool gated = false);
+cudaError_t launch_scan(lj_ctx *c, bool gated = false);
 cudaError_t launch_scatter(lj_ctx *c, const double *x, bool wrap);
 cudaError_t launch_force(lj_ctx *c, void *f, bool energy);
 cudaError_t launch_energy_reduce(lj_ctx *c);
 cudaError_t launch_kick_drift_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick);
 cudaError_t launch_kick(lj_ctx *c, double *v, const void *f);
+// Skin mode: kick + drift + displacement tracking, then the rebuild decision.
+cudaError_t launch_kick_drift_skin(lj_ctx *c, double *x, double *v, const void *f, int nkick);
 cudaError_t launch_ekin(lj_ctx *c, const double *v);
 cudaError_t launch_counts_from_start(lj_ctx *c, int32_t *count);
 cudaError_t force_configure(lj_ctx *c);

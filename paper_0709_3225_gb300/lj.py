@@ -69,6 +69,8 @@ _SIGS = {
     "lj_get_cells": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "lj_forces_n2": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "lj_srand48_state": ([ctypes.c_int64], ctypes.c_uint64),
+    "lj_set_skin": ([_P, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
+    "lj_skin_stats": ([_P, _P, _P], ctypes.c_int),
     "lj_rand48_jump": ([ctypes.c_int64, _P, _P], ctypes.c_int),
     "lj_rand48_seed": ([_P, ctypes.c_int64, ctypes.c_uint64, _P], ctypes.c_int),
     "lj_rand48_lrand": ([_P, ctypes.c_int64, ctypes.c_int64, _P, _P], ctypes.c_int),
@@ -242,6 +244,22 @@ def lj_forces_n2(ctx: Context, x, f, energy: bool = False):
         return e.value, w.value
     _ck(load().lj_forces_n2(ctx.handle, xp, fp, None, None), "lj_forces_n2")
     return None
+
+
+def lj_set_skin(ctx: Context, skin: float, max_interval: int = 0) -> None:
+    """Cell lists with a skin: cells >= (rc + skin) wide, rebuilt only when
+    some particle has moved skin/2 (or every max_interval steps)."""
+    import math
+    _ck(load().lj_set_skin(ctx.handle, float(skin), int(max_interval)), "lj_set_skin")
+    k = ctx.params.cell_subdiv or 1
+    ctx.nc = int(math.floor((k * ctx.params.box) / (ctx.params.rc + float(skin))))
+
+
+def lj_skin_stats(ctx: Context) -> tuple[int, int]:
+    r = ctypes.c_int64()
+    n = ctypes.c_int64()
+    _ck(load().lj_skin_stats(ctx.handle, ctypes.byref(r), ctypes.byref(n)), "lj_skin_stats")
+    return r.value, n.value
 
 
 def lj_srand48_state(seed: int) -> int:
