@@ -250,6 +250,36 @@ def run_langevin(x, v, L, w, stream):
             "scheme": "BAOAB, Box-Muller normals from the rand48 series (one stream per particle)"}
 
 
+def run_aop_density(stream):
+    """The paper's density study (Section 3.2): force time at fixed N =
+    131,072 over densities 0.2 .. 1.0 for the fixed-capacity cell arrays
+    (kernel 4, the paper's layout: work per cell fixed, so time follows the
+    number of cells) and the default CSR warp kernel (time follows the pair
+    count)."""
+    import torch
+    from paper_0709_3225_gb300 import inputs, lj
+    out = []
+    for rho in (0.2, 0.4, 0.6, 0.8, 1.0):
+        x, L = inputs.lattice_gas(131072, rho, 17)
+        s = lj.System(x, None, L)
+        row = {"rho": rho, "cells": s.ctx.nc ** 3, "mean_per_cell": 131072 / s.ctx.nc ** 3}
+        for name, kern in (("csr_ms", 3), ("aop_ms", 4)):
+            lj.lj_set_tuning(s.ctx, kern)
+            s.forces()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(20):
+                s.forces()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[name] = e0.elapsed_time(e1) / 20
+        s.check()
+        s.close()
+        out.append(row)
+    return out
+
+
 def run_skin(x, v, L, w, stream, steps=60):
     """Cell lists with a skin on the 4M workload: ms per step and rebuilds
     for a few skins, beside the per-step rebuild (skin 0)."""
@@ -489,6 +519,7 @@ def run_gpu(args):
     rng = None if (args.no_ensemble or rank != 0) else run_rand48(stream, (read_peaks() or {}).get("hbm_gbs"))
     langevin = None if (args.no_ensemble or rank != 0) else run_langevin(x, v, L, w, stream)
     skin = None if (args.no_ensemble or rank != 0) else run_skin(x, v, L, w, stream)
+    aop = None if (args.no_ensemble or rank != 0) else run_aop_density(stream)
 
     if rank != 0:
         if world > 1:
@@ -531,6 +562,7 @@ def run_gpu(args):
         "rand48": rng,
         "langevin": langevin,
         "skin": skin,
+        "aop_vs_csr_density": aop,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64},

@@ -275,7 +275,10 @@ int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);
  * kernel 0 = warp-per-cell kernel (FP32-mixed only) with the velocity-Verlet
  * update of lj_step fused into it, 1 = run kernel with bulk-copy staging,
  * 2 = run kernel reading global memory, 3 = warp-per-cell kernel with the
- * update in a separate kernel (the FP32-mixed default); kernels 1 and 2
+ * update in a separate kernel (the FP32-mixed default), 4 = the paper's
+ * fixed-capacity cell arrays (Section 3.1: 32 placeholders per cell, empty
+ * ones computed as virtual particles; FP32-mixed; a cell with more than 32
+ * particles latches LJ_EOVERFLOW, reported by lj_check); kernels 1, 2 and 4
  * need cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
  * in chunks of this many lanes, the other 32 / group_width lane groups
  * splitting the candidates; 0 = chosen per cell to minimise idle lanes, or

@@ -5,7 +5,8 @@ It picks, by timing velocity-Verlet steps on a copy of the state:
                      stencil, or 2, the 125-cell stencil of half-size cells),
                      force kernel (warp-per-cell with the velocity-Verlet
                      update separate or fused into it, run kernel with
-                     bulk-copy staging, run kernel reading global memory),
+                     bulk-copy staging, run kernel reading global memory,
+                     the paper's fixed-capacity cell arrays),
                      the lane-group width of the warp kernel (home particles
                      per chunk; 0 = chosen per cell) and the cells per pull
                      from its work counter (0 = static striding);
@@ -86,8 +87,8 @@ def system_candidates(precision: str) -> list[dict]:
         return [{"subdiv": 1, "kernel": k, "gw": 0, "grab": 0} for k in (1, 2)]
     warp = [{"subdiv": 1, "kernel": 3, "gw": g, "grab": c} for g in (0, 4, 8, 16) for c in (0, 4)]
     return warp + [{"subdiv": 1, "kernel": 0, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 1, "gw": 0, "grab": 0},
-                   {"subdiv": 1, "kernel": 2, "gw": 0, "grab": 0}, {"subdiv": 2, "kernel": 3, "gw": 0, "grab": 4},
-                   {"subdiv": 2, "kernel": 3, "gw": 2, "grab": 4}]
+                   {"subdiv": 1, "kernel": 2, "gw": 0, "grab": 0}, {"subdiv": 1, "kernel": 4, "gw": 0, "grab": 0},
+                   {"subdiv": 2, "kernel": 3, "gw": 0, "grab": 4}, {"subdiv": 2, "kernel": 3, "gw": 2, "grab": 4}]
 
 
 def _apply(system: lj.System, choice: dict) -> None:
@@ -132,9 +133,13 @@ def tune_system(system: lj.System, rho: float, steps: int = 10, warmup: int = 3,
                 continue
             x, v, f = target.x.clone(), target.v.clone(), target.f.clone()
             _apply(target, cand)
-            lj.lj_forces(target.ctx, x, f)
-            ms = _time_steps(lambda k: lj.lj_step(target.ctx, x, v, f, k), steps, warmup)
-            lj.lj_check(target.ctx)
+            try:
+                lj.lj_forces(target.ctx, x, f)
+                ms = _time_steps(lambda k: lj.lj_step(target.ctx, x, v, f, k), steps, warmup)
+                lj.lj_check(target.ctx)
+            except lj.LJError as err:   # e.g. a cell over the fixed AOP capacity
+                results.append(dict(cand, ms_per_step=float("inf"), error=str(err)))
+                continue
             results.append(dict(cand, ms_per_step=ms))
     finally:
         for sub, t in copies.items():

@@ -99,6 +99,7 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->fs);
     cudaFree(c->g4);
     cudaFree(c->n2_scratch);
+    cudaFree(c->aop);
     cudaFree(c->r48_state);
     cudaFree(c->disp);
     cudaFree(c->skin_flags);
@@ -126,6 +127,7 @@ int sync_and_check(lj_ctx *c)
     if (bits & LJ_ERRBIT_NONFINITE) return LJ_ENONFINITE;
     if (bits & LJ_ERRBIT_TIMEOUT) return LJ_ETIMEOUT;
     if (bits & LJ_ERRBIT_SCAN) return LJ_ECUDA;
+    if (bits & LJ_ERRBIT_OVERFLOW) return LJ_EOVERFLOW;
     return LJ_OK;
 }
 
@@ -645,7 +647,15 @@ extern "C" int lj_skin_stats(lj_ctx *c, int64_t *rebuilds, int64_t *steps)
 
 extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int32_t cells_per_grab)
 {
-    if (!c || kernel < 0 || kernel > 3 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
+    if (!c || kernel < 0 || kernel > 4 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
+    if (kernel == 4) {   // the paper's fixed-capacity cell arrays: FP32-mixed, 27-cell stencil
+        if (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2) return LJ_EINVAL;
+        c->use_aop = 1;
+        c->use_run_kernel = 0;
+        c->fuse_update = 0;
+        return LJ_OK;
+    }
+    c->use_aop = 0;
     if (group_width != 0 && group_width != 2 && group_width != 4 && group_width != 8 && group_width != 16 &&
         group_width != 32)
         return LJ_EINVAL;

@@ -450,6 +450,7 @@ cudaError_t force_configure(lj_ctx *c)
 cudaError_t launch_force(lj_ctx *c, void *f, bool energy)
 {
     if (c->p.n == 0) return cudaSuccess;
+    if (c->use_aop) return launch_force_aop(c, f, energy);   // sets npartial
     if (!c->use_run_kernel) {
         c->npartial = c->wforce_grid;
         return launch_force_warp(c, f, energy);

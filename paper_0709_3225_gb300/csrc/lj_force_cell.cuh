@@ -476,4 +476,31 @@ __device__ __forceinline__ void process_home_cell(const WarpParams &k, const flo
         cell_plain<R, MODE, ENERGY, NC>(k, pos, out, stab, spre, s_home, n_home, eacc, wacc);
 }
 
+// Kernel parameters of a context: geometry, tuning and the pair coefficients
+// in FP32 (U = c12 r^-12 - c6 r^-6, F/r = r^-2 (a12 r^-12 - b6 r^-6)).
+inline WarpParams warp_params_of(const lj_ctx *c)
+{
+    WarpParams k;
+    k.gw = c->gw;
+    k.grab = c->grab;
+    k.work = c->work;
+    k.n = (int)c->p.n;
+    k.nc = c->nc;
+    k.cap = c->wcap;
+    k.ncell = c->ncell;
+    k.cw = (float)c->cw;
+    const double eps = c->p.eps, sg = c->p.sigma, rc = c->p.rc;
+    const double s6 = sg * sg * sg * sg * sg * sg, s12 = s6 * s6;
+    const double rci2 = 1.0 / (rc * rc), rci6 = rci2 * rci2 * rci2;
+    k.rc2 = (float)(rc * rc);
+    k.rc = (float)rc;
+    k.a12 = (float)(48.0 * eps * s12);
+    k.b6 = (float)(24.0 * eps * s6);
+    k.c12 = (float)(4.0 * eps * s12);
+    k.c6 = (float)(4.0 * eps * s6);
+    k.uc = (float)(rci6 * (4.0 * eps * s12 * rci6 - 4.0 * eps * s6));
+    k.fc = (float)(rc * rci2 * rci6 * (48.0 * eps * s12 * rci6 - 24.0 * eps * s6));
+    return k;
+}
+
 }  // namespace

@@ -170,31 +170,6 @@ cudaError_t warp_force_configure(lj_ctx *c)
 
 namespace {
 
-WarpParams warp_params(const lj_ctx *c)
-{
-    WarpParams k;
-    k.gw = c->gw;
-    k.grab = c->grab;
-    k.work = c->work;
-    k.n = (int)c->p.n;
-    k.nc = c->nc;
-    k.cap = c->wcap;
-    k.ncell = c->ncell;
-    k.cw = (float)c->cw;
-    const double eps = c->p.eps, sg = c->p.sigma, rc = c->p.rc;
-    const double s6 = sg * sg * sg * sg * sg * sg, s12 = s6 * s6;
-    const double rci2 = 1.0 / (rc * rc), rci6 = rci2 * rci2 * rci2;
-    k.rc2 = (float)(rc * rc);
-    k.rc = (float)rc;
-    k.a12 = (float)(48.0 * eps * s12);
-    k.b6 = (float)(24.0 * eps * s6);
-    k.c12 = (float)(4.0 * eps * s12);
-    k.c6 = (float)(4.0 * eps * s6);
-    k.uc = (float)(rci6 * (4.0 * eps * s12 * rci6 - 4.0 * eps * s6));
-    k.fc = (float)(rc * rci2 * rci6 * (48.0 * eps * s12 * rci6 - 24.0 * eps * s6));
-    return k;
-}
-
 cudaError_t launch_warp(lj_ctx *c, void *kern, WarpParams k, void *f, KickDriftBin kd)
 {
     const float4 *pos = (const float4 *)c->pos;
@@ -219,7 +194,7 @@ cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
 {
     KickDriftBin kd;
     memset(&kd, 0, sizeof(kd));
-    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, energy), warp_params(c), f, kd);
+    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, energy), warp_params_of(c), f, kd);
 }
 
 cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bool last)
@@ -243,5 +218,5 @@ cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bo
     kd.rank = c->rank;
     kd.count = c->count;
     kd.err = c->err;
-    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, false, true), warp_params(c), f, kd);
+    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, false, true), warp_params_of(c), f, kd);
 }

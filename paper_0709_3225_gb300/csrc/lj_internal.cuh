@@ -17,6 +17,7 @@ enum : int32_t {
     LJ_ERRBIT_NONFINITE = 1,
     LJ_ERRBIT_TIMEOUT = 2,
     LJ_ERRBIT_SCAN = 4,
+    LJ_ERRBIT_OVERFLOW = 8,   // a cell held more particles than the AOP capacity
 };
 
 // Force-kernel geometry: a work item is a run of up to kRunMax consecutive
@@ -72,6 +73,9 @@ struct lj_ctx {
     int npartial_cap;    // capacity of `partial` in (energy, virial) pairs
     void *g4;            // sorted cotangents for the adjoint (lazily allocated)
     void *n2_scratch;    // all-pairs kernel scratch (lazily allocated)
+    void *aop;           // fixed-capacity cell arrays of the AOP kernel (lazily allocated)
+    size_t aop_bytes;
+    int use_aop;         // tuning: force kernel 4 (AOP layout)
     uint64_t *r48_state; // Langevin thermostat: one rand48 stream per particle (lazily allocated)
     // cell lists with a skin (lj_set_skin): 0 = rebuilt every step
     double skin;
@@ -227,6 +231,9 @@ cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);
 // rand48 streams and the Langevin update (lj_rand48.cu).
 cudaError_t launch_r48_seed(uint64_t *state, int64_t S, uint64_t x0, cudaStream_t stream);
 cudaError_t launch_langevin_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick, double gamma, double kT);
+
+// Forces with the paper's fixed-capacity cell arrays (lj_force_aop.cu).
+cudaError_t launch_force_aop(lj_ctx *c, void *f, bool energy);
 
 // All-pairs forces (lj_n2.cu); energies into c->scalars[0..1] when energy.
 cudaError_t launch_forces_n2(lj_ctx *c, const double *x, void *f, bool energy);
