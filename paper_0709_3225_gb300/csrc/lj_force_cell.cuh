@@ -294,8 +294,10 @@ __device__ __forceinline__ void compute_chunks(const WarpParams &k, const float4
 // margin covers FP32 rounding of the box test).  Kept candidates are
 // appended in ballot order, so the home particles (entry 0, all inside the
 // box) occupy 0 .. n_home-1.
+// Returns false, having computed nothing, when the kept candidates would not
+// fit the slice (then the caller takes the plain path).
 template <int R, int MODE, bool ENERGY, bool NC, class Out>
-__device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *__restrict__ pos, const Out &out,
+__device__ __forceinline__ bool cell_staged(const WarpParams &k, const float4 *__restrict__ pos, const Out &out,
                                             float *X, float *Y, float *Z, const float4 *stab, const int *spre,
                                             int Ttot, int s_home, int n_home, double &eacc, double &wacc)
 {
@@ -354,8 +356,13 @@ __device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *_
                 q[u] = load_pos<NC>(pos + __float_as_int(sh[u].w) + (t - kb));
             }
         }
+        bool full = false;
 #pragma unroll
         for (int u = 0; u < kStageBatch; u++) {
+            if (T + 64 > k.cap) {   // this round (<= 32) plus the padding might not fit
+                full = true;
+                break;
+            }
             const int t = t0 + 32 * u + lane;
             const float cx = q[u].x + sh[u].x;
             const float cy = q[u].y + sh[u].y;
@@ -373,6 +380,10 @@ __device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *_
             }
             T += __popc(kept);
         }
+        if (full) {
+            __syncwarp();   // the slice is rewritten by the next cell
+            return false;
+        }
     }
     X[T + lane] = kFar;   // padding up to the next multiple of 2S (T + 32 <= cap)
     Y[T + lane] = kFar;
@@ -385,6 +396,7 @@ __device__ __forceinline__ void cell_staged(const WarpParams &k, const float4 *_
         case 16: compute_chunks<16, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
         default: compute_chunks<32, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
     }
+    return true;
 }
 
 // Plain path: any occupancy; each stencil cell read from global memory with
@@ -470,10 +482,12 @@ __device__ __forceinline__ void process_home_cell(const WarpParams &k, const flo
     const int n_home = spre[1];
     if (n_home == 0) return;
     const int s_home = __float_as_int(stab[0].w);
-    if (carry + 32 <= k.cap)
-        cell_staged<R, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, stab, spre, carry, s_home, n_home, eacc, wacc);
-    else
-        cell_plain<R, MODE, ENERGY, NC>(k, pos, out, stab, spre, s_home, n_home, eacc, wacc);
+    // Staged unless even the pruned stencil clearly cannot fit; the staging
+    // itself gives up (and the plain path runs) if the kept candidates do not.
+    if (carry <= 2 * k.cap &&
+        cell_staged<R, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, stab, spre, carry, s_home, n_home, eacc, wacc))
+        return;
+    cell_plain<R, MODE, ENERGY, NC>(k, pos, out, stab, spre, s_home, n_home, eacc, wacc);
 }
 
 // Kernel parameters of a context: geometry, tuning and the pair coefficients

@@ -153,6 +153,12 @@ cudaError_t warp_force_configure(lj_ctx *c)
             void *kern = warp_kernel(subdiv, mode, en == 1, en == 2);
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->wforce_smem);
             if (e != cudaSuccess) return e;
+            // shared memory for 4 resident CTAs and no more: the rest of the
+            // SM's 256 KB stays L1, which caches the stencil reads
+            const int pct = (int)((100.0 * 4.0 * (c->wforce_smem + 1024 + 2 * (kWarpForceThreads / 32) * 8)) /
+                                  (228.0 * 1024.0)) + 1;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
+            if (e != cudaSuccess) return e;
             int nb = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kWarpForceThreads, c->wforce_smem);
             if (e != cudaSuccess) return e;
