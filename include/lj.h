@@ -278,8 +278,10 @@ int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);
  * update in a separate kernel (the FP32-mixed default), 4 = the paper's
  * fixed-capacity cell arrays (Section 3.1: 32 placeholders per cell, empty
  * ones computed as virtual particles; FP32-mixed; a cell with more than 32
- * particles latches LJ_EOVERFLOW, reported by lj_check); kernels 1, 2 and 4
- * need cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
+ * particles latches LJ_EOVERFLOW, reported by lj_check), 5 = the warp
+ * kernel with each cell's stencil bulk-copied into shared memory while the
+ * previous cell computes (FP32-mixed); kernels 1, 2, 4 and 5 need
+ * cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
  * in chunks of this many lanes, the other 32 / group_width lane groups
  * splitting the candidates; 0 = chosen per cell to minimise idle lanes, or
  * 2, 4, 8, 16, 32.  cells_per_grab: 0 = the warp kernel's warps take cells

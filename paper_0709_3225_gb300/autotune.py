@@ -6,7 +6,8 @@ It picks, by timing velocity-Verlet steps on a copy of the state:
                      force kernel (warp-per-cell with the velocity-Verlet
                      update separate or fused into it, run kernel with
                      bulk-copy staging, run kernel reading global memory,
-                     the paper's fixed-capacity cell arrays),
+                     the paper's fixed-capacity cell arrays, the warp kernel
+                     with bulk-copied stencils),
                      the lane-group width of the warp kernel (home particles
                      per chunk; 0 = chosen per cell) and the cells per pull
                      from its work counter (0 = static striding);
@@ -88,6 +89,7 @@ def system_candidates(precision: str) -> list[dict]:
     warp = [{"subdiv": 1, "kernel": 3, "gw": g, "grab": c} for g in (0, 4, 8, 16) for c in (0, 4)]
     return warp + [{"subdiv": 1, "kernel": 0, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 1, "gw": 0, "grab": 0},
                    {"subdiv": 1, "kernel": 2, "gw": 0, "grab": 0}, {"subdiv": 1, "kernel": 4, "gw": 0, "grab": 0},
+                   {"subdiv": 1, "kernel": 5, "gw": 0, "grab": 4},
                    {"subdiv": 2, "kernel": 3, "gw": 0, "grab": 4}, {"subdiv": 2, "kernel": 3, "gw": 2, "grab": 4}]
 
 

@@ -287,6 +287,8 @@ int setup_grid(lj_ctx *c, int nc)
     LJ_GRID_CK(cudaMalloc(&c->tile_sum, (size_t)c->ntiles * sizeof(int32_t)));
     LJ_GRID_CK(force_configure(c));
     if (c->p.precision == LJ_PREC_MIXED) LJ_GRID_CK(warp_force_configure(c));
+    c->pipe_grid = 0;
+    if (c->p.precision == LJ_PREC_MIXED && c->p.cell_subdiv != 2) LJ_GRID_CK(pipe_force_configure(c));
     {
         int np = c->force_grid > c->wforce_grid ? c->force_grid : c->wforce_grid;
         if (np < 32 * c->nsm) np = 32 * c->nsm;   // room for the adjoint kernel's grid
@@ -647,7 +649,7 @@ extern "C" int lj_skin_stats(lj_ctx *c, int64_t *rebuilds, int64_t *steps)
 
 extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int32_t cells_per_grab)
 {
-    if (!c || kernel < 0 || kernel > 4 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
+    if (!c || kernel < 0 || kernel > 5 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
     if (kernel == 4) {   // the paper's fixed-capacity cell arrays: FP32-mixed, 27-cell stencil
         if (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2) return LJ_EINVAL;
         c->use_aop = 1;
@@ -656,6 +658,9 @@ extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int
         return LJ_OK;
     }
     c->use_aop = 0;
+    if (kernel == 5 && (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2)) return LJ_EINVAL;
+    c->pipe = kernel == 5 ? 1 : 0;
+    if (kernel == 5) kernel = 3;   // warp kernel, stencils bulk-copied one cell ahead
     if (group_width != 0 && group_width != 2 && group_width != 4 && group_width != 8 && group_width != 16 &&
         group_width != 32)
         return LJ_EINVAL;

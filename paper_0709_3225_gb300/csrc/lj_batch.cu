@@ -449,7 +449,7 @@ cudaError_t configure(lj_batch *b)
     for (int mode = 0; mode < 3; mode++)
         for (int en = 0; en < 2; en++) {
             void *kern = batch_kernel(mode, en != 0);
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem);
+            cudaError_t e = raise_dyn_smem(kern, b->smem);
             if (e != cudaSuccess) return e;
             int nb = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBatchThreads, b->smem);

@@ -432,7 +432,7 @@ cudaError_t force_configure(lj_ctx *c)
         for (int en = 0; en < 2; en++) {
             void *kern = vsize == sizeof(float4) ? pick_kernel<float>(mode, en != 0)
                                                  : pick_kernel<double>(mode, en != 0);
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->force_smem);
+            cudaError_t e = raise_dyn_smem(kern, c->force_smem);
             if (e != cudaSuccess) return e;
             int nb = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kForceThreads, c->force_smem);

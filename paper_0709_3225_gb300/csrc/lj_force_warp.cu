@@ -151,7 +151,7 @@ cudaError_t warp_force_configure(lj_ctx *c)
     for (int mode = 0; mode < 3; mode++)
         for (int en = 0; en < 3; en++) {
             void *kern = warp_kernel(subdiv, mode, en == 1, en == 2);
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->wforce_smem);
+            cudaError_t e = raise_dyn_smem(kern, c->wforce_smem);
             if (e != cudaSuccess) return e;
             // shared memory for 4 resident CTAs and no more: the rest of the
             // SM's 256 KB stays L1, which caches the stencil reads
@@ -198,6 +198,8 @@ cudaError_t launch_warp(lj_ctx *c, void *kern, WarpParams k, void *f, KickDriftB
 
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
 {
+    // tuning choice: stencils bulk-copied one cell ahead (lj_force_pipe.cu)
+    if (c->p.cell_subdiv != 2 && c->pipe) return launch_force_pipe(c, f, energy);
     KickDriftBin kd;
     memset(&kd, 0, sizeof(kd));
     return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, energy), warp_params_of(c), f, kd);

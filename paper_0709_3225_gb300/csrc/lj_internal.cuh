@@ -66,6 +66,9 @@ struct lj_ctx {
     // ... and warp-per-cell kernel (lj_force_warp.cu, FP32-mixed)
     int wcap, wforce_smem, wforce_grid;
     int gw;              // tuning: lane-group width of the warp kernel (0 = per-cell choice)
+    // pipelined warp kernel (lj_force_pipe.cu): slice capacities, launch shape
+    int pcap, praw, pipe_smem, pipe_grid;
+    int pipe;            // tuning: 1 = warp kernel with bulk-copied stencils (kernel 5)
     int fuse_update;     // warp kernel applies the velocity-Verlet update (lj_step)
     int grab;            // tuning: cells per work pull in the warp kernel (0 = static)
     unsigned *work;      // work counter of the warp kernel, zeroed by k_scan_tiles
@@ -218,6 +221,19 @@ cudaError_t launch_kick_drift_skin(lj_ctx *c, double *x, double *v, const void *
 cudaError_t launch_ekin(lj_ctx *c, const double *v);
 cudaError_t launch_counts_from_start(lj_ctx *c, int32_t *count);
 cudaError_t force_configure(lj_ctx *c);
+// Allow kernel `kern` at least `bytes` of dynamic shared memory.  The limit
+// is a property of the function, shared by every context in the process, so
+// it is only ever raised: a context configured later with smaller slices
+// must not lower it under one configured earlier.
+inline cudaError_t raise_dyn_smem(const void *kern, int bytes)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kern);
+    if (e != cudaSuccess) return e;
+    if (a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 // LJ_OK if ptr is device (or managed) memory aligned to `align` bytes, else
 // LJ_EINVAL (lj_api.cu).
 int check_dev_ptr(const void *ptr, size_t align);
@@ -228,6 +244,9 @@ int warp_stencil_cap(double mean_occupancy, int subdiv, int threads, int static_
 cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, double *dparam);
 cudaError_t launch_axpy(lj_ctx *c, double *y, const double *x, double a);
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);
+// Pipelined warp kernel (lj_force_pipe.cu): configuration and launch.
+cudaError_t pipe_force_configure(lj_ctx *c);
+cudaError_t launch_force_pipe(lj_ctx *c, void *f, bool energy);
 // rand48 streams and the Langevin update (lj_rand48.cu).
 cudaError_t launch_r48_seed(uint64_t *state, int64_t S, uint64_t x0, cudaStream_t stream);
 cudaError_t launch_langevin_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick, double gamma, double kT);

@@ -277,7 +277,7 @@ cudaError_t run_n2(lj_ctx *c, const double *x, void *f, bool energy)
     p.fc = rc * rci2 * rci6 * (p.a12 * rci6 - p.b6);
     void *kern = n2_kernel<T>(c->p.shift_mode, energy);
     const int smem = 2 * kN2Tile * (int)sizeof(V) + 2 * (int)sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = raise_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
     V *dst = nsplit == 1 ? fo : part;
     int32_t *err = c->err;

@@ -209,3 +209,25 @@ def test_full_size_4m_sampled(oracle_mod, precision, subdiv):
     net = np.abs(f[:, :3].sum(axis=0)).max()
     unit = 1e-5 if precision == "mixed" else 1e-14
     assert net <= 10 * np.sqrt(x.shape[0]) * unit * frms
+
+
+@pytest.mark.parametrize("gw", [0, 2, 4, 16, 32])
+def test_bulk_copied_stencils(oracle_mod, gw):
+    """Kernel 5 (each cell's stencil bulk-copied into shared memory while the
+    previous cell computes) gives the oracle's forces, including cells that
+    take its plain path (dense cluster) and every lane-group width."""
+    from paper_0709_3225_gb300 import lj
+    for x, L in (inputs.jittered_fcc(9, 0.8442, 0.12, 200 + gw), dense_cluster_state(4)):
+        s = lj.System(x, None, L)
+        lj.lj_set_tuning(s.ctx, 5, gw, 4)
+        e, w = s.forces(energy=True)
+        s.check()
+        f = s.f.double().cpu().numpy()
+        s.close()
+        fo, epo, eo, wo = oracle_mod.forces_cells(x, L, mode=1)
+        near = oracle_mod.near_cutoff(x, L, band=1e-5)
+        K, S = oracle_mod.stiffness(x, L, mode=1)
+        d = np.abs(f[:, :3] - fo).max(axis=1)
+        assert rel_rms(f[:, :3], fo) <= 1e-5
+        assert np.all(d[~near] <= (6e-7 * K + 1e-5 * S)[~near])
+        assert abs(e - eo) <= 2e-6 * np.abs(epo).sum() + 1e-12
