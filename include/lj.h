@@ -283,7 +283,8 @@ int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);
  * previous cell computes (FP32-mixed); kernels 1, 2, 4 and 5 need
  * cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
  * in chunks of this many lanes, the other 32 / group_width lane groups
- * splitting the candidates; 0 = chosen per cell to minimise idle lanes, or
+ * splitting the candidates; 0 = the compiled-in default (16 for
+ * cell_subdiv 1, 4 for 2), -1 = chosen per cell to minimise idle lanes, or
  * 2, 4, 8, 16, 32.  cells_per_grab: 0 = the warp kernel's warps take cells
  * by static striding, 1..1024 = they pull that many cells at a time from an
  * atomic work counter (a new context uses 4).  LJ_EINVAL for other values. */
@@ -316,8 +317,8 @@ int lj_batch_info(const lj_batch *b, int64_t *ntot, int64_t *ncell, int32_t *gri
 
 /* Tuning: cells a warp takes per pull from the work counter (1..1024),
  * whether steps are graph-replayed (1) or launched directly (0), and the
- * lane-group width of the warp kernel (0 = per cell, 2, 4, 8, 16, 32; as in
- * lj_set_tuning). */
+ * lane-group width of the warp kernel (0 or -1 = per cell, 2, 4, 8, 16, 32;
+ * as in lj_set_tuning). */
 int lj_batch_set_tuning(lj_batch *b, int32_t cells_per_grab, int32_t use_graph, int32_t group_width);
 
 /* Forces of every replica at x into f (device arrays as above); with

@@ -9,7 +9,8 @@ It picks, by timing velocity-Verlet steps on a copy of the state:
                      the paper's fixed-capacity cell arrays, the warp kernel
                      with bulk-copied stencils),
                      the lane-group width of the warp kernel (home particles
-                     per chunk; 0 = chosen per cell) and the cells per pull
+                     per chunk; 0 = compiled default, -1 = chosen per cell)
+                     and the cells per pull
                      from its work counter (0 = static striding);
   batches         -- cells per pull from the work counter, lane-group width,
                      graph replay or direct launches.
@@ -86,7 +87,7 @@ def _time_steps(run, steps: int, warmup: int) -> float:
 def system_candidates(precision: str) -> list[dict]:
     if precision == "fp64":
         return [{"subdiv": 1, "kernel": k, "gw": 0, "grab": 0} for k in (1, 2)]
-    warp = [{"subdiv": 1, "kernel": 3, "gw": g, "grab": c} for g in (0, 4, 8, 16) for c in (0, 4)]
+    warp = [{"subdiv": 1, "kernel": 3, "gw": g, "grab": c} for g in (0, -1, 8, 32) for c in (0, 4)]
     return warp + [{"subdiv": 1, "kernel": 0, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 1, "gw": 0, "grab": 0},
                    {"subdiv": 1, "kernel": 2, "gw": 0, "grab": 0}, {"subdiv": 1, "kernel": 4, "gw": 0, "grab": 0},
                    {"subdiv": 1, "kernel": 5, "gw": 0, "grab": 4},

@@ -661,8 +661,8 @@ extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int
     if (kernel == 5 && (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2)) return LJ_EINVAL;
     c->pipe = kernel == 5 ? 1 : 0;
     if (kernel == 5) kernel = 3;   // warp kernel, stencils bulk-copied one cell ahead
-    if (group_width != 0 && group_width != 2 && group_width != 4 && group_width != 8 && group_width != 16 &&
-        group_width != 32)
+    if (group_width != 0 && group_width != -1 && group_width != 2 && group_width != 4 && group_width != 8 &&
+        group_width != 16 && group_width != 32)
         return LJ_EINVAL;
     const bool warp = kernel == 0 || kernel == 3;
     if (warp && c->p.precision == LJ_PREC_FP64) return LJ_EINVAL;   // warp kernel is FP32-mixed

@@ -271,7 +271,7 @@ __device__ void phase_force(const BatchDev &b, const WarpParams &k, float4 *__re
             int cx, cy, cz;
             decode_cell((int)(c - b.coff[r]), nc, cx, cy, cz);
             const StoreForce<MODE, ENERGY> out{f, k.n};
-            process_home_cell<1, MODE, ENERGY, false>(k, b.pos, b.start, out, slice, cx, cy, cz, nc, b.coff[r],
+            process_home_cell<1, MODE, ENERGY, false, 0>(k, b.pos, b.start, out, slice, cx, cy, cz, nc, b.coff[r],
                                                       (float)b.cw[r], eacc, wacc);
         }
     }
@@ -694,8 +694,8 @@ extern "C" int lj_batch_info(const lj_batch *b, int64_t *ntot, int64_t *ncell, i
 extern "C" int lj_batch_set_tuning(lj_batch *b, int32_t cells_per_grab, int32_t use_graph, int32_t group_width)
 {
     if (!b || cells_per_grab < 1 || cells_per_grab > 1024) return LJ_EINVAL;
-    if (group_width != 0 && group_width != 2 && group_width != 4 && group_width != 8 && group_width != 16 &&
-        group_width != 32)
+    if (group_width != 0 && group_width != -1 && group_width != 2 && group_width != 4 && group_width != 8 &&
+        group_width != 16 && group_width != 32)
         return LJ_EINVAL;
     b->d.cells_per_grab = cells_per_grab;
     b->k.gw = group_width;

@@ -13,7 +13,7 @@ constexpr int kStageBatch = 4;   // staging rounds whose loads are in flight tog
 
 struct WarpParams {
     int n, nc, cap;              // cap: staged candidates per warp (multiple of 8, >= 40)
-    int gw;                      // lane-group width of the compute phase (0 = per-cell choice, 2 .. 32)
+    int gw;                      // lane-group width: 0 compiled default, -1 per-cell choice, 2 .. 32 fixed
     int grab;                    // cells per pull from *work (0 = static striding)
     unsigned *work;              // work counter, zero at launch
     int64_t ncell;
@@ -217,6 +217,13 @@ __host__ __device__ constexpr int warp_slice_words(int cap, int R)
            (((2 * R + 1) * (2 * R + 1) * (2 * R + 1) + 1 + 3) & ~3);
 }
 
+// Compiled-in group width of the default kernels: 16 for the 27-cell
+// stencil (~13 particles per cell), 4 for the 125-cell one (~1.7).
+template <int R>
+struct DefaultGroup {
+    static constexpr int value = R == 1 ? 16 : 4;
+};
+
 // Lane-group width of the compute phase: the warp takes the home particles
 // in chunks of G; lane g of a group owns particle g of the chunk and the
 // S = 32 / G groups split the candidates (group s takes candidate pairs
@@ -225,7 +232,7 @@ __host__ __device__ constexpr int warp_slice_words(int cap, int R)
 // count as about one iteration).
 __device__ __forceinline__ int choose_group(int n_home, int T, int fixed)
 {
-    if (fixed) return fixed;
+    if (fixed > 0) return fixed;
     int best = 4, best_cost = 1 << 30;
 #pragma unroll
     for (int lg = 1; lg <= 4; lg++) {
@@ -296,7 +303,7 @@ __device__ __forceinline__ void compute_chunks(const WarpParams &k, const float4
 // box) occupy 0 .. n_home-1.
 // Returns false, having computed nothing, when the kept candidates would not
 // fit the slice (then the caller takes the plain path).
-template <int R, int MODE, bool ENERGY, bool NC, class Out>
+template <int R, int MODE, bool ENERGY, bool NC, int GFIX, class Out>
 __device__ __forceinline__ bool cell_staged(const WarpParams &k, const float4 *__restrict__ pos, const Out &out,
                                             float *X, float *Y, float *Z, const float4 *stab, const int *spre,
                                             int Ttot, int s_home, int n_home, double &eacc, double &wacc)
@@ -389,12 +396,19 @@ __device__ __forceinline__ bool cell_staged(const WarpParams &k, const float4 *_
     Y[T + lane] = kFar;
     Z[T + lane] = kFar;
     __syncwarp();
-    switch (choose_group(n_home, T, k.gw)) {
-        case 2: compute_chunks<2, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
-        case 4: compute_chunks<4, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
-        case 8: compute_chunks<8, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
-        case 16: compute_chunks<16, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
-        default: compute_chunks<32, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+    if constexpr (GFIX > 0) {
+        // one compiled group width: a single compute path keeps the kernel
+        // small and its registers unspilled (measured faster than choosing
+        // per cell)
+        compute_chunks<GFIX, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc);
+    } else {
+        switch (choose_group(n_home, T, k.gw)) {
+            case 2: compute_chunks<2, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+            case 4: compute_chunks<4, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+            case 8: compute_chunks<8, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+            case 16: compute_chunks<16, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+            default: compute_chunks<32, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, T, s_home, n_home, hid, eacc, wacc); break;
+        }
     }
     return true;
 }
@@ -432,7 +446,7 @@ __device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, 
 // whose linear ids start at cell_base in start[] (0 for a single system),
 // cell side cw.  Builds the stencil table in the warp's slice and runs the
 // staged path, or the plain path when the stencil does not fit the slice.
-template <int R, int MODE, bool ENERGY, bool NC, class Out>
+template <int R, int MODE, bool ENERGY, bool NC, int GFIX, class Out>
 __device__ __forceinline__ void process_home_cell(const WarpParams &k, const float4 *__restrict__ pos,
                                                   const int32_t *__restrict__ start, const Out &out_in,
                                                   float *slice, int cx, int cy, int cz, int nc, int64_t cell_base,
@@ -485,7 +499,7 @@ __device__ __forceinline__ void process_home_cell(const WarpParams &k, const flo
     // Staged unless even the pruned stencil clearly cannot fit; the staging
     // itself gives up (and the plain path runs) if the kept candidates do not.
     if (carry <= 2 * k.cap &&
-        cell_staged<R, MODE, ENERGY, NC>(k, pos, out, X, Y, Z, stab, spre, carry, s_home, n_home, eacc, wacc))
+        cell_staged<R, MODE, ENERGY, NC, GFIX>(k, pos, out, X, Y, Z, stab, spre, carry, s_home, n_home, eacc, wacc))
         return;
     cell_plain<R, MODE, ENERGY, NC>(k, pos, out, stab, spre, s_home, n_home, eacc, wacc);
 }

@@ -33,7 +33,9 @@ namespace {
 
 // EPI 0: store forces (and energies); EPI 1: apply the fused velocity-Verlet
 // update (KickDriftBin) to each particle instead.
-template <int R, int MODE, bool ENERGY, int EPI>
+// GFIX > 0: that group width compiled in (the default); 0: chosen per cell
+// or fixed at run time by the tuning (k.gw).
+template <int R, int MODE, bool ENERGY, int EPI, int GFIX>
 __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams k, const float4 *__restrict__ pos,
                                                                   const int32_t *__restrict__ start,
                                                                   float4 *__restrict__ fout,
@@ -49,9 +51,9 @@ __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams 
         const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
         if constexpr (EPI == 0) {
             const StoreForce<MODE, ENERGY> out{fout, k.n};
-            process_home_cell<R, MODE, ENERGY, true>(k, pos, start, out, slice, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
+            process_home_cell<R, MODE, ENERGY, true, GFIX>(k, pos, start, out, slice, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
         } else {
-            process_home_cell<R, MODE, ENERGY, true>(k, pos, start, kd, slice, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
+            process_home_cell<R, MODE, ENERGY, true, GFIX>(k, pos, start, kd, slice, cx, cy, cz, nc, 0, k.cw, eacc, wacc);
         }
     };
     if (k.grab > 0) {
@@ -91,29 +93,38 @@ __global__ void __launch_bounds__(kWarpForceThreads, 4) k_force_warp(WarpParams 
     }
 }
 
-template <int R>
-void *warp_kernel_r(int mode, bool energy, bool fused)
+template <int R, int G>
+void *warp_kernel_rg(int mode, bool energy, bool fused)
 {
     if (fused) {
         switch (mode) {
-            case 0: return (void *)k_force_warp<R, 0, false, 1>;
-            case 1: return (void *)k_force_warp<R, 1, false, 1>;
-            default: return (void *)k_force_warp<R, 2, false, 1>;
+            case 0: return (void *)k_force_warp<R, 0, false, 1, G>;
+            case 1: return (void *)k_force_warp<R, 1, false, 1, G>;
+            default: return (void *)k_force_warp<R, 2, false, 1, G>;
         }
     }
     switch (mode * 2 + (energy ? 1 : 0)) {
-        case 0: return (void *)k_force_warp<R, 0, false, 0>;
-        case 1: return (void *)k_force_warp<R, 0, true, 0>;
-        case 2: return (void *)k_force_warp<R, 1, false, 0>;
-        case 3: return (void *)k_force_warp<R, 1, true, 0>;
-        case 4: return (void *)k_force_warp<R, 2, false, 0>;
-        default: return (void *)k_force_warp<R, 2, true, 0>;
+        case 0: return (void *)k_force_warp<R, 0, false, 0, G>;
+        case 1: return (void *)k_force_warp<R, 0, true, 0, G>;
+        case 2: return (void *)k_force_warp<R, 1, false, 0, G>;
+        case 3: return (void *)k_force_warp<R, 1, true, 0, G>;
+        case 4: return (void *)k_force_warp<R, 2, false, 0, G>;
+        default: return (void *)k_force_warp<R, 2, true, 0, G>;
     }
 }
 
-void *warp_kernel(int subdiv, int mode, bool energy, bool fused = false)
+// The default width (gw 0) runs the kernel with it compiled in; any other
+// tuning (a fixed width, or -1 = choose per cell) runs the general kernel.
+template <int R>
+void *warp_kernel_r(int mode, bool energy, bool fused, int gw)
 {
-    return subdiv == 2 ? warp_kernel_r<2>(mode, energy, fused) : warp_kernel_r<1>(mode, energy, fused);
+    if (gw == 0) return warp_kernel_rg<R, DefaultGroup<R>::value>(mode, energy, fused);
+    return warp_kernel_rg<R, 0>(mode, energy, fused);
+}
+
+void *warp_kernel(int subdiv, int mode, bool energy, bool fused, int gw)
+{
+    return subdiv == 2 ? warp_kernel_r<2>(mode, energy, fused, gw) : warp_kernel_r<1>(mode, energy, fused, gw);
 }
 
 }  // namespace
@@ -149,8 +160,8 @@ cudaError_t warp_force_configure(lj_ctx *c)
     c->wforce_smem = (kWarpForceThreads / 32) * warp_slice_words(c->wcap, subdiv) * (int)sizeof(float);
     int minblk = 1 << 30;
     for (int mode = 0; mode < 3; mode++)
-        for (int en = 0; en < 3; en++) {
-            void *kern = warp_kernel(subdiv, mode, en == 1, en == 2);
+        for (int en = 0; en < 6; en++) {
+            void *kern = warp_kernel(subdiv, mode, en % 3 == 1, en % 3 == 2, en < 3 ? 0 : -1);
             cudaError_t e = raise_dyn_smem(kern, c->wforce_smem);
             if (e != cudaSuccess) return e;
             // shared memory for 4 resident CTAs and no more: the rest of the
@@ -202,7 +213,7 @@ cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
     if (c->p.cell_subdiv != 2 && c->pipe) return launch_force_pipe(c, f, energy);
     KickDriftBin kd;
     memset(&kd, 0, sizeof(kd));
-    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, energy), warp_params_of(c), f, kd);
+    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, energy, false, c->gw), warp_params_of(c), f, kd);
 }
 
 cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bool last)
@@ -226,5 +237,5 @@ cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bo
     kd.rank = c->rank;
     kd.count = c->count;
     kd.err = c->err;
-    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, false, true), warp_params_of(c), f, kd);
+    return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, false, true, c->gw), warp_params_of(c), f, kd);
 }

@@ -65,7 +65,7 @@ struct lj_ctx {
     int run_len, runs, nitems, cap, force_grid, force_smem, use_tma, use_run_kernel;
     // ... and warp-per-cell kernel (lj_force_warp.cu, FP32-mixed)
     int wcap, wforce_smem, wforce_grid;
-    int gw;              // tuning: lane-group width of the warp kernel (0 = per-cell choice)
+    int gw;              // tuning: lane-group width of the warp kernel (0 compiled default, -1 per cell)
     // pipelined warp kernel (lj_force_pipe.cu): slice capacities, launch shape
     int pcap, praw, pipe_smem, pipe_grid;
     int pipe;            // tuning: 1 = warp kernel with bulk-copied stencils (kernel 5)

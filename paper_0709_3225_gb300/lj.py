@@ -386,8 +386,8 @@ def lj_vv_adjoint_step(ctx: Context, x_n, x_n1, lam_x, lam_v, dparam) -> None:
 def lj_set_tuning(ctx: Context, kernel: int, group_width: int = 0, cells_per_grab: int = 4) -> None:
     """Force kernel of a context: 0 warp-per-cell with fused update (mixed),
     1 run-staged, 2 run-direct, 3 warp-per-cell with separate update (mixed);
-    group_width 0 (per cell), 2, 4, 8, 16 or 32; cells_per_grab 0 (static
-    striding) or 1..1024."""
+    group_width 0 (compiled default), -1 (per cell), 2, 4, 8, 16 or 32;
+    cells_per_grab 0 (static striding) or 1..1024."""
     _ck(load().lj_set_tuning(ctx.handle, int(kernel), int(group_width), int(cells_per_grab)), "lj_set_tuning")
 
 

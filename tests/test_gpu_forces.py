@@ -88,10 +88,11 @@ def test_subdivision_two(oracle_mod, mode):
 
 
 @pytest.mark.parametrize("subdiv", [1, 2])
-@pytest.mark.parametrize("gw", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("gw", [0, -1, 2, 4, 8, 16, 32])
 def test_group_widths(oracle_mod, subdiv, gw):
-    """Every fixed lane-group width (chunks of gw home particles, 32 / gw
-    candidate streams) gives the oracle's forces."""
+    """Every lane-group width (chunks of gw home particles, 32 / gw candidate
+    streams; 0 the compiled-in default, -1 chosen per cell) gives the
+    oracle's forces."""
     x, L = inputs.jittered_fcc(7, 0.8442, 0.12, 30 + gw)
     _check(x, L, oracle_mod, "mixed", 1, subdiv=subdiv, gw=gw)
 
