@@ -177,7 +177,7 @@ def make_system(x, v, box: float, rho: float, *, use_cache: bool = True, path: s
 
 
 def batch_candidates() -> list[dict]:
-    out = [{"cells_per_grab": c, "gw": g, "graph": True} for c in (1, 2, 4, 8, 16) for g in (0, 8)]
+    out = [{"cells_per_grab": c, "gw": g, "graph": True} for c in (1, 2, 4, 8, 16) for g in (0, 8, -1)]
     out.append({"cells_per_grab": 4, "gw": 0, "graph": False})
     return out
 

@@ -251,7 +251,7 @@ __device__ void phase_scatter(const BatchDev &b, int op, const double *__restric
 }
 
 // Phase 4: forces, cells pulled in chunks from the work counter.
-template <int MODE, bool ENERGY>
+template <int MODE, bool ENERGY, int GFIX>
 __device__ void phase_force(const BatchDev &b, const WarpParams &k, float4 *__restrict__ f)
 {
     extern __shared__ __align__(16) float bsmem[];
@@ -271,13 +271,14 @@ __device__ void phase_force(const BatchDev &b, const WarpParams &k, float4 *__re
             int cx, cy, cz;
             decode_cell((int)(c - b.coff[r]), nc, cx, cy, cz);
             const StoreForce<MODE, ENERGY> out{f, k.n};
-            process_home_cell<1, MODE, ENERGY, false, 0>(k, b.pos, b.start, out, slice, cx, cy, cz, nc, b.coff[r],
+            process_home_cell<1, MODE, ENERGY, false, GFIX>(k, b.pos, b.start, out, slice, cx, cy, cz, nc, b.coff[r],
                                                       (float)b.cw[r], eacc, wacc);
         }
     }
 }
 
-template <int MODE, bool ENERGY>
+// GFIX as in k_force_warp: 16 compiled in (group width 0), 0 general.
+template <int MODE, bool ENERGY, int GFIX>
 __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_step(BatchDev b, WarpParams k, int op, double *x,
                                                                   double *v, float4 *f)
 {
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_step(BatchDev b, War
     if (!grid_barrier(b)) return;
     phase_scatter(b, op, x);
     if (!grid_barrier(b)) return;
-    phase_force<MODE, ENERGY>(b, k, f);
+    phase_force<MODE, ENERGY, GFIX>(b, k, f);
 }
 
 // Closing half kick of the last step: v += h f.
@@ -360,16 +361,22 @@ __global__ void __launch_bounds__(kReduceThreads) k_batch_energy(const double *_
     }
 }
 
-void *batch_kernel(int mode, bool energy)
+template <int G>
+void *batch_kernel_g(int mode, bool energy)
 {
     switch (mode * 2 + (energy ? 1 : 0)) {
-        case 0: return (void *)k_batch_step<0, false>;
-        case 1: return (void *)k_batch_step<0, true>;
-        case 2: return (void *)k_batch_step<1, false>;
-        case 3: return (void *)k_batch_step<1, true>;
-        case 4: return (void *)k_batch_step<2, false>;
-        default: return (void *)k_batch_step<2, true>;
+        case 0: return (void *)k_batch_step<0, false, G>;
+        case 1: return (void *)k_batch_step<0, true, G>;
+        case 2: return (void *)k_batch_step<1, false, G>;
+        case 3: return (void *)k_batch_step<1, true, G>;
+        case 4: return (void *)k_batch_step<2, false, G>;
+        default: return (void *)k_batch_step<2, true, G>;
     }
+}
+
+void *batch_kernel(int mode, bool energy, int gw)
+{
+    return gw == 0 ? batch_kernel_g<16>(mode, energy) : batch_kernel_g<0>(mode, energy);
 }
 
 // Same threshold construction as lj_create (smallest t with t * s >= k).
@@ -447,8 +454,8 @@ cudaError_t configure(lj_batch *b)
     b->smem = (kBatchThreads / 32) * warp_slice_words(cap, 1) * (int)sizeof(float);
     int minblk = 1 << 30;
     for (int mode = 0; mode < 3; mode++)
-        for (int en = 0; en < 2; en++) {
-            void *kern = batch_kernel(mode, en != 0);
+        for (int en = 0; en < 4; en++) {
+            void *kern = batch_kernel(mode, en % 2 != 0, en < 2 ? 0 : -1);
             cudaError_t e = raise_dyn_smem(kern, b->smem);
             if (e != cudaSuccess) return e;
             int nb = 0;
@@ -463,7 +470,7 @@ cudaError_t configure(lj_batch *b)
 
 cudaError_t launch_step_kernel(lj_batch *b, bool energy, int op, double *x, double *v, float4 *f)
 {
-    void *kern = batch_kernel(b->p.shift_mode, energy);
+    void *kern = batch_kernel(b->p.shift_mode, energy, b->k.gw);
     void *args[] = {&b->d, &b->k, &op, &x, &v, &f};
     b->launches++;
     return cudaLaunchCooperativeKernel(kern, dim3(b->grid), dim3(kBatchThreads), args, b->smem, b->stream);

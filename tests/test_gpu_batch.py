@@ -102,7 +102,7 @@ def test_tuning_knobs_give_same_forces():
     b.forces()
     ref = b.f.clone()
     rms = float(ref[:, :3].double().pow(2).sum(dim=1).mean().sqrt())
-    for cpg, gw in ((1, 0), (16, 32), (3, 16), (2, 2), (5, 4)):
+    for cpg, gw in ((1, 0), (16, 32), (3, 16), (2, 2), (5, 4), (4, -1)):
         b.set_tuning(cells_per_grab=cpg, use_graph=True, group_width=gw)
         b.forces()
         # same arithmetic up to the order of FP32 sums
