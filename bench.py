@@ -528,7 +528,10 @@ def run_gpu(args):
         return 0
 
     peaks = read_peaks()
-    traffic = force_traffic()
+    # the committed ncu figures describe the default kernel; report them only
+    # when the tuner kept it
+    default_kernel = (tuning.get("kernel"), tuning.get("gw"), tuning.get("subdiv", 1)) == (3, 0, 1)
+    traffic = force_traffic() if default_kernel else None
 
     line = {
         "metric": METRIC,
@@ -551,9 +554,12 @@ def run_gpu(args):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "k_force (mixed)", "force_ms_per_launch": force_avg_ms,
+                     "kernel": "k_force_warp (mixed, default tuning)", "force_ms_per_launch": force_avg_ms,
                      "flops_per_launch": FLOPS_PER_PAIR * pairs,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                     "fp32_pipe_busy": force_traffic("fp32_pipe_busy") if default_kernel else None,
+                     "fp32_pipe_busy_source": "ncu sm__pipe_fmaheavy_cycles_active of the default force "
+                                              "kernel at this size (profiles/k_force_warp_traffic_fluid-4m.md)"},
         "other_kernels_ms_per_step": other_ms,
         "tuning": tuning,
         "ensemble": ensemble,
@@ -586,9 +592,10 @@ FORCE_SOURCES = [os.path.join(ROOT, "paper_0709_3225_gb300", "csrc", f)
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_force_warp_traffic_fluid-4m.md")
 
 
-def force_traffic():
-    """DRAM bytes per force launch from the committed ncu summary, or None
-    when the summary is missing or was taken on a different kernel source."""
+def force_traffic(field="dram_bytes_per_launch"):
+    """A figure of the committed ncu summary of the force kernel (DRAM bytes
+    per launch, or the FP32-pipe activity), or None when the summary is
+    missing or was taken on a different kernel source."""
     import hashlib
     try:
         h = hashlib.sha1()
@@ -599,7 +606,8 @@ def force_traffic():
         fields = {}
         with open(TRAFFIC_SUMMARY) as fh:
             for line in fh:
-                if ":" in line and line.strip().startswith(("kernel_source_sha1", "dram_bytes_per_launch")):
+                if ":" in line and line.strip().startswith(("kernel_source_sha1", "dram_bytes_per_launch",
+                                                            "fp32_pipe_busy")):
                     k, v = line.split(":", 1)
                     fields[k.strip()] = v.strip().strip("`")
     except OSError:
@@ -607,7 +615,7 @@ def force_traffic():
     if fields.get("kernel_source_sha1") != sha:
         return None
     try:
-        return float(fields["dram_bytes_per_launch"])
+        return float(fields[field])
     except (KeyError, ValueError):
         return None
 
