@@ -9,7 +9,7 @@
 namespace {
 
 constexpr float kFar = 1.0e4f;   // padding candidate: r^2 ~ 1e8 > rc^2
-constexpr int kStageBatch = 4;   // staging rounds whose loads are in flight together
+constexpr int kStageBatch = 2;   // staging rounds whose loads are in flight together (measured: 2 > 4 > 1)
 
 struct WarpParams {
     int n, nc, cap;              // cap: staged candidates per warp (multiple of 8, >= 40)
@@ -276,7 +276,7 @@ __device__ __forceinline__ void compute_chunks(const WarpParams &k, const float4
         int m = 0;
         for (; m < ihome; m++)
             pair2<MODE, ENERGY, true>(xs, ys, zs, X2[m * S], Y2[m * S], Z2[m * S], k, fx, fy, fz, e, w);
-#pragma unroll 4
+#pragma unroll 8
         for (; m < iters; m++)
             pair2<MODE, ENERGY, false>(xs, ys, zs, X2[m * S], Y2[m * S], Z2[m * S], k, fx, fy, fz, e, w);
         float Fx = fx.x + fx.y, Fy = fy.x + fy.y, Fz = fz.x + fz.y, E = e.x + e.y, Wv = w.x + w.y;
