@@ -280,6 +280,34 @@ def run_aop_density(stream):
     return out
 
 
+def run_graph_small(stream, steps=200):
+    """Small systems, where launches rather than the GPU bound a step: ms per
+    step with direct launches and with graph replay of the middle steps
+    (lj_set_graph), for the 2,048- and 131,072-particle fluids."""
+    import torch
+    from paper_0709_3225_gb300 import inputs, lj
+    out = []
+    for name in ("fluid-2k", "fluid-131k"):
+        x, v, L, w = inputs.workload_state(name)
+        row = {"workload": name, "n": w.n}
+        for graph in (False, True):
+            s = lj.System(x, v, L, dt=w.dt, rc=w.rc)
+            lj.lj_set_graph(s.ctx, graph)
+            s.forces()
+            s.step(10)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s.check()
+            s.close()
+            row["graph_ms_per_step" if graph else "direct_ms_per_step"] = e0.elapsed_time(e1) / steps
+        out.append(row)
+    return out
+
+
 def run_skin(x, v, L, w, stream, steps=60):
     """Cell lists with a skin on the 4M workload: ms per step and rebuilds
     for a few skins, beside the per-step rebuild (skin 0)."""
@@ -520,6 +548,7 @@ def run_gpu(args):
     langevin = None if (args.no_ensemble or rank != 0) else run_langevin(x, v, L, w, stream)
     skin = None if (args.no_ensemble or rank != 0) else run_skin(x, v, L, w, stream)
     aop = None if (args.no_ensemble or rank != 0) else run_aop_density(stream)
+    small = None if (args.no_ensemble or rank != 0) else run_graph_small(stream)
 
     if rank != 0:
         if world > 1:
@@ -569,6 +598,7 @@ def run_gpu(args):
         "langevin": langevin,
         "skin": skin,
         "aop_vs_csr_density": aop,
+        "small_systems_graph": small,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64},

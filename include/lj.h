@@ -267,6 +267,16 @@ int lj_vv_adjoint_step(lj_ctx *ctx, const double *x_n, const double *x_n1, doubl
  * or skin < 0.  Synchronizes. */
 int lj_set_skin(lj_ctx *ctx, double skin, int32_t max_interval);
 
+/* Graph replay for lj_step (enable 1, 0 = direct launches, the default).
+ * With it on, a call of nsteps >= 3 launches its first and last steps
+ * directly and replays one captured CUDA graph of a middle step for the
+ * others (one launch per step instead of four or five).  The graph is
+ * captured on the first such call and again whenever x, v or f point
+ * elsewhere or lj_set_tuning / lj_set_skin / lj_set_params changed the
+ * context; it is not used while lj_set_timing is on.  Same results as
+ * direct launches. */
+int lj_set_graph(lj_ctx *ctx, int32_t enable);
+
 /* Rebuilds and steps counted in skin mode since lj_set_skin (a full
  * rebuild by lj_forces is not counted).  Host pointers; synchronizes. */
 int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);

@@ -99,6 +99,7 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->fs);
     cudaFree(c->g4);
     cudaFree(c->n2_scratch);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     cudaFree(c->aop);
     cudaFree(c->r48_state);
     cudaFree(c->disp);
@@ -154,9 +155,17 @@ int do_bin(lj_ctx *c, const double *x, bool wrap_in_scatter)
 // Cell lists with a skin: the cells are rebuilt only when the device-side
 // decision (k_skin_decide) asks for it; otherwise the sorted positions are
 // refreshed from x in the old cell order (the scatter with the old ranks).
-int do_steps_skin(lj_ctx *c, double *x, double *v, void *f, int nsteps)
+bool fused_mode(const lj_ctx *c) { return !c->use_run_kernel && c->fuse_update && c->skin <= 0.0; }
+
+// The launches of step s of an nsteps-call (see do_steps).  Steps other
+// than the first and the last issue the same launches, which is what the
+// graph replay captures.
+int one_step(lj_ctx *c, double *x, double *v, void *f, int s, int nsteps)
 {
-    for (int s = 0; s < nsteps; s++) {
+    if (c->skin > 0.0) {
+        // cell lists with a skin: the cells are rebuilt only when the
+        // device-side decision (k_skin_decide) asks for it; otherwise the
+        // sorted positions are refreshed from x in the old cell order
         LJ_CK(launch_kick_drift_skin(c, x, v, f, s == 0 ? 1 : 2));
         const bool gated = !c->skin_dirty;
         LJ_CK(launch_bin_count(c, x, gated));
@@ -167,33 +176,89 @@ int do_steps_skin(lj_ctx *c, double *x, double *v, void *f, int nsteps)
             if (r) return r;
         }
         LJ_CK(launch_force(c, f, false));
+        return LJ_OK;
     }
-    if (nsteps > 0) LJ_CK(launch_kick(c, v, f));
+    if (fused_mode(c)) {
+        // FP32-mixed warp kernel with the update fused: every force launch
+        // applies the next step's update to the particles it has just
+        // finished (the last one only the closing half kick)
+        LJ_CK(launch_scan(c));
+        LJ_CK(launch_scatter(c, x, false));
+        LJ_CK(launch_force_warp_fused(c, f, x, v, s == nsteps - 1));
+        return LJ_OK;
+    }
+    LJ_CK(launch_kick_drift_bin(c, x, v, f, s == 0 ? 1 : 2));
+    LJ_CK(launch_scan(c));
+    LJ_CK(launch_scatter(c, x, false));
+    LJ_CK(launch_force(c, f, false));
     return LJ_OK;
 }
 
+// Capture the launches of one middle step for (x, v, f) into c->gexec.
+int capture_middle_step(lj_ctx *c, double *x, double *v, void *f)
+{
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    cudaStream_t cs = c->stream;
+    bool own = false;
+    if (!cs) {   // the legacy stream cannot be captured
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return LJ_ECUDA;
+        own = true;
+    }
+    cudaGraph_t g = nullptr;
+    const int64_t k0 = c->kernel_launches;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int r = LJ_OK;
+    if (e == cudaSuccess) {
+        cudaStream_t keep = c->stream;
+        c->stream = cs;
+        r = one_step(c, x, v, f, 1, 3);
+        c->stream = keep;
+        e = cudaStreamEndCapture(cs, &g);
+    }
+    c->glaunches = c->kernel_launches - k0;
+    c->kernel_launches = k0;
+    if (e == cudaSuccess && r == LJ_OK) e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (own) cudaStreamDestroy(cs);
+    if (e != cudaSuccess || r != LJ_OK || !c->gexec) {
+        cudaGetLastError();
+        c->gexec = nullptr;
+        return r != LJ_OK ? r : LJ_ECUDA;
+    }
+    c->gx = x;
+    c->gv = v;
+    c->gf = f;
+    c->ggen = c->gen;
+    return LJ_OK;
+}
+
+// nsteps velocity-Verlet steps: [fused: the first kick + drift + bin],
+// the steps, [unfused: the closing half kick].  With graph replay on, the
+// middle steps are replays of one captured step.
 int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps)
 {
-    if (c->skin > 0.0) return do_steps_skin(c, x, v, f, nsteps);
-    if (!c->use_run_kernel && c->fuse_update && nsteps > 0) {
-        // FP32-mixed warp kernel: the first kick + drift + bin runs alone; every
-        // force launch then applies the next step's update to the particles it
-        // has just finished (the last one only the closing half kick).
-        LJ_CK(launch_kick_drift_bin(c, x, v, f, 1));
-        for (int s = 0; s < nsteps; s++) {
-            LJ_CK(launch_scan(c));
-            LJ_CK(launch_scatter(c, x, false));
-            LJ_CK(launch_force_warp_fused(c, f, x, v, s == nsteps - 1));
-        }
-        return LJ_OK;
-    }
+    if (nsteps <= 0) return LJ_OK;
+    if (fused_mode(c)) LJ_CK(launch_kick_drift_bin(c, x, v, f, 1));
+    const bool graph = c->use_graph && !c->timing && nsteps >= 3;
     for (int s = 0; s < nsteps; s++) {
-        LJ_CK(launch_kick_drift_bin(c, x, v, f, s == 0 ? 1 : 2));
-        LJ_CK(launch_scan(c));
-        LJ_CK(launch_scatter(c, x, false));
-        LJ_CK(launch_force(c, f, false));
+        // after step 0 (which does any lazy set-up outside the capture and
+        // settles a pending skin rebuild) the middle steps are graph replays
+        if (graph && s > 0 && s < nsteps - 1 && !c->skin_dirty) {
+            if (!c->gexec || c->gx != x || c->gv != v || c->gf != f || c->ggen != c->gen) {
+                int r = capture_middle_step(c, x, v, f);
+                if (r) return r;
+            }
+            LJ_CK(cudaGraphLaunch(c->gexec, c->stream));
+            c->kernel_launches += c->glaunches;
+        } else {
+            int r = one_step(c, x, v, f, s, nsteps);
+            if (r) return r;
+        }
     }
-    if (nsteps > 0) LJ_CK(launch_kick(c, v, f));
+    if (!fused_mode(c)) LJ_CK(launch_kick(c, v, f));
     return LJ_OK;
 }
 
@@ -563,6 +628,7 @@ extern "C" int lj_set_params(lj_ctx *c, double eps, double sigma)
     if (!c || !(sigma > 0.0) || !isfinite(sigma) || !(eps >= 0.0) || !isfinite(eps)) return LJ_EINVAL;
     c->p.eps = eps;
     c->p.sigma = sigma;
+    c->gen++;   // captured steps hold the old coefficients
     return LJ_OK;
 }
 
@@ -607,6 +673,7 @@ extern "C" int lj_vv_adjoint_step(lj_ctx *c, const double *x_n, const double *x_
 
 extern "C" int lj_set_skin(lj_ctx *c, double skin, int32_t max_interval)
 {
+    if (c) c->gen++;   // captured steps hold the old configuration
     if (!c || !(skin >= 0.0) || !isfinite(skin) || max_interval < 0) return LJ_EINVAL;
     if (skin > 0.0 && c->fuse_update) return LJ_EINVAL;   // the fused update bins in the force kernel
     const int k = c->p.cell_subdiv == 2 ? 2 : 1;
@@ -634,6 +701,18 @@ extern "C" int lj_set_skin(lj_ctx *c, double skin, int32_t max_interval)
     return LJ_OK;
 }
 
+extern "C" int lj_set_graph(lj_ctx *c, int32_t enable)
+{
+    if (!c || (enable != 0 && enable != 1)) return LJ_EINVAL;
+    c->use_graph = enable;
+    if (!enable && c->gexec) {
+        LJ_CK(cudaStreamSynchronize(c->stream));
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return LJ_OK;
+}
+
 extern "C" int lj_skin_stats(lj_ctx *c, int64_t *rebuilds, int64_t *steps)
 {
     if (!c) return LJ_EINVAL;
@@ -649,6 +728,7 @@ extern "C" int lj_skin_stats(lj_ctx *c, int64_t *rebuilds, int64_t *steps)
 
 extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int32_t cells_per_grab)
 {
+    if (c) c->gen++;   // captured steps hold the old configuration
     if (!c || kernel < 0 || kernel > 5 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
     if (kernel == 4) {   // the paper's fixed-capacity cell arrays: FP32-mixed, 27-cell stencil
         if (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2) return LJ_EINVAL;

@@ -87,6 +87,12 @@ struct lj_ctx {
     int32_t *skin_flags; // [0] max |disp|^2 (float bits), [1] rebuild now, [2] steps since rebuild
     long long *skin_counts;  // [0] rebuilds, [1] steps (skin mode)
     int skin_dirty;      // the grid changed: the next step rebuilds unconditionally
+    // graph replay of the middle steps of lj_step (lj_set_graph)
+    int use_graph;
+    cudaGraphExec_t gexec;   // one captured middle step
+    const void *gx, *gv, *gf;
+    int gen, ggen;       // configuration generation; the one captured
+    int64_t glaunches;   // kernel launches in one captured step
     size_t n2_bytes;
     int ekin_grid;
 
