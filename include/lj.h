@@ -267,14 +267,25 @@ int lj_vv_adjoint_step(lj_ctx *ctx, const double *x_n, const double *x_n1, doubl
  * or skin < 0.  Synchronizes. */
 int lj_set_skin(lj_ctx *ctx, double skin, int32_t max_interval);
 
+/* Deterministic cell order (enable 1; 0, the default, leaves the order in
+ * which the binning atomics placed the particles).  With it on, every
+ * binning sorts each cell's particles by index -- the order of a serial
+ * counting sort -- so lj_get_cells returns exactly that permutation and
+ * the forces are bitwise reproducible from run to run (energies summed
+ * with dynamic work pulls still differ in the last bits; cells_per_grab 0
+ * makes them reproducible too).  Costs one pass over the sorted positions
+ * per binning and a second sorted-position buffer.  Synchronous only
+ * through the allocation on first use. */
+int lj_set_deterministic(lj_ctx *ctx, int32_t enable);
+
 /* Graph replay for lj_step (enable 1, 0 = direct launches, the default).
  * With it on, a call of nsteps >= 3 launches its first and last steps
  * directly and replays one captured CUDA graph of a middle step for the
  * others (one launch per step instead of four or five).  The graph is
  * captured on the first such call and again whenever x, v or f point
- * elsewhere or lj_set_tuning / lj_set_skin / lj_set_params changed the
- * context; it is not used while lj_set_timing is on.  Same results as
- * direct launches. */
+ * elsewhere or lj_set_tuning, lj_set_skin, lj_set_params or
+ * lj_set_deterministic changed the context; it is not used while
+ * lj_set_timing is on.  Same results as direct launches. */
 int lj_set_graph(lj_ctx *ctx, int32_t enable);
 
 /* Rebuilds and steps counted in skin mode since lj_set_skin (a full

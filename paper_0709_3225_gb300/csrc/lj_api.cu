@@ -99,6 +99,8 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->fs);
     cudaFree(c->g4);
     cudaFree(c->n2_scratch);
+    cudaFree(c->pos_alt);
+    cudaFree(c->perm_alt);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     cudaFree(c->aop);
     cudaFree(c->r48_state);
@@ -698,6 +700,19 @@ extern "C" int lj_set_skin(lj_ctx *c, double skin, int32_t max_interval)
     c->skin_max_interval = max_interval;
     c->skin_dirty = 1;
     LJ_CK(cudaStreamSynchronize(c->stream));
+    return LJ_OK;
+}
+
+extern "C" int lj_set_deterministic(lj_ctx *c, int32_t enable)
+{
+    if (!c || (enable != 0 && enable != 1)) return LJ_EINVAL;
+    if (enable && !c->pos_alt) {
+        const size_t n1 = (size_t)(c->p.n > 0 ? c->p.n : 1);
+        LJ_CK(cudaMalloc(&c->pos_alt, n1 * force_vsize(c)));
+        LJ_CK(cudaMalloc(&c->perm_alt, n1 * sizeof(int32_t)));
+    }
+    c->deterministic = enable;
+    c->gen++;   // captured steps do not sort
     return LJ_OK;
 }
 

@@ -167,6 +167,47 @@ __global__ void k_scatter(const double *__restrict__ x, int n, double L, double 
     pos[slot] = q;
 }
 
+// Deterministic order inside the cells: particle p of cell c moves to slot
+// start[c] + (number of particles of c with a smaller index), i.e. the cells
+// are sorted by particle index -- the order a serial counting sort gives.
+// One warp per cell; the cell's indices are read as warp-uniform loads.
+// Writes the sorted copy to (pos_out, perm_out) and the new ranks.
+template <typename T>
+__global__ void k_cell_sort(const int32_t *__restrict__ start, int64_t ncell,
+                            const typename Vec4<T>::type *__restrict__ pos, const int32_t *__restrict__ perm,
+                            typename Vec4<T>::type *__restrict__ pos_out, int32_t *__restrict__ perm_out,
+                            int32_t *__restrict__ rank)   // rank: nullptr = not needed afterwards
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c <= ncell; c += nwarps) {
+        const int s = start[c], n = start[c + 1] - s;
+        if (n <= 32) {
+            // the cell's indices sit in the lanes: compare by shuffles
+            const int my = lane < n ? perm[s + lane] : 0x7fffffff;
+            int below = 0;
+            for (int j = 0; j < n; j++) below += __shfl_sync(0xffffffffu, my, j) < my ? 1 : 0;
+            if (lane < n) {
+                pos_out[s + below] = pos[s + lane];
+                perm_out[s + below] = my;
+                if (rank) rank[my] = below;
+            }
+            continue;
+        }
+        for (int p0 = 0; p0 < n; p0 += 32) {
+            const int p = p0 + lane;
+            const int my = p < n ? perm[s + p] : 0x7fffffff;
+            int below = 0;
+            for (int j = 0; j < n; j++) below += perm[s + j] < my ? 1 : 0;
+            if (p < n) {
+                pos_out[s + below] = pos[s + p];
+                perm_out[s + below] = my;
+                if (rank) rank[my] = below;
+            }
+        }
+    }
+}
+
 __global__ void k_counts_from_start(const int32_t *__restrict__ start, int64_t ncell, int32_t *__restrict__ count)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -213,6 +254,26 @@ cudaError_t launch_scatter(lj_ctx *c, const double *x, bool wrap)
             k_scatter<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(
                 x, n, c->p.box, c->wrap_hi, c->wrap_lo, c->centre, c->nc, wrap, c->cell_of, c->rank, c->start, c->perm, (float4 *)c->pos);
         c->kernel_launches++;
+    }
+    if (n > 0 && c->deterministic) {
+        // sorted copy into the spare buffers, which then become the current
+        // ones; the ranks are rewritten only where a later refresh reuses
+        // them (cells with a skin)
+        int32_t *rk = c->skin > 0.0 ? c->rank : nullptr;
+        const unsigned grid = (unsigned)((c->ncell + 1 + 7) / 8);
+        if (c->p.precision == LJ_PREC_FP64)
+            k_cell_sort<double><<<grid, 256, 0, c->stream>>>(c->start, c->ncell, (const double4_16a *)c->pos, c->perm,
+                                                              (double4_16a *)c->pos_alt, c->perm_alt, rk);
+        else
+            k_cell_sort<float><<<grid, 256, 0, c->stream>>>(c->start, c->ncell, (const float4 *)c->pos, c->perm,
+                                                             (float4 *)c->pos_alt, c->perm_alt, rk);
+        c->kernel_launches++;
+        void *tp = c->pos;
+        c->pos = c->pos_alt;
+        c->pos_alt = tp;
+        int32_t *tq = c->perm;
+        c->perm = c->perm_alt;
+        c->perm_alt = tq;
     }
     return cudaGetLastError();
 }

@@ -87,6 +87,11 @@ struct lj_ctx {
     int32_t *skin_flags; // [0] max |disp|^2 (float bits), [1] rebuild now, [2] steps since rebuild
     long long *skin_counts;  // [0] rebuilds, [1] steps (skin mode)
     int skin_dirty;      // the grid changed: the next step rebuilds unconditionally
+    // deterministic order inside the cells (lj_set_deterministic): a sorted
+    // copy goes to the spare buffers, which then swap with pos / perm
+    int deterministic;
+    void *pos_alt;
+    int32_t *perm_alt;
     // graph replay of the middle steps of lj_step (lj_set_graph)
     int use_graph;
     cudaGraphExec_t gexec;   // one captured middle step

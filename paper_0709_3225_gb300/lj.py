@@ -71,6 +71,7 @@ _SIGS = {
     "lj_srand48_state": ([ctypes.c_int64], ctypes.c_uint64),
     "lj_set_skin": ([_P, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
     "lj_set_graph": ([_P, ctypes.c_int32], ctypes.c_int),
+    "lj_set_deterministic": ([_P, ctypes.c_int32], ctypes.c_int),
     "lj_skin_stats": ([_P, _P, _P], ctypes.c_int),
     "lj_rand48_jump": ([ctypes.c_int64, _P, _P], ctypes.c_int),
     "lj_rand48_seed": ([_P, ctypes.c_int64, ctypes.c_uint64, _P], ctypes.c_int),
@@ -254,6 +255,11 @@ def lj_set_skin(ctx: Context, skin: float, max_interval: int = 0) -> None:
     _ck(load().lj_set_skin(ctx.handle, float(skin), int(max_interval)), "lj_set_skin")
     k = ctx.params.cell_subdiv or 1
     ctx.nc = int(math.floor((k * ctx.params.box) / (ctx.params.rc + float(skin))))
+
+
+def lj_set_deterministic(ctx: Context, enable: bool = True) -> None:
+    """Sort each cell's particles by index at every binning."""
+    _ck(load().lj_set_deterministic(ctx.handle, 1 if enable else 0), "lj_set_deterministic")
 
 
 def lj_set_graph(ctx: Context, enable: bool = True) -> None:

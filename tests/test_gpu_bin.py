@@ -93,3 +93,44 @@ def test_full_size_4m(oracle_mod):
     cells are uneven)."""
     x, L = inputs.jittered_fcc(100, 0.8442, 0.3, 11)
     _compare(x, L, oracle_mod)
+
+
+@pytest.mark.parametrize("subdiv", [1, 2])
+def test_deterministic_order_is_the_serial_counting_sort(oracle_mod, subdiv):
+    """lj_set_deterministic: every cell's particles in index order, so the
+    whole permutation equals the oracle's serial counting sort bit for bit."""
+    from paper_0709_3225_gb300 import lj
+    x, L = inputs.jittered_fcc(9, 0.8442, 0.2, 61)
+    x[11, 0] = np.nan   # the extra cell is sorted too
+    s = lj.System(x, None, L, cell_subdiv=subdiv)
+    lj.lj_set_deterministic(s.ctx)
+    cell_of, count, start, perm = (t.cpu().numpy() for t in s.cells())
+    with pytest.raises(lj.LJError):
+        s.check()
+    good = np.isfinite(x).all(axis=1)
+    nc = s.ctx.nc
+    s.close()
+    o_cell, o_count, o_start, o_perm = oracle_mod.bin_cells(np.ascontiguousarray(x[good]), L, nc)
+    idx = np.flatnonzero(good)
+    assert np.array_equal(perm[:good.sum()], idx[o_perm])
+    assert perm[-1] == 11
+
+
+def test_deterministic_forces_and_trajectories_repeat_bitwise():
+    import torch
+    from paper_0709_3225_gb300 import lj
+    x, L = inputs.jittered_fcc(10, 0.8442, 0.1, 62)
+    v = inputs.velocities(x.shape[0], 1.0, 62)
+    runs = []
+    for rep in range(2):
+        s = lj.System(x, v, L)
+        lj.lj_set_deterministic(s.ctx)
+        lj.lj_set_graph(s.ctx)
+        s.forces()
+        f0 = s.f.clone()
+        s.step(25)
+        s.check()
+        runs.append((f0, s.x.clone(), s.v.clone()))
+        s.close()
+    assert torch.equal(runs[0][0], runs[1][0])
+    assert torch.equal(runs[0][1], runs[1][1]) and torch.equal(runs[0][2], runs[1][2])

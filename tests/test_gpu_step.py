@@ -151,8 +151,9 @@ def test_drift_131k_mixed_vs_fp64():
         assert abs(d) < 1e-2, (k, d)
 
 
-@pytest.mark.parametrize("kernel,skin", [(3, 0.0), (0, 0.0), (3, 0.4), (1, 0.0)])
-def test_graph_replay_matches_oracle(oracle_mod, kernel, skin):
+@pytest.mark.parametrize("kernel,skin,det", [(3, 0.0, 0), (0, 0.0, 0), (3, 0.4, 0), (1, 0.0, 0), (3, 0.0, 1),
+                                             (0, 0.0, 1), (3, 0.4, 1)])
+def test_graph_replay_matches_oracle(oracle_mod, kernel, skin, det):
     """lj_step with graph replay of its middle steps (lj_set_graph): the same
     trajectory as the oracle, for the separate and fused updates, cells with a
     skin and the run kernel; re-captured when the arrays or the tuning change."""
@@ -166,6 +167,8 @@ def test_graph_replay_matches_oracle(oracle_mod, kernel, skin):
     lj.lj_set_tuning(s.ctx, kernel, 0, 4)
     if skin:
         lj.lj_set_skin(s.ctx, skin)
+    if det:
+        lj.lj_set_deterministic(s.ctx)
     lj.lj_set_graph(s.ctx)
     s.step(6)
     # fresh arrays: the captured step must not be reused on the old pointers
