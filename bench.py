@@ -123,13 +123,22 @@ def barrier(world):
 
 
 def max_over_ranks(world, value: float) -> float:
+    """The largest value over the ranks (NCCL on GPUs, gloo on the CPU)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(world, units_per_rank: float, seconds_this_rank: float) -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time.  Returns (rate, max seconds)."""
+    t = max_over_ranks(world, seconds_this_rank)
+    return world * units_per_rank / t, t
 
 
 def run_ensemble(args, stream, world):
@@ -496,9 +505,9 @@ def run_gpu(args):
     force_ms, force_n, k1 = lj.lj_read_timing(s.ctx)
     lj.lj_set_timing(s.ctx, False)
     launches = k1 - k0
-    ms_total = max_over_ranks(world, ms_total)
+    value, t_max = job_rate(world, args.steps, ms_total / 1e3)
+    ms_total = t_max * 1e3
     ms_step = ms_total / args.steps
-    value = world * args.steps / (ms_total / 1e3)
     force_avg_ms = force_ms / max(force_n, 1)
     achieved_tflops = FLOPS_PER_PAIR * pairs / (force_avg_ms / 1e3) / 1e12
     clocks = clk.summary()
@@ -517,8 +526,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         lj.lj_step_host(s.ctx, xh, vh, fh, 1)
-    t_e2e = max_over_ranks(world, time.perf_counter() - t0)
-    e2e_value = world * e2e_steps / t_e2e
+    e2e_value, t_e2e = job_rate(world, e2e_steps, time.perf_counter() - t0)
     bytes_h2d = n * (3 * 8 + 3 * 8 + 4 * 4)
     s.close()
     del s
