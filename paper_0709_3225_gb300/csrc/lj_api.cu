@@ -99,6 +99,8 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->fs);
     cudaFree(c->g4);
     cudaFree(c->n2_scratch);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->ev_xfinal) cudaEventDestroy(c->ev_xfinal);
     cudaFree(c->pos_alt);
     cudaFree(c->perm_alt);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -162,7 +164,7 @@ bool fused_mode(const lj_ctx *c) { return !c->use_run_kernel && c->fuse_update &
 // The launches of step s of an nsteps-call (see do_steps).  Steps other
 // than the first and the last issue the same launches, which is what the
 // graph replay captures.
-int one_step(lj_ctx *c, double *x, double *v, void *f, int s, int nsteps)
+int one_step(lj_ctx *c, double *x, double *v, void *f, int s, int nsteps, cudaEvent_t x_final = nullptr)
 {
     if (c->skin > 0.0) {
         // cell lists with a skin: the cells are rebuilt only when the
@@ -173,6 +175,7 @@ int one_step(lj_ctx *c, double *x, double *v, void *f, int s, int nsteps)
         LJ_CK(launch_bin_count(c, x, gated));
         LJ_CK(launch_scan(c, gated));
         LJ_CK(launch_scatter(c, x, false));
+        if (x_final) LJ_CK(cudaEventRecord(x_final, c->stream));
         if (!gated) {
             int r = skin_restart(c);
             if (r) return r;
@@ -192,6 +195,7 @@ int one_step(lj_ctx *c, double *x, double *v, void *f, int s, int nsteps)
     LJ_CK(launch_kick_drift_bin(c, x, v, f, s == 0 ? 1 : 2));
     LJ_CK(launch_scan(c));
     LJ_CK(launch_scatter(c, x, false));
+    if (x_final) LJ_CK(cudaEventRecord(x_final, c->stream));   // x holds its final value
     LJ_CK(launch_force(c, f, false));
     return LJ_OK;
 }
@@ -240,7 +244,10 @@ int capture_middle_step(lj_ctx *c, double *x, double *v, void *f)
 // nsteps velocity-Verlet steps: [fused: the first kick + drift + bin],
 // the steps, [unfused: the closing half kick].  With graph replay on, the
 // middle steps are replays of one captured step.
-int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps)
+// x_final (optional): recorded once x holds its final value (after the
+// last step's scatter; unfused updates only), so that its copy can overlap
+// the last force evaluation.
+int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps, cudaEvent_t x_final = nullptr)
 {
     if (nsteps <= 0) return LJ_OK;
     if (fused_mode(c)) LJ_CK(launch_kick_drift_bin(c, x, v, f, 1));
@@ -256,11 +263,12 @@ int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps)
             LJ_CK(cudaGraphLaunch(c->gexec, c->stream));
             c->kernel_launches += c->glaunches;
         } else {
-            int r = one_step(c, x, v, f, s, nsteps);
+            int r = one_step(c, x, v, f, s, nsteps, s == nsteps - 1 && !fused_mode(c) ? x_final : nullptr);
             if (r) return r;
         }
     }
     if (!fused_mode(c)) LJ_CK(launch_kick(c, v, f));
+    if (x_final && fused_mode(c)) LJ_CK(cudaEventRecord(x_final, c->stream));
     return LJ_OK;
 }
 
@@ -581,13 +589,24 @@ extern "C" int lj_step_host(lj_ctx *c, double *x, double *v, void *f, int32_t ns
         LJ_CK(cudaMemcpyAsync(c->vs, v, bx, cudaMemcpyHostToDevice, c->stream));
         LJ_CK(cudaMemcpyAsync(c->fs, f, bf, cudaMemcpyHostToDevice, c->stream));
     }
-    r = do_steps(c, c->xs, c->vs, c->fs, nsteps);
+    // x is final after the last scatter: its copy back runs on a second
+    // stream while the last force evaluation and kick run
+    if (!c->copy_stream) LJ_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    if (!c->ev_xfinal) LJ_CK(cudaEventCreateWithFlags(&c->ev_xfinal, cudaEventDisableTiming));
+    const bool overlap = n > 0 && nsteps > 0;
+    r = do_steps(c, c->xs, c->vs, c->fs, nsteps, overlap ? c->ev_xfinal : nullptr);
     if (r) return r;
     if (n > 0) {
-        LJ_CK(cudaMemcpyAsync(x, c->xs, bx, cudaMemcpyDeviceToHost, c->stream));
+        if (overlap) {
+            LJ_CK(cudaStreamWaitEvent(c->copy_stream, c->ev_xfinal, 0));
+            LJ_CK(cudaMemcpyAsync(x, c->xs, bx, cudaMemcpyDeviceToHost, c->copy_stream));
+        } else {
+            LJ_CK(cudaMemcpyAsync(x, c->xs, bx, cudaMemcpyDeviceToHost, c->stream));
+        }
         LJ_CK(cudaMemcpyAsync(v, c->vs, bx, cudaMemcpyDeviceToHost, c->stream));
         LJ_CK(cudaMemcpyAsync(f, c->fs, bf, cudaMemcpyDeviceToHost, c->stream));
     }
+    LJ_CK(cudaStreamSynchronize(c->copy_stream));
     return sync_and_check(c);
 }
 

@@ -92,6 +92,9 @@ struct lj_ctx {
     int deterministic;
     void *pos_alt;
     int32_t *perm_alt;
+    // lj_step_host: the copy of x back overlaps the last force evaluation
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_xfinal;
     // graph replay of the middle steps of lj_step (lj_set_graph)
     int use_graph;
     cudaGraphExec_t gexec;   // one captured middle step

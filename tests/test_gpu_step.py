@@ -199,3 +199,31 @@ def test_graph_replay_counts_the_same_kernels():
         s.close()
     # the library counts kernels either way; replays count their kernels too
     assert counts[0] == counts[1]
+
+
+@pytest.mark.parametrize("kernel,skin", [(3, 0.0), (0, 0.0), (3, 0.4)])
+def test_step_host_one_step_calls(kernel, skin):
+    """One step per lj_step_host call (the copy of x back overlaps the last
+    force evaluation): the same trajectory as lj_step on device arrays."""
+    import torch
+    from paper_0709_3225_gb300 import lj
+    x, v, L = _liquid(seed=14)
+    a = lj.System(x, v, L, shift_mode=2)
+    b = lj.System(x, v, L, shift_mode=2)
+    for s in (a, b):
+        lj.lj_set_tuning(s.ctx, kernel, 0, 4)
+        lj.lj_set_deterministic(s.ctx)
+        if skin:
+            lj.lj_set_skin(s.ctx, skin)
+        s.forces()
+    xh = torch.from_numpy(b.x.cpu().numpy()).pin_memory()
+    vh = torch.from_numpy(b.v.cpu().numpy()).pin_memory()
+    fh = torch.from_numpy(b.f.cpu().numpy()).pin_memory()
+    for _ in range(6):
+        a.step(1)
+        lj.lj_step_host(b.ctx, xh, vh, fh, 1)
+    a.check()
+    b.check()
+    assert torch.equal(xh, a.x.cpu()) and torch.equal(vh, a.v.cpu()) and torch.equal(fh, a.f.cpu())
+    a.close()
+    b.close()
