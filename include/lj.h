@@ -267,6 +267,14 @@ int lj_vv_adjoint_step(lj_ctx *ctx, const double *x_n, const double *x_n1, doubl
  * or skin < 0.  Synchronizes. */
 int lj_set_skin(lj_ctx *ctx, double skin, int32_t max_interval);
 
+/* Failure-detection self test.  Runs one device-side wait that cannot be
+ * satisfied -- an mbarrier phase expecting 16 bytes that no copy delivers --
+ * with the same bound as every bulk-copy wait of the force kernels: after
+ * about 2^31 SM cycles (~1 s) it gives up, latches the timeout and the
+ * kernel returns.  Returns what lj_check then reports: LJ_ETIMEOUT when the
+ * bound works.  The context stays usable.  Synchronizes. */
+int lj_wait_selftest(lj_ctx *ctx);
+
 /* Deterministic cell order (enable 1; 0, the default, leaves the order in
  * which the binning atomics placed the particles).  With it on, every
  * binning sorts each cell's particles by index -- the order of a serial

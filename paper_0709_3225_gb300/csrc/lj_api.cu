@@ -722,6 +722,13 @@ extern "C" int lj_set_skin(lj_ctx *c, double skin, int32_t max_interval)
     return LJ_OK;
 }
 
+extern "C" int lj_wait_selftest(lj_ctx *c)
+{
+    if (!c) return LJ_EINVAL;
+    LJ_CK(launch_wait_selftest(c));
+    return sync_and_check(c);
+}
+
 extern "C" int lj_set_deterministic(lj_ctx *c, int32_t enable)
 {
     if (!c || (enable != 0 && enable != 1)) return LJ_EINVAL;

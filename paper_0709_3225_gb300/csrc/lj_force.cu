@@ -326,6 +326,24 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceParams p, const ty
     }
 }
 
+// Failure-detection self test: one bounded wait on an mbarrier phase that
+// cannot complete (it expects 16 bytes that no copy delivers).  The wait
+// gives up after its bound (~2^31 SM cycles, about a second), latches
+// LJ_ERRBIT_TIMEOUT and the kernel returns: the path every bulk-copy wait of
+// the force kernels takes when a copy never lands.
+__global__ void k_wait_selftest(int32_t *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16u);
+    __syncwarp();
+    mbar_wait_bounded(&bar, 0u, err);
+}
+
 // Sum the per-CTA (energy, virial) partials in a fixed order.
 __global__ void k_reduce_pairs(const double *__restrict__ partial, int n, double *__restrict__ out)
 {
@@ -479,6 +497,13 @@ cudaError_t launch_force(lj_ctx *c, void *f, bool energy)
 cudaError_t launch_energy_reduce(lj_ctx *c)
 {
     k_reduce_pairs<<<1, kReduceThreads, 0, c->stream>>>(c->partial, c->npartial, c->scalars);
+    c->kernel_launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(lj_ctx *c)
+{
+    k_wait_selftest<<<1, 32, 0, c->stream>>>(c->err);
     c->kernel_launches++;
     return cudaGetLastError();
 }

@@ -265,6 +265,9 @@ cudaError_t launch_force_pipe(lj_ctx *c, void *f, bool energy);
 cudaError_t launch_r48_seed(uint64_t *state, int64_t S, uint64_t x0, cudaStream_t stream);
 cudaError_t launch_langevin_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick, double gamma, double kT);
 
+// One bounded mbarrier wait that cannot complete (lj_force.cu).
+cudaError_t launch_wait_selftest(lj_ctx *c);
+
 // Forces with the paper's fixed-capacity cell arrays (lj_force_aop.cu).
 cudaError_t launch_force_aop(lj_ctx *c, void *f, bool energy);
 

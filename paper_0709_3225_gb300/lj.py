@@ -72,6 +72,7 @@ _SIGS = {
     "lj_set_skin": ([_P, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
     "lj_set_graph": ([_P, ctypes.c_int32], ctypes.c_int),
     "lj_set_deterministic": ([_P, ctypes.c_int32], ctypes.c_int),
+    "lj_wait_selftest": ([_P], ctypes.c_int),
     "lj_skin_stats": ([_P, _P, _P], ctypes.c_int),
     "lj_rand48_jump": ([ctypes.c_int64, _P, _P], ctypes.c_int),
     "lj_rand48_seed": ([_P, ctypes.c_int64, ctypes.c_uint64, _P], ctypes.c_int),
@@ -255,6 +256,12 @@ def lj_set_skin(ctx: Context, skin: float, max_interval: int = 0) -> None:
     _ck(load().lj_set_skin(ctx.handle, float(skin), int(max_interval)), "lj_set_skin")
     k = ctx.params.cell_subdiv or 1
     ctx.nc = int(math.floor((k * ctx.params.box) / (ctx.params.rc + float(skin))))
+
+
+def lj_wait_selftest(ctx: Context) -> int:
+    """Run one unsatisfiable bounded device wait; returns the status lj_check
+    reports afterwards (LJ_ETIMEOUT when the bound works)."""
+    return int(load().lj_wait_selftest(ctx.handle))
 
 
 def lj_set_deterministic(ctx: Context, enable: bool = True) -> None:

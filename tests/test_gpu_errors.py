@@ -140,3 +140,23 @@ def test_nonfinite_replica_particle_is_isolated(oracle_mod):
         fo = oracle_mod.forces_cells(xs[r], e.box[r], mode=1)[0]
         assert rel_rms(b.replica(f, r), fo) <= 1e-5, r
     b.close()
+
+
+def test_bounded_wait_times_out_and_context_survives(oracle_mod):
+    """A device wait that nothing satisfies (an mbarrier expecting bytes no
+    copy delivers) gives up after its bound and reports LJ_ETIMEOUT; the
+    context then computes correct forces again."""
+    import time
+    from paper_0709_3225_gb300 import lj
+    x, L = inputs.jittered_fcc(6, 0.8442, 0.05, 1)
+    s = lj.System(x, None, L)
+    t0 = time.perf_counter()
+    assert lj.lj_wait_selftest(s.ctx) == lj.LJ_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    s.check()                                   # the latch was cleared
+    s.forces()
+    s.check()
+    fo = oracle_mod.forces_cells(x, L, mode=1)[0]
+    f = s.f.double().cpu().numpy()[:, :3]
+    assert np.sqrt(((f - fo) ** 2).sum() / (fo ** 2).sum()) <= 1e-5
+    s.close()
