@@ -40,6 +40,32 @@ def unique_pairs(n: int, rho: float, rc: float) -> float:
     return n * (2.0 / 3.0) * math.pi * rc ** 3 * rho
 
 
+CANDIDATE_FLOPS = 7          # flop convention per candidate distance test
+
+
+def stencil_candidates(ctx) -> float:
+    """Candidate pairs the full (2k+1)^3 stencil presents in one force
+    evaluation, sum_c n_c * sum_{c' in stencil(c)} n_c', from the cell counts
+    of the context's last binning (both directions, self pairs included)."""
+    import torch
+    from paper_0709_3225_gb300 import lj
+    nc = ctx.nc
+    count = torch.empty(nc ** 3, dtype=torch.int32, device="cuda")
+    lj.lj_get_cells(ctx, count=count)
+    return candidate_pairs(count.double().view(nc, nc, nc), ctx.params.cell_subdiv or 1)
+
+
+def candidate_pairs(g, k: int) -> float:
+    """sum_c g[c] * sum_{|d|_inf <= k} g[c + d] over a periodic grid of counts."""
+    import torch
+    nb = torch.zeros_like(g)
+    for dz in range(-k, k + 1):
+        for dy in range(-k, k + 1):
+            for dx in range(-k, k + 1):
+                nb += torch.roll(g, shifts=(dz, dy, dx), dims=(0, 1, 2))
+    return float((g * nb).sum())
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -404,7 +430,7 @@ def run_adjoint(x4m, L4m, stream):
             "vjp_4m_ms": vjp_ms, "vjp_4m_pairs_per_s": unique_pairs(4_000_000, 0.8442, 2.5) / (vjp_ms / 1e3)}
 
 
-def cpu_baseline(x, v, L, w, max_seconds: float = 20.0, max_steps: int = 3):
+def cpu_baseline(x, v, L, w, max_seconds: float = 20.0, max_steps: int = 3, one_core: bool = True):
     """The FP64 oracle as it stands, on this host's cores: full velocity-Verlet
     steps of the same workload until ~max_seconds of work, scaled to steps/s."""
     import oracle
@@ -422,10 +448,19 @@ def cpu_baseline(x, v, L, w, max_seconds: float = 20.0, max_steps: int = 3):
         if time.perf_counter() - t0 > max_seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": steps / dt, "unit": "steps/s", "cores": used, "kind": "oracle",
-            "sample": f"{steps} full FP64 velocity-Verlet step(s) of the {w.n}-particle workload "
-                      f"(plus one initial force evaluation, {t_force:.1f} s, untimed)",
-            "pair_interactions_per_s": unique_pairs(w.n, w.rho, w.rc) * steps / dt}
+    out = {"value": steps / dt, "unit": "steps/s", "cores": used, "kind": "oracle",
+           "sample": f"{steps} full FP64 velocity-Verlet step(s) of the {w.n}-particle workload "
+                     f"(plus one initial force evaluation, {t_force:.1f} s, untimed)",
+           "pair_interactions_per_s": unique_pairs(w.n, w.rho, w.rc) * steps / dt}
+    if one_core:
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.vv(xo, vo, fo, L, 1, dt=w.dt, rc=w.rc, mode=1)
+        dt1 = time.perf_counter() - t0
+        oracle.set_threads(used)
+        out["one_core"] = {"value": 1.0 / dt1, "unit": "steps/s", "cores": 1,
+                           "sample": "1 full FP64 velocity-Verlet step, one thread"}
+    return out
 
 
 def run_reference(args):
@@ -515,6 +550,32 @@ def run_gpu(args):
     # HBM view of the non-force kernels: algorithmic bytes per particle per step
     # (kick-drift-bin 120 B, scatter 56 B, force in/out 32 B).
     other_ms = ms_step - force_avg_ms
+    candidates = stencil_candidates(s.ctx)
+    issued_tflops = (CANDIDATE_FLOPS * candidates + FLOPS_PER_PAIR * 2 * pairs) / (force_avg_ms / 1e3) / 1e12
+
+    # ---- the same system as an equilibrated fluid ---------------------------
+    # The lattice start melts within ~100 steps; 1000 steps after it the cell
+    # occupancies have the fluid's spread.  Timed the same way.
+    eq_total = 1000
+    s.step(max(0, eq_total - args.warmup - args.steps))
+    s.check()
+    lj.lj_set_timing(s.ctx, True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    lj.lj_step(s.ctx, s.x, s.v, s.f, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    s.check()
+    fl_force_ms, fl_force_n, _ = lj.lj_read_timing(s.ctx)
+    lj.lj_set_timing(s.ctx, False)
+    fl_value, fl_t = job_rate(world, args.steps, ev0.elapsed_time(ev1) / 1e3)
+    fluid = {"start": f"the lattice start after {max(eq_total, args.warmup + args.steps)} FP32-mixed steps",
+             "value": fl_value, "unit": "steps/s", "ms_per_step": fl_t * 1e3 / args.steps,
+             "force_ms_per_launch": fl_force_ms / max(fl_force_n, 1),
+             "pair_interactions_per_s": pairs * fl_value,
+             "stencil_candidates_per_launch": stencil_candidates(s.ctx)}
 
     # ---- end to end through the host-buffer entry point ------------------
     e2e_steps = max(3, min(20, args.steps))
@@ -593,6 +654,10 @@ def run_gpu(args):
                      "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": traffic,
                      "kernel": "k_force_warp (mixed, default tuning)", "force_ms_per_launch": force_avg_ms,
                      "flops_per_launch": FLOPS_PER_PAIR * pairs,
+                     "stencil_candidates_per_launch": candidates,
+                     "issued_flops_per_launch": CANDIDATE_FLOPS * candidates + FLOPS_PER_PAIR * 2 * pairs,
+                     "issued_frac": issued_tflops / FP32_PEAK_TFLOPS,
+                     "issued_convention": "7 flop per full-stencil candidate + 20 per pair, both directions",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                      "fp32_pipe_busy": force_traffic("fp32_pipe_busy") if default_kernel else None,
                      "fp32_pipe_busy_source": "ncu sm__pipe_fmaheavy_cycles_active of the default force "
@@ -607,6 +672,7 @@ def run_gpu(args):
         "skin": skin,
         "aop_vs_csr_density": aop,
         "small_systems_graph": small,
+        "fluid_start": fluid,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64},

@@ -72,3 +72,24 @@ def test_reference_arm_runs_on_rank_zero_only():
                        env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_candidate_pairs_counts_the_full_stencil():
+    """The issued-work count of the bench: every ordered pair (i, j) whose
+    cells are within k cells of each other on the periodic grid, self pairs
+    included, checked by brute force over particles on small grids."""
+    import itertools
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(3)
+    for nc, k in ((5, 1), (6, 2), (3, 1)):
+        g = rng.integers(0, 4, size=(nc, nc, nc))
+        cells = [c for c in itertools.product(range(nc), repeat=3) for _ in range(g[c])]
+        brute = 0
+        for a in cells:
+            for b in cells:
+                d = [min((a[i] - b[i]) % nc, (b[i] - a[i]) % nc) for i in range(3)]
+                brute += max(d) <= k
+        assert bench.candidate_pairs(torch.from_numpy(g).double(), k) == brute
