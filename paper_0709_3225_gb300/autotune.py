@@ -86,7 +86,9 @@ def _time_steps(run, steps: int, warmup: int) -> float:
 
 def system_candidates(precision: str) -> list[dict]:
     if precision == "fp64":
-        return [{"subdiv": 1, "kernel": k, "gw": 0, "grab": 0} for k in (1, 2)]
+        # the warp kernel with compacted pair lists, and the two run kernels
+        return ([{"subdiv": 1, "kernel": 3, "gw": 0, "grab": c} for c in (1, 4)] +
+                [{"subdiv": 1, "kernel": k, "gw": 0, "grab": 0} for k in (1, 2)])
     warp = [{"subdiv": 1, "kernel": 3, "gw": g, "grab": c} for g in (0, -1, 8, 32) for c in (0, 4)]
     return warp + [{"subdiv": 1, "kernel": 0, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 1, "gw": 0, "grab": 0},
                    {"subdiv": 1, "kernel": 2, "gw": 0, "grab": 0}, {"subdiv": 1, "kernel": 4, "gw": 0, "grab": 0},

@@ -361,7 +361,7 @@ int setup_grid(lj_ctx *c, int nc)
     c->ntiles = (int)((c->ncell + 1 + kScanTile - 1) / kScanTile);
     LJ_GRID_CK(cudaMalloc(&c->tile_sum, (size_t)c->ntiles * sizeof(int32_t)));
     LJ_GRID_CK(force_configure(c));
-    if (c->p.precision == LJ_PREC_MIXED) LJ_GRID_CK(warp_force_configure(c));
+    LJ_GRID_CK(c->p.precision == LJ_PREC_MIXED ? warp_force_configure(c) : w64_force_configure(c));
     c->pipe_grid = 0;
     if (c->p.precision == LJ_PREC_MIXED && c->p.cell_subdiv != 2) LJ_GRID_CK(pipe_force_configure(c));
     {
@@ -390,10 +390,10 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     c->wrap_hi = p->box * (1.0 - ldexp(1.0, -50));
     c->wrap_lo = p->box * ldexp(1.0, -50);
     c->stream = (cudaStream_t)stream;
-    // Kernel choice: FP32-mixed defaults to the warp-per-cell kernel, FP64
-    // to the run-staged kernel; the flags force a run kernel.
+    // Kernel choice: the warp-per-cell kernels (FP32-mixed, and FP64 with
+    // compacted pair lists) by default; the flags force a run kernel.
     c->use_tma = (p->flags & LJ_FLAG_RUN_DIRECT) ? 0 : 1;
-    c->use_run_kernel = (p->precision == LJ_PREC_FP64 || (p->flags & (LJ_FLAG_RUN_STAGED | LJ_FLAG_RUN_DIRECT))) ? 1 : 0;
+    c->use_run_kernel = (p->flags & (LJ_FLAG_RUN_STAGED | LJ_FLAG_RUN_DIRECT)) ? 1 : 0;
     // The update runs as its own coalesced kernel by default: fused into the
     // force kernel (lj_set_tuning kernel 0) it measured slower at N = 4M
     // (1.35 vs 1.20 ms per step) from the scattered x, v accesses.
@@ -786,10 +786,11 @@ extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int
         group_width != 16 && group_width != 32)
         return LJ_EINVAL;
     const bool warp = kernel == 0 || kernel == 3;
-    if (warp && c->p.precision == LJ_PREC_FP64) return LJ_EINVAL;   // warp kernel is FP32-mixed
+    if (kernel == 0 && c->p.precision == LJ_PREC_FP64) return LJ_EINVAL;   // fused update: FP32-mixed
     if (!warp && c->p.cell_subdiv == 2) return LJ_EINVAL;            // run kernels: 27-cell stencil only
     if (kernel == 0 && c->skin > 0.0) return LJ_EINVAL;              // fused update bins every step
-    if (warp && c->wforce_grid == 0) LJ_CK(warp_force_configure(c));
+    if (warp && c->wforce_grid == 0)
+        LJ_CK(c->p.precision == LJ_PREC_MIXED ? warp_force_configure(c) : w64_force_configure(c));
     c->use_run_kernel = warp ? 0 : 1;
     c->fuse_update = kernel == 0 ? 1 : 0;
     c->grab = cells_per_grab;

@@ -1,0 +1,622 @@
+// Lennard-Jones forces over cell lists in FP64, warp per home cell with the
+// in-range pairs compacted before any FP64 arithmetic.
+//
+// Same method as the other force kernels (Section 3: a particle interacts
+// with the particles of its own and the neighbouring cells; Section 2 pair
+// force, truncated / shifted), organised for a GPU whose FP64 rate is a
+// small fraction of its FP32 rate (GB300: about 2 FP64 FMAs per clock per
+// SM against 128 FP32).  Only ~15-25 % of the stencil's candidates lie
+// within rc, so FP64 work is spent on those alone:
+//  * Staging (per home cell, as in the FP32-mixed warp kernel): the stencil
+//    table, then one flat pass over the stencil's candidates.  Each is
+//    converted to the home-cell frame twice: in FP64 (kept for the force)
+//    and, from a truncated FP32 copy of its coordinates, in FP32 for the
+//    filters.  Candidates farther than rc from the home particles' bounding
+//    box are dropped.
+//  * Phase A (FP32 and integer work only): for each home particle, the
+//    indices of the staged candidates within rc (FP32 test with a relative
+//    margin of 1e-4, far above the conversion error) are appended to one
+//    list, particle after particle.
+//  * Phase B (FP64): the 32 lanes split the concatenated list into equal
+//    contiguous ranges, so every lane evaluates the same number of pairs
+//    whatever the occupancy.  A lane sums its entries in order; a particle
+//    whose entries all lie in one lane is stored by that lane; a particle
+//    split over several lanes is combined by the lane holding its first
+//    entry, adding the other lanes' partial sums in lane order.  The exact
+//    FP64 cutoff test decides each pair.  Sums are in a fixed order, so the
+//    forces are reproducible for a fixed in-cell order.
+//  * Cells whose pruned stencil does not fit the warp's slice take a plain
+//    FP64 path reading global memory per stencil cell.
+#include <math.h>
+#include <string.h>
+
+#include "lj_force_cell.cuh"
+#include "lj_pair.cuh"
+
+namespace {
+
+constexpr int kW64Threads = 128;   // 4 warps per CTA
+constexpr int kW64PMax = 64;       // home particles per list batch
+constexpr int kW64Comp = 5;        // fx, fy, fz, energy, virial
+
+struct W64Params {
+    int n, nc, cap, lcap, grab;
+    unsigned *work;
+    int64_t ncell;
+    float cwf;                                    // cell side (FP32, filter shifts)
+    float rc2_box, rc2_pair;                      // FP32 filter cutoffs squared (with margins)
+    double cw;                                    // cell side (FP64 shifts)
+    double rc2, rc, a12, b6, c12, c6, uc, fc;     // pair coefficients, as in Coef<double>
+};
+
+// Byte layout of one warp's shared-memory slice:
+//   X64, Y64, Z64   double[cap]   staged candidates, home frame, FP64
+//   part            double[2][kW64Comp][32]   per-lane partial sums (first, head)
+//   stab            float4[NS]    stencil table: FP32 shift xyz, start index
+//   S64             double[3][NS] stencil shifts in FP64 (padded to 16 B)
+//   X, Y, Z         float[cap]    staged candidates, home frame, FP32
+//   spre            int[NS + 1]   stencil prefix sums (padded to 4)
+//   off             int[kW64PMax + 4]   list offsets of the batch's particles
+//   list            uint16[lcap]  in-range candidate indices
+struct W64Layout {
+    int x64, part, stab, s64, x32, spre, off, list, bytes;
+    __host__ __device__ W64Layout(int cap, int R, int lcap)
+    {
+        const int ns = (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
+        x64 = 0;
+        part = x64 + 24 * cap;
+        stab = part + 2 * kW64Comp * 32 * 8;
+        s64 = stab + 16 * ns;
+        x32 = s64 + ((24 * ns + 15) & ~15);
+        spre = x32 + 12 * cap;
+        off = spre + 4 * ((ns + 1 + 3) & ~3);
+        list = off + 4 * (kW64PMax + 4);
+        bytes = (list + 2 * lcap + 15) & ~15;
+    }
+};
+
+// FP32 value of a double by truncation of its IEEE-754 fields (relative
+// error below 2^-23; |x| < 2^-126 gives 0).  Exponent bias 1023 -> 127 is a
+// subtraction of 896 << 20 from the high word; the 23-bit mantissa is the
+// high word's 20 bits and the top 3 bits of the low word.  Integer
+// operations only: the filters never touch the FP64 pipe.
+__device__ __forceinline__ float f32_trunc(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned mag = hi & 0x7fffffffu;
+    const unsigned b = mag >= (897u << 20) ? (((mag - (896u << 20)) << 3) | (lo >> 29)) : 0u;
+    return __uint_as_float(b | (hi & 0x80000000u));
+}
+
+__device__ __forceinline__ double3 load_xyz(const double4_16a *__restrict__ pos, int i)
+{
+    const double2 *p2 = reinterpret_cast<const double2 *>(pos + i);
+    const double2 a = __ldg(p2);
+    const double2 b = __ldg(p2 + 1);
+    return make_double3(a.x, a.y, b.x);
+}
+
+struct Acc64 {
+    double fx, fy, fz, e, w;
+    __device__ __forceinline__ void zero() { fx = fy = fz = e = w = 0.0; }
+};
+
+// Final sums of home particle `slot` (sorted index): force, and its energy
+// share and virial when ENERGY.
+template <bool ENERGY>
+__device__ __forceinline__ void w64_store(const W64Params &k, const double4_16a *__restrict__ pos,
+                                          double4_16a *__restrict__ fout, int slot, const Acc64 &a, double &eacc,
+                                          double &wacc)
+{
+    const int idx = (int)__ldg(&pos[slot].w);
+    if ((unsigned)idx >= (unsigned)k.n) return;
+    double4_16a o;
+    o.x = a.fx;
+    o.y = a.fy;
+    o.z = a.fz;
+    o.w = ENERGY ? 0.5 * a.e : 0.0;
+    fout[idx] = o;
+    if constexpr (ENERGY) {
+        eacc += 0.5 * a.e;
+        wacc += 0.5 * a.w;
+    }
+}
+
+// Plain path: lanes own home particles, FP64 over every candidate read from
+// global memory per stencil cell (cells whose stencil overflows the slice).
+template <int R, int MODE, bool ENERGY>
+__device__ void w64_plain(const W64Params &k, const Coef<double> &kc, const double4_16a *__restrict__ pos,
+                          double4_16a *__restrict__ fout, const float4 *stab, const double *S64, const int *spre,
+                          int s_home, int n_home, double &eacc, double &wacc)
+{
+    constexpr int NS = Stencil<R>::NS;
+    const int lane = threadIdx.x & 31;
+    for (int p0 = 0; p0 < n_home; p0 += 32) {
+        const int i = p0 + lane;
+        const bool vi = i < n_home;
+        const double3 pi = load_xyz(pos, s_home + (vi ? i : 0));
+        Acc64 a;
+        a.zero();
+        for (int kk = 0; kk < NS; kk++) {
+            const int s = __float_as_int(stab[kk].w);
+            const int nn = spre[kk + 1] - spre[kk];
+            const double xs = pi.x - S64[kk], ys = pi.y - S64[NS + kk], zs = pi.z - S64[2 * NS + kk];
+            for (int j = 0; j < nn; j++) {
+                const double3 q = load_xyz(pos, s + j);
+                pair_accum<double, MODE, ENERGY>(xs - q.x, ys - q.y, zs - q.z, kc, a.fx, a.fy, a.fz, a.e, a.w);
+            }
+        }
+        if (vi) w64_store<ENERGY>(k, pos, fout, s_home + i, a, eacc, wacc);
+    }
+}
+
+// Staging of one home cell's stencil: returns the number of kept candidates
+// T, or -1 (nothing written that matters) when they would not fit the slice
+// with the 64 padding entries Phase A reads.
+template <int R>
+__device__ __forceinline__ int w64_stage(const W64Params &k, const double4_16a *__restrict__ pos, float *X, float *Y,
+                                         float *Z, double *X64, double *Y64, double *Z64, const float4 *stab,
+                                         const double *S64, const int *spre, int Ttot, int s_home, int n_home)
+{
+    constexpr int NS = Stencil<R>::NS, P2 = Stencil<R>::P2;
+    const int lane = threadIdx.x & 31;
+    float bxl = 3.4e38f, byl = 3.4e38f, bzl = 3.4e38f, bxh = -3.4e38f, byh = -3.4e38f, bzh = -3.4e38f;
+    for (int p0 = 0; p0 < n_home; p0 += 32) {
+        if (p0 + lane < n_home) {
+            const double3 q = load_xyz(pos, s_home + p0 + lane);
+            const float qx = f32_trunc(q.x), qy = f32_trunc(q.y), qz = f32_trunc(q.z);
+            bxl = fminf(bxl, qx);
+            byl = fminf(byl, qy);
+            bzl = fminf(bzl, qz);
+            bxh = fmaxf(bxh, qx);
+            byh = fmaxf(byh, qy);
+            bzh = fmaxf(bzh, qz);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
+        byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
+        bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
+        bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
+        byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
+        bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    int T = 0;
+    for (int t0 = 0; t0 < Ttot; t0 += 32 * kStageBatch) {
+        double3 q[kStageBatch];
+        float4 sh[kStageBatch];
+        int kcs[kStageBatch];
+#pragma unroll
+        for (int u = 0; u < kStageBatch; u++) {
+            const int t = t0 + 32 * u + lane;
+            q[u] = make_double3(0.0, 0.0, 0.0);
+            sh[u] = make_float4(kFar, kFar, kFar, 0.f);
+            kcs[u] = 0;
+            if (t < Ttot) {
+                int kc = 0, kb = 0;
+#pragma unroll
+                for (int step = P2 / 2; step > 0; step >>= 1) {
+                    const int m = kc + step;
+                    if (m < NS) {
+                        const int v = spre[m];
+                        if (v <= t) {
+                            kc = m;
+                            kb = v;
+                        }
+                    }
+                }
+                sh[u] = stab[kc];
+                kcs[u] = kc;
+                q[u] = load_xyz(pos, __float_as_int(sh[u].w) + (t - kb));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStageBatch; u++) {
+            if (T + 96 > k.cap) {   // this round (<= 32) plus 64 padding entries might not fit
+                __syncwarp();
+                return -1;
+            }
+            const int t = t0 + 32 * u + lane;
+            const float cx = f32_trunc(q[u].x) + sh[u].x;
+            const float cy = f32_trunc(q[u].y) + sh[u].y;
+            const float cz = f32_trunc(q[u].z) + sh[u].z;
+            const float dx = fmaxf(fmaxf(bxl - cx, cx - bxh), 0.f);
+            const float dy = fmaxf(fmaxf(byl - cy, cy - byh), 0.f);
+            const float dz = fmaxf(fmaxf(bzl - cz, cz - bzh), 0.f);
+            const bool keep = t < Ttot && dx * dx + dy * dy + dz * dz < k.rc2_box;
+            const unsigned kept = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int sl = T + __popc(kept & lt);
+                const int kc = kcs[u];
+                X[sl] = cx;
+                Y[sl] = cy;
+                Z[sl] = cz;
+                X64[sl] = q[u].x + S64[kc];
+                Y64[sl] = q[u].y + S64[NS + kc];
+                Z64[sl] = q[u].z + S64[2 * NS + kc];
+            }
+            T += __popc(kept);
+        }
+    }
+    X[T + lane] = kFar;
+    Y[T + lane] = kFar;
+    Z[T + lane] = kFar;
+    X[T + 32 + lane] = kFar;
+    Y[T + 32 + lane] = kFar;
+    Z[T + 32 + lane] = kFar;
+    __syncwarp();
+    return T;
+}
+
+// Phase B over one batch: entries [0, E) of the list, particles pb .. pb + P
+// - 1 of the home cell with list offsets off[0 .. P].
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void w64_pairs(const W64Params &k, const Coef<double> &kc,
+                                          const double4_16a *__restrict__ pos, double4_16a *__restrict__ fout,
+                                          const double *X64, const double *Y64, const double *Z64,
+                                          const uint16_t *list, const int *off, double *part, int E, int P,
+                                          int pb, int s_home, double &eacc, double &wacc)
+{
+    const int lane = threadIdx.x & 31;
+    double *first = part;                 // [kW64Comp][32]
+    double *head = part + kW64Comp * 32;  // [kW64Comp][32]
+    const int lo = (lane * E) >> 5;
+    const int hi = ((lane + 1) * E) >> 5;
+    int headq = -1;
+    if (lo < hi) {
+        // q: the particle whose entries contain lo (largest q < P with off[q] <= lo)
+        int q = 0;
+#pragma unroll
+        for (int step = kW64PMax / 2; step > 0; step >>= 1)
+            if (q + step < P && off[q + step] <= lo) q += step;
+        int nxt = off[q + 1];
+        double xp = X64[pb + q], yp = Y64[pb + q], zp = Z64[pb + q];
+        Acc64 a;
+        a.zero();
+        auto flush = [&]() {
+            const bool starts = off[q] >= lo;
+            const bool ends = nxt <= hi;
+            if (starts && ends) {
+                w64_store<ENERGY>(k, pos, fout, s_home + pb + q, a, eacc, wacc);
+            } else {
+                double *dst = starts ? head : first;
+                dst[0 * 32 + lane] = a.fx;
+                dst[1 * 32 + lane] = a.fy;
+                dst[2 * 32 + lane] = a.fz;
+                if constexpr (ENERGY) {
+                    dst[3 * 32 + lane] = a.e;
+                    dst[4 * 32 + lane] = a.w;
+                }
+                if (starts) headq = q;
+            }
+        };
+        for (int e = lo; e < hi; e++) {
+            if (e == nxt) {
+                flush();
+                do {
+                    q++;
+                    nxt = off[q + 1];
+                } while (nxt == e);   // particles without entries were stored in Phase A
+                xp = X64[pb + q];
+                yp = Y64[pb + q];
+                zp = Z64[pb + q];
+                a.zero();
+            }
+            const int j = list[e];
+            pair_accum<double, MODE, ENERGY>(xp - X64[j], yp - Y64[j], zp - Z64[j], kc, a.fx, a.fy, a.fz, a.e, a.w);
+        }
+        flush();
+    }
+    __syncwarp();
+    if (headq >= 0) {
+        // this lane holds the first entries of particle headq; the rest are
+        // the first segments of the following non-empty lanes
+        Acc64 a;
+        a.fx = head[0 * 32 + lane];
+        a.fy = head[1 * 32 + lane];
+        a.fz = head[2 * 32 + lane];
+        a.e = ENERGY ? head[3 * 32 + lane] : 0.0;
+        a.w = ENERGY ? head[4 * 32 + lane] : 0.0;
+        const int end = off[headq + 1];
+        for (int l2 = lane + 1; l2 < 32; l2++) {
+            const int lo2 = (l2 * E) >> 5, hi2 = ((l2 + 1) * E) >> 5;
+            if (lo2 == hi2) continue;
+            a.fx += first[0 * 32 + l2];
+            a.fy += first[1 * 32 + l2];
+            a.fz += first[2 * 32 + l2];
+            if constexpr (ENERGY) {
+                a.e += first[3 * 32 + l2];
+                a.w += first[4 * 32 + l2];
+            }
+            if (end <= hi2) break;
+        }
+        w64_store<ENERGY>(k, pos, fout, s_home + pb + headq, a, eacc, wacc);
+    }
+    __syncwarp();   // part, list and off are rewritten by the next batch
+}
+
+template <int R, int MODE, bool ENERGY>
+__device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const double4_16a *__restrict__ pos,
+                         const int32_t *__restrict__ start, double4_16a *__restrict__ fout, unsigned char *slice,
+                         int cx, int cy, int cz, double &eacc, double &wacc)
+{
+    constexpr int NS = Stencil<R>::NS;
+    const W64Layout L(k.cap, R, k.lcap);
+    double *X64 = reinterpret_cast<double *>(slice + L.x64);
+    double *Y64 = X64 + k.cap;
+    double *Z64 = Y64 + k.cap;
+    double *part = reinterpret_cast<double *>(slice + L.part);
+    float4 *stab = reinterpret_cast<float4 *>(slice + L.stab);
+    double *S64 = reinterpret_cast<double *>(slice + L.s64);
+    float *X = reinterpret_cast<float *>(slice + L.x32);
+    float *Y = X + k.cap;
+    float *Z = Y + k.cap;
+    int *spre = reinterpret_cast<int *>(slice + L.spre);
+    int *off = reinterpret_cast<int *>(slice + L.off);
+    uint16_t *list = reinterpret_cast<uint16_t *>(slice + L.list);
+    const int lane = threadIdx.x & 31;
+    const int nc = k.nc;
+
+    __syncwarp();   // the slice still holds the previous cell's data
+    int carry = 0;
+#pragma unroll 1
+    for (int b0 = 0; b0 < NS; b0 += 32) {
+        const int kk = b0 + lane;
+        int nn = 0;
+        if (kk < NS) {
+            int dx, dy, dz;
+            stencil_delta<R>(kk, dx, dy, dz);
+            int ux = cx + dx, uy = cy + dy, uz = cz + dz;
+            ux += ux < 0 ? nc : 0;
+            ux -= ux >= nc ? nc : 0;
+            uy += uy < 0 ? nc : 0;
+            uy -= uy >= nc ? nc : 0;
+            uz += uz < 0 ? nc : 0;
+            uz -= uz >= nc ? nc : 0;
+            const int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
+            const int s = start[cn];
+            nn = start[cn + 1] - s;
+            stab[kk] = make_float4((float)dx * k.cwf, (float)dy * k.cwf, (float)dz * k.cwf, __int_as_float(s));
+            S64[kk] = (double)dx * k.cw;
+            S64[NS + kk] = (double)dy * k.cw;
+            S64[2 * NS + kk] = (double)dz * k.cw;
+        }
+        int P = nn;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, P, o);
+            if (lane >= o) P += y;
+        }
+        if (kk < NS) spre[kk] = carry + P - nn;
+        carry += __shfl_sync(0xffffffffu, P, 31);
+    }
+    if (lane == 0) spre[NS] = carry;
+    __syncwarp();
+    const int n_home = spre[1];
+    if (n_home == 0) return;
+    const int s_home = __float_as_int(stab[0].w);
+    const int T = carry <= 2 * k.cap
+                      ? w64_stage<R>(k, pos, X, Y, Z, X64, Y64, Z64, stab, S64, spre, carry, s_home, n_home)
+                      : -1;
+    if (T < 0) {
+        w64_plain<R, MODE, ENERGY>(k, kc, pos, fout, stab, S64, spre, s_home, n_home, eacc, wacc);
+        return;
+    }
+    const float2 *X2 = reinterpret_cast<const float2 *>(X);
+    const float2 *Y2 = reinterpret_cast<const float2 *>(Y);
+    const float2 *Z2 = reinterpret_cast<const float2 *>(Z);
+    const unsigned lt = (1u << lane) - 1u;
+    int p = 0;
+    while (p < n_home) {
+        // Phase A: lists of the batch's particles (home particle p sits at
+        // staged position p; its list has at most T - 1 entries)
+        const int pb = p;
+        int E = 0;
+        if (lane == 0) off[0] = 0;
+        while (p < n_home && p - pb < kW64PMax && E + T <= k.lcap) {
+            const float2 xs = make_float2(X[p], X[p]), ys = make_float2(Y[p], Y[p]), zs = make_float2(Z[p], Z[p]);
+            const int E0 = E;
+            for (int j0 = 0; j0 < T; j0 += 64) {
+                const int jx = j0 + 2 * lane;
+                const float2 qx = X2[(j0 >> 1) + lane], qy = Y2[(j0 >> 1) + lane], qz = Z2[(j0 >> 1) + lane];
+                const float2 m1 = make_float2(-1.0f, -1.0f);
+                const float2 dx = __ffma2_rn(qx, m1, xs);
+                const float2 dy = __ffma2_rn(qy, m1, ys);
+                const float2 dz = __ffma2_rn(qz, m1, zs);
+                float2 r2 = __fmul2_rn(dx, dx);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                const bool ina = r2.x < k.rc2_pair && jx != p;
+                const bool inb = r2.y < k.rc2_pair && jx + 1 != p;
+                const unsigned ba = __ballot_sync(0xffffffffu, ina);
+                const unsigned bb = __ballot_sync(0xffffffffu, inb);
+                if (ina) list[E + __popc(ba & lt)] = (uint16_t)jx;
+                if (inb) list[E + __popc(ba) + __popc(bb & lt)] = (uint16_t)(jx + 1);
+                E += __popc(ba) + __popc(bb);
+            }
+            if (lane == 0) off[p - pb + 1] = E;
+            if (E == E0 && lane == 0) {
+                // no candidate within rc: the force is zero
+                Acc64 a;
+                a.zero();
+                w64_store<ENERGY>(k, pos, fout, s_home + p, a, eacc, wacc);
+            }
+            p++;
+        }
+        __syncwarp();
+        // Phase B
+        w64_pairs<MODE, ENERGY>(k, kc, pos, fout, X64, Y64, Z64, list, off, part, E, p - pb, pb, s_home, eacc,
+                                wacc);
+    }
+}
+
+template <int R, int MODE, bool ENERGY>
+__global__ void __launch_bounds__(kW64Threads) k_force_w64(W64Params k, const double4_16a *__restrict__ pos,
+                                                           const int32_t *__restrict__ start,
+                                                           double4_16a *__restrict__ fout,
+                                                           double *__restrict__ partial)
+{
+    extern __shared__ __align__(16) unsigned char w64smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const W64Layout L(k.cap, R, k.lcap);
+    unsigned char *slice = w64smem + (size_t)warp * L.bytes;
+    const Coef<double> kc(k);
+    const int nc = k.nc;
+    double eacc = 0.0, wacc = 0.0;
+    auto one_cell = [&](int64_t c) {
+        const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+        w64_cell<R, MODE, ENERGY>(k, kc, pos, start, fout, slice, cx, cy, cz, eacc, wacc);
+    };
+    if (k.grab > 0) {
+        for (;;) {
+            unsigned c0 = 0;
+            if (lane == 0) c0 = atomicAdd(k.work, (unsigned)k.grab);
+            c0 = __shfl_sync(0xffffffffu, c0, 0);
+            if ((int64_t)c0 >= k.ncell) break;
+            const int64_t c1 = min((int64_t)c0 + k.grab, k.ncell);
+            for (int64_t c = c0; c < c1; c++) one_cell(c);
+        }
+    } else {
+        const int64_t nwarps = (int64_t)gridDim.x * (kW64Threads / 32);
+        for (int64_t c = (int64_t)blockIdx.x * (kW64Threads / 32) + warp; c < k.ncell; c += nwarps) one_cell(c);
+    }
+    if constexpr (ENERGY) {
+        __shared__ double red[2 * (kW64Threads / 32)];
+        for (int o = 16; o > 0; o >>= 1) {
+            eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+            wacc += __shfl_xor_sync(0xffffffffu, wacc, o);
+        }
+        if (lane == 0) {
+            red[2 * warp] = eacc;
+            red[2 * warp + 1] = wacc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double es = 0.0, ws = 0.0;
+            for (int q = 0; q < kW64Threads / 32; q++) {
+                es += red[2 * q];
+                ws += red[2 * q + 1];
+            }
+            partial[2 * blockIdx.x] = es;
+            partial[2 * blockIdx.x + 1] = ws;
+        }
+    }
+}
+
+template <int R>
+void *w64_kernel_r(int mode, bool energy)
+{
+    switch (mode * 2 + (energy ? 1 : 0)) {
+        case 0: return (void *)k_force_w64<R, 0, false>;
+        case 1: return (void *)k_force_w64<R, 0, true>;
+        case 2: return (void *)k_force_w64<R, 1, false>;
+        case 3: return (void *)k_force_w64<R, 1, true>;
+        case 4: return (void *)k_force_w64<R, 2, false>;
+        default: return (void *)k_force_w64<R, 2, true>;
+    }
+}
+
+// FP64 contexts use the 27-cell stencil (subdivision 1) only.
+void *w64_kernel(int mode, bool energy) { return w64_kernel_r<1>(mode, energy); }
+
+W64Params w64_params_of(const lj_ctx *c)
+{
+    W64Params k;
+    memset(&k, 0, sizeof(k));
+    k.n = (int)c->p.n;
+    k.nc = c->nc;
+    k.cap = c->wcap;
+    k.lcap = c->w64_lcap;
+    k.grab = c->grab;
+    k.work = c->work;
+    k.ncell = c->ncell;
+    k.cwf = (float)c->cw;
+    k.cw = c->cw;
+    const double eps = c->p.eps, sg = c->p.sigma, rc = c->p.rc;
+    const double s6 = sg * sg * sg * sg * sg * sg, s12 = s6 * s6;
+    const double rci2 = 1.0 / (rc * rc), rci6 = rci2 * rci2 * rci2;
+    k.rc2 = rc * rc;
+    k.rc = rc;
+    // FP32 filters: the bounding-box test as in the FP32-mixed kernel, the
+    // pair test with a relative margin of 1e-4 on rc^2 (the truncated FP32
+    // coordinates are within ~1e-6 of the FP64 ones)
+    k.rc2_box = (float)(rc * rc) * 1.0001f;
+    k.rc2_pair = (float)(rc * rc * (1.0 + 1e-4));
+    k.a12 = 48.0 * eps * s12;
+    k.b6 = 24.0 * eps * s6;
+    k.c12 = 4.0 * eps * s12;
+    k.c6 = 4.0 * eps * s6;
+    k.uc = rci6 * (4.0 * eps * s12 * rci6 - 4.0 * eps * s6);
+    k.fc = rc * rci2 * rci6 * (48.0 * eps * s12 * rci6 - 24.0 * eps * s6);
+    return k;
+}
+
+}  // namespace
+
+cudaError_t w64_force_configure(lj_ctx *c)
+{
+    if (c->p.cell_subdiv == 2) return cudaErrorInvalidValue;
+    const int subdiv = 1;
+    const int ns = (2 * subdiv + 1) * (2 * subdiv + 1) * (2 * subdiv + 1);
+    const double mean = c->ncell > 0 ? (double)c->p.n / (double)c->ncell : 0.0;
+    // Kept candidates: about 0.65 of the stencil population m after the
+    // bounding-box pruning; capacity 0.75 m + 4 sqrt(m) + the 96 entries of
+    // the last round and the padding, at least 160, at most what fits 227 KB
+    // per CTA.  The list holds 2048 entries (~55 per particle at liquid
+    // density); a cell's particles whose lists exceed it are taken in batches.
+    // Denser systems than the slice holds take the plain path in the cells
+    // that overflow.  lcap >= cap, so one particle's list always fits.
+    const double m = (double)ns * mean;
+    int cap = (int)(0.75 * m + 4.0 * sqrt(m)) + 96;
+    cap = cap < 160 ? 160 : cap;
+    cap = (cap + 7) & ~7;
+    const int lcap = 2048;
+    const int warps = kW64Threads / 32;
+    const int limit = 227 * 1024 - 2 * warps * (int)sizeof(double) - 256;
+    while (cap > 160 && (cap > lcap || warps * W64Layout(cap, subdiv, lcap).bytes > limit)) cap -= 8;
+    if (warps * W64Layout(cap, subdiv, lcap).bytes > limit) return cudaErrorInvalidValue;
+    c->wcap = cap;
+    c->w64_lcap = lcap;
+    c->wforce_smem = warps * W64Layout(cap, subdiv, lcap).bytes;
+    int minblk = 1 << 30;
+    for (int mode = 0; mode < 3; mode++)
+        for (int en = 0; en < 2; en++) {
+            void *kern = w64_kernel(mode, en != 0);
+            cudaError_t e = raise_dyn_smem(kern, c->wforce_smem);
+            if (e != cudaSuccess) return e;
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kW64Threads, c->wforce_smem);
+            if (e != cudaSuccess) return e;
+            if (nb < minblk) minblk = nb;
+        }
+    if (minblk < 1) minblk = 1;
+    const int64_t need = (c->ncell + warps - 1) / warps;
+    int64_t grid = (int64_t)minblk * c->nsm;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    c->wforce_grid = (int)grid;
+    return cudaSuccess;
+}
+
+cudaError_t launch_force_w64(lj_ctx *c, void *f, bool energy)
+{
+    W64Params k = w64_params_of(c);
+    const double4_16a *pos = (const double4_16a *)c->pos;
+    const int32_t *start = c->start;
+    double *partial = c->partial;
+    void *args[] = {&k, (void *)&pos, (void *)&start, &f, &partial};
+    void *kern = w64_kernel(c->p.shift_mode, energy);
+    if (c->timing && c->ev_used + 2 <= c->nev) cudaEventRecord(c->ev[c->ev_used], c->stream);
+    cudaError_t e = cudaLaunchKernel(kern, dim3(c->wforce_grid), dim3(kW64Threads), args, c->wforce_smem, c->stream);
+    if (c->timing && c->ev_used + 2 <= c->nev) {
+        cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+        c->ev_used += 2;
+    }
+    c->kernel_launches++;
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}

@@ -209,6 +209,7 @@ cudaError_t launch_warp(lj_ctx *c, void *kern, WarpParams k, void *f, KickDriftB
 
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
 {
+    if (c->p.precision == LJ_PREC_FP64) return launch_force_w64(c, f, energy);
     // tuning choice: stencils bulk-copied one cell ahead (lj_force_pipe.cu)
     if (c->p.cell_subdiv != 2 && c->pipe) return launch_force_pipe(c, f, energy);
     KickDriftBin kd;

@@ -71,6 +71,7 @@ struct lj_ctx {
     int pipe;            // tuning: 1 = warp kernel with bulk-copied stencils (kernel 5)
     int fuse_update;     // warp kernel applies the velocity-Verlet update (lj_step)
     int grab;            // tuning: cells per work pull in the warp kernel (0 = static)
+    int w64_lcap;        // FP64 warp kernel: list entries per warp
     unsigned *work;      // work counter of the warp kernel, zeroed by k_scan_tiles
     int npartial;        // partials written by the last energy launch
     int npartial_cap;    // capacity of `partial` in (energy, virial) pairs
@@ -258,6 +259,10 @@ int warp_stencil_cap(double mean_occupancy, int subdiv, int threads, int static_
 cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, double *dparam);
 cudaError_t launch_axpy(lj_ctx *c, double *y, const double *x, double a);
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);
+// FP64 warp kernel with compacted pair lists (lj_force_w64.cu); it uses the
+// warp kernel's slice capacity, shared memory and grid fields.
+cudaError_t w64_force_configure(lj_ctx *c);
+cudaError_t launch_force_w64(lj_ctx *c, void *f, bool energy);
 // Pipelined warp kernel (lj_force_pipe.cu): configuration and launch.
 cudaError_t pipe_force_configure(lj_ctx *c);
 cudaError_t launch_force_pipe(lj_ctx *c, void *f, bool energy);

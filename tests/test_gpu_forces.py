@@ -128,6 +128,43 @@ def test_dense_cluster_and_overflow(oracle_mod, precision, flags):
             _check(x, L, oracle_mod, precision, gw=gw)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_fp64_pair_lists_in_batches(oracle_mod, mode):
+    """FP64 warp kernel: a dense liquid (rho 1.1) with rc = 3, so a home
+    cell's in-range pair lists (~30 particles x ~120 partners) exceed one
+    list batch and are taken in several; the same forces as the oracle and
+    as the FP64 run kernel."""
+    from paper_0709_3225_gb300 import lj
+    x, L = inputs.jittered_fcc(8, 1.1, 0.05, 50 + mode)
+    f, _ = _check(x, L, oracle_mod, "fp64", mode, rc=3.0)
+    s = lj.System(x, None, L, precision="fp64", shift_mode=mode, rc=3.0)
+    lj.lj_set_tuning(s.ctx, 1)
+    e, w = s.forces(energy=True)
+    fr = s.f.cpu().numpy()
+    s.check()
+    s.close()
+    assert np.abs(fr - f).max() <= 1e-12 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("grab", [0, 1, 4])
+def test_fp64_kernels_agree(grab):
+    """FP64 warp kernel (static striding or work pulls) against the run
+    kernel, on a liquid with empty, sparse and crowded cells."""
+    from paper_0709_3225_gb300 import lj
+    x, L = dense_cluster_state(seed=7)
+    out = []
+    for kernel in (3, 1):
+        s = lj.System(x, None, L, precision="fp64")
+        lj.lj_set_tuning(s.ctx, kernel, 0, grab)
+        e, w = s.forces(energy=True)
+        out.append((s.f.cpu().numpy(), e, w))
+        s.check()
+        s.close()
+    (fa, ea, wa), (fb, eb, wb) = out
+    assert np.abs(fa - fb).max() <= 1e-11 * np.abs(fb).max()
+    assert ea == pytest.approx(eb, rel=1e-12) and wa == pytest.approx(wb, rel=1e-12)
+
+
 def test_ragged_random_gas(oracle_mod):
     # Uniform random gas with a minimum-distance filter: empty cells, uneven
     # counts, particle count not a multiple of anything.
