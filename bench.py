@@ -33,6 +33,7 @@ WORKLOAD = "fluid-4m"
 FLOPS_PER_PAIR = 20          # flop convention per in-range pair evaluation
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 rate of the part (no measured figure)
 
 
 def unique_pairs(n: int, rho: float, rc: float) -> float:
@@ -675,7 +676,13 @@ def run_gpu(args):
         "fluid_start": fluid,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
-                 "pair_interactions_per_s": pairs * 1e3 / ms64},
+                 "pair_interactions_per_s": pairs * 1e3 / ms64,
+                 "kernel": "k_force_w64 (compacted in-range pair lists)",
+                 "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                              "achieved": FLOPS_PER_PAIR * pairs / (f64_ms / max(f64_n, 1) / 1e3) / 1e12,
+                              "frac": FLOPS_PER_PAIR * pairs / (f64_ms / max(f64_n, 1) / 1e3) / 1e12
+                              / FP64_PEAK_TFLOPS,
+                              "peak_source": "nominal GB300 FP64 rate"}},
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": bytes_h2d,
                 "d2h_bytes_per_step": bytes_h2d, "steps": e2e_steps,
                 "api": "lj_step_host, pinned host x, v, f; 1 step per call"},

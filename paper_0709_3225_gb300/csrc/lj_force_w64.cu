@@ -23,7 +23,7 @@
 //    whose entries all lie in one lane is stored by that lane; a particle
 //    split over several lanes is combined by the lane holding its first
 //    entry, adding the other lanes' partial sums in lane order.  The exact
-//    FP64 cutoff test decides each pair.  Sums are in a fixed order, so the
+//    FP64 cutoff test decides each pair (pair64).  Sums are in a fixed order, so the
 //    forces are reproducible for a fixed in-cell order.
 //  * Cells whose pruned stencil does not fit the warp's slice take a plain
 //    FP64 path reading global memory per stencil cell.
@@ -95,6 +95,64 @@ __device__ __forceinline__ double3 load_xyz(const double4_16a *__restrict__ pos,
     const double2 a = __ldg(p2);
     const double2 b = __ldg(p2 + 1);
     return make_double3(a.x, a.y, b.x);
+}
+
+// The FP64 pair term of Phase B.  Same formulas as pair_accum<double>, with
+// two changes that keep FP64-pipe work down and the result at FP64 accuracy:
+//  * the cutoff and self tests compare bit patterns as integers (r^2 >= +0,
+//    and non-negative doubles order as their bit patterns), off the FP64 pipe;
+//  * 1/r^2 (or 1/r for the force-shifted form) starts from the hardware's
+//    approximate FP64 reciprocal (reciprocal square root) and takes two
+//    Newton-Raphson steps, y <- y + y (1 - x y) (y <- y + (y/2)(1 - x y^2)),
+//    each of which squares the relative error.  Against IEEE division and
+//    square root the forces differ by at most ~1e-15 relative.
+__device__ __forceinline__ double rcp64_approx(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
+__device__ __forceinline__ double rsqrt64_approx(double x)
+{
+    double r;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void pair64(double dx, double dy, double dz, const Coef<double> &k, double &fx, double &fy,
+                                       double &fz, double &e, double &w)
+{
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    const long long b = __double_as_longlong(r2);
+    const bool in = b < __double_as_longlong(k.rc2) && b != 0;
+    double ri, rinv = 0.0;
+    if constexpr (MODE == 2) {
+        double y = rsqrt64_approx(r2);
+#pragma unroll
+        for (int it = 0; it < 2; it++) y = fma(0.5 * y, fma(-r2 * y, y, 1.0), y);
+        rinv = in ? y : 0.0;
+        ri = rinv * rinv;
+    } else {
+        double y = rcp64_approx(r2);
+#pragma unroll
+        for (int it = 0; it < 2; it++) y = fma(y, fma(-r2, y, 1.0), y);
+        ri = in ? y : 0.0;
+    }
+    const double r6 = ri * ri * ri;
+    double ff = ri * r6 * (k.a12 * r6 - k.b6);
+    if constexpr (MODE == 2) ff -= k.fc * rinv;
+    fx = fma(ff, dx, fx);
+    fy = fma(ff, dy, fy);
+    fz = fma(ff, dz, fz);
+    if constexpr (ENERGY) {
+        double u = r6 * (k.c12 * r6 - k.c6);
+        if constexpr (MODE >= 1) u -= k.uc;
+        if constexpr (MODE == 2) u += (r2 * rinv - k.rc) * k.fc;
+        e += in ? u : 0.0;
+        w += ff * r2;
+    }
 }
 
 struct Acc64 {
@@ -306,7 +364,7 @@ __device__ __forceinline__ void w64_pairs(const W64Params &k, const Coef<double>
                 a.zero();
             }
             const int j = list[e];
-            pair_accum<double, MODE, ENERGY>(xp - X64[j], yp - Y64[j], zp - Z64[j], kc, a.fx, a.fy, a.fz, a.e, a.w);
+            pair64<MODE, ENERGY>(xp - X64[j], yp - Y64[j], zp - Z64[j], kc, a.fx, a.fy, a.fz, a.e, a.w);
         }
         flush();
     }
