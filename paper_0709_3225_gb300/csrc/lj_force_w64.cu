@@ -35,7 +35,7 @@
 
 namespace {
 
-constexpr int kW64Threads = 128;   // 4 warps per CTA
+constexpr int kW64Threads = 32;    // one warp per CTA: residency set by each warp's slice alone
 constexpr int kW64PMax = 64;       // home particles per list batch
 constexpr int kW64Comp = 5;        // fx, fy, fz, energy, virial
 
@@ -102,10 +102,11 @@ __device__ __forceinline__ double3 load_xyz(const double4_16a *__restrict__ pos,
 //  * the cutoff and self tests compare bit patterns as integers (r^2 >= +0,
 //    and non-negative doubles order as their bit patterns), off the FP64 pipe;
 //  * 1/r^2 (or 1/r for the force-shifted form) starts from the hardware's
-//    approximate FP64 reciprocal (reciprocal square root) and takes two
-//    Newton-Raphson steps, y <- y + y (1 - x y) (y <- y + (y/2)(1 - x y^2)),
-//    each of which squares the relative error.  Against IEEE division and
-//    square root the forces differ by at most ~1e-15 relative.
+//    approximate FP64 reciprocal (reciprocal square root), relative error
+//    h ~ 1e-6, and takes one third-order correction: the first three terms
+//    of the series of 1/(1 - h) (of (1 - h)^(-1/2)), which cube the error.
+//    Against IEEE division and square root the forces differ by ~1e-14
+//    relative at most.
 __device__ __forceinline__ double rcp64_approx(double x)
 {
     double r;
@@ -130,14 +131,14 @@ __device__ __forceinline__ void pair64(double dx, double dy, double dz, const Co
     double ri, rinv = 0.0;
     if constexpr (MODE == 2) {
         double y = rsqrt64_approx(r2);
-#pragma unroll
-        for (int it = 0; it < 2; it++) y = fma(0.5 * y, fma(-r2 * y, y, 1.0), y);
+        const double h = fma(-r2 * y, y, 1.0);             // y = (1 - h)^(1/2) / sqrt(r2)
+        y = fma(y, h * fma(h, 0.375, 0.5), y);               // (1 - h)^(-1/2) ~ 1 + h/2 + 3h^2/8
         rinv = in ? y : 0.0;
         ri = rinv * rinv;
     } else {
         double y = rcp64_approx(r2);
-#pragma unroll
-        for (int it = 0; it < 2; it++) y = fma(y, fma(-r2, y, 1.0), y);
+        const double h = fma(-r2, y, 1.0);                  // y = (1 - h) / r2
+        y = fma(y, fma(h, h, h), y);                         // 1 / (1 - h) ~ 1 + h + h^2
         ri = in ? y : 0.0;
     }
     const double r6 = ri * ri * ri;
@@ -624,15 +625,18 @@ cudaError_t w64_force_configure(lj_ctx *c)
     // Kept candidates: about 0.65 of the stencil population m after the
     // bounding-box pruning; capacity 0.75 m + 4 sqrt(m) + the 96 entries of
     // the last round and the padding, at least 160, at most what fits 227 KB
-    // per CTA.  The list holds 2048 entries (~55 per particle at liquid
-    // density); a cell's particles whose lists exceed it are taken in batches.
+    // per CTA.  The list holds 1024 entries (~55 per particle at liquid
+    // density, ~730 per cell); a cell's particles whose lists exceed it are
+    // taken in batches.  A smaller slice means more resident warps: 10 per
+    // SM at liquid density (measured 8.40 -> 7.73 ms at 4M against 8 warps
+    // with a 2048-entry list).
     // Denser systems than the slice holds take the plain path in the cells
     // that overflow.  lcap >= cap, so one particle's list always fits.
     const double m = (double)ns * mean;
     int cap = (int)(0.75 * m + 4.0 * sqrt(m)) + 96;
     cap = cap < 160 ? 160 : cap;
     cap = (cap + 7) & ~7;
-    const int lcap = 2048;
+    const int lcap = 1024;
     const int warps = kW64Threads / 32;
     const int limit = 227 * 1024 - 2 * warps * (int)sizeof(double) - 256;
     while (cap > 160 && (cap > lcap || warps * W64Layout(cap, subdiv, lcap).bytes > limit)) cap -= 8;
