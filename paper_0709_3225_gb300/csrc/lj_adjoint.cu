@@ -98,7 +98,11 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp(int n, int nc, int64_t ncel
             const V pi = pos[s_home + (vi ? i : 0)];
             const V gi = g4[s_home + (vi ? i : 0)];
             T ax = 0, ay = 0, az = 0;
-            double ae = 0.0, as = 0.0;   // parameter sums over pairs: FP64 (cancelling sums of FP32 terms)
+            // Parameter sums over pairs: per stencil cell in the working
+            // precision (a few dozen terms), then in FP64 across cells and
+            // particles (the totals cancel).  One FP64 addition per stencil
+            // cell, not per candidate: FP64 is rationed on this GPU.
+            double ae = 0.0, as = 0.0;
             for (int kk = 0; kk < NS; kk++) {
                 int s, nn;
                 T shx, shy, shz;
@@ -106,6 +110,7 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp(int n, int nc, int64_t ncel
                 const T xs = pi.x - shx;
                 const T ys = pi.y - shy;
                 const T zs = pi.z - shz;
+                T ae_c = 0, as_c = 0;
                 for (int j = 0; j < nn; j++) {
                     const V qj = pos[s + j];
                     const V gj = g4[s + j];
@@ -136,9 +141,11 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp(int n, int nc, int64_t ncel
                     ax += phi * gx + dphi * dot * dx_;
                     ay += phi * gy + dphi * dot * dy_;
                     az += phi * gz + dphi * dot * dz_;
-                    ae += (double)(phi1 * gid);
-                    as += (double)(eps * dsig1 * gid);
+                    ae_c += phi1 * gid;
+                    as_c += eps * dsig1 * gid;
                 }
+                ae += (double)ae_c;
+                as += (double)as_c;
             }
             if (vi) {
                 int idx;
