@@ -19,10 +19,12 @@ from gpu_util import min_image, rel_rms
 pytestmark = pytest.mark.gpu
 
 
-def _vjp_gpu(x, L, g, precision, mode, eps, sigma, scale=1.0, calls=1, subdiv=1):
+def _vjp_gpu(x, L, g, precision, mode, eps, sigma, scale=1.0, calls=1, subdiv=1, deterministic=False):
     import torch
     from paper_0709_3225_gb300 import lj
     s = lj.System(x, None, L, precision=precision, shift_mode=mode, eps=eps, sigma=sigma, cell_subdiv=subdiv)
+    if deterministic:
+        lj.lj_set_deterministic(s.ctx)
     gt = torch.as_tensor(g, device="cuda")
     dx = torch.zeros_like(s.x)
     dp = torch.zeros(2, dtype=torch.float64, device="cuda")
@@ -68,13 +70,35 @@ def test_vjp_matches_oracle(oracle_mod, precision, mode, subdiv):
         assert abs(dp_f[1] - ods_f) <= 1e-6 * abs(ods_f)
 
 
-def test_vjp_accumulates_with_scale(oracle_mod):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_vjp_accumulates_with_scale(oracle_mod, precision):
+    """Four calls with scale 1/4 add up to one call with scale 1 (every call
+    bins again: the deterministic in-cell order keeps the FP32 sums identical)."""
     x, L = inputs.jittered_fcc(6, 0.8442, 0.1, 43)
     g = np.random.default_rng(4).standard_normal(x.shape)
-    dx1, dp1 = _vjp_gpu(x, L, g, "fp64", 2, 1.0, 1.0, scale=1.0, calls=1)
-    dx2, dp2 = _vjp_gpu(x, L, g, "fp64", 2, 1.0, 1.0, scale=0.25, calls=4)
+    dx1, dp1 = _vjp_gpu(x, L, g, precision, 2, 1.0, 1.0, scale=1.0, calls=1, deterministic=True)
+    dx2, dp2 = _vjp_gpu(x, L, g, precision, 2, 1.0, 1.0, scale=0.25, calls=4, deterministic=True)
     np.testing.assert_allclose(dx2, dx1, rtol=1e-12, atol=1e-12 * np.abs(dx1).max())
     np.testing.assert_allclose(dp2, dp1, rtol=1e-12)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_vjp_dense_cluster(oracle_mod, mode):
+    """A dilute gas holding a compressed blob: cells with > 32 particles and
+    stencils over the staging capacity, which the FP32-mixed VJP takes on its
+    plain path; against the oracle, and the mixed against the FP64 GPU VJP."""
+    from gpu_util import dense_cluster_state
+    x, L = dense_cluster_state()
+    g = np.random.default_rng(11).standard_normal(x.shape)
+    dxm, dpm = _vjp_gpu(x, L, g, "mixed", mode, 1.0, 1.0)
+    dxd, dpd = _vjp_gpu(x, L, g, "fp64", mode, 1.0, 1.0)
+    odx, ode, ods = oracle_mod.forces_vjp(x, L, g, eps=1.0, sigma=1.0, mode=mode)
+    print(f"mode {mode}: mixed dx rel RMS {rel_rms(dxm, odx):.2e}, d_eps {abs(dpm[0] - ode) / abs(ode):.2e}, "
+          f"d_sigma {abs(dpm[1] - ods) / abs(ods):.2e}")
+    assert rel_rms(dxd, odx) <= 1e-11
+    assert abs(dpd[0] - ode) <= 1e-11 * abs(ode) and abs(dpd[1] - ods) <= 1e-11 * abs(ods)
+    assert rel_rms(dxm, odx) <= 1e-5
+    assert abs(dpm[0] - ode) <= 5e-6 * abs(ode) and abs(dpm[1] - ods) <= 5e-6 * abs(ods)
 
 
 def test_autograd_forces_against_finite_differences():
