@@ -318,17 +318,19 @@ def run_aop_density(stream):
 
 def run_graph_small(stream, steps=200):
     """Small systems, where launches rather than the GPU bound a step: ms per
-    step with direct launches and with graph replay of the middle steps
-    (lj_set_graph), for the 2,048- and 131,072-particle fluids."""
+    step with direct launches, with graph replay of the middle steps
+    (lj_set_graph), and with each step one persistent cooperative launch
+    (lj_set_tuning kernel 6), for the 2,048- and 131,072-particle fluids."""
     import torch
     from paper_0709_3225_gb300 import inputs, lj
     out = []
     for name in ("fluid-2k", "fluid-131k"):
         x, v, L, w = inputs.workload_state(name)
         row = {"workload": name, "n": w.n}
-        for graph in (False, True):
+        for label, graph, kernel in (("direct", False, 3), ("graph", True, 3), ("persistent", True, 6)):
             s = lj.System(x, v, L, dt=w.dt, rc=w.rc)
             lj.lj_set_graph(s.ctx, graph)
+            lj.lj_set_tuning(s.ctx, kernel, 0, 1 if kernel == 6 else 4)
             s.forces()
             s.step(10)
             torch.cuda.synchronize()
@@ -339,7 +341,7 @@ def run_graph_small(stream, steps=200):
             torch.cuda.synchronize()
             s.check()
             s.close()
-            row["graph_ms_per_step" if graph else "direct_ms_per_step"] = e0.elapsed_time(e1) / steps
+            row[f"{label}_ms_per_step"] = e0.elapsed_time(e1) / steps
         out.append(row)
     return out
 

@@ -304,13 +304,18 @@ int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);
  * kernel 0 = warp-per-cell kernel (FP32-mixed only) with the velocity-Verlet
  * update of lj_step fused into it, 1 = run kernel with bulk-copy staging,
  * 2 = run kernel reading global memory, 3 = warp-per-cell kernel with the
- * update in a separate kernel (the FP32-mixed default), 4 = the paper's
+ * update in a separate kernel (the default; in FP64 contexts the FP64 warp
+ * kernel that compacts the in-range pairs before any FP64 arithmetic), 4 = the paper's
  * fixed-capacity cell arrays (Section 3.1: 32 placeholders per cell, empty
  * ones computed as virtual particles; FP32-mixed; a cell with more than 32
  * particles latches LJ_EOVERFLOW, reported by lj_check), 5 = the warp
  * kernel with each cell's stencil bulk-copied into shared memory while the
- * previous cell computes (FP32-mixed); kernels 1, 2, 4 and 5 need
- * cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
+ * previous cell computes (FP32-mixed), 6 = kernel 3 for forces, with
+ * lj_step's steps run as one cooperative persistent launch each (the
+ * batched kernel below with one replica: no gaps between the phases of a
+ * step, for small systems; FP32-mixed; steps with a skin or the
+ * deterministic in-cell order take the regular path); kernels 1, 2, 4, 5
+ * and 6 need cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
  * in chunks of this many lanes, the other 32 / group_width lane groups
  * splitting the candidates; 0 = the compiled-in default (16 for
  * cell_subdiv 1, 4 for 2), -1 = chosen per cell to minimise idle lanes, or

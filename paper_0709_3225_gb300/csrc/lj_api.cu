@@ -111,6 +111,7 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->skin_counts);
     if (c->host_scalars) cudaFreeHost(c->host_scalars);
     if (c->host_err) cudaFreeHost(c->host_err);
+    if (c->pers) lj_batch_destroy(c->pers);
     if (c->ev) {
         for (int i = 0; i < c->nev; i++) cudaEventDestroy(c->ev[i]);
         free(c->ev);
@@ -129,11 +130,13 @@ int sync_and_check(lj_ctx *c)
         LJ_CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
         LJ_CK(cudaStreamSynchronize(c->stream));
     }
+    // steps taken by the persistent one-replica batch latch their own flags
+    const int rp = c->pers ? lj_batch_check(c->pers) : LJ_OK;
     if (bits & LJ_ERRBIT_NONFINITE) return LJ_ENONFINITE;
     if (bits & LJ_ERRBIT_TIMEOUT) return LJ_ETIMEOUT;
     if (bits & LJ_ERRBIT_SCAN) return LJ_ECUDA;
     if (bits & LJ_ERRBIT_OVERFLOW) return LJ_EOVERFLOW;
-    return LJ_OK;
+    return rp;
 }
 
 // Restart the skin bookkeeping after a full rebuild (the ungated count
@@ -247,9 +250,43 @@ int capture_middle_step(lj_ctx *c, double *x, double *v, void *f)
 // x_final (optional): recorded once x holds its final value (after the
 // last step's scatter; unfused updates only), so that its copy can overlap
 // the last force evaluation.
+// Tuning kernel 6: the steps run as one cooperative persistent launch each
+// (the batched-ensemble kernel with one replica), which removes the gaps
+// between the five kernels of a step; for small systems.  Cells with a skin
+// and the deterministic in-cell order keep the regular path.
+bool persistent_mode(const lj_ctx *c)
+{
+    return c->use_pers && c->skin <= 0.0 && !c->deterministic && c->p.precision == LJ_PREC_MIXED &&
+           c->p.cell_subdiv == 1 && c->p.n > 0;
+}
+
+int persistent_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps, cudaEvent_t x_final)
+{
+    if (!c->pers) {
+        const int64_t n = c->p.n;
+        const double box = c->p.box;
+        int r = lj_batch_create(&c->pers, 1, &n, &box, &c->p, (void *)c->stream);
+        if (r != LJ_OK) {
+            c->pers = nullptr;
+            return r;
+        }
+        r = lj_batch_set_tuning(c->pers, 1, 1, 0);
+        if (r != LJ_OK) return r;
+    }
+    int64_t l0 = 0, l1 = 0;
+    lj_batch_launches(c->pers, &l0, nullptr);
+    const int r = lj_batch_step(c->pers, x, v, f, nsteps);
+    lj_batch_launches(c->pers, &l1, nullptr);
+    c->kernel_launches += l1 - l0;
+    if (r != LJ_OK) return r;
+    if (x_final) LJ_CK(cudaEventRecord(x_final, c->stream));
+    return LJ_OK;
+}
+
 int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps, cudaEvent_t x_final = nullptr)
 {
     if (nsteps <= 0) return LJ_OK;
+    if (persistent_mode(c)) return persistent_steps(c, x, v, f, nsteps, x_final);
     if (fused_mode(c)) LJ_CK(launch_kick_drift_bin(c, x, v, f, 1));
     const bool graph = c->use_graph && !c->timing && nsteps >= 3;
     for (int s = 0; s < nsteps; s++) {
@@ -650,6 +687,11 @@ extern "C" int lj_set_params(lj_ctx *c, double eps, double sigma)
     c->p.eps = eps;
     c->p.sigma = sigma;
     c->gen++;   // captured steps hold the old coefficients
+    if (c->pers) {   // the persistent batch holds them too: rebuilt at the next step
+        LJ_CK(cudaStreamSynchronize(c->stream));
+        lj_batch_destroy(c->pers);
+        c->pers = nullptr;
+    }
     return LJ_OK;
 }
 
@@ -770,7 +812,15 @@ extern "C" int lj_skin_stats(lj_ctx *c, int64_t *rebuilds, int64_t *steps)
 extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int32_t cells_per_grab)
 {
     if (c) c->gen++;   // captured steps hold the old configuration
-    if (!c || kernel < 0 || kernel > 5 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
+    if (!c || kernel < 0 || kernel > 6 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
+    if (kernel == 6) {   // lj_step as one persistent launch per step; forces by the warp kernel
+        if (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2) return LJ_EINVAL;
+        const int r = lj_set_tuning(c, 3, group_width, cells_per_grab);
+        if (r != LJ_OK) return r;
+        c->use_pers = 1;
+        return LJ_OK;
+    }
+    c->use_pers = 0;
     if (kernel == 4) {   // the paper's fixed-capacity cell arrays: FP32-mixed, 27-cell stencil
         if (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2) return LJ_EINVAL;
         c->use_aop = 1;

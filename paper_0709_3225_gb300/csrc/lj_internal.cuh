@@ -72,6 +72,8 @@ struct lj_ctx {
     int fuse_update;     // warp kernel applies the velocity-Verlet update (lj_step)
     int grab;            // tuning: cells per work pull in the warp kernel (0 = static)
     int w64_lcap;        // FP64 warp kernel: list entries per warp
+    int use_pers;        // tuning kernel 6: lj_step through a one-replica persistent batch
+    lj_batch *pers;      // created by the first such step
     unsigned *work;      // work counter of the warp kernel, zeroed by k_scan_tiles
     int npartial;        // partials written by the last energy launch
     int npartial_cap;    // capacity of `partial` in (energy, virial) pairs

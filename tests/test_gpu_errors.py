@@ -123,6 +123,34 @@ def test_nonfinite_particles_go_to_the_extra_cell(oracle_mod, kernel, grab):
     s.close()
 
 
+def test_nonfinite_particle_in_persistent_steps():
+    """Steps through the persistent one-replica batch (tuning kernel 6)
+    report a non-finite particle through lj_check like the regular path, and
+    the context steps on normally once the state is finite again."""
+    import torch
+    from paper_0709_3225_gb300 import lj
+    x, L = inputs.jittered_fcc(8, 0.8442, 0.05, 5)
+    v = inputs.velocities(x.shape[0], 0.7, 5)
+    s = lj.System(x, v, L)
+    lj.lj_set_tuning(s.ctx, 6, 0, 1)
+    s.forces()
+    s.step(3)
+    s.check()
+    x_ok, v_ok, f_ok = s.x.clone(), s.v.clone(), s.f.clone()
+    s.x[11, 2] = float("nan")
+    s.step(2)
+    with pytest.raises(lj.LJError) as ei:
+        s.check()
+    assert ei.value.code == lj.LJ_ENONFINITE
+    s.x.copy_(x_ok)
+    s.v.copy_(v_ok)
+    s.f.copy_(f_ok)
+    s.step(4)
+    s.check()
+    assert bool(torch.isfinite(s.x).all())
+    s.close()
+
+
 def test_nonfinite_replica_particle_is_isolated(oracle_mod):
     from paper_0709_3225_gb300 import lj
     from gpu_util import rel_rms

@@ -38,11 +38,11 @@ def test_trajectory_matches_oracle(oracle_mod, precision, xtol, vtol, mode):
 
 
 @pytest.mark.parametrize("kernel,grab,subdiv", [(0, 0, 1), (3, 0, 1), (3, 1, 1), (3, 8, 1), (1, 0, 1),
-                                                (3, 4, 2), (0, 4, 2)])
+                                                (3, 4, 2), (0, 4, 2), (6, 1, 1), (6, 4, 1)])
 def test_update_paths_agree(oracle_mod, kernel, grab, subdiv):
-    """The fused update (kernel 0), the separate update (3) and the run kernel
-    (1), with cell subdivision 1 or 2, integrate the same trajectory
-    (force-shifted, FP32 rounding only)."""
+    """The fused update (kernel 0), the separate update (3), the run kernel
+    (1) and the persistent one-launch step (6), with cell subdivision 1 or
+    2, integrate the same trajectory (force-shifted, FP32 rounding only)."""
     from paper_0709_3225_gb300 import lj
     x, v, L = _liquid(seed=17)
     xo, vo = x.copy(), v.copy()
@@ -152,7 +152,7 @@ def test_drift_131k_mixed_vs_fp64():
 
 
 @pytest.mark.parametrize("kernel,skin,det", [(3, 0.0, 0), (0, 0.0, 0), (3, 0.4, 0), (1, 0.0, 0), (3, 0.0, 1),
-                                             (0, 0.0, 1), (3, 0.4, 1)])
+                                             (0, 0.0, 1), (3, 0.4, 1), (6, 0.0, 0), (6, 0.4, 0), (6, 0.0, 1)])
 def test_graph_replay_matches_oracle(oracle_mod, kernel, skin, det):
     """lj_step with graph replay of its middle steps (lj_set_graph): the same
     trajectory as the oracle, for the separate and fused updates, cells with a
@@ -174,8 +174,8 @@ def test_graph_replay_matches_oracle(oracle_mod, kernel, skin, det):
     # fresh arrays: the captured step must not be reused on the old pointers
     x2, v2, f2 = s.x.clone(), s.v.clone(), s.f.clone()
     lj.lj_step(s.ctx, x2, v2, f2, 7)
-    if kernel == 3:
-        lj.lj_set_tuning(s.ctx, 3, 8, 4)   # new configuration: captured again
+    if kernel in (3, 6):
+        lj.lj_set_tuning(s.ctx, kernel, 8, 4)   # new configuration: captured again
     lj.lj_step(s.ctx, x2, v2, f2, 7)
     s.check()
     assert np.abs(min_image(x2.cpu().numpy() - xo, L)).max() <= 2e-6
@@ -227,3 +227,24 @@ def test_step_host_one_step_calls(kernel, skin):
     assert torch.equal(xh, a.x.cpu()) and torch.equal(vh, a.v.cpu()) and torch.equal(fh, a.f.cpu())
     a.close()
     b.close()
+
+
+def test_persistent_steps_follow_parameter_changes(oracle_mod):
+    """lj_set_params between persistent steps (tuning kernel 6): the next
+    steps use the new eps and sigma, as the regular path does."""
+    from paper_0709_3225_gb300 import lj
+    x, v, L = _liquid(seed=19)
+    out = []
+    for kernel in (3, 6):
+        s = lj.System(x, v, L, shift_mode=2)
+        lj.lj_set_tuning(s.ctx, kernel, 0, 1)
+        s.forces()
+        s.step(5)
+        lj.lj_set_params(s.ctx, 0.9, 1.05)
+        s.forces()
+        s.step(5)
+        s.check()
+        out.append((s.x.cpu().numpy(), s.v.cpu().numpy()))
+        s.close()
+    assert np.abs(min_image(out[0][0] - out[1][0], L)).max() <= 2e-6
+    assert np.abs(out[0][1] - out[1][1]).max() <= 2e-4
