@@ -692,7 +692,13 @@ def run_gpu(args):
         "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(x, v, L, w)
+        cpu = cpu_baseline(x, v, L, w)
+        # the paper's speed-up form, T_CPU / T_GPU, for the FP32-mixed and FP64
+        # GPU paths against the oracle on all host cores and on one
+        ref = {"all_cores": cpu["value"], "one_core": cpu.get("one_core", {}).get("value")}
+        cpu["gpu_speedup"] = {f"{path}_vs_{k}": (val / r if r else None)
+                              for path, val in (("mixed", value), ("fp64", 1e3 / ms64)) for k, r in ref.items()}
+        line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

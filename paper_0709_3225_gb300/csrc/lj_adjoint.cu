@@ -326,37 +326,7 @@ __device__ __forceinline__ void vjp_cell(const VjpWarpCoef &k, int n, int cap, c
     float4 *stab = reinterpret_cast<float4 *>(HZ + cap);
     int *spre = reinterpret_cast<int *>(stab + NS);
     __syncwarp();   // the slice still holds the previous cell's data
-    int carry = 0;
-#pragma unroll 1
-    for (int b0 = 0; b0 < NS; b0 += 32) {
-        const int kk = b0 + lane;
-        int nn = 0;
-        if (kk < NS) {
-            int dx, dy, dz;
-            stencil_delta<R>(kk, dx, dy, dz);
-            int ux = cx + dx, uy = cy + dy, uz = cz + dz;
-            ux += ux < 0 ? nc : 0;
-            ux -= ux >= nc ? nc : 0;
-            uy += uy < 0 ? nc : 0;
-            uy -= uy >= nc ? nc : 0;
-            uz += uz < 0 ? nc : 0;
-            uz -= uz >= nc ? nc : 0;
-            const int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
-            const int s = start[cn];
-            nn = start[cn + 1] - s;
-            stab[kk] = make_float4((float)dx * k.cw, (float)dy * k.cw, (float)dz * k.cw, __int_as_float(s));
-        }
-        int P = nn;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, P, o);
-            if (lane >= o) P += y;
-        }
-        if (kk < NS) spre[kk] = carry + P - nn;
-        carry += __shfl_sync(0xffffffffu, P, 31);
-    }
-    if (lane == 0) spre[NS] = carry;
-    __syncwarp();
+    const int carry = stencil_table<R>(start, 0, cx, cy, cz, nc, k.cw, stab, spre);
     const int n_home = spre[1];
     if (n_home == 0) return;
     const int s_home = __float_as_int(stab[0].w);
@@ -678,6 +648,15 @@ cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, dou
     k.eps = c->p.eps;
     k.inv_sigma = 1.0 / sg;
     if (!fp64) return launch_vjp_warp(c, k, scale, dx, dparam);
+    if (c->p.cell_subdiv != 2 && c->wcap > 0 && c->w64_lcap > 0) {
+        // FP64: the warp kernel with compacted in-range pair lists
+        int grid = 0;
+        cudaError_t e = launch_vjp_w64(c, scale, dx, k.a1, k.b1, k.fc1, k.dfc1, &grid);
+        if (e != cudaSuccess) return e;
+        k_accum_params<<<1, kReduceThreads, 0, c->stream>>>(c->partial, grid, scale, dparam);
+        c->kernel_launches++;
+        return cudaGetLastError();
+    }
     const int grid = vjp_grid(c);
     if (grid > c->npartial_cap) return cudaErrorInvalidValue;
     void *kern = vjp_kernel<double>(c->p.shift_mode, c->p.cell_subdiv);

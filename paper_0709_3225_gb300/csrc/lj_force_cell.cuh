@@ -442,26 +442,21 @@ __device__ void cell_plain(const WarpParams &k, const float4 *__restrict__ pos, 
     }
 }
 
-// One home cell at cell coordinates (cx, cy, cz) of a grid of nc^3 cells
-// whose linear ids start at cell_base in start[] (0 for a single system),
-// cell side cw.  Builds the stencil table in the warp's slice and runs the
-// staged path, or the plain path when the stencil does not fit the slice.
-template <int R, int MODE, bool ENERGY, bool NC, int GFIX, class Out>
-__device__ __forceinline__ void process_home_cell(const WarpParams &k, const float4 *__restrict__ pos,
-                                                  const int32_t *__restrict__ start, const Out &out_in,
-                                                  float *slice, int cx, int cy, int cz, int nc, int64_t cell_base,
-                                                  float cw, double &eacc, double &wacc)
+// Stencil table of home cell (cx, cy, cz) in a grid of nc^3 cells whose
+// linear ids start at cell_base in start[] (0 for a single system), cell
+// side cw: per stencil entry kk the shift to the home frame and the first
+// particle, stab[kk] = (dx cw, dy cw, dz cw, start), and the exclusive
+// prefix sums of the entries' counts, spre[0 .. NS].  With s64 it also
+// writes the shifts in FP64, s64[kk], s64[NS + kk], s64[2 NS + kk] (cell
+// side cw64).  Returns the stencil population spre[NS].  Called by all 32
+// lanes; the table is visible to the warp on return.
+template <int R>
+__device__ __forceinline__ int stencil_table(const int32_t *__restrict__ start, int64_t cell_base, int cx, int cy,
+                                             int cz, int nc, float cw, float4 *stab, int *spre,
+                                             double *s64 = nullptr, double cw64 = 0.0)
 {
     constexpr int NS = Stencil<R>::NS;
-    Out out = out_in;
-    out.set_home(cx, cy, cz);
     const int lane = threadIdx.x & 31;
-    float *X = slice;
-    float *Y = X + k.cap;
-    float *Z = Y + k.cap;
-    float4 *stab = reinterpret_cast<float4 *>(Z + k.cap);
-    int *spre = reinterpret_cast<int *>(stab + NS);
-    __syncwarp();   // the slice still holds the previous cell's data
     int carry = 0;
 #pragma unroll 1
     for (int b0 = 0; b0 < NS; b0 += 32) {
@@ -481,6 +476,11 @@ __device__ __forceinline__ void process_home_cell(const WarpParams &k, const flo
             const int s = start[cn];
             nn = start[cn + 1] - s;
             stab[kk] = make_float4((float)dx * cw, (float)dy * cw, (float)dz * cw, __int_as_float(s));
+            if (s64) {
+                s64[kk] = (double)dx * cw64;
+                s64[NS + kk] = (double)dy * cw64;
+                s64[2 * NS + kk] = (double)dz * cw64;
+            }
         }
         int P = nn;
 #pragma unroll
@@ -493,6 +493,29 @@ __device__ __forceinline__ void process_home_cell(const WarpParams &k, const flo
     }
     if (lane == 0) spre[NS] = carry;
     __syncwarp();
+    return carry;
+}
+
+// One home cell at cell coordinates (cx, cy, cz) of a grid of nc^3 cells
+// whose linear ids start at cell_base in start[] (0 for a single system),
+// cell side cw.  Builds the stencil table in the warp's slice and runs the
+// staged path, or the plain path when the stencil does not fit the slice.
+template <int R, int MODE, bool ENERGY, bool NC, int GFIX, class Out>
+__device__ __forceinline__ void process_home_cell(const WarpParams &k, const float4 *__restrict__ pos,
+                                                  const int32_t *__restrict__ start, const Out &out_in,
+                                                  float *slice, int cx, int cy, int cz, int nc, int64_t cell_base,
+                                                  float cw, double &eacc, double &wacc)
+{
+    constexpr int NS = Stencil<R>::NS;
+    Out out = out_in;
+    out.set_home(cx, cy, cz);
+    float *X = slice;
+    float *Y = X + k.cap;
+    float *Z = Y + k.cap;
+    float4 *stab = reinterpret_cast<float4 *>(Z + k.cap);
+    int *spre = reinterpret_cast<int *>(stab + NS);
+    __syncwarp();   // the slice still holds the previous cell's data
+    const int carry = stencil_table<R>(start, cell_base, cx, cy, cz, nc, cw, stab, spre);
     const int n_home = spre[1];
     if (n_home == 0) return;
     const int s_home = __float_as_int(stab[0].w);

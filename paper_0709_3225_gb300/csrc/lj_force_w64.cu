@@ -47,10 +47,17 @@ struct W64Params {
     float rc2_box, rc2_pair;                      // FP32 filter cutoffs squared (with margins)
     double cw;                                    // cell side (FP64 shifts)
     double rc2, rc, a12, b6, c12, c6, uc, fc;     // pair coefficients, as in Coef<double>
+    // VJP (OP 2) only: sorted cotangents, dx += scale dL/dx, and the
+    // coefficients of the derivative terms (eps = 1 forms, see vjp64)
+    const double4_16a *g4;
+    double *dxo;
+    double scale;
+    double va1, vb1, vfc1, vdfc1, veps, visg;
 };
 
 // Byte layout of one warp's shared-memory slice:
 //   X64, Y64, Z64   double[cap]   staged candidates, home frame, FP64
+//   HX64 .. HZ64    double[cap]   their cotangents (VJP only)
 //   part            double[2][kW64Comp][32]   per-lane partial sums (first, head)
 //   stab            float4[NS]    stencil table: FP32 shift xyz, start index
 //   S64             double[3][NS] stencil shifts in FP64 (padded to 16 B)
@@ -59,12 +66,13 @@ struct W64Params {
 //   off             int[kW64PMax + 4]   list offsets of the batch's particles
 //   list            uint16[lcap]  in-range candidate indices
 struct W64Layout {
-    int x64, part, stab, s64, x32, spre, off, list, bytes;
-    __host__ __device__ W64Layout(int cap, int R, int lcap)
+    int x64, h64, part, stab, s64, x32, spre, off, list, bytes;
+    __host__ __device__ W64Layout(int cap, int R, int lcap, bool vjp = false)
     {
         const int ns = (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
         x64 = 0;
-        part = x64 + 24 * cap;
+        h64 = x64 + 24 * cap;
+        part = h64 + (vjp ? 24 * cap : 0);
         stab = part + 2 * kW64Comp * 32 * 8;
         s64 = stab + 16 * ns;
         x32 = s64 + ((24 * ns + 15) & ~15);
@@ -156,20 +164,86 @@ __device__ __forceinline__ void pair64(double dx, double dy, double dz, const Co
     }
 }
 
+// The FP64 VJP term of one pair (the adjoint of the force, rc fixed): with
+// d = x_i - x_j, phi = F(r)/r, g = g_i - g_j,
+//   a  += phi g + (phi'(r)/r) (d . g) d      (J_ij (g_i - g_j)),
+//   ae += phi|eps=1 (d . g_i)                (dF_i/deps . g_i),
+//   as += eps (dphi/dsigma) (d . g_i)        (dF_i/dsigma . g_i);
+// with q = r^2, phi = eps (A q^-7 - B q^-4) (A = 48 sigma^12, B = 24
+// sigma^6), phi'(r)/r = eps q^-5 (8 B - 14 A q^-3), dphi/dsigma = eps (12 A
+// q^-7 - 6 B q^-4) / sigma; the force shift adds -Fc/r to phi, +Fc/r^3 to
+// phi'(r)/r and -(dFc/dsigma)/r to dphi/dsigma.  Same cutoff test and
+// reciprocal as pair64.
+template <int MODE>
+__device__ __forceinline__ void vjp64(double dx, double dy, double dz, double gix, double giy, double giz,
+                                      double gjx, double gjy, double gjz, const W64Params &k, double &ax,
+                                      double &ay, double &az, double &ae, double &as)
+{
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    const long long b = __double_as_longlong(r2);
+    const bool in = b < __double_as_longlong(k.rc2) && b != 0;
+    double ri, rinv = 0.0;
+    if constexpr (MODE == 2) {
+        double y = rsqrt64_approx(r2);
+        const double h = fma(-r2 * y, y, 1.0);
+        y = fma(y, h * fma(h, 0.375, 0.5), y);
+        rinv = in ? y : 0.0;
+        ri = rinv * rinv;
+    } else {
+        double y = rcp64_approx(r2);
+        const double h = fma(-r2, y, 1.0);
+        y = fma(y, fma(h, h, h), y);
+        ri = in ? y : 0.0;
+    }
+    const double r6 = ri * ri * ri;
+    const double r8 = ri * r6;
+    double phi1 = r8 * (k.va1 * r6 - k.vb1);
+    double dphi1 = r8 * ri * (8.0 * k.vb1 - 14.0 * k.va1 * r6);
+    double dsig1 = r8 * (12.0 * k.va1 * r6 - 6.0 * k.vb1) * k.visg;
+    if constexpr (MODE == 2) {
+        phi1 -= k.vfc1 * rinv;
+        dphi1 += k.vfc1 * rinv * ri;
+        dsig1 -= k.vdfc1 * rinv;
+    }
+    const double phi = k.veps * phi1, dphi = k.veps * dphi1;
+    const double gx = gix - gjx, gy = giy - gjy, gz = giz - gjz;
+    const double dot = fma(dz, gz, fma(dy, gy, dx * gx));
+    const double gid = fma(dz, giz, fma(dy, giy, dx * gix));
+    const double t = dphi * dot;
+    ax = fma(t, dx, fma(phi, gx, ax));
+    ay = fma(t, dy, fma(phi, gy, ay));
+    az = fma(t, dz, fma(phi, gz, az));
+    ae = fma(phi1, gid, ae);
+    as = fma(k.veps * dsig1, gid, as);
+}
+
 struct Acc64 {
     double fx, fy, fz, e, w;
     __device__ __forceinline__ void zero() { fx = fy = fz = e = w = 0.0; }
 };
 
-// Final sums of home particle `slot` (sorted index): force, and its energy
-// share and virial when ENERGY.
-template <bool ENERGY>
+// OP: 0 = forces, 1 = forces with energies and virials, 2 = VJP (the five
+// sums are then dL/dx and the two parameter terms).
+
+// Final sums of home particle `slot` (sorted index): the force, and its
+// energy share and virial for OP 1; for OP 2 dx += scale a and the
+// parameter terms into (eacc, wacc).
+template <int OP>
 __device__ __forceinline__ void w64_store(const W64Params &k, const double4_16a *__restrict__ pos,
                                           double4_16a *__restrict__ fout, int slot, const Acc64 &a, double &eacc,
                                           double &wacc)
 {
+    constexpr bool ENERGY = OP == 1;
     const int idx = (int)__ldg(&pos[slot].w);
     if ((unsigned)idx >= (unsigned)k.n) return;
+    if constexpr (OP == 2) {
+        k.dxo[3 * (int64_t)idx] += k.scale * a.fx;
+        k.dxo[3 * (int64_t)idx + 1] += k.scale * a.fy;
+        k.dxo[3 * (int64_t)idx + 2] += k.scale * a.fz;
+        eacc += a.e;
+        wacc += a.w;
+        return;
+    }
     double4_16a o;
     o.x = a.fx;
     o.y = a.fy;
@@ -184,7 +258,7 @@ __device__ __forceinline__ void w64_store(const W64Params &k, const double4_16a 
 
 // Plain path: lanes own home particles, FP64 over every candidate read from
 // global memory per stencil cell (cells whose stencil overflows the slice).
-template <int R, int MODE, bool ENERGY>
+template <int R, int MODE, int OP>
 __device__ void w64_plain(const W64Params &k, const Coef<double> &kc, const double4_16a *__restrict__ pos,
                           double4_16a *__restrict__ fout, const float4 *stab, const double *S64, const int *spre,
                           int s_home, int n_home, double &eacc, double &wacc)
@@ -195,6 +269,8 @@ __device__ void w64_plain(const W64Params &k, const Coef<double> &kc, const doub
         const int i = p0 + lane;
         const bool vi = i < n_home;
         const double3 pi = load_xyz(pos, s_home + (vi ? i : 0));
+        double3 gi = make_double3(0.0, 0.0, 0.0);
+        if constexpr (OP == 2) gi = load_xyz(k.g4, s_home + (vi ? i : 0));
         Acc64 a;
         a.zero();
         for (int kk = 0; kk < NS; kk++) {
@@ -203,20 +279,28 @@ __device__ void w64_plain(const W64Params &k, const Coef<double> &kc, const doub
             const double xs = pi.x - S64[kk], ys = pi.y - S64[NS + kk], zs = pi.z - S64[2 * NS + kk];
             for (int j = 0; j < nn; j++) {
                 const double3 q = load_xyz(pos, s + j);
-                pair_accum<double, MODE, ENERGY>(xs - q.x, ys - q.y, zs - q.z, kc, a.fx, a.fy, a.fz, a.e, a.w);
+                if constexpr (OP == 2) {
+                    const double3 h = load_xyz(k.g4, s + j);
+                    vjp64<MODE>(xs - q.x, ys - q.y, zs - q.z, gi.x, gi.y, gi.z, h.x, h.y, h.z, k, a.fx, a.fy, a.fz,
+                                a.e, a.w);
+                } else {
+                    pair_accum<double, MODE, OP == 1>(xs - q.x, ys - q.y, zs - q.z, kc, a.fx, a.fy, a.fz, a.e, a.w);
+                }
             }
         }
-        if (vi) w64_store<ENERGY>(k, pos, fout, s_home + i, a, eacc, wacc);
+        if (vi) w64_store<OP>(k, pos, fout, s_home + i, a, eacc, wacc);
     }
 }
 
 // Staging of one home cell's stencil: returns the number of kept candidates
 // T, or -1 (nothing written that matters) when they would not fit the slice
-// with the 64 padding entries Phase A reads.
+// with the 64 padding entries Phase A reads.  With HX64 (VJP) the kept
+// candidates' cotangents are staged too.
 template <int R>
 __device__ __forceinline__ int w64_stage(const W64Params &k, const double4_16a *__restrict__ pos, float *X, float *Y,
-                                         float *Z, double *X64, double *Y64, double *Z64, const float4 *stab,
-                                         const double *S64, const int *spre, int Ttot, int s_home, int n_home)
+                                         float *Z, double *X64, double *Y64, double *Z64, double *HX64,
+                                         double *HY64, double *HZ64, const float4 *stab, const double *S64,
+                                         const int *spre, int Ttot, int s_home, int n_home)
 {
     constexpr int NS = Stencil<R>::NS, P2 = Stencil<R>::P2;
     const int lane = threadIdx.x & 31;
@@ -247,13 +331,14 @@ __device__ __forceinline__ int w64_stage(const W64Params &k, const double4_16a *
     for (int t0 = 0; t0 < Ttot; t0 += 32 * kStageBatch) {
         double3 q[kStageBatch];
         float4 sh[kStageBatch];
-        int kcs[kStageBatch];
+        int kcs[kStageBatch], src[kStageBatch];
 #pragma unroll
         for (int u = 0; u < kStageBatch; u++) {
             const int t = t0 + 32 * u + lane;
             q[u] = make_double3(0.0, 0.0, 0.0);
             sh[u] = make_float4(kFar, kFar, kFar, 0.f);
             kcs[u] = 0;
+            src[u] = 0;
             if (t < Ttot) {
                 int kc = 0, kb = 0;
 #pragma unroll
@@ -269,7 +354,8 @@ __device__ __forceinline__ int w64_stage(const W64Params &k, const double4_16a *
                 }
                 sh[u] = stab[kc];
                 kcs[u] = kc;
-                q[u] = load_xyz(pos, __float_as_int(sh[u].w) + (t - kb));
+                src[u] = __float_as_int(sh[u].w) + (t - kb);
+                q[u] = load_xyz(pos, src[u]);
             }
         }
 #pragma unroll
@@ -296,6 +382,12 @@ __device__ __forceinline__ int w64_stage(const W64Params &k, const double4_16a *
                 X64[sl] = q[u].x + S64[kc];
                 Y64[sl] = q[u].y + S64[NS + kc];
                 Z64[sl] = q[u].z + S64[2 * NS + kc];
+                if (HX64) {
+                    const double3 h = load_xyz(k.g4, src[u]);
+                    HX64[sl] = h.x;
+                    HY64[sl] = h.y;
+                    HZ64[sl] = h.z;
+                }
             }
             T += __popc(kept);
         }
@@ -312,13 +404,15 @@ __device__ __forceinline__ int w64_stage(const W64Params &k, const double4_16a *
 
 // Phase B over one batch: entries [0, E) of the list, particles pb .. pb + P
 // - 1 of the home cell with list offsets off[0 .. P].
-template <int MODE, bool ENERGY>
+template <int MODE, int OP>
 __device__ __forceinline__ void w64_pairs(const W64Params &k, const Coef<double> &kc,
                                           const double4_16a *__restrict__ pos, double4_16a *__restrict__ fout,
                                           const double *X64, const double *Y64, const double *Z64,
+                                          const double *HX64, const double *HY64, const double *HZ64,
                                           const uint16_t *list, const int *off, double *part, int E, int P,
                                           int pb, int s_home, double &eacc, double &wacc)
 {
+    constexpr bool ENERGY = OP >= 1;   // five sums, not three
     const int lane = threadIdx.x & 31;
     double *first = part;                 // [kW64Comp][32]
     double *head = part + kW64Comp * 32;  // [kW64Comp][32]
@@ -333,13 +427,19 @@ __device__ __forceinline__ void w64_pairs(const W64Params &k, const Coef<double>
             if (q + step < P && off[q + step] <= lo) q += step;
         int nxt = off[q + 1];
         double xp = X64[pb + q], yp = Y64[pb + q], zp = Z64[pb + q];
+        double gpx = 0.0, gpy = 0.0, gpz = 0.0;
+        if constexpr (OP == 2) {
+            gpx = HX64[pb + q];
+            gpy = HY64[pb + q];
+            gpz = HZ64[pb + q];
+        }
         Acc64 a;
         a.zero();
         auto flush = [&]() {
             const bool starts = off[q] >= lo;
             const bool ends = nxt <= hi;
             if (starts && ends) {
-                w64_store<ENERGY>(k, pos, fout, s_home + pb + q, a, eacc, wacc);
+                w64_store<OP>(k, pos, fout, s_home + pb + q, a, eacc, wacc);
             } else {
                 double *dst = starts ? head : first;
                 dst[0 * 32 + lane] = a.fx;
@@ -362,10 +462,20 @@ __device__ __forceinline__ void w64_pairs(const W64Params &k, const Coef<double>
                 xp = X64[pb + q];
                 yp = Y64[pb + q];
                 zp = Z64[pb + q];
+                if constexpr (OP == 2) {
+                    gpx = HX64[pb + q];
+                    gpy = HY64[pb + q];
+                    gpz = HZ64[pb + q];
+                }
                 a.zero();
             }
             const int j = list[e];
-            pair64<MODE, ENERGY>(xp - X64[j], yp - Y64[j], zp - Z64[j], kc, a.fx, a.fy, a.fz, a.e, a.w);
+            if constexpr (OP == 2) {
+                vjp64<MODE>(xp - X64[j], yp - Y64[j], zp - Z64[j], gpx, gpy, gpz, HX64[j], HY64[j], HZ64[j], k, a.fx,
+                            a.fy, a.fz, a.e, a.w);
+            } else {
+                pair64<MODE, ENERGY>(xp - X64[j], yp - Y64[j], zp - Z64[j], kc, a.fx, a.fy, a.fz, a.e, a.w);
+            }
         }
         flush();
     }
@@ -392,21 +502,23 @@ __device__ __forceinline__ void w64_pairs(const W64Params &k, const Coef<double>
             }
             if (end <= hi2) break;
         }
-        w64_store<ENERGY>(k, pos, fout, s_home + pb + headq, a, eacc, wacc);
+        w64_store<OP>(k, pos, fout, s_home + pb + headq, a, eacc, wacc);
     }
     __syncwarp();   // part, list and off are rewritten by the next batch
 }
 
-template <int R, int MODE, bool ENERGY>
+template <int R, int MODE, int OP>
 __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const double4_16a *__restrict__ pos,
                          const int32_t *__restrict__ start, double4_16a *__restrict__ fout, unsigned char *slice,
                          int cx, int cy, int cz, double &eacc, double &wacc)
 {
-    constexpr int NS = Stencil<R>::NS;
-    const W64Layout L(k.cap, R, k.lcap);
+    const W64Layout L(k.cap, R, k.lcap, OP == 2);
     double *X64 = reinterpret_cast<double *>(slice + L.x64);
     double *Y64 = X64 + k.cap;
     double *Z64 = Y64 + k.cap;
+    double *HX64 = OP == 2 ? reinterpret_cast<double *>(slice + L.h64) : nullptr;
+    double *HY64 = OP == 2 ? HX64 + k.cap : nullptr;
+    double *HZ64 = OP == 2 ? HY64 + k.cap : nullptr;
     double *part = reinterpret_cast<double *>(slice + L.part);
     float4 *stab = reinterpret_cast<float4 *>(slice + L.stab);
     double *S64 = reinterpret_cast<double *>(slice + L.s64);
@@ -420,48 +532,16 @@ __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const doubl
     const int nc = k.nc;
 
     __syncwarp();   // the slice still holds the previous cell's data
-    int carry = 0;
-#pragma unroll 1
-    for (int b0 = 0; b0 < NS; b0 += 32) {
-        const int kk = b0 + lane;
-        int nn = 0;
-        if (kk < NS) {
-            int dx, dy, dz;
-            stencil_delta<R>(kk, dx, dy, dz);
-            int ux = cx + dx, uy = cy + dy, uz = cz + dz;
-            ux += ux < 0 ? nc : 0;
-            ux -= ux >= nc ? nc : 0;
-            uy += uy < 0 ? nc : 0;
-            uy -= uy >= nc ? nc : 0;
-            uz += uz < 0 ? nc : 0;
-            uz -= uz >= nc ? nc : 0;
-            const int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
-            const int s = start[cn];
-            nn = start[cn + 1] - s;
-            stab[kk] = make_float4((float)dx * k.cwf, (float)dy * k.cwf, (float)dz * k.cwf, __int_as_float(s));
-            S64[kk] = (double)dx * k.cw;
-            S64[NS + kk] = (double)dy * k.cw;
-            S64[2 * NS + kk] = (double)dz * k.cw;
-        }
-        int P = nn;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, P, o);
-            if (lane >= o) P += y;
-        }
-        if (kk < NS) spre[kk] = carry + P - nn;
-        carry += __shfl_sync(0xffffffffu, P, 31);
-    }
-    if (lane == 0) spre[NS] = carry;
-    __syncwarp();
+    const int carry = stencil_table<R>(start, 0, cx, cy, cz, nc, k.cwf, stab, spre, S64, k.cw);
     const int n_home = spre[1];
     if (n_home == 0) return;
     const int s_home = __float_as_int(stab[0].w);
     const int T = carry <= 2 * k.cap
-                      ? w64_stage<R>(k, pos, X, Y, Z, X64, Y64, Z64, stab, S64, spre, carry, s_home, n_home)
+                      ? w64_stage<R>(k, pos, X, Y, Z, X64, Y64, Z64, HX64, HY64, HZ64, stab, S64, spre, carry,
+                                     s_home, n_home)
                       : -1;
     if (T < 0) {
-        w64_plain<R, MODE, ENERGY>(k, kc, pos, fout, stab, S64, spre, s_home, n_home, eacc, wacc);
+        w64_plain<R, MODE, OP>(k, kc, pos, fout, stab, S64, spre, s_home, n_home, eacc, wacc);
         return;
     }
     const float2 *X2 = reinterpret_cast<const float2 *>(X);
@@ -497,22 +577,22 @@ __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const doubl
                 E += __popc(ba) + __popc(bb);
             }
             if (lane == 0) off[p - pb + 1] = E;
-            if (E == E0 && lane == 0) {
-                // no candidate within rc: the force is zero
+            if (OP != 2 && E == E0 && lane == 0) {
+                // no candidate within rc: the force is zero (a VJP adds nothing)
                 Acc64 a;
                 a.zero();
-                w64_store<ENERGY>(k, pos, fout, s_home + p, a, eacc, wacc);
+                w64_store<OP>(k, pos, fout, s_home + p, a, eacc, wacc);
             }
             p++;
         }
         __syncwarp();
         // Phase B
-        w64_pairs<MODE, ENERGY>(k, kc, pos, fout, X64, Y64, Z64, list, off, part, E, p - pb, pb, s_home, eacc,
-                                wacc);
+        w64_pairs<MODE, OP>(k, kc, pos, fout, X64, Y64, Z64, HX64, HY64, HZ64, list, off, part, E, p - pb, pb,
+                            s_home, eacc, wacc);
     }
 }
 
-template <int R, int MODE, bool ENERGY>
+template <int R, int MODE, int OP>
 __global__ void __launch_bounds__(kW64Threads) k_force_w64(W64Params k, const double4_16a *__restrict__ pos,
                                                            const int32_t *__restrict__ start,
                                                            double4_16a *__restrict__ fout,
@@ -521,14 +601,14 @@ __global__ void __launch_bounds__(kW64Threads) k_force_w64(W64Params k, const do
     extern __shared__ __align__(16) unsigned char w64smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const W64Layout L(k.cap, R, k.lcap);
+    const W64Layout L(k.cap, R, k.lcap, OP == 2);
     unsigned char *slice = w64smem + (size_t)warp * L.bytes;
     const Coef<double> kc(k);
     const int nc = k.nc;
     double eacc = 0.0, wacc = 0.0;
     auto one_cell = [&](int64_t c) {
         const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
-        w64_cell<R, MODE, ENERGY>(k, kc, pos, start, fout, slice, cx, cy, cz, eacc, wacc);
+        w64_cell<R, MODE, OP>(k, kc, pos, start, fout, slice, cx, cy, cz, eacc, wacc);
     };
     if (k.grab > 0) {
         for (;;) {
@@ -543,7 +623,7 @@ __global__ void __launch_bounds__(kW64Threads) k_force_w64(W64Params k, const do
         const int64_t nwarps = (int64_t)gridDim.x * (kW64Threads / 32);
         for (int64_t c = (int64_t)blockIdx.x * (kW64Threads / 32) + warp; c < k.ncell; c += nwarps) one_cell(c);
     }
-    if constexpr (ENERGY) {
+    if constexpr (OP >= 1) {   // energy and virial, or the two parameter sums
         __shared__ double red[2 * (kW64Threads / 32)];
         for (int o = 16; o > 0; o >>= 1) {
             eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
@@ -566,21 +646,19 @@ __global__ void __launch_bounds__(kW64Threads) k_force_w64(W64Params k, const do
     }
 }
 
-template <int R>
-void *w64_kernel_r(int mode, bool energy)
+// FP64 contexts use the 27-cell stencil (subdivision 1) only.  op: see OP.
+void *w64_kernel(int mode, int op)
 {
-    switch (mode * 2 + (energy ? 1 : 0)) {
-        case 0: return (void *)k_force_w64<R, 0, false>;
-        case 1: return (void *)k_force_w64<R, 0, true>;
-        case 2: return (void *)k_force_w64<R, 1, false>;
-        case 3: return (void *)k_force_w64<R, 1, true>;
-        case 4: return (void *)k_force_w64<R, 2, false>;
-        default: return (void *)k_force_w64<R, 2, true>;
+    if (op == 2) return mode == 2 ? (void *)k_force_w64<1, 2, 2> : (void *)k_force_w64<1, 0, 2>;   // modes 0, 1: same force
+    switch (mode * 2 + (op == 1 ? 1 : 0)) {
+        case 0: return (void *)k_force_w64<1, 0, 0>;
+        case 1: return (void *)k_force_w64<1, 0, 1>;
+        case 2: return (void *)k_force_w64<1, 1, 0>;
+        case 3: return (void *)k_force_w64<1, 1, 1>;
+        case 4: return (void *)k_force_w64<1, 2, 0>;
+        default: return (void *)k_force_w64<1, 2, 1>;
     }
 }
-
-// FP64 contexts use the 27-cell stencil (subdivision 1) only.
-void *w64_kernel(int mode, bool energy) { return w64_kernel_r<1>(mode, energy); }
 
 W64Params w64_params_of(const lj_ctx *c)
 {
@@ -647,7 +725,7 @@ cudaError_t w64_force_configure(lj_ctx *c)
     int minblk = 1 << 30;
     for (int mode = 0; mode < 3; mode++)
         for (int en = 0; en < 2; en++) {
-            void *kern = w64_kernel(mode, en != 0);
+            void *kern = w64_kernel(mode, en);
             cudaError_t e = raise_dyn_smem(kern, c->wforce_smem);
             if (e != cudaSuccess) return e;
             int nb = 0;
@@ -671,7 +749,7 @@ cudaError_t launch_force_w64(lj_ctx *c, void *f, bool energy)
     const int32_t *start = c->start;
     double *partial = c->partial;
     void *args[] = {&k, (void *)&pos, (void *)&start, &f, &partial};
-    void *kern = w64_kernel(c->p.shift_mode, energy);
+    void *kern = w64_kernel(c->p.shift_mode, energy ? 1 : 0);
     if (c->timing && c->ev_used + 2 <= c->nev) cudaEventRecord(c->ev[c->ev_used], c->stream);
     cudaError_t e = cudaLaunchKernel(kern, dim3(c->wforce_grid), dim3(kW64Threads), args, c->wforce_smem, c->stream);
     if (c->timing && c->ev_used + 2 <= c->nev) {
@@ -680,5 +758,43 @@ cudaError_t launch_force_w64(lj_ctx *c, void *f, bool energy)
     }
     c->kernel_launches++;
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vjp_w64(lj_ctx *c, double scale, double *dx, double a1, double b1, double fc1, double dfc1,
+                           int *grid_out)
+{
+    W64Params k = w64_params_of(c);
+    k.g4 = (const double4_16a *)c->g4;
+    k.dxo = dx;
+    k.scale = scale;
+    k.va1 = a1;
+    k.vb1 = b1;
+    k.vfc1 = fc1;
+    k.vdfc1 = dfc1;
+    k.veps = c->p.eps;
+    k.visg = 1.0 / c->p.sigma;
+    k.grab = 0;   // static striding: the work counter belongs to the force kernel
+    const int smem = (kW64Threads / 32) * W64Layout(c->wcap, 1, c->w64_lcap, true).bytes;
+    void *kern = w64_kernel(c->p.shift_mode, 2);
+    cudaError_t e = raise_dyn_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kW64Threads, smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (int64_t)(nb > 0 ? nb : 1) * c->nsm;
+    const int64_t need = (c->ncell + kW64Threads / 32 - 1) / (kW64Threads / 32);
+    if (grid > need) grid = need;
+    if (grid > c->npartial_cap) grid = c->npartial_cap;
+    if (grid < 1) grid = 1;
+    const double4_16a *pos = (const double4_16a *)c->pos;
+    const int32_t *start = c->start;
+    double4_16a *fout = nullptr;
+    double *partial = c->partial;
+    void *args[] = {&k, (void *)&pos, (void *)&start, &fout, &partial};
+    e = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(kW64Threads), args, smem, c->stream);
+    c->kernel_launches++;
+    if (e != cudaSuccess) return e;
+    *grid_out = (int)grid;
     return cudaGetLastError();
 }

@@ -265,6 +265,11 @@ cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy);
 // warp kernel's slice capacity, shared memory and grid fields.
 cudaError_t w64_force_configure(lj_ctx *c);
 cudaError_t launch_force_w64(lj_ctx *c, void *f, bool energy);
+// Its VJP form (FP64 contexts): dx += scale J g over the sorted cotangents
+// c->g4; per-CTA parameter sums into c->partial, *grid_out of them.
+// a1, b1, fc1, dfc1: the eps = 1 coefficients of the VJP (lj_adjoint.cu).
+cudaError_t launch_vjp_w64(lj_ctx *c, double scale, double *dx, double a1, double b1, double fc1, double dfc1,
+                           int *grid_out);
 // Pipelined warp kernel (lj_force_pipe.cu): configuration and launch.
 cudaError_t pipe_force_configure(lj_ctx *c);
 cudaError_t launch_force_pipe(lj_ctx *c, void *f, bool energy);

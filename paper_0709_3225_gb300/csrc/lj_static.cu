@@ -110,8 +110,7 @@ extern "C" int lj_forces_static(const lj_params *p, const double *x, void *f, vo
     c.wrap_lo = p->box * ldexp(1.0, -50);
     c.stream = (cudaStream_t)stream;
     c.use_tma = (p->flags & LJ_FLAG_RUN_DIRECT) ? 0 : 1;
-    c.use_run_kernel =
-        (p->precision == LJ_PREC_FP64 || (p->flags & (LJ_FLAG_RUN_STAGED | LJ_FLAG_RUN_DIRECT))) ? 1 : 0;
+    c.use_run_kernel = (p->flags & (LJ_FLAG_RUN_STAGED | LJ_FLAG_RUN_DIRECT)) ? 1 : 0;   // as lj_create
     cudaError_t e = cudaGetDevice(&c.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, c.device);
     if (e != cudaSuccess) return map_err(e);
@@ -129,7 +128,8 @@ extern "C" int lj_forces_static(const lj_params *p, const double *x, void *f, vo
     c.err = (int32_t *)(base + kOffErr);
 
     if ((e = force_configure(&c)) != cudaSuccess) return map_err(e);
-    if (p->precision == LJ_PREC_MIXED && (e = warp_force_configure(&c)) != cudaSuccess) return map_err(e);
+    e = p->precision == LJ_PREC_MIXED ? warp_force_configure(&c) : w64_force_configure(&c);
+    if (e != cudaSuccess) return map_err(e);
     if (c.force_grid > kMaxPartials || c.wforce_grid > kMaxPartials) return LJ_EOVERFLOW;
     if (p->n == 0) return LJ_OK;
 
