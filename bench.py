@@ -411,26 +411,31 @@ def run_adjoint(x4m, L4m, stream):
     torch.cuda.synchronize()
     t_grad = (time.perf_counter() - t0) / reps
     s.close()
-    # one VJP of the 4M system
-    s4 = lj.System(x4m, None, L4m)
-    g4 = torch.randn((s4.n, 3), dtype=torch.float64, device="cuda")
-    dx = torch.zeros_like(s4.x)
-    dp = torch.zeros(2, dtype=torch.float64, device="cuda")
-    lj.lj_forces_vjp(s4.ctx, s4.x, g4, 1.0, dx, dp)
-    torch.cuda.synchronize()
+    # one VJP of the 4M system (binning, cotangent gather and the VJP kernel),
+    # FP32-mixed and FP64
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(3):
+    vjp_ms = {}
+    for precision in ("mixed", "fp64"):
+        s4 = lj.System(x4m, None, L4m, precision=precision)
+        g4 = torch.randn((s4.n, 3), dtype=torch.float64, device="cuda")
+        dx = torch.zeros_like(s4.x)
+        dp = torch.zeros(2, dtype=torch.float64, device="cuda")
         lj.lj_forces_vjp(s4.ctx, s4.x, g4, 1.0, dx, dp)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    s4.check()
-    vjp_ms = ev0.elapsed_time(ev1) / 3
-    s4.close()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(3):
+            lj.lj_forces_vjp(s4.ctx, s4.x, g4, 1.0, dx, dp)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        s4.check()
+        vjp_ms[precision] = ev0.elapsed_time(ev1) / 3
+        s4.close()
+    pairs4m = unique_pairs(4_000_000, 0.8442, 2.5)
     return {"workload": "fm-32k force matching, 50 steps, checkpoints every 10", "n": n,
             "gradient_s": t_grad, "gradients_per_s": 1.0 / t_grad,
             "dL_dtheta": [float(g[0]), float(g[1])],
-            "vjp_4m_ms": vjp_ms, "vjp_4m_pairs_per_s": unique_pairs(4_000_000, 0.8442, 2.5) / (vjp_ms / 1e3)}
+            "vjp_4m_ms": vjp_ms["mixed"], "vjp_4m_pairs_per_s": pairs4m / (vjp_ms["mixed"] / 1e3),
+            "vjp_4m_fp64_ms": vjp_ms["fp64"], "vjp_4m_fp64_pairs_per_s": pairs4m / (vjp_ms["fp64"] / 1e3)}
 
 
 def cpu_baseline(x, v, L, w, max_seconds: float = 20.0, max_steps: int = 3, one_core: bool = True):
