@@ -346,6 +346,60 @@ def run_graph_small(stream, steps=200):
     return out
 
 
+def run_accuracy_131k(with_oracle: bool, max_oracle_s: float = 60.0):
+    """The 131,072-particle fluid (FCC 4*32^3 start, T = 0.728): the force
+    error of both GPU paths against the FP64 oracle at the start, and the
+    total-energy drift per particle over 1000 velocity-Verlet steps of the
+    FP32-mixed and FP64 GPU paths and, with with_oracle, of the oracle itself
+    (on the host cores, stopped early and scaled if it would pass
+    max_oracle_s)."""
+    import torch
+    from paper_0709_3225_gb300 import inputs, lj
+    x, v, L, w = inputs.workload_state("fluid-131k")
+    n = w.n
+    out = {"workload": "fluid-131k", "n": n, "steps": w.steps}
+    xj, Lj = inputs.jittered_fcc(32, w.rho, 0.1, 7)   # a non-lattice state for the force error
+    fo = None
+    if with_oracle:
+        import oracle
+        fo = oracle.forces_cells(xj, Lj, rc=w.rc, mode=1)[0]
+    for precision in ("mixed", "fp64"):
+        row = {}
+        if fo is not None:
+            s = lj.System(xj, None, Lj, precision=precision, rc=w.rc)
+            s.forces()
+            fg = s.f.double().cpu().numpy()[:, :3]
+            s.check()
+            s.close()
+            row["force_rel_rms_vs_oracle"] = float(np.sqrt(((fg - fo) ** 2).sum() / (fo ** 2).sum()))
+        s = lj.System(x, v, L, precision=precision, dt=w.dt, rc=w.rc)
+        e0 = s.energy()[2]
+        s.step(w.steps)
+        e1 = s.energy()[2]
+        s.check()
+        s.close()
+        torch.cuda.synchronize()
+        row["energy_drift_per_particle"] = (e1 - e0) / n
+        row["e_total_start_per_particle"] = e0 / n
+        out[precision] = row
+    if with_oracle:
+        import oracle
+        xo, vo = x.copy(), v.copy()
+        f, _, ep0, _ = oracle.forces_cells(xo, L, rc=w.rc, mode=1)
+        e0 = ep0 + oracle.ekin(vo)
+        t0 = time.perf_counter()
+        done = 0
+        while done < w.steps and time.perf_counter() - t0 < max_oracle_s:
+            k = min(100, w.steps - done)
+            ep, _ = oracle.vv(xo, vo, f, L, k, dt=w.dt, rc=w.rc, mode=1)
+            done += k
+        e1 = ep + oracle.ekin(vo)
+        out["oracle"] = {"steps": done, "energy_drift_per_particle": (e1 - e0) / n,
+                         "energy_drift_per_particle_per_1000_steps": (e1 - e0) / n * 1000.0 / done,
+                         "seconds": time.perf_counter() - t0}
+    return out
+
+
 def run_skin(x, v, L, w, stream, steps=60):
     """Cell lists with a skin on the 4M workload: ms per step and rebuilds
     for a few skins, beside the per-step rebuild (skin 0)."""
@@ -626,6 +680,7 @@ def run_gpu(args):
     skin = None if (args.no_ensemble or rank != 0) else run_skin(x, v, L, w, stream)
     aop = None if (args.no_ensemble or rank != 0) else run_aop_density(stream)
     small = None if (args.no_ensemble or rank != 0) else run_graph_small(stream)
+    accuracy = None if (args.no_ensemble or rank != 0) else run_accuracy_131k(world == 1 and not args.no_cpu_baseline)
 
     if rank != 0:
         if world > 1:
@@ -681,6 +736,7 @@ def run_gpu(args):
         "aop_vs_csr_density": aop,
         "small_systems_graph": small,
         "fluid_start": fluid,
+        "accuracy_131k": accuracy,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64,
