@@ -3,8 +3,9 @@
   python -m paper_0709_3225_gb300.profile_run --op force --n-fcc 80 --reps 3
 
 Builds a jittered FCC liquid of 4 n^3 particles at rho = 0.8442, then runs
-``--reps`` force evaluations (``--op force``) or velocity-Verlet steps
-(``--op step``) through the C ABI after one untimed warm-up, and prints the
+``--reps`` force evaluations (``--op force``), velocity-Verlet steps
+(``--op step``) or force VJPs with a seeded Gaussian cotangent (``--op
+vjp``) through the C ABI after one untimed warm-up, and prints the
 CUDA-event time per call.  It reports no benchmark figures; use bench.py for
 those.
 """
@@ -19,7 +20,7 @@ from . import inputs, lj
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["force", "step"], default="force")
+    ap.add_argument("--op", choices=["force", "step", "vjp"], default="force")
     ap.add_argument("--n-fcc", type=int, default=80)
     ap.add_argument("--rho", type=float, default=0.8442)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
@@ -34,6 +35,13 @@ def main(argv=None) -> int:
     if args.group_width is not None:
         lj.lj_set_tuning(s.ctx, 3, args.group_width, 4)
     s.forces()
+    g = dx = dp = None
+    if args.op == "vjp":
+        gen = torch.Generator(device="cuda").manual_seed(1)
+        g = torch.randn((s.n, 3), dtype=torch.float64, device="cuda", generator=gen)
+        dx = torch.zeros_like(s.x)
+        dp = torch.zeros(2, dtype=torch.float64, device="cuda")
+        lj.lj_forces_vjp(s.ctx, s.x, g, 1.0, dx, dp)
     if args.op == "step":
         s.step(1)
     torch.cuda.synchronize()
@@ -42,6 +50,8 @@ def main(argv=None) -> int:
     for _ in range(args.reps):
         if args.op == "force":
             s.forces()
+        elif args.op == "vjp":
+            lj.lj_forces_vjp(s.ctx, s.x, g, 1.0, dx, dp)
         else:
             s.step(1)
     e1.record()
