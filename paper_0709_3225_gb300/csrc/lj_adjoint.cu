@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp(int n, int nc, int64_t ncel
 // bounding-box pruning, and takes the home particles in chunks of G lanes,
 // the S = 32 / G lane groups splitting the candidates, two candidates per
 // lane and step with packed FP32x2 arithmetic.  Parameter terms are summed
-// in FP32 over 8 steps (16 candidates, a handful in range) and then in FP64.
+// in FP32 over 16 steps (32 candidates, a handful in range) and then in FP64.
 // Cells whose pruned stencil does not fit the slice take the plain path.
 
 constexpr int kVjpWarpThreads = 256;
@@ -440,10 +440,10 @@ __device__ __forceinline__ void vjp_cell(const VjpWarpCoef &k, int n, int cap, c
             ae += (double)(te.x + te.y);
             as += (double)(ts.x + ts.y);
         }
-        for (; m < iters; m += 8) {
+        for (; m < iters; m += 16) {
             float2 te = f2(0.f), ts = f2(0.f);
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
+            for (int u = 0; u < 16; u++) {
                 if (m + u < iters)
                     vjp_pair2<MODE, false>(xs, ys, zs, gix, giy, giz, X2[(m + u) * S], Y2[(m + u) * S],
                                            Z2[(m + u) * S], HX2[(m + u) * S], HY2[(m + u) * S], HZ2[(m + u) * S], k,
@@ -475,7 +475,7 @@ __device__ __forceinline__ void vjp_cell(const VjpWarpCoef &k, int n, int cap, c
 }
 
 template <int R, int MODE>
-__global__ void __launch_bounds__(kVjpWarpThreads, 2) k_vjp_warp(int n, int nc, int64_t ncell, int cap, VjpWarpCoef k,
+__global__ void __launch_bounds__(kVjpWarpThreads, 3) k_vjp_warp(int n, int nc, int64_t ncell, int cap, VjpWarpCoef k,
                                                                  const float4 *__restrict__ pos,
                                                                  const float4 *__restrict__ g4,
                                                                  const int32_t *__restrict__ start, double scale,
@@ -583,7 +583,11 @@ cudaError_t launch_vjp_warp(lj_ctx *c, const VjpCoef &kd, double scale, double *
     const int warps = kVjpWarpThreads / 32;
     const double mean = c->ncell > 0 ? (double)c->p.n / (double)c->ncell : 0.0;
     const double m = (double)ns * mean;
-    int cap = (((int)(m + 4.0 * sqrt(m)) + 64) + 7) & ~7;
+    // 0.65 m + 3 sqrt(m) + 64: room for the ~0.64 m candidates the pruning
+    // keeps plus the padding, small enough for 3 CTAs (24 warps) per SM;
+    // a cell that overflows takes the plain path (measured: 2.46 -> 2.32 ms
+    // at 4M against m + 4 sqrt(m) + 64 and 2 CTAs per SM)
+    int cap = (((int)(0.65 * m + 3.0 * sqrt(m)) + 64) + 7) & ~7;
     const int limit = 227 * 1024 - 2 * warps * (int)sizeof(double) - 256;
     while (cap > 96 && warps * vjp_slice_words(cap, R) * (int)sizeof(float) > limit) cap -= 8;
     const int smem = warps * vjp_slice_words(cap, R) * (int)sizeof(float);
