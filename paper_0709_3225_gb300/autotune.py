@@ -7,7 +7,9 @@ It picks, by timing velocity-Verlet steps on a copy of the state:
                      update separate or fused into it, run kernel with
                      bulk-copy staging, run kernel reading global memory,
                      the paper's fixed-capacity cell arrays, the warp kernel
-                     with bulk-copied stencils),
+                     with bulk-copied stencils, the warp kernel with each
+                     step one persistent launch; FP64: the FP64 warp kernel
+                     or the run kernels),
                      the lane-group width of the warp kernel (home particles
                      per chunk; 0 = compiled default, -1 = chosen per cell)
                      and the cells per pull
