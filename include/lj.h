@@ -312,9 +312,10 @@ int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);
  * kernel with each cell's stencil bulk-copied into shared memory while the
  * previous cell computes (FP32-mixed), 6 = kernel 3 for forces, with
  * lj_step's steps run as one cooperative persistent launch each (the
- * batched kernel below with one replica: no gaps between the phases of a
- * step, for small systems; FP32-mixed; steps with a skin or the
- * deterministic in-cell order take the regular path); kernels 1, 2, 4, 5
+ * batched kernel below with one replica, given this call's group_width
+ * and cells_per_grab (0 taken as 1): no gaps between the phases of a step,
+ * for small systems; FP32-mixed; steps with a skin or the deterministic
+ * in-cell order take the regular path); kernels 1, 2, 4, 5
  * and 6 need cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
  * in chunks of this many lanes, the other 32 / group_width lane groups
  * splitting the candidates; 0 = the compiled-in default (16 for

@@ -95,6 +95,7 @@ def system_candidates(precision: str) -> list[dict]:
     return warp + [{"subdiv": 1, "kernel": 0, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 1, "gw": 0, "grab": 0},
                    {"subdiv": 1, "kernel": 2, "gw": 0, "grab": 0}, {"subdiv": 1, "kernel": 4, "gw": 0, "grab": 0},
                    {"subdiv": 1, "kernel": 5, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 6, "gw": 0, "grab": 1},
+                   {"subdiv": 1, "kernel": 6, "gw": 0, "grab": 4},
                    {"subdiv": 2, "kernel": 3, "gw": 0, "grab": 4}, {"subdiv": 2, "kernel": 3, "gw": 2, "grab": 4}]
 
 

@@ -270,8 +270,12 @@ int persistent_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps, cudaE
             c->pers = nullptr;
             return r;
         }
-        r = lj_batch_set_tuning(c->pers, 1, 1, 0);
+        c->pers_gen = c->gen - 1;
+    }
+    if (c->pers_gen != c->gen) {   // cells per pull and lane-group width of the tuning
+        const int r = lj_batch_set_tuning(c->pers, c->grab > 0 ? c->grab : 1, 1, c->gw);
         if (r != LJ_OK) return r;
+        c->pers_gen = c->gen;
     }
     int64_t l0 = 0, l1 = 0;
     lj_batch_launches(c->pers, &l0, nullptr);

@@ -74,6 +74,7 @@ struct lj_ctx {
     int w64_lcap;        // FP64 warp kernel: list entries per warp
     int use_pers;        // tuning kernel 6: lj_step through a one-replica persistent batch
     lj_batch *pers;      // created by the first such step
+    int pers_gen;        // tuning generation last applied to it
     unsigned *work;      // work counter of the warp kernel, zeroed by k_scan_tiles
     int npartial;        // partials written by the last energy launch
     int npartial_cap;    // capacity of `partial` in (energy, virial) pairs
