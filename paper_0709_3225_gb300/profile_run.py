@@ -6,7 +6,9 @@ Builds a jittered FCC liquid of 4 n^3 particles at rho = 0.8442, then runs
 ``--reps`` force evaluations (``--op force``), velocity-Verlet steps
 (``--op step``) or force VJPs with a seeded Gaussian cotangent (``--op
 vjp``) through the C ABI after one untimed warm-up, and prints the
-CUDA-event time per call.  It reports no benchmark figures; use bench.py for
+CUDA-event time per call.  ``--op batch`` instead steps the 256-replica
+ensemble (one cooperative launch per step, direct launches, 1 cell per
+pull) after its 50 relaxation steps.  It reports no benchmark figures; use bench.py for
 those.
 """
 from __future__ import annotations
@@ -18,9 +20,30 @@ import torch
 from . import inputs, lj
 
 
+def run_batch(reps: int) -> int:
+    e = inputs.ensemble()
+    xs, vs = inputs.ensemble_state(e)
+    b = lj.Batch(xs, vs, e.box)
+    b.relax(50, 1e-3, 0.05)
+    b.set_tuning(1, False, 0)
+    b.forces()
+    b.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        b.step(1)
+    e1.record()
+    torch.cuda.synchronize()
+    b.check()
+    print(f"batch n={b.ntot} replicas={b.nrep} {e0.elapsed_time(e1) / reps:.3f} ms per step")
+    b.close()
+    return 0
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["force", "step", "vjp"], default="force")
+    ap.add_argument("--op", choices=["force", "step", "vjp", "batch"], default="force")
     ap.add_argument("--n-fcc", type=int, default=80)
     ap.add_argument("--rho", type=float, default=0.8442)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
@@ -29,6 +52,8 @@ def main(argv=None) -> int:
     ap.add_argument("--subdiv", type=int, default=1, help="cell subdivision k (1 or 2)")
     ap.add_argument("--group-width", type=int, default=None, help="warp-kernel lane-group width (0 = per cell)")
     args = ap.parse_args(argv)
+    if args.op == "batch":
+        return run_batch(args.reps)
     x, L = inputs.jittered_fcc(args.n_fcc, args.rho, 0.1, 1)
     v = inputs.velocities(x.shape[0], 1.0, 1)
     s = lj.System(x, v, L, precision=args.precision, flags=args.flags, cell_subdiv=args.subdiv)
