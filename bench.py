@@ -610,7 +610,7 @@ def run_gpu(args):
     clocks = clk.summary()
 
     # HBM view of the non-force kernels: algorithmic bytes per particle per step
-    # (kick-drift-bin 120 B, scatter 56 B, force in/out 32 B).
+    # (kick-drift-bin 124 B, scatter 56 B, force in/out 32 B).
     other_ms = ms_step - force_avg_ms
     candidates = stencil_candidates(s.ctx)
     issued_tflops = (CANDIDATE_FLOPS * candidates + FLOPS_PER_PAIR * 2 * pairs) / (force_avg_ms / 1e3) / 1e12

@@ -1,7 +1,7 @@
 """GPU force parity against the FP64 oracle (Section 2 pair force over the
 Section 3 cell list).
 
-Tolerances (from the arithmetic, "Tolerances"):
+Tolerances (derived from the arithmetic):
   mixed: relative RMS force error <= 1e-5 over all particles; per particle
          and component |df_i| <= 6e-7 K_i + 1e-5 S_i, where K_i = sum_j
          (|F'(r_ij)| + |F(r_ij)|/r_ij) and S_i = sum_j |F(r_ij)| (FP32
