@@ -234,8 +234,11 @@ int lj_set_params(lj_ctx *ctx, double eps, double sigma);
  *             product of the potential energy; device (n, 3) double);
  *   dparam += scale * (dL/deps, dL/dsigma)  (device double[2]).
  * The cell list is piecewise constant in x and contributes nothing.  Pair
- * arithmetic in the context's precision, parameter sums in FP64.  Allocates
- * an (n)-element cotangent buffer on first use.  Asynchronous. */
+ * arithmetic in the context's precision; parameter sums in FP64 (FP32-mixed:
+ * FP32 partial sums over groups of 32 candidates, then FP64).  Each call
+ * bins x again, so with the atomic in-cell order FP32 results can differ in
+ * their last bits between calls (lj_set_deterministic makes them repeat).
+ * Allocates an (n)-element cotangent buffer on first use.  Asynchronous. */
 int lj_forces_vjp(lj_ctx *ctx, const double *x, const double *g, double scale, double *dx, double *dparam);
 
 /* One step of the adjoint of lj_step's velocity Verlet (Section 2), from the
