@@ -23,10 +23,13 @@
 //    whose entries all lie in one lane is stored by that lane; a particle
 //    split over several lanes is combined by the lane holding its first
 //    entry, adding the other lanes' partial sums in lane order.  The exact
-//    FP64 cutoff test decides each pair (pair64).  Sums are in a fixed order, so the
-//    forces are reproducible for a fixed in-cell order.
+//    FP64 cutoff test decides each pair (pair64).  Sums are in a fixed
+//    order, so the forces are reproducible for a fixed in-cell order.
 //  * Cells whose pruned stencil does not fit the warp's slice take a plain
 //    FP64 path reading global memory per stencil cell.
+// The same kernel, with the cotangents staged beside the positions, gives
+// the FP64 VJP of the forces (OP 2, vjp64): the pair lists are the same,
+// only the FP64 pair term and what is stored differ.
 #include <math.h>
 #include <string.h>
 
