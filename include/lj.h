@@ -189,6 +189,24 @@ int lj_rand48_drand(uint64_t *state, int64_t S, int64_t R, double *out, void *st
 int lj_langevin_seed(lj_ctx *ctx, int64_t seed);
 int lj_langevin_step(lj_ctx *ctx, double *x, double *v, void *f, int32_t nsteps, double gamma, double kT);
 
+/* Checkpoint / resume of the thermostat's random series (the paper has no
+ * checkpointing; the rest of a run's state -- x, v, f -- is caller-owned).
+ * lj_get_rng_state copies the context's n stream states (uint64, each the
+ * 48-bit series element that stream outputs next) to the caller's device
+ * array `state`; LJ_EINVAL before lj_langevin_seed or lj_set_rng_state.
+ * lj_set_rng_state copies n states from `state` into the context
+ * (allocating n uint64 on first use, as lj_langevin_seed); the values must
+ * be below 2^48, as lj_get_rng_state returns them (larger ones cause no
+ * fault but are no rand48 series).  A context given the state, x, v and f that
+ * another context of the same parameters held between two calls continues
+ * the run as that context would have: bitwise with lj_set_deterministic on
+ * (the in-cell order then does not depend on the binning atomics) and no
+ * skin (a skin's cell lists are rebuilt on the first step of a context).
+ * Both: device pointers, 8-byte aligned (LJ_EINVAL otherwise); async on the
+ * context's stream; n = 0 is a no-op. */
+int lj_get_rng_state(lj_ctx *ctx, uint64_t *state);
+int lj_set_rng_state(lj_ctx *ctx, const uint64_t *state);
+
 /* All-pairs forces (Section 2, Eq. n2_force with the cutoff): the same
  * forces as lj_forces computed without cells, every pair at the minimum
  * image, O(n^2) work.  For small systems, as a GPU brute-force cross-check,

@@ -561,6 +561,30 @@ extern "C" int lj_langevin_seed(lj_ctx *c, int64_t seed)
     return LJ_OK;
 }
 
+extern "C" int lj_get_rng_state(lj_ctx *c, uint64_t *state)
+{
+    if (!c) return LJ_EINVAL;
+    if (c->p.n == 0) return LJ_OK;
+    if (!c->r48_state) return LJ_EINVAL;   // no series yet
+    int r = check_dev_ptr(state, 8);
+    if (r) return r;
+    LJ_CK(cudaMemcpyAsync(state, c->r48_state, (size_t)c->p.n * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                          c->stream));
+    return LJ_OK;
+}
+
+extern "C" int lj_set_rng_state(lj_ctx *c, const uint64_t *state)
+{
+    if (!c) return LJ_EINVAL;
+    if (c->p.n == 0) return LJ_OK;
+    int r = check_dev_ptr(state, 8);
+    if (r) return r;
+    if (!c->r48_state) LJ_CK(cudaMalloc(&c->r48_state, (size_t)c->p.n * sizeof(uint64_t)));
+    LJ_CK(cudaMemcpyAsync(c->r48_state, state, (size_t)c->p.n * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                          c->stream));
+    return LJ_OK;
+}
+
 extern "C" int lj_langevin_step(lj_ctx *c, double *x, double *v, void *f, int32_t nsteps, double gamma, double kT)
 {
     if (!c || nsteps < 0 || !(gamma >= 0.0) || !isfinite(gamma) || !(kT >= 0.0) || !isfinite(kT)) return LJ_EINVAL;

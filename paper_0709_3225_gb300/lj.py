@@ -80,6 +80,8 @@ _SIGS = {
     "lj_rand48_drand": ([_P, ctypes.c_int64, ctypes.c_int64, _P, _P], ctypes.c_int),
     "lj_langevin_seed": ([_P, ctypes.c_int64], ctypes.c_int),
     "lj_langevin_step": ([_P, _P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "lj_get_rng_state": ([_P, _P], ctypes.c_int),
+    "lj_set_rng_state": ([_P, _P], ctypes.c_int),
     "lj_forces": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lj_step": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "lj_step_host": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
@@ -339,6 +341,22 @@ def lj_langevin_step(ctx: Context, x, v, f, nsteps: int, gamma: float, kT: float
                                 int(nsteps), float(gamma), float(kT)), "lj_langevin_step")
 
 
+def lj_get_rng_state(ctx: Context, state=None):
+    """The thermostat's n stream states (CUDA int64 tensor of uint64 bit
+    patterns, each below 2^48); raises LJ_EINVAL before it was seeded."""
+    import torch
+    if state is None:
+        state = torch.empty(ctx.n, dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
+    _ck(load().lj_get_rng_state(ctx.handle, _dev(state, torch.int64, (ctx.n,), "state")), "lj_get_rng_state")
+    return state
+
+
+def lj_set_rng_state(ctx: Context, state) -> None:
+    """Load n stream states (CUDA int64 tensor, as lj_get_rng_state gives)."""
+    import torch
+    _ck(load().lj_set_rng_state(ctx.handle, _dev(state, torch.int64, (ctx.n,), "state")), "lj_set_rng_state")
+
+
 def lj_step(ctx: Context, x, v, f, nsteps: int) -> None:
     import torch
     _ck(load().lj_step(ctx.handle, _dev(x, torch.float64, (ctx.n, 3), "x"),
@@ -536,6 +554,69 @@ def lj_read_timing(ctx: Context) -> tuple[float, int, int]:
     return ms.value, nf.value, nk.value
 
 
+# ---- checkpoint files ------------------------------------------------------
+# One .npz per checkpoint: the parameters, x, v, f, whether f holds the forces
+# of x, the step count, the in-cell order mode and, once the thermostat was
+# seeded, its n rand48 stream states.  The cell arrays are not saved: they
+# are a function of x and are rebuilt by the first step after loading.
+
+CHECKPOINT_VERSION = 1
+_PARAM_FIELDS = [name for name, _ in lj_params._fields_]
+_RAND48_LIMIT = 1 << 48
+
+
+def write_checkpoint(path, params: lj_params, x, v, f, *, steps: int = 0, forces_valid: bool = True,
+                     deterministic: bool = False, rng=None) -> None:
+    """Write a checkpoint file (host arrays: x, v (n, 3) float64, f (n, 4)
+    float32 or float64 per the precision, rng (n,) uint64 or None)."""
+    n = int(params.n)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    fdt = np.float32 if params.precision == LJ_PREC_MIXED else np.float64
+    f = np.asarray(f)
+    if x.shape != (n, 3) or v.shape != (n, 3) or f.shape != (n, 4) or f.dtype != fdt:
+        raise ValueError("checkpoint arrays do not match the parameters")
+    arrays = {"version": np.int64(CHECKPOINT_VERSION),
+              "params": np.array([getattr(params, k) for k in _PARAM_FIELDS], dtype=np.float64),
+              "param_names": np.array(_PARAM_FIELDS),
+              "x": x, "v": v, "f": f, "steps": np.int64(steps),
+              "forces_valid": np.bool_(forces_valid), "deterministic": np.bool_(deterministic)}
+    if rng is not None:
+        rng = np.ascontiguousarray(rng).view(np.uint64) if np.asarray(rng).dtype == np.int64 else \
+            np.ascontiguousarray(rng, dtype=np.uint64)
+        if rng.shape != (n,) or np.any(rng >= _RAND48_LIMIT):
+            raise ValueError("rng must hold n stream states below 2^48")
+        arrays["rng"] = rng
+    with open(path, "wb") as fh:
+        np.savez(fh, **arrays)
+
+
+def read_checkpoint(path) -> dict:
+    """Read and validate a checkpoint file: a dict with params (lj_params),
+    x, v, f, steps, forces_valid, deterministic and rng (None if absent)."""
+    with np.load(path, allow_pickle=False) as z:
+        if "version" not in z.files or int(z["version"]) != CHECKPOINT_VERSION:
+            raise ValueError(f"{path}: not a version {CHECKPOINT_VERSION} checkpoint")
+        names = [str(k) for k in z["param_names"]]
+        if names != _PARAM_FIELDS:
+            raise ValueError(f"{path}: parameter fields {names} differ from {_PARAM_FIELDS}")
+        vals = dict(zip(names, z["params"].tolist()))
+        params = lj_params(*[(int(vals[k]) if t is not ctypes.c_double else float(vals[k]))
+                             for k, t in lj_params._fields_])
+        out = {"params": params, "x": z["x"], "v": z["v"], "f": z["f"], "steps": int(z["steps"]),
+               "forces_valid": bool(z["forces_valid"]), "deterministic": bool(z["deterministic"]),
+               "rng": z["rng"] if "rng" in z.files else None}
+    n = int(params.n)
+    fdt = np.float32 if params.precision == LJ_PREC_MIXED else np.float64
+    if (out["x"].shape != (n, 3) or out["v"].shape != (n, 3) or out["f"].shape != (n, 4)
+            or out["x"].dtype != np.float64 or out["v"].dtype != np.float64 or out["f"].dtype != fdt):
+        raise ValueError(f"{path}: arrays do not match the parameters")
+    if out["rng"] is not None and (out["rng"].shape != (n,) or out["rng"].dtype != np.uint64
+                                   or np.any(out["rng"] >= _RAND48_LIMIT)):
+        raise ValueError(f"{path}: rng must hold n stream states below 2^48")
+    return out
+
+
 class System:
     """Convenience owner of a context and its device state (x, v, f).
 
@@ -556,6 +637,9 @@ class System:
         self.ctx = Context(self.params, stream)
         self.f = torch.zeros((n, 4), dtype=self.ctx.force_dtype, device=device)
         self._forces_valid = False
+        self.steps = 0
+        self.deterministic = False
+        self._rng_seeded = False
 
     @property
     def n(self) -> int:
@@ -570,6 +654,52 @@ class System:
         if not self._forces_valid:
             self.forces()
         lj_step(self.ctx, self.x, self.v, self.f, nsteps)
+        self.steps += int(nsteps)
+
+    def set_deterministic(self, enable: bool = True) -> None:
+        lj_set_deterministic(self.ctx, enable)
+        self.deterministic = bool(enable)
+
+    def langevin_seed(self, seed: int) -> None:
+        lj_langevin_seed(self.ctx, seed)
+        self._rng_seeded = self.n > 0
+
+    def langevin_step(self, nsteps: int, gamma: float, kT: float) -> None:
+        if not self._forces_valid:
+            self.forces()
+        lj_langevin_step(self.ctx, self.x, self.v, self.f, nsteps, gamma, kT)
+        self.steps += int(nsteps)
+
+    def save(self, path) -> None:
+        """Write a checkpoint of this system (synchronizes its stream)."""
+        rng = lj_get_rng_state(self.ctx) if self._rng_seeded else None
+        lj_check(self.ctx)
+        rng = None if rng is None else rng.cpu().numpy().view(np.uint64)
+        write_checkpoint(path, self.params, self.x.cpu().numpy(), self.v.cpu().numpy(), self.f.cpu().numpy(),
+                         steps=self.steps, forces_valid=self._forces_valid, deterministic=self.deterministic,
+                         rng=rng)
+
+    @classmethod
+    def load(cls, path, device=None, stream=None) -> "System":
+        """A new system continuing from a checkpoint: same parameters, x, v,
+        f, step count, in-cell order mode and thermostat series.  Tuning, the
+        skin and graph replay are not part of a checkpoint; set them again."""
+        import torch
+        ck = read_checkpoint(path)
+        p = ck["params"]
+        s = cls(ck["x"], ck["v"], p.box, eps=p.eps, sigma=p.sigma, rc=p.rc, dt=p.dt, mass=p.mass,
+                shift_mode=p.shift_mode, precision=p.precision, flags=p.flags, cell_subdiv=p.cell_subdiv,
+                device=device, stream=stream)
+        s.f.copy_(torch.from_numpy(ck["f"]))
+        s._forces_valid = ck["forces_valid"]
+        s.steps = ck["steps"]
+        if ck["deterministic"]:
+            s.set_deterministic(True)
+        if ck["rng"] is not None and s.n > 0:
+            lj_set_rng_state(s.ctx, torch.from_numpy(ck["rng"].view(np.int64)).to(s.x.device))
+            s._rng_seeded = True
+        lj_check(s.ctx)
+        return s
 
     def energy(self):
         return lj_energy(self.ctx, self.x, self.v)
