@@ -17,9 +17,6 @@ __device__ __forceinline__ void load_f(const F4 *__restrict__ f, int i, double &
 }
 
 // nkick half kicks v += h f (1 on the first step of a call, 2 when the
-// closing half kick of the previous step is fused in), drift x += dt v, wrap
-// into [0, L), cell id and rank (atomic count) of the new position.
-// nkick half kicks v += h f (1 on the first step of a call, 2 when the
 // closing half kick of the previous step is fused in, applied as one FP64
 // FMA with nkick*h), drift x += dt v (FP64 FMA), wrap into [0, L), cell id
 // (exact, from the previous cell as a guess) and rank of the new position
