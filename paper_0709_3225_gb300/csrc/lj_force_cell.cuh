@@ -295,8 +295,9 @@ __device__ __forceinline__ void compute_chunks(const WarpParams &k, const float4
 }
 
 // Staged path.  The stencil's candidates are taken as one flat index space
-// t = 0 .. Ttot-1 (lane l takes t = l, l + 32, ...; the stencil entry of t is
-// found by binary search in the prefix sums), converted to the home-cell
+// t = 0 .. Ttot-1 (lane l takes t = l, l + 32, ...; the stencil entry of t
+// comes from warp votes for the 27-entry stencil and from a binary search of
+// the prefix sums for the 125-entry one), converted to the home-cell
 // frame and kept only if within rc of the home particles' bounding box (the
 // margin covers FP32 rounding of the box test).  Kept candidates are
 // appended in ballot order, so the home particles (entry 0, all inside the
@@ -335,8 +336,30 @@ __device__ __forceinline__ bool cell_staged(const WarpParams &k, const float4 *_
     }
     const float rcut2 = k.rc2 * 1.0001f;
     const unsigned lt = (1u << lane) - 1u;
+    // Stencil entry of a candidate t.  With one entry per lane (NS <= 32) it
+    // comes from warp votes instead of a search: lane e holds entry e's first
+    // candidate s_e; the non-empty entries have distinct s_e, and the entry
+    // of t is the last non-empty one with s_e <= t.  Per round of 32
+    // candidates starting at tb, the non-empty entries with s_e <= tb are
+    // counted (the last of them holds tb), and those starting inside the
+    // round set bit s_e - tb of a mask, so lane l's entry is the
+    // (count + set bits 1 .. l)-th non-empty entry; lane j holds the index
+    // of the j-th non-empty entry (0 past their number), passed through the
+    // X array before the staging fills it.
+    [[maybe_unused]] int s_e = 0, j_entry = 0;
+    [[maybe_unused]] bool ne = false;
+    if constexpr (NS <= 32) {
+        s_e = lane < NS ? spre[lane] : 0x7fffffff;
+        ne = lane < NS && spre[lane + 1] > s_e;
+        const unsigned nem = __ballot_sync(0xffffffffu, ne);
+        if (ne) X[__popc(nem & lt)] = __int_as_float(lane);
+        __syncwarp();
+        j_entry = lane < __popc(nem) ? __float_as_int(X[lane]) : 0;
+        __syncwarp();
+    }
+    const unsigned le = (2u << lane) - 1u;   // bits 0 .. lane
     int T = 0;
-    // Batches of kStageBatch rounds: the stencil-entry searches and the
+    // Batches of kStageBatch rounds: the stencil-entry lookups and the
     // position loads of a batch are issued before any of them is used,
     // so their latencies overlap.
     for (int t0 = 0; t0 < Ttot; t0 += 32 * kStageBatch) {
@@ -344,18 +367,28 @@ __device__ __forceinline__ bool cell_staged(const WarpParams &k, const float4 *_
 #pragma unroll
         for (int u = 0; u < kStageBatch; u++) {
             const int t = t0 + 32 * u + lane;
+            int kc = 0, kb = 0;   // stencil entry of t and its prefix
+            if constexpr (NS <= 32) {
+                const int tb = t0 + 32 * u;
+                const int o = s_e - tb;
+                const unsigned inside = __reduce_or_sync(0xffffffffu, (ne && o >= 1 && o <= 31) ? (1u << o) : 0u);
+                const int jc = __popc(__ballot_sync(0xffffffffu, ne && o <= 0)) - 1 + __popc(inside & le);
+                kc = __shfl_sync(0xffffffffu, j_entry, jc & 31);
+                kb = __shfl_sync(0xffffffffu, s_e, kc);
+            }
             q[u] = make_float4(kFar, kFar, kFar, 0.f);
             sh[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (t < Ttot) {
-                int kc = 0, kb = 0;   // stencil entry of t and its prefix
+                if constexpr (NS > 32) {
 #pragma unroll
-                for (int step = P2 / 2; step > 0; step >>= 1) {
-                    const int m = kc + step;
-                    if (m < NS) {
-                        const int v = spre[m];
-                        if (v <= t) {
-                            kc = m;
-                            kb = v;
+                    for (int step = P2 / 2; step > 0; step >>= 1) {
+                        const int m = kc + step;
+                        if (m < NS) {
+                            const int v = spre[m];
+                            if (v <= t) {
+                                kc = m;
+                                kb = v;
+                            }
                         }
                     }
                 }

@@ -17,7 +17,9 @@
 //    absolute resolution) and dropping candidates farther than rc from the
 //    home particles' bounding box.
 //  * The compute phase takes the home particles in chunks of G lanes
-//    (G = 2 .. 32, chosen per cell to minimise idle lanes): lane g of a
+//    (by default G = 16 for the 27-cell stencil and 4 for the 125-cell one,
+//    compiled in; a general kernel takes G from the tuning or chooses it per
+//    cell to minimise idle lanes): lane g of a
 //    group owns particle g of the chunk, the S = 32/G groups split the
 //    candidates.  Staged data are SoA, so one 8-byte shared load gives a
 //    lane its next two candidates, evaluated together with packed FP32x2
