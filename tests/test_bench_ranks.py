@@ -1,7 +1,8 @@
 """The multi-rank logic of bench.py on the CPU: two gloo ranks run the
 barrier, the max-over-ranks reduction and the whole-job rate of independent
 replicas (the path has no data exchange between GPUs: replicas only), and
-the reference arm leaves every rank but 0 without work."""
+the reference arm leaves every rank but 0 without work, and on rank 0 prints
+the line the bench contract asks of it."""
 import os
 import socket
 import subprocess
@@ -93,3 +94,29 @@ def test_candidate_pairs_counts_the_full_stencil():
                 d = [min((a[i] - b[i]) % nc, (b[i] - a[i]) % nc) for i in range(3)]
                 brute += max(d) <= k
         assert bench.candidate_pairs(torch.from_numpy(g).double(), k) == brute
+
+
+@pytest.mark.slow
+def test_reference_arm_line():
+    """The reference arm (the oracle on the host cores) prints one JSON line
+    with the native arm's metric, unit and workload, the requested warm-up
+    steps (at least 3), a cpu_baseline describing the run and an e2e entry
+    with no host-device bytes."""
+    import json
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    for key in ("RANK", "LOCAL_RANK", "WORLD_SIZE"):
+        env.pop(key, None)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "steps/s"
+    assert d["config"]["workload"] == bench.WORKLOAD and d["config"]["n"] == 4_000_000
+    assert d["steps"] == 1 and d["warmup"] == 3 and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
