@@ -1,8 +1,8 @@
 """The multi-rank logic of bench.py on the CPU: two gloo ranks run the
 barrier, the max-over-ranks reduction and the whole-job rate of independent
 replicas (the path has no data exchange between GPUs: replicas only), and
-the reference arm leaves every rank but 0 without work, and on rank 0 prints
-the line the bench contract asks of it."""
+the reference arm leaves every rank but 0 without work and on rank 0 prints
+one JSON line for the native arm's metric and workload."""
 import os
 import socket
 import subprocess
