@@ -31,9 +31,25 @@ if ROOT not in sys.path:
 METRIC = "LJ steps/s & pair-interactions/s at N=4M, FP32-mixed vs FP64, % FP32 peak"
 WORKLOAD = "fluid-4m"
 FLOPS_PER_PAIR = 20          # flop convention per in-range pair evaluation
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
-FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 rate of the part (no measured figure)
+FP32_LANES, SM_MAX_MHZ = 128, 2070.0   # for the derived cross-check beside the measured peak
+
+
+def measure_peaks() -> dict:
+    """FP32 and FP64 FMA peaks measured on this device at its current clocks
+    (lj_measure_peak: chains of FMAs on every SM), with the SM count queried
+    from the device and the datasheet-style derivation beside them as a
+    cross-check."""
+    from paper_0709_3225_gb300 import lj
+    fp32, ms32, nsm = lj.lj_measure_peak(lj.PEAK_FP32)
+    fp32x2, ms32x2, _ = lj.lj_measure_peak(lj.PEAK_FP32X2)
+    fp64, ms64, _ = lj.lj_measure_peak(lj.PEAK_FP64)
+    return {"fp32_tflops": max(fp32, fp32x2) / 1e12, "fp32_scalar_tflops": fp32 / 1e12,
+            "fp32_packed_tflops": fp32x2 / 1e12, "fp64_tflops": fp64 / 1e12, "sms": nsm,
+            "launch_ms": {"fp32": ms32, "fp32x2": ms32x2, "fp64": ms64},
+            "derived_fp32_tflops": nsm * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12,
+            "how": "lj_measure_peak: 8 independent FMA chains per thread, 8 CTAs x 256 threads per SM, "
+                   "launch lengthened to >= 20 ms, fastest of 3 (CUDA events); FP32 = max(scalar fmaf, "
+                   "packed __ffma2_rn)"}
 
 
 def unique_pairs(n: int, rho: float, rc: float) -> float:
@@ -581,6 +597,8 @@ def run_gpu(args):
     x, v, L, w = inputs.workload_state(WORKLOAD)
     n = w.n
     pairs = unique_pairs(n, w.rho, w.rc)
+    mpk = measure_peaks()
+    FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS = mpk["fp32_tflops"], mpk["fp64_tflops"]
 
     # ---- FP32-mixed, device-resident (the headline `value`) --------------
     from paper_0709_3225_gb300 import autotune
@@ -725,7 +743,8 @@ def run_gpu(args):
                      "issued_flops_per_launch": CANDIDATE_FLOPS * candidates + FLOPS_PER_PAIR * 2 * pairs,
                      "issued_frac": issued_tflops / FP32_PEAK_TFLOPS,
                      "issued_convention": "7 flop per full-stencil candidate + 20 per pair, both directions",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                     "peak_source": "measured (lj_measure_peak, FP32 FMA chains; see measured_fp_peaks)",
+                     "frac_of_derived": achieved_tflops / mpk["derived_fp32_tflops"],
                      "fp32_pipe_busy": force_traffic("fp32_pipe_busy") if default_kernel else None,
                      "fp32_pipe_busy_source": "ncu sm__pipe_fmaheavy_cycles_active of the default force "
                                               "kernel at this size (profiles/k_force_warp_traffic_fluid-4m.md)"},
@@ -749,12 +768,13 @@ def run_gpu(args):
                               "achieved": FLOPS_PER_PAIR * pairs / (f64_ms / max(f64_n, 1) / 1e3) / 1e12,
                               "frac": FLOPS_PER_PAIR * pairs / (f64_ms / max(f64_n, 1) / 1e3) / 1e12
                               / FP64_PEAK_TFLOPS,
-                              "peak_source": "nominal GB300 FP64 rate"}},
+                              "peak_source": "measured (lj_measure_peak, FP64 FMA chains)"}},
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": bytes_h2d,
                 "d2h_bytes_per_step": bytes_h2d, "steps": e2e_steps,
                 "api": "lj_step_host, pinned host x, v, f; 1 step per call"},
         "clocks": clocks,
         "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
+        "measured_fp_peaks": mpk,
     }
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x, v, L, w)

@@ -113,25 +113,33 @@ const char *lj_strerror(int code);
  * LJ_EINVAL for bad parameters. */
 int lj_grid(const lj_params *p, int32_t *nc_out);
 
-/* Create a context on the current CUDA device.  Allocates all device
+/* Create a context on the current CUDA device for the simulation of
+ * Sections 2 and 3: p gives N, the box, eps, sigma, rc, dt and the cell grid
+ * (validated as by lj_grid: at least 2k + 1 cells per side, the Section 3.2
+ * lower limit of three cells per dimension for k = 1).  Allocates all device
  * scratch (cell arrays, sorted positions, partial sums) once; no later call
- * allocates on the device except lj_step_host and lj_energy, which allocate
- * their staging buffers on first use.  stream is a cudaStream_t (NULL = the
- * legacy default stream).  On error *out is NULL. */
+ * allocates on the device except lj_step_host, lj_energy and
+ * lj_observables, which allocate their staging buffers on first use.
+ * stream is a cudaStream_t (NULL = the legacy default stream).  On error
+ * *out is NULL. */
 int lj_create(lj_ctx **out, const lj_params *p, void *stream);
 
 /* Free a context (synchronizes its stream).  NULL is ignored. */
 void lj_destroy(lj_ctx *ctx);
 
-/* Bin x into cells (counting sort): for each particle the wrapped position
+/* Bin x into cells (counting sort; Section 3.1 keeps each cell's particles
+ * together in memory, here as one array sorted by cell, in CSR form with
+ * per-cell counts and starts; the paper leaves the binning rule unstated,
+ * read here as follows).  For each particle the wrapped position
  * w = x - L floor(x / L) (w >= L folds to w - L), the cell coordinate
  * c = trunc(w * (n_x / L)) clamped to [0, n_x - 1] per axis, the linear id
  * c_x + n_x (c_y + n_x c_z); per-cell counts and exclusive starts; the
  * sorted order.  x: device (n, 3) double, not modified. */
 int lj_bin(lj_ctx *ctx, const double *x);
 
-/* Copy the result of the last binning to caller-owned DEVICE arrays (any
- * may be NULL): cell_of[n], count[n_x^3], start[n_x^3 + 1], perm[n], where
+/* Copy the result of the last binning (the Section 3.1 cell lists) to
+ * caller-owned DEVICE arrays (any may be NULL; 4-byte aligned, else
+ * LJ_EINVAL): cell_of[n], count[n_x^3], start[n_x^3 + 1], perm[n], where
  * perm[start[c] .. start[c+1]) lists the particles of cell c (their order
  * within a cell is unspecified). */
 int lj_get_cells(lj_ctx *ctx, int32_t *cell_of, int32_t *count, int32_t *start, int32_t *perm);
@@ -230,10 +238,28 @@ int lj_step(lj_ctx *ctx, double *x, double *v, void *f, int32_t nsteps);
  * device, steps, copies them back, synchronizes. */
 int lj_step_host(lj_ctx *ctx, double *x, double *v, void *f, int32_t nsteps);
 
-/* out[0] = kinetic energy (1/2) m sum v^2, out[1] = potential energy at x,
- * out[2] = their sum; FP64; out is a HOST array of 3.  x, v: device.
- * Synchronizes. */
+/* Energies of the state (x, v): out[0] = kinetic energy (1/2) m sum v^2,
+ * out[1] = potential energy sum_{i<j} U(r_ij) at x (the Section 2 pair
+ * potential, truncated/shifted per shift_mode), out[2] = their sum, the
+ * quantity whose conservation Section 5 names as the test of
+ * single-precision runs; FP64; out is a HOST array of 3.  x, v: device.
+ * Allocates a force buffer on first use.  Synchronizes. */
 int lj_energy(lj_ctx *ctx, const double *x, const double *v, double *out);
+
+/* Thermodynamic observables of the state (x, v), FP64, into the HOST array
+ * out[6] (synchronizes):
+ *   out[0] = E_kin = (1/2) m sum v^2,  out[1] = E_pot = sum_{i<j} U(r_ij),
+ *   out[2] = E_kin + E_pot (the conserved energy whose drift Section 5 names
+ *            as the test of single-precision runs),
+ *   out[3] = W = sum_{i<j} r_ij F(r_ij), the virial of lj_forces,
+ *   out[4] = T = 2 E_kin / (3n - 3) (k_B = 1; velocity Verlet conserves the
+ *            total momentum, leaving 3n - 3 degrees of freedom; 0 for n < 2;
+ *            the temperature a thermostat holds, Section 1),
+ *   out[5] = P = (2 E_kin + W) / (3 L^3), the virial pressure.
+ * E_pot and W come from the force kernels (Section 2 pair terms over the
+ * Section 3 cells); T and P are formed on the device from the FP64 sums.
+ * x, v: device (n, 3) double.  Errors as lj_energy. */
+int lj_observables(lj_ctx *ctx, const double *x, const double *v, double *out);
 
 /* Synchronize the stream and return (and clear) any error latched by a
  * kernel since the last check. */
@@ -414,18 +440,35 @@ int lj_batch_launches(const lj_batch *b, int64_t *launches, int32_t *graph);
  * context: the cell arrays and sorted positions live in one fixed buffer of
  * about 1.8 MB inside liblj.so, which every GPU that loads the library holds
  * until the process exits.  x (n, 3) double and f (n, 4) float or double are
- * caller-owned DEVICE arrays; p is validated as by lj_grid.
+ * caller-owned DEVICE arrays; p is validated as by lj_grid, and p->flags
+ * must be 0 (the warp kernels; LJ_EINVAL otherwise).
  * Limits: p->n <= LJ_STATIC_MAX_N and n_x^3 <= LJ_STATIC_MAX_CELLS; larger
  * sizes return LJ_EOVERFLOW before any work is queued.
- * Set-up: the first call on a device (with that device current) looks up
- * the buffer's device address and keeps it; make that first call before any
- * stream capture.
+ * Set-up: every call looks up the buffer's device address on the current
+ * device (a host-side lookup; it is not kept, so a cudaDeviceReset between
+ * calls is safe).  The first call on a device, and the first after a reset,
+ * loads the library's device code: make it before any stream capture.
  * All calls share the one buffer, which keeps the previous call's contents
- * (the kernels clear what must start at zero).  Calls whose work overlaps on
+ * (the call clears what must start at zero).  Calls whose work overlaps on
  * the GPU -- two streams, two host threads -- race on it: serialize them.
  * Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream)
- * and not synchronized; non-finite coordinates are not reported here. */
+ * and not synchronized.  Errors the kernels find are not reported here:
+ * a particle with a non-finite coordinate gets no force written, and the
+ * binning's consistency check goes unread. */
 int lj_forces_static(const lj_params *p, const double *x, void *f, void *stream);
+
+/* Measured floating-point peak of the current device at its current clocks
+ * (Section 1 compares the GPU's peak floating-point rate with a CPU's; the
+ * roofline fractions divide by this measurement, not a datasheet figure).
+ * kind 0: FP32 fused multiply-adds (fmaf), 1: FP32 packed pairs
+ * (__ffma2_rn, two FMAs per instruction), 2: FP64 (fma).  Runs chains of
+ * FMAs on every SM (8 CTAs of 256 threads per SM, 8 independent chains per
+ * thread) on a private stream, lengthened until one launch takes >= 20 ms,
+ * and returns the fastest of three timed launches: flop/s (an FMA counts 2)
+ * in *flops_per_s, that launch's milliseconds in *ms and the SM count in
+ * *sms (both optional).  Host pointers; synchronizes; allocates nothing on
+ * the device.  LJ_EINVAL for another kind or a NULL flops_per_s. */
+int lj_measure_peak(int32_t kind, double *flops_per_s, double *ms, int32_t *sms);
 
 /* Enable (1) or disable (0) CUDA-event timing of the force kernel on the
  * context's stream; enabling resets the counters. */

@@ -25,6 +25,13 @@ Parity status of each function (what pins it, in tests/test_oracle_*.py):
                    rand48_series)
   langevin      -- gamma = 0 is velocity Verlet; the ideal gas thermalises
                    to kT; Box-Muller normals have unit variance (pinned)
+  stiffness     -- K and S of two- and three-body systems against the pair
+                   force and its central-difference slope (pinned)
+  near_cutoff   -- pairs at rc +- band/2 flagged, at rc +- 2 band not, in the
+                   brute-force and the cell branch (pinned)
+  observables   -- ideal gas P V = (2/3) E_kin; two-body virial r F(r); the
+                   pressure equals -dE_pot/dV under uniform scaling; T of
+                   hand-set velocities (pinned)
 """
 from __future__ import annotations
 
@@ -363,3 +370,28 @@ def langevin(x, v, f, L: float, nsteps: int, seed: int, gamma: float, kT: float,
     if r != 0:
         raise ValueError("box too small for the cell stencil")
     return E.value, W.value
+
+
+def observables(x, v, L: float, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5, mode: int = 1,
+                k: int = 1, mass: float = 1.0) -> dict:
+    """Thermodynamic observables of one state, by their definitions (FP64).
+
+    The paper names energy conservation as the check on its single-precision
+    runs (Section 5) and the temperature as what a thermostat holds (Section
+    1); the quantities are the textbook ones (k_B = 1):
+      E_kin = (1/2) m sum_i v_i^2,  E_pot = sum_{i<j} U(r_ij)  (Section 2),
+      W     = sum_{i<j} r_ij F(r_ij)                        (the virial),
+      T     = 2 E_kin / (3N - 3)   (momentum conserved: 3N - 3 degrees of
+                                    freedom; 0 for N < 2),
+      P     = (2 E_kin + W) / (3V),  V = L^3               (virial pressure).
+    """
+    x = _pos(x)
+    n = x.shape[0]
+    Ek = ekin(v, mass)
+    if n > 0:
+        _, _, Ep, W = forces_cells(x, L, eps, sigma, rc, mode, k)
+    else:
+        Ep, W = 0.0, 0.0
+    T = 2.0 * Ek / (3 * n - 3) if n >= 2 else 0.0
+    P = (2.0 * Ek + W) / (3.0 * L ** 3)
+    return {"e_kin": Ek, "e_pot": Ep, "e_tot": Ek + Ep, "virial": W, "T": T, "P": P}

@@ -169,6 +169,20 @@ __global__ void __launch_bounds__(kReduceThreads) k_sum_scaled(const double *__r
     if (threadIdx.x == 0) *out = scale * s[0];
 }
 
+// Observables from the FP64 sums (one thread): E_tot = E_kin + E_pot,
+// T = 2 E_kin / (3n - 3) (k_B = 1; the total momentum is conserved, so
+// 3n - 3 degrees of freedom; 0 for n < 2) and the virial pressure
+// P = (2 E_kin + W) / (3V), inv3v = 1 / (3 L^3).
+__global__ void k_observables(double *__restrict__ s, int64_t n, double inv3v)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double ep = s[0], w = s[1], ek = s[2];
+        s[3] = ek + ep;
+        s[4] = n >= 2 ? 2.0 * ek / (double)(3 * n - 3) : 0.0;
+        s[5] = (2.0 * ek + w) * inv3v;
+    }
+}
+
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
@@ -231,5 +245,13 @@ cudaError_t launch_ekin(lj_ctx *c, const double *v)
     k_sum_scaled<<<1, kReduceThreads, 0, c->stream>>>(c->ekin_partial, c->ekin_grid, 0.5 * c->p.mass,
                                                       c->scalars + 2);
     c->kernel_launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observables(lj_ctx *c)
+{
+    const double L = c->p.box;
+    k_observables<<<1, 32, 0, c->stream>>>(c->scalars, c->p.n, 1.0 / (3.0 * L * L * L));
+    c->kernel_launches++;
     return cudaGetLastError();
 }

@@ -56,9 +56,9 @@ struct lj_ctx {
     int ntiles;
     double *partial;     // force-kernel per-block (energy, virial) partials
     double *ekin_partial;
-    double *scalars;     // [0] = E_pot, [1] = virial, [2] = E_kin
+    double *scalars;     // 8 doubles: [0] = E_pot, [1] = virial, [2] = E_kin, [3] = E_tot, [4] = T, [5] = P
     int32_t *err;
-    double *host_scalars;   // pinned, 4 doubles
+    double *host_scalars;   // pinned, 8 doubles
     int32_t *host_err;      // pinned
 
     // force kernel configuration: run-staged kernel (lj_force.cu) ...
@@ -237,6 +237,8 @@ cudaError_t launch_kick(lj_ctx *c, double *v, const void *f);
 // Skin mode: kick + drift + displacement tracking, then the rebuild decision.
 cudaError_t launch_kick_drift_skin(lj_ctx *c, double *x, double *v, const void *f, int nkick);
 cudaError_t launch_ekin(lj_ctx *c, const double *v);
+// Temperature and virial pressure from scalars[0..2] into scalars[3..5].
+cudaError_t launch_observables(lj_ctx *c);
 cudaError_t launch_counts_from_start(lj_ctx *c, int32_t *count);
 cudaError_t force_configure(lj_ctx *c);
 // Allow kernel `kern` at least `bytes` of dynamic shared memory.  The limit

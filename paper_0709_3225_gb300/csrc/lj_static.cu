@@ -5,12 +5,15 @@
 //
 // All scratch (cell arrays, sorted positions, scan sums) lives in one
 // file-scope device array of fixed size.  Host code cannot use the array's
-// name as a device address, so the first call on each device looks the
-// address up with cudaGetSymbolAddress (with that device current) and keeps
-// it; later calls on that device reuse it.  The same launchers as lj_forces
-// run on a context built on the host stack whose pointers point into the
-// array.  No cudaMalloc, cudaFree or allocating library routine is called.
-#include <atomic>
+// name as a device address, so every call looks the address up with
+// cudaGetSymbolAddress for the current device (a host-side lookup, no
+// stream work).  The address is not cached: after a cudaDeviceReset the
+// library's device code is loaded again and the array can move, and a kept
+// address would then point at freed memory.  The first call on a device
+// (and the first after a reset) loads the device code.  The same launchers
+// as lj_forces run on a context built on the host stack whose pointers
+// point into the array.  No cudaMalloc, cudaFree or allocating library
+// routine is called.
 #include <string.h>
 
 #include "lj_internal.cuh"
@@ -20,7 +23,6 @@ namespace {
 constexpr int64_t kMaxN = LJ_STATIC_MAX_N;
 constexpr int64_t kMaxCells = LJ_STATIC_MAX_CELLS;
 constexpr int kMaxNc = 32;               // 32^3 == kMaxCells
-constexpr int kMaxDevices = 64;
 constexpr int64_t kMaxPartials = 4096;    // energy partials are not written here
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -41,8 +43,6 @@ constexpr size_t kScratchBytes = kOffErr + 256;
 
 static __device__ __align__(256) unsigned char g_lj_static_scratch[kScratchBytes];
 
-std::atomic<unsigned char *> g_scratch_ptr[kMaxDevices];
-
 __global__ void k_static_centres(double *centre, int nc, double cw)
 {
     const int k = threadIdx.x;
@@ -62,23 +62,15 @@ int check_ptr(const void *ptr, size_t align)
     return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? LJ_OK : LJ_EINVAL;
 }
 
-// Device address of the static buffer on the current device (set-up on the
-// first call per device).
+// Device address of the static buffer on the current device, looked up on
+// every call (see the file header for why it is not kept).
 int scratch_for_current_device(unsigned char **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_lj_static_scratch);
     if (e != cudaSuccess) return map_err(e);
-    if (dev < 0 || dev >= kMaxDevices) return LJ_EINVAL;
-    unsigned char *p = g_scratch_ptr[dev].load(std::memory_order_acquire);
-    if (!p) {
-        void *addr = nullptr;
-        e = cudaGetSymbolAddress(&addr, g_lj_static_scratch);
-        if (e != cudaSuccess || !addr) return e != cudaSuccess ? map_err(e) : LJ_ECUDA;
-        p = (unsigned char *)addr;
-        g_scratch_ptr[dev].store(p, std::memory_order_release);
-    }
-    *out = p;
+    if (!addr) return LJ_ECUDA;
+    *out = (unsigned char *)addr;
     return LJ_OK;
 }
 
@@ -89,6 +81,9 @@ extern "C" int lj_forces_static(const lj_params *p, const double *x, void *f, vo
     int32_t nc = 0;
     int r = lj_grid(p, &nc);
     if (r != LJ_OK) return r;
+    // Only the warp kernels: the run kernels' bounded waits report a timeout
+    // through the error word, which no caller of this entry point can read.
+    if (p->flags != 0) return LJ_EINVAL;
     const int64_t ncell = (int64_t)nc * nc * nc;
     if (p->n > kMaxN || ncell > kMaxCells) return LJ_EOVERFLOW;
     if (p->n > 0) {
@@ -109,8 +104,8 @@ extern "C" int lj_forces_static(const lj_params *p, const double *x, void *f, vo
     c.wrap_hi = p->box * (1.0 - ldexp(1.0, -50));
     c.wrap_lo = p->box * ldexp(1.0, -50);
     c.stream = (cudaStream_t)stream;
-    c.use_tma = (p->flags & LJ_FLAG_RUN_DIRECT) ? 0 : 1;
-    c.use_run_kernel = (p->flags & (LJ_FLAG_RUN_STAGED | LJ_FLAG_RUN_DIRECT)) ? 1 : 0;   // as lj_create
+    c.use_tma = 1;
+    c.use_run_kernel = 0;
     cudaError_t e = cudaGetDevice(&c.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, c.device);
     if (e != cudaSuccess) return map_err(e);

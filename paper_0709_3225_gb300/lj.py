@@ -86,6 +86,7 @@ _SIGS = {
     "lj_step": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "lj_step_host": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "lj_energy": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "lj_observables": ([_P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lj_check": ([_P], ctypes.c_int),
     "lj_set_params": ([_P, ctypes.c_double, ctypes.c_double], ctypes.c_int),
     "lj_set_tuning": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
@@ -104,6 +105,8 @@ _SIGS = {
     "lj_forces_vjp": ([_P, _P, _P, ctypes.c_double, _P, _P], ctypes.c_int),
     "lj_vv_adjoint_step": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "lj_forces_static": ([ctypes.POINTER(lj_params), _P, _P, _P], ctypes.c_int),
+    "lj_measure_peak": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "lj_set_timing": ([_P, ctypes.c_int32], ctypes.c_int),
     "lj_read_timing": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                         ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -395,6 +398,17 @@ def lj_energy(ctx: Context, x, v) -> tuple[float, float, float]:
     return out[0], out[1], out[2]
 
 
+def lj_observables(ctx: Context, x, v) -> dict:
+    """E_kin, E_pot, E_tot, virial W, temperature T and virial pressure P
+    (FP64; T and P formed on the device)."""
+    import torch
+    out = (ctypes.c_double * 6)()
+    _ck(load().lj_observables(ctx.handle, _dev(x, torch.float64, (ctx.n, 3), "x"),
+                              _dev(v, torch.float64, (ctx.n, 3), "v"), out), "lj_observables")
+    keys = ("e_kin", "e_pot", "e_tot", "virial", "T", "P")
+    return {k: out[i] for i, k in enumerate(keys)}
+
+
 def lj_set_params(ctx: Context, eps: float, sigma: float) -> None:
     _ck(load().lj_set_params(ctx.handle, float(eps), float(sigma)), "lj_set_params")
     ctx.params.eps = float(eps)
@@ -534,6 +548,20 @@ def lj_forces_static(params: lj_params, x, f, stream=None) -> None:
     fdt = torch.float64 if params.precision == LJ_PREC_FP64 else torch.float32
     _ck(load().lj_forces_static(ctypes.byref(params), _dev(x, torch.float64, (n, 3), "x"),
                                 _dev(f, fdt, (n, 4), "f"), _stream_ptr(stream)), "lj_forces_static")
+
+
+PEAK_FP32, PEAK_FP32X2, PEAK_FP64 = 0, 1, 2
+
+
+def lj_measure_peak(kind: int) -> tuple[float, float, int]:
+    """Measured FMA peak of the current device: (flop/s, ms of the timed
+    launch, SM count); kind PEAK_FP32, PEAK_FP32X2 (packed pairs) or PEAK_FP64."""
+    fl = ctypes.c_double()
+    ms = ctypes.c_double()
+    sms = ctypes.c_int32()
+    _ck(load().lj_measure_peak(int(kind), ctypes.byref(fl), ctypes.byref(ms), ctypes.byref(sms)),
+        "lj_measure_peak")
+    return fl.value, ms.value, sms.value
 
 
 def lj_check(ctx: Context) -> None:
@@ -703,6 +731,9 @@ class System:
 
     def energy(self):
         return lj_energy(self.ctx, self.x, self.v)
+
+    def observables(self) -> dict:
+        return lj_observables(self.ctx, self.x, self.v)
 
     def cells(self):
         import torch

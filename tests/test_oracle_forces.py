@@ -117,3 +117,69 @@ def test_box_too_small_rejected(oracle_mod):
     x = inputs.uniform(10, 7.0, 0)
     with pytest.raises(ValueError):
         oracle_mod.forces_cells(x, 7.0, rc=2.5)
+
+
+def _dFdr(oracle_mod, r, mode, eps=1.0, sigma=1.0, h=1e-6):
+    # dF/dr by central differences of the pinned pair force (not a retyped formula)
+    Fp, _ = oracle_mod.pair(r + h, eps=eps, sigma=sigma, mode=mode)
+    Fm, _ = oracle_mod.pair(r - h, eps=eps, sigma=sigma, mode=mode)
+    return (Fp - Fm) / (2 * h)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("eps,sigma", [(1.0, 1.0), (0.7, 1.1)])
+def test_stiffness_two_and_three_body(oracle_mod, mode, eps, sigma):
+    # K_i = sum_j |F'(r_ij)| + |F(r_ij)| / r_ij and S_i = sum_j |F(r_ij)| over
+    # partners within rc, checked on hand-built configurations: the per-particle
+    # bound of every mixed-precision parity test is built from them.
+    L = 10.0
+    u = np.array([2.0, -1.0, 2.0]) / 3.0
+    w = np.array([0.0, 0.6, -0.8])
+    r1, r2, r3 = 1.05, 1.9, 2.45
+    # two bodies across the periodic boundary
+    x = np.array([[9.7, 0.3, 5.0], [0.0, 0.0, 0.0]])
+    x[1] = np.mod(x[0] + r1 * u, L)
+    K, S = oracle_mod.stiffness(x, L, eps=eps, sigma=sigma, mode=mode)
+    F1, _ = oracle_mod.pair(r1, eps=eps, sigma=sigma, mode=mode)
+    k1 = abs(_dFdr(oracle_mod, r1, mode, eps, sigma)) + abs(F1) / r1
+    np.testing.assert_allclose(K, [k1, k1], rtol=1e-7)
+    np.testing.assert_allclose(S, [abs(F1), abs(F1)], rtol=1e-12)
+    # three bodies: 0 has partners at r1 and r2; 1 and 2 are more than rc apart
+    # (|r1 u - r2 w| > 2.5), so each has particle 0 only
+    x3 = np.array([[5.0, 5.0, 5.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    x3[1] = x3[0] + r1 * u
+    x3[2] = x3[0] + r2 * w
+    assert np.linalg.norm(r1 * u - r2 * w) > 2.5
+    K3, S3 = oracle_mod.stiffness(x3, L, eps=eps, sigma=sigma, mode=mode)
+    F2, _ = oracle_mod.pair(r2, eps=eps, sigma=sigma, mode=mode)
+    k2 = abs(_dFdr(oracle_mod, r2, mode, eps, sigma)) + abs(F2) / r2
+    np.testing.assert_allclose(K3, [k1 + k2, k1, k2], rtol=1e-7)
+    np.testing.assert_allclose(S3, [abs(F1) + abs(F2), abs(F1), abs(F2)], rtol=1e-12)
+    # a partner at r3 < rc counts, one just beyond rc does not
+    x4 = np.array([[5.0, 5.0, 5.0], [5.0 + r3, 5.0, 5.0], [5.0, 5.0 - 2.5 - 1e-9, 5.0]])
+    K4, S4 = oracle_mod.stiffness(x4, L, eps=eps, sigma=sigma, mode=mode)
+    F3, _ = oracle_mod.pair(r3, eps=eps, sigma=sigma, mode=mode)
+    k3 = abs(_dFdr(oracle_mod, r3, mode, eps, sigma)) + abs(F3) / r3
+    np.testing.assert_allclose(K4[:2], [k3, k3], rtol=1e-6)
+    np.testing.assert_allclose(S4, [abs(F3), abs(F3), 0.0], rtol=1e-12, atol=0)
+    assert K4[2] == 0.0
+    # a subset of particles (idx) returns the same rows
+    Ks, Ss = oracle_mod.stiffness(x3, L, eps=eps, sigma=sigma, mode=mode, idx=[2, 0])
+    np.testing.assert_array_equal(Ks, K3[[2, 0]])
+    np.testing.assert_array_equal(Ss, S3[[2, 0]])
+
+
+@pytest.mark.parametrize("L", [7.0, 11.0])   # 2 cells per side: brute force; 4: the cell branch
+def test_near_cutoff_band(oracle_mod, L):
+    # A pair at |r - rc| < band flags both particles; pairs at 2 band from rc,
+    # on either side, flag neither.  The band is on the distance r itself
+    # (a band on r^2 would miss r = rc + 0.5 band for band << rc).
+    rc, band = 2.5, 1e-3
+    assert (oracle_mod.ncells(L, rc + band) >= 3) == (L > 8.0)
+    u = np.array([1.0, 2.0, 2.0]) / 3.0
+    pairs = [(rc + 0.5 * band, True), (rc - 0.5 * band, True), (rc + 2 * band, False), (rc - 2 * band, False)]
+    for r, flagged in pairs:
+        x = np.array([[L - 0.2, 0.1, 0.5 * L], [0.0, 0.0, 0.0], [0.5 * L, 0.5 * L, 0.1]])
+        x[1] = np.mod(x[0] + r * u, L)       # across the periodic boundary
+        near = oracle_mod.near_cutoff(x, L, rc=rc, band=band)
+        assert list(near) == [flagged, flagged, False], r
