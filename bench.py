@@ -389,14 +389,17 @@ def run_accuracy_131k(with_oracle: bool, max_oracle_s: float = 60.0):
             s.close()
             row["force_rel_rms_vs_oracle"] = float(np.sqrt(((fg - fo) ** 2).sum() / (fo ** 2).sum()))
         s = lj.System(x, v, L, precision=precision, dt=w.dt, rc=w.rc)
-        e0 = s.energy()[2]
+        o0 = s.observables()
         s.step(w.steps)
-        e1 = s.energy()[2]
+        o1 = s.observables()
         s.check()
         s.close()
         torch.cuda.synchronize()
+        e0, e1 = o0["e_tot"], o1["e_tot"]
         row["energy_drift_per_particle"] = (e1 - e0) / n
         row["e_total_start_per_particle"] = e0 / n
+        row["T_start"], row["T_end"] = o0["T"], o1["T"]
+        row["P_start"], row["P_end"] = o0["P"], o1["P"]
         out[precision] = row
     if with_oracle:
         import oracle
@@ -414,6 +417,37 @@ def run_accuracy_131k(with_oracle: bool, max_oracle_s: float = 60.0):
                          "energy_drift_per_particle_per_1000_steps": (e1 - e0) / n * 1000.0 / done,
                          "seconds": time.perf_counter() - t0}
     return out
+
+
+def run_accuracy_2k():
+    """The fluid-2k workload as stated (N = 2,048 FCC start, rho 0.8442,
+    T 0.728, 100 FP64 velocity-Verlet steps): the GPU's FP64 trajectory
+    against the oracle's trajectory with all-pairs forces (Section 2, no
+    cells), and both total-energy drifts, with the temperature and pressure
+    at the end."""
+    import oracle
+    from paper_0709_3225_gb300 import inputs, lj
+    x, v, L, w = inputs.workload_state("fluid-2k")
+    xo, vo = x.copy(), v.copy()
+    fo, _, ep0, _ = oracle.forces_brute(xo, L, rc=w.rc)
+    e0 = ep0 + oracle.ekin(vo)
+    ep1, _ = oracle.vv(xo, vo, fo, L, w.steps, dt=w.dt, rc=w.rc, k=0)
+    e1 = ep1 + oracle.ekin(vo)
+    ob = oracle.observables(xo, vo, L, rc=w.rc)
+    s = lj.System(x, v, L, precision="fp64", dt=w.dt, rc=w.rc)
+    g0 = s.observables()
+    s.step(w.steps)
+    g1 = s.observables()
+    s.check()
+    d = s.x.cpu().numpy() - xo
+    d -= L * np.round(d / L)
+    s.close()
+    return {"workload": "fluid-2k", "n": w.n, "steps": w.steps, "precision": "fp64",
+            "oracle_forces": "all pairs (Section 2), no cells",
+            "max_abs_dx_vs_oracle": float(np.abs(d).max()),
+            "gpu": {"energy_drift_per_particle": (g1["e_tot"] - g0["e_tot"]) / w.n, "T_end": g1["T"],
+                    "P_end": g1["P"]},
+            "oracle": {"energy_drift_per_particle": (e1 - e0) / w.n, "T_end": ob["T"], "P_end": ob["P"]}}
 
 
 def run_skin(x, v, L, w, stream, steps=60):
@@ -703,6 +737,7 @@ def run_gpu(args):
     aop = None if (args.no_ensemble or rank != 0) else run_aop_density(stream)
     small = None if (args.no_ensemble or rank != 0) else run_graph_small(stream)
     accuracy = None if (args.no_ensemble or rank != 0) else run_accuracy_131k(world == 1 and not args.no_cpu_baseline)
+    accuracy_2k = None if (args.no_ensemble or rank != 0) else run_accuracy_2k()
 
     if rank != 0:
         if world > 1:
@@ -760,6 +795,7 @@ def run_gpu(args):
         "small_systems_graph": small,
         "fluid_start": fluid,
         "accuracy_131k": accuracy,
+        "accuracy_2k": accuracy_2k,
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64,

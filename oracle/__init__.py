@@ -313,7 +313,9 @@ def ekin(v, mass: float = 1.0) -> float:
 def vv(x, v, f, L: float, nsteps: int, dt: float = 0.005, eps: float = 1.0,
        sigma: float = 1.0, rc: float = 2.5, mode: int = 1, k: int = 1, mass: float = 1.0):
     """Velocity Verlet (Section 2) for nsteps; x, v, f are updated IN PLACE
-    (f must hold F(x) on entry).  Returns (e_pot, virial) at the end."""
+    (f must hold F(x) on entry).  k = 0 takes the forces from the all-pairs
+    sum of Eq. (n2_force) (forces_brute) instead of the cell list.  Returns
+    (e_pot, virial) at the end."""
     for a in (x, v, f):
         if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
                 and a.ndim == 2 and a.shape[1] == 3):

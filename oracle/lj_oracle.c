@@ -507,8 +507,10 @@ double or_ekin(int64_t n, const double *v, double mass)
  *   v <- v + (dt / 2m) f.
  * On entry f must hold F(x) (as returned by or_forces_cells); on exit it
  * holds the forces at the final positions.  The cell list is rebuilt from
- * scratch at every force evaluation.  e_pot/virial receive the values at the
- * final positions.  Returns -1 on a bad box. */
+ * scratch at every force evaluation.  k = 0 takes the forces from the
+ * Section 2 all-pairs sum instead (or_forces_brute: Eq. n2_force over every
+ * pair at the minimum image, no cells).  e_pot/virial receive the values at
+ * the final positions.  Returns -1 on a bad box. */
 int or_vv(int64_t n, double *x, double *v, double *f, double L, double eps,
           double sigma, double rc, int mode, int k, double dt, double mass,
           int nsteps, double *e_pot, double *virial)
@@ -520,7 +522,9 @@ int or_vv(int64_t n, double *x, double *v, double *f, double L, double eps,
             v[q] = v[q] + h * f[q];
             x[q] = wrap1(x[q] + dt * v[q], L);
         }
-        if (or_forces_cells(n, x, L, eps, sigma, rc, mode, k, f, NULL, &E, &W) != 0)
+        if (k == 0)
+            or_forces_brute(n, x, L, eps, sigma, rc, mode, f, NULL, &E, &W);
+        else if (or_forces_cells(n, x, L, eps, sigma, rc, mode, k, f, NULL, &E, &W) != 0)
             return -1;
         for (int64_t q = 0; q < 3 * n; q++) v[q] = v[q] + h * f[q];
     }
@@ -646,7 +650,9 @@ int or_langevin(int64_t n, double *x, double *v, double *f, double L, double eps
                 v[j] = vv;
             }
         }
-        if (or_forces_cells(n, x, L, eps, sigma, rc, mode, k, f, NULL, &E, &W) != 0)
+        if (k == 0)
+            or_forces_brute(n, x, L, eps, sigma, rc, mode, f, NULL, &E, &W);
+        else if (or_forces_cells(n, x, L, eps, sigma, rc, mode, k, f, NULL, &E, &W) != 0)
             return -1;
         for (int64_t q = 0; q < 3 * n; q++) v[q] = v[q] + h * f[q];
     }

@@ -59,7 +59,7 @@ def _check(x, L, oracle_mod, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=
     assert abs(w - wo) <= t["e"] * 0.5 * rc * S.sum() + 1e-12
     # per-particle energies in f[:, 3]
     escale = np.abs(epo).max() if epo.size else 1.0
-    assert np.all(np.abs(f[~near, 3] - epo[~near]) <= (1e-4 if precision == "mixed" else 1e-10) * escale)
+    assert np.all(np.abs(f[~near, 3] - epo[~near]) <= (1e-5 if precision == "mixed" else 1e-10) * escale)
     return f, fo
 
 

@@ -248,3 +248,31 @@ def test_persistent_steps_follow_parameter_changes(oracle_mod):
         s.close()
     assert np.abs(min_image(out[0][0] - out[1][0], L)).max() <= 2e-6
     assert np.abs(out[0][1] - out[1][1]).max() <= 2e-4
+
+
+def test_fluid_2k_100_fp64_steps_against_all_pairs_oracle(oracle_mod):
+    """The fluid-2k workload as stated (N = 2,048 FCC start, rho 0.8442,
+    T 0.728, dt 0.005, 100 velocity-Verlet steps, FP64 throughout) on the GPU
+    against the oracle's trajectory whose forces come from the Section 2
+    all-pairs sum (no cells): positions, velocities, forces, and the total
+    energy's drift over the run."""
+    from paper_0709_3225_gb300 import lj
+    x, v, L, w = inputs.workload_state("fluid-2k")
+    xo, vo = x.copy(), v.copy()
+    fo, _, e0_pot, _ = oracle_mod.forces_brute(xo, L)
+    e0 = e0_pot + oracle_mod.ekin(vo)
+    e1_pot, _ = oracle_mod.vv(xo, vo, fo, L, w.steps, dt=w.dt, k=0)
+    e1 = e1_pot + oracle_mod.ekin(vo)
+    s = lj.System(x, v, L, precision="fp64", dt=w.dt)
+    g0 = s.energy()
+    s.step(w.steps)
+    s.check()
+    g1 = s.energy()
+    xg, vg, fg = s.x.cpu().numpy(), s.v.cpu().numpy(), s.f.double().cpu().numpy()[:, :3]
+    s.close()
+    assert np.abs(min_image(xg - xo, L)).max() <= 1e-10
+    assert np.abs(vg - vo).max() <= 1e-9
+    assert np.abs(fg - fo).max() <= 1e-8 * np.abs(fo).max()
+    assert g0[2] == pytest.approx(e0, rel=1e-11)
+    # drift of the total energy over the 100 steps: the same on both sides
+    assert abs((g1[2] - g0[2]) - (e1 - e0)) <= 1e-9 * abs(e0)

@@ -111,3 +111,24 @@ def test_lattice_gas_inputs():
     e = inputs.ensemble(8, seed=1)
     assert len(e.n) == 8 and np.all((e.n >= 500) & (e.n <= 50000))
     assert np.all((e.rho >= 0.7) & (e.rho <= 0.9)) and np.all((e.temperature >= 0.7) & (e.temperature <= 1.5))
+
+
+def test_all_pairs_and_cell_list_trajectories_agree(oracle_mod):
+    # The fluid-2k workload (FCC 4*8^3, rho 0.8442, T 0.728), 100 steps of
+    # velocity Verlet with the Section 2 all-pairs forces (k = 0) and with the
+    # Section 3 cell list (k = 1): two independent force sums, one trajectory.
+    x0, v0, L, w = inputs.workload_state("fluid-2k")
+    traj = []
+    for k in (0, 1):
+        x, v = x0.copy(), v0.copy()
+        f = oracle_mod.forces_brute(x, L)[0] if k == 0 else oracle_mod.forces_cells(x, L)[0]
+        E, W = oracle_mod.vv(x, v, f, L, w.steps, dt=w.dt, k=k)
+        traj.append((x, v, f, E, W))
+    (xa, va, fa, Ea, Wa), (xb, vb, fb, Eb, Wb) = traj
+    d = xa - xb
+    d -= L * np.round(d / L)
+    assert np.abs(d).max() < 1e-11
+    assert np.abs(va - vb).max() < 1e-10
+    assert np.abs(fa - fb).max() < 1e-9 * np.abs(fb).max()
+    assert Ea == pytest.approx(Eb, rel=1e-12)
+    assert Wa == pytest.approx(Wb, rel=1e-12)
