@@ -88,9 +88,10 @@ typedef struct lj_params {
 } lj_params;
 
 /* lj_params.flags select the force kernel (same results; for comparison).
- * Default (0): FP32-mixed uses the warp-per-cell kernel, which stages each
- * cell's 27-cell stencil in shared memory relative to the cell centre; FP64
- * uses the run kernel with bulk-copy staging.
+ * Default (0): FP32-mixed uses the warp-per-cell kernel that takes each pair
+ * once over the half stencil (lj_set_tuning kernel 7; kernel 3, the 27-cell
+ * stencil, for cell_subdiv 2), staged in shared memory relative to the cell
+ * centre; FP64 uses the FP64 warp kernel (kernel 3).
  * LJ_FLAG_RUN_STAGED: the run kernel (a CTA per run of cells along x) with its
  *   9 neighbour-row windows staged by bulk asynchronous copies.
  * LJ_FLAG_RUN_DIRECT: the run kernel reading neighbour cells from global
@@ -350,9 +351,16 @@ int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);
 /* Choose the force kernel of a context (same results; for autotuning):
  * kernel 0 = warp-per-cell kernel (FP32-mixed only) with the velocity-Verlet
  * update of lj_step fused into it, 1 = run kernel with bulk-copy staging,
- * 2 = run kernel reading global memory, 3 = warp-per-cell kernel with the
- * update in a separate kernel (the default; in FP64 contexts the FP64 warp
- * kernel that compacts the in-range pairs before any FP64 arithmetic), 4 = the paper's
+ * 2 = run kernel reading global memory, 3 = warp-per-cell kernel over the
+ * 27-cell stencil with the update in a separate kernel (the FP64 default: in
+ * FP64 contexts the FP64 warp kernel that compacts the in-range pairs before
+ * any FP64 arithmetic), 7 = warp-per-cell kernel that evaluates each pair
+ * once (Newton's third law: Eq. n2_force is antisymmetric, so the pair force
+ * is added to i and subtracted from j; the home cell with itself and with
+ * the 13 neighbours of positive offset; the FP32-mixed default for
+ * cell_subdiv 1; f is zeroed and the contributions are added with atomics,
+ * so its FP32 sums are not bitwise reproducible between runs, and contexts
+ * with lj_set_deterministic on take kernel 3 instead), 4 = the paper's
  * fixed-capacity cell arrays (Section 3.1: 32 placeholders per cell, empty
  * ones computed as virtual particles; FP32-mixed; a cell with more than 32
  * particles latches LJ_EOVERFLOW, reported by lj_check), 5 = the warp
@@ -362,8 +370,8 @@ int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);
  * batched kernel below with one replica, given this call's group_width
  * and cells_per_grab (0 taken as 1): no gaps between the phases of a step,
  * for small systems; FP32-mixed; steps with a skin or the deterministic
- * in-cell order take the regular path); kernels 1, 2, 4, 5
- * and 6 need cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
+ * in-cell order take the regular path); kernels 1, 2, 4, 5, 6
+ * and 7 need cell_subdiv 1.  group_width: the warp kernel takes a cell's particles
  * in chunks of this many lanes, the other 32 / group_width lane groups
  * splitting the candidates; 0 = the compiled-in default (16 for
  * cell_subdiv 1, 4 for 2), -1 = chosen per cell to minimise idle lanes, or

@@ -3,7 +3,9 @@
 It picks, by timing velocity-Verlet steps on a copy of the state:
   single systems  -- cell subdivision k (cell side >= rc / k: 1, the 27-cell
                      stencil, or 2, the 125-cell stencil of half-size cells),
-                     force kernel (warp-per-cell with the velocity-Verlet
+                     force kernel (warp-per-cell over the half stencil
+                     with each pair once, warp-per-cell over the 27-cell
+                     stencil with the velocity-Verlet
                      update separate or fused into it, run kernel with
                      bulk-copy staging, run kernel reading global memory,
                      the paper's fixed-capacity cell arrays, the warp kernel
@@ -92,7 +94,8 @@ def system_candidates(precision: str) -> list[dict]:
         return ([{"subdiv": 1, "kernel": 3, "gw": 0, "grab": c} for c in (1, 4)] +
                 [{"subdiv": 1, "kernel": k, "gw": 0, "grab": 0} for k in (1, 2)])
     warp = [{"subdiv": 1, "kernel": 3, "gw": g, "grab": c} for g in (0, -1, 8, 32) for c in (0, 4)]
-    return warp + [{"subdiv": 1, "kernel": 0, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 1, "gw": 0, "grab": 0},
+    n3 = [{"subdiv": 1, "kernel": 7, "gw": 0, "grab": c} for c in (0, 1, 4)]
+    return n3 + warp + [{"subdiv": 1, "kernel": 0, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 1, "gw": 0, "grab": 0},
                    {"subdiv": 1, "kernel": 2, "gw": 0, "grab": 0}, {"subdiv": 1, "kernel": 4, "gw": 0, "grab": 0},
                    {"subdiv": 1, "kernel": 5, "gw": 0, "grab": 4}, {"subdiv": 1, "kernel": 6, "gw": 0, "grab": 1},
                    {"subdiv": 1, "kernel": 6, "gw": 0, "grab": 4},

@@ -405,6 +405,7 @@ int setup_grid(lj_ctx *c, int nc)
     LJ_GRID_CK(c->p.precision == LJ_PREC_MIXED ? warp_force_configure(c) : w64_force_configure(c));
     c->pipe_grid = 0;
     if (c->p.precision == LJ_PREC_MIXED && c->p.cell_subdiv != 2) LJ_GRID_CK(pipe_force_configure(c));
+    if (c->p.precision == LJ_PREC_MIXED && c->p.cell_subdiv != 2) LJ_GRID_CK(n3_force_configure(c));
     {
         int np = c->force_grid > c->wforce_grid ? c->force_grid : c->wforce_grid;
         if (np < 32 * c->nsm) np = 32 * c->nsm;   // room for the adjoint kernel's grid
@@ -439,6 +440,10 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     // force kernel (lj_set_tuning kernel 0) it measured slower at N = 4M
     // (1.35 vs 1.20 ms per step) from the scattered x, v accesses.
     c->fuse_update = 0;
+    // FP32-mixed forces with cell subdivision 1 take each pair once
+    // (Newton's third law, lj_set_tuning kernel 7) unless a flag asks for a
+    // run kernel.
+    c->n3 = (p->precision == LJ_PREC_MIXED && c->p.cell_subdiv == 1 && !c->use_run_kernel) ? 1 : 0;
 
 #define LJ_CREATE_CK(call)            \
     do {                              \
@@ -872,7 +877,15 @@ extern "C" int lj_skin_stats(lj_ctx *c, int64_t *rebuilds, int64_t *steps)
 extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int32_t cells_per_grab)
 {
     if (c) c->gen++;   // captured steps hold the old configuration
-    if (!c || kernel < 0 || kernel > 6 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
+    if (!c || kernel < 0 || kernel > 7 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
+    if (kernel == 7) {   // each pair once (Newton's third law): FP32-mixed, 27-cell stencil
+        if (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2) return LJ_EINVAL;
+        const int r = lj_set_tuning(c, 3, group_width, cells_per_grab);   // gw: for the deterministic fallback
+        if (r != LJ_OK) return r;
+        c->n3 = 1;
+        return LJ_OK;
+    }
+    c->n3 = 0;
     if (kernel == 6) {   // lj_step as one persistent launch per step; forces by the warp kernel
         if (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2) return LJ_EINVAL;
         const int r = lj_set_tuning(c, 3, group_width, cells_per_grab);

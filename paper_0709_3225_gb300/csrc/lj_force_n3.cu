@@ -1,0 +1,564 @@
+// Lennard-Jones forces over cell lists with Newton's third law (FP32-mixed).
+//
+// The method is that of lj_force_warp.cu (Section 3: each particle
+// interacts with the particles of its own cell and of the 26 neighbouring
+// cells; Section 2 pair force), but every pair is evaluated ONCE: the pair
+// force F(r) d / r is added to particle i and subtracted from particle j
+// (Eq. n2_force is antisymmetric in i and j).  A home cell is paired with
+// itself (pairs i < j) and with the 13 neighbours whose offset (dz, dy, dx)
+// is lexicographically positive; the other 13 neighbours pair with it when
+// they are the home cell.  For cell grids of n >= 3 per side no cell pair is
+// visited twice: d and -d cannot both be positive, and no two offsets of
+// the stencil coincide modulo n.
+//
+// Organisation for GB300 (one warp per home cell, persistent grid, dynamic
+// pulls of consecutive cells, as the 27-cell kernel):
+//  * Staging: the half stencil's candidates are taken as one flat index
+//    space (warp-vote stencil lookup), converted to the home-cell-centre
+//    frame, pruned against the home particles' bounding box (rc plus a
+//    0.01 % margin) and appended to SoA arrays X, Y, Z with the particle
+//    index; the home particles come first, in their sorted order.
+//  * Compute ("candidate-stationary"): the warp is A groups of B = 32 / A
+//    lanes (A = 2, or 4 when a cell holds more than 16 home particles).
+//    Lane b of group a owns two candidates of the current block of 2B and
+//    keeps their reactions in registers; it holds up to 8 home particles
+//    (u A + a, u = 0..7) and their partial forces in registers as well.
+//    Every (home, candidate) pair is one packed FP32x2 evaluation; the home
+//    positions are never re-read and the candidates are read once per block.
+//  * After a block the reactions are summed over the A groups (shuffles) and
+//    added to f[j] with one float4 atomic add per candidate (skipped when
+//    zero); after the last block the home partial forces are summed over the
+//    B lanes of their group through a shared-memory transpose and added to
+//    f[i] the same way.  f is zeroed before the launch.
+//  * Energies: per-particle f.w gets half of each pair energy on both sides;
+//    the FP64 totals take each pair once.
+//  * A cell whose pruned half stencil does not fit the warp's slice takes a
+//    plain path over global memory (home particle per lane, reactions
+//    reduced over the warp).
+// The FP32 sums of a particle's force are formed in an order set by the
+// atomics, so forces are not bitwise reproducible between runs (their
+// rounding error is that of any order); the deterministic mode uses the
+// 27-cell kernel.
+#include <string.h>
+
+#include "lj_force_cell.cuh"
+
+namespace {
+
+constexpr int kN3Threads = 128;   // 4 warps per CTA
+constexpr int kN3Home = 8;        // home particles per lane per pass
+constexpr int kN3Half = 14;       // home cell + 13 forward neighbours
+
+// Offset of half-stencil entry e: e = 0 the home cell, e = 1 .. 13 the
+// neighbours with (dz, dy, dx) > 0 lexicographically (x-fastest index
+// 13 + e of the 3 x 3 x 3 block).
+__device__ __forceinline__ void half_delta(int e, int &dx, int &dy, int &dz)
+{
+    const int idx = 13 + e;
+    dx = idx % 3 - 1;
+    dy = (idx / 3) % 3 - 1;
+    dz = idx / 9 - 1;
+}
+
+// 32-bit words of one warp's slice: X, Y, Z, I (cap each), the half-stencil
+// table (14 float4), its prefix sums (15 ints, padded to 16) and the home
+// transpose buffer (8 x 32 float4).
+__host__ __device__ constexpr int n3_slice_words(int cap) { return 4 * cap + 4 * kN3Half + 16 + 4 * kN3Home * 32; }
+
+// Half-stencil table of home cell (cx, cy, cz): stab[e] = (shift to the home
+// frame, first particle), spre[0 .. 14] exclusive prefix sums of the
+// counts.  Returns the total.  Called by all 32 lanes.
+__device__ __forceinline__ int half_table(const int32_t *__restrict__ start, int cx, int cy, int cz, int nc, float cw,
+                                          float4 *stab, int *spre)
+{
+    const int lane = threadIdx.x & 31;
+    int nn = 0;
+    if (lane < kN3Half) {
+        int dx, dy, dz;
+        half_delta(lane, dx, dy, dz);
+        int ux = cx + dx, uy = cy + dy, uz = cz + dz;
+        ux += ux < 0 ? nc : 0;
+        ux -= ux >= nc ? nc : 0;
+        uy += uy < 0 ? nc : 0;
+        uy -= uy >= nc ? nc : 0;
+        uz += uz < 0 ? nc : 0;
+        uz -= uz >= nc ? nc : 0;
+        const int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
+        const int s = start[cn];
+        nn = start[cn + 1] - s;
+        stab[lane] = make_float4((float)dx * cw, (float)dy * cw, (float)dz * cw, __int_as_float(s));
+    }
+    int P = nn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, P, o);
+        if (lane >= o) P += y;
+    }
+    if (lane < kN3Half) spre[lane] = P - nn;
+    if (lane == kN3Half - 1) spre[kN3Half] = P;
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, P, kN3Half - 1);
+}
+
+// One (home particle, candidate pair) evaluation: d = x_home - x_cand for
+// the two candidates j0, j0 + 1; the home particle's force accumulates in
+// (fx, fy, fz) (two partial sums each, combined at the end), the
+// candidates' reactions with the opposite sign in (rx, ry, rz).  SELF: the
+// block holds home particles, and a home-home pair counts only for p < j.
+template <int MODE, bool ENERGY, bool SELF>
+__device__ __forceinline__ void pair2_n3(float hx, float hy, float hz, int p, float2 cx, float2 cy, float2 cz, int j0,
+                                         const WarpParams &k, float2 &fx, float2 &fy, float2 &fz, float2 &fe,
+                                         float2 &fw, float2 &rx, float2 &ry, float2 &rz, float2 &re)
+{
+    const float2 m1 = f2(-1.0f);
+    const float2 dx = __ffma2_rn(cx, m1, f2(hx));
+    const float2 dy = __ffma2_rn(cy, m1, f2(hy));
+    const float2 dz = __ffma2_rn(cz, m1, f2(hz));
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    bool ina = r2.x < k.rc2, inb = r2.y < k.rc2;
+    if constexpr (SELF) {
+        ina = ina && (j0 > p);
+        inb = inb && (j0 + 1 > p);
+    }
+    float2 ri, rinv = f2(0.0f);
+    if constexpr (MODE == 2) {
+        rinv.x = ina ? rsqrt_approx(r2.x) : 0.0f;
+        rinv.y = inb ? rsqrt_approx(r2.y) : 0.0f;
+        ri = __fmul2_rn(rinv, rinv);
+    } else {
+        ri.x = ina ? rcp_approx(r2.x) : 0.0f;
+        ri.y = inb ? rcp_approx(r2.y) : 0.0f;
+    }
+    const float2 r6 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+    const float2 t = __ffma2_rn(f2(k.a12), r6, f2(-k.b6));
+    float2 ff = __fmul2_rn(__fmul2_rn(ri, r6), t);
+    if constexpr (MODE == 2) ff = __ffma2_rn(f2(-k.fc), rinv, ff);
+    fx = __ffma2_rn(ff, dx, fx);
+    fy = __ffma2_rn(ff, dy, fy);
+    fz = __ffma2_rn(ff, dz, fz);
+    rx = __ffma2_rn(ff, dx, rx);
+    ry = __ffma2_rn(ff, dy, ry);
+    rz = __ffma2_rn(ff, dz, rz);
+    if constexpr (ENERGY) {
+        float2 u = __fmul2_rn(r6, __ffma2_rn(f2(k.c12), r6, f2(-k.c6)));
+        if constexpr (MODE >= 1) u = __fadd2_rn(u, f2(-k.uc));
+        if constexpr (MODE == 2) u = __ffma2_rn(__ffma2_rn(r2, rinv, f2(-k.rc)), f2(k.fc), u);
+        u.x = ina ? u.x : 0.0f;
+        u.y = inb ? u.y : 0.0f;
+        fe = __fadd2_rn(fe, u);
+        re = __fadd2_rn(re, u);
+        fw = __ffma2_rn(ff, r2, fw);
+    }
+}
+
+__device__ __forceinline__ void add_force(float4 *fout, int idx, float4 v)
+{
+    if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f) atomicAdd(fout + idx, v);
+}
+
+// Compute phase over the staged list (T candidates, home particles at
+// 0 .. n_home-1, padded with far points to a multiple of 32).
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restrict__ fout, const float *X,
+                                           const float *Y, const float *Z, const int *I, float4 *part, int T,
+                                           int n_home, double &eacc, double &wacc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int p0 = 0; p0 < n_home; p0 += 32) {
+        const int hp = min(n_home - p0, 32);
+        const int lgB = hp > 16 ? 3 : 4;
+        const int B = 1 << lgB, A = 32 >> lgB;
+        const int a = lane >> lgB, b = lane & (B - 1);
+        const int nu = (hp + A - 1) >> (5 - lgB);
+        float hx[kN3Home], hy[kN3Home], hz[kN3Home];
+        float2 fx[kN3Home], fy[kN3Home], fz[kN3Home], fe[kN3Home], fw[kN3Home];
+#pragma unroll
+        for (int u = 0; u < kN3Home; u++) {
+            const int q = u * A + a;   // home particle p0 + q of this lane
+            const bool v = u < nu && q < hp;
+            hx[u] = v ? X[p0 + q] : -kFar;
+            hy[u] = v ? Y[p0 + q] : -kFar;
+            hz[u] = v ? Z[p0 + q] : -kFar;
+            fx[u] = fy[u] = fz[u] = fe[u] = fw[u] = f2(0.0f);
+        }
+        const int bs = 2 * B;
+        const int nblk = (T + bs - 1) / bs;
+        for (int blk = 0; blk < nblk; blk++) {
+            const int j0 = blk * bs + 2 * b;
+            const float2 cx = *reinterpret_cast<const float2 *>(X + j0);
+            const float2 cy = *reinterpret_cast<const float2 *>(Y + j0);
+            const float2 cz = *reinterpret_cast<const float2 *>(Z + j0);
+            float2 rx = f2(0.0f), ry = f2(0.0f), rz = f2(0.0f), re = f2(0.0f);
+            if (blk * bs < n_home) {
+#pragma unroll
+                for (int u = 0; u < kN3Home; u++)
+                    if (u < nu)
+                        pair2_n3<MODE, ENERGY, true>(hx[u], hy[u], hz[u], p0 + u * A + a, cx, cy, cz, j0, k, fx[u],
+                                                     fy[u], fz[u], fe[u], fw[u], rx, ry, rz, re);
+            } else {
+#pragma unroll
+                for (int u = 0; u < kN3Home; u++)
+                    if (u < nu)
+                        pair2_n3<MODE, ENERGY, false>(hx[u], hy[u], hz[u], 0, cx, cy, cz, j0, k, fx[u], fy[u], fz[u],
+                                                      fe[u], fw[u], rx, ry, rz, re);
+            }
+            // reactions of the two candidates: sum over the A groups
+            for (int o = B; o < 32; o <<= 1) {
+                rx.x += __shfl_xor_sync(0xffffffffu, rx.x, o);
+                rx.y += __shfl_xor_sync(0xffffffffu, rx.y, o);
+                ry.x += __shfl_xor_sync(0xffffffffu, ry.x, o);
+                ry.y += __shfl_xor_sync(0xffffffffu, ry.y, o);
+                rz.x += __shfl_xor_sync(0xffffffffu, rz.x, o);
+                rz.y += __shfl_xor_sync(0xffffffffu, rz.y, o);
+                if constexpr (ENERGY) {
+                    re.x += __shfl_xor_sync(0xffffffffu, re.x, o);
+                    re.y += __shfl_xor_sync(0xffffffffu, re.y, o);
+                }
+            }
+            if (a < 2) {   // group 0 adds candidate j0, group 1 candidate j0 + 1
+                const int j = j0 + a;
+                if (j < T) {
+                    const float4 v = a == 0 ? make_float4(-rx.x, -ry.x, -rz.x, ENERGY ? 0.5f * re.x : 0.0f)
+                                            : make_float4(-rx.y, -ry.y, -rz.y, ENERGY ? 0.5f * re.y : 0.0f);
+                    add_force(fout, I[j], v);
+                }
+            }
+        }
+        // home forces: sum over the B lanes of each group via a transpose
+        // through shared memory (rows u, lanes a B + b)
+        int hidx = 0;
+        if (lane < hp) hidx = I[p0 + lane];
+#pragma unroll
+        for (int u = 0; u < kN3Home; u++) {
+            if (u < nu) {
+                part[u * 32 + lane] = make_float4(fx[u].x + fx[u].y, fy[u].x + fy[u].y, fz[u].x + fz[u].y,
+                                                  ENERGY ? fe[u].x + fe[u].y : 0.0f);
+                if constexpr (ENERGY) {
+                    eacc += (double)(fe[u].x + fe[u].y);
+                    wacc += (double)(fw[u].x + fw[u].y);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < hp) {
+            const int u = lane >> (5 - lgB), g = lane & (A - 1);
+            const float4 *row = part + u * 32 + g * B;
+            float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int bb = 0; bb < B; bb++) {
+                const float4 q = row[(bb + lane) & (B - 1)];   // rotated: no bank conflicts
+                s.x += q.x;
+                s.y += q.y;
+                s.z += q.z;
+                s.w += q.w;
+            }
+            s.w *= 0.5f;
+            add_force(fout, hidx, s);
+        }
+        __syncwarp();
+    }
+}
+
+// Staging of the half stencil (see the file header).  Returns false, having
+// computed nothing, when the kept candidates would not fit the slice.
+__device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__restrict__ pos, float *X, float *Y,
+                                         float *Z, int *I, const float4 *stab, const int *spre, int Ttot, int s_home,
+                                         int n_home, int &T_out)
+{
+    const int lane = threadIdx.x & 31;
+    float bxl = 3.4e38f, byl = 3.4e38f, bzl = 3.4e38f, bxh = -3.4e38f, byh = -3.4e38f, bzh = -3.4e38f;
+    for (int p0 = 0; p0 < n_home; p0 += 32) {
+        if (p0 + lane < n_home) {
+            const float4 q = __ldg(pos + s_home + p0 + lane);
+            bxl = fminf(bxl, q.x);
+            byl = fminf(byl, q.y);
+            bzl = fminf(bzl, q.z);
+            bxh = fmaxf(bxh, q.x);
+            byh = fmaxf(byh, q.y);
+            bzh = fmaxf(bzh, q.z);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
+        byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
+        bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
+        bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
+        byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
+        bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
+    }
+    const float rcut2 = k.rc2 * 1.0001f;
+    const unsigned lt = (1u << lane) - 1u;
+    // warp-vote stencil lookup (as the 27-cell kernel): lane e holds entry
+    // e's first candidate s_e; lane j the index of the j-th non-empty entry
+    const int s_e = lane < kN3Half ? spre[lane] : 0x7fffffff;
+    const bool ne = lane < kN3Half && spre[lane + 1] > s_e;
+    const unsigned nem = __ballot_sync(0xffffffffu, ne);
+    if (ne) I[__popc(nem & lt)] = lane;
+    __syncwarp();
+    const int j_entry = lane < __popc(nem) ? I[lane] : 0;
+    __syncwarp();
+    const unsigned le = (2u << lane) - 1u;
+    int T = 0;
+    for (int t0 = 0; t0 < Ttot; t0 += 32 * kStageBatch) {
+        float4 q[kStageBatch], sh[kStageBatch];
+#pragma unroll
+        for (int u = 0; u < kStageBatch; u++) {
+            const int t = t0 + 32 * u + lane;
+            const int tb = t0 + 32 * u;
+            const int o = s_e - tb;
+            const unsigned inside = __reduce_or_sync(0xffffffffu, (ne && o >= 1 && o <= 31) ? (1u << o) : 0u);
+            const int jc = __popc(__ballot_sync(0xffffffffu, ne && o <= 0)) - 1 + __popc(inside & le);
+            const int kc = __shfl_sync(0xffffffffu, j_entry, jc & 31);
+            const int kb = __shfl_sync(0xffffffffu, s_e, kc);
+            q[u] = make_float4(kFar, kFar, kFar, 0.f);
+            sh[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < Ttot) {
+                sh[u] = stab[kc];
+                q[u] = __ldg(pos + __float_as_int(sh[u].w) + (t - kb));
+            }
+        }
+        bool full = false;
+#pragma unroll
+        for (int u = 0; u < kStageBatch; u++) {
+            if (T + 64 > k.cap) {   // this round (<= 32) plus the padding might not fit
+                full = true;
+                break;
+            }
+            const int t = t0 + 32 * u + lane;
+            const float cx = q[u].x + sh[u].x;
+            const float cy = q[u].y + sh[u].y;
+            const float cz = q[u].z + sh[u].z;
+            const float dx = fmaxf(fmaxf(bxl - cx, cx - bxh), 0.f);
+            const float dy = fmaxf(fmaxf(byl - cy, cy - byh), 0.f);
+            const float dz = fmaxf(fmaxf(bzl - cz, cz - bzh), 0.f);
+            const bool keep = t < Ttot && dx * dx + dy * dy + dz * dz < rcut2;
+            const unsigned kept = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int sl = T + __popc(kept & lt);
+                X[sl] = cx;
+                Y[sl] = cy;
+                Z[sl] = cz;
+                I[sl] = __float_as_int(q[u].w);
+            }
+            T += __popc(kept);
+        }
+        if (full) {
+            __syncwarp();
+            return false;
+        }
+    }
+    X[T + lane] = kFar;   // padding to the next multiple of 32 (T + 32 <= cap)
+    Y[T + lane] = kFar;
+    Z[T + lane] = kFar;
+    __syncwarp();
+    T_out = T;
+    return true;
+}
+
+// Plain path for a cell whose pruned half stencil overflows the slice: lane
+// = home particle, candidates read from global memory (all lanes the same
+// one), reactions summed over the warp.
+template <int MODE, bool ENERGY>
+__device__ void n3_plain(const WarpParams &k, const float4 *__restrict__ pos, float4 *__restrict__ fout,
+                         const float4 *stab, const int *spre, int s_home, int n_home, double &eacc, double &wacc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int p0 = 0; p0 < n_home; p0 += 32) {
+        const int i = p0 + lane;
+        const bool vi = i < n_home;
+        const float4 pi = __ldg(pos + s_home + (vi ? i : 0));
+        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, w = 0.f;
+        for (int kk = 0; kk < kN3Half; kk++) {
+            const float4 sh = stab[kk];
+            const int s = __float_as_int(sh.w);
+            const int nn = spre[kk + 1] - spre[kk];
+            const float xs = pi.x - sh.x, ys = pi.y - sh.y, zs = pi.z - sh.z;
+            for (int j = (kk == 0 ? p0 + 1 : 0); j < nn; j++) {
+                const float4 q = __ldg(pos + s + j);
+                const float dx = xs - q.x, dy = ys - q.y, dz = zs - q.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const bool in = vi && r2 < k.rc2 && (kk != 0 || j > i);
+                float ri, rinv = 0.0f;
+                if constexpr (MODE == 2) {
+                    rinv = in ? rsqrt_approx(r2) : 0.0f;
+                    ri = rinv * rinv;
+                } else {
+                    ri = in ? rcp_approx(r2) : 0.0f;
+                }
+                const float r6 = ri * ri * ri;
+                float ff = ri * r6 * (k.a12 * r6 - k.b6);
+                if constexpr (MODE == 2) ff -= k.fc * rinv;
+                float u = 0.0f;
+                if constexpr (ENERGY) {
+                    u = r6 * (k.c12 * r6 - k.c6);
+                    if constexpr (MODE >= 1) u -= k.uc;
+                    if constexpr (MODE == 2) u += (r2 * rinv - k.rc) * k.fc;
+                    u = in ? u : 0.0f;
+                    e += u;
+                    w += ff * r2;
+                }
+                fx += ff * dx;
+                fy += ff * dy;
+                fz += ff * dz;
+                float rx = ff * dx, ry = ff * dy, rz = ff * dz, ru = u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    rx += __shfl_xor_sync(0xffffffffu, rx, o);
+                    ry += __shfl_xor_sync(0xffffffffu, ry, o);
+                    rz += __shfl_xor_sync(0xffffffffu, rz, o);
+                    if constexpr (ENERGY) ru += __shfl_xor_sync(0xffffffffu, ru, o);
+                }
+                if (lane == 0) add_force(fout, __float_as_int(q.w), make_float4(-rx, -ry, -rz, 0.5f * ru));
+            }
+        }
+        if (vi) {
+            add_force(fout, __float_as_int(pi.w), make_float4(fx, fy, fz, 0.5f * e));
+            if constexpr (ENERGY) {
+                eacc += (double)e;
+                wacc += (double)w;
+            }
+        }
+    }
+}
+
+template <int MODE, bool ENERGY>
+__global__ void __launch_bounds__(kN3Threads, 4) k_force_n3(WarpParams k, const float4 *__restrict__ pos,
+                                                         const int32_t *__restrict__ start, float4 *__restrict__ fout,
+                                                         double *__restrict__ partial)
+{
+    extern __shared__ __align__(16) float nsmem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float *slice = nsmem + (size_t)warp * n3_slice_words(k.cap);
+    float *X = slice;
+    float *Y = X + k.cap;
+    float *Z = Y + k.cap;
+    int *I = reinterpret_cast<int *>(Z + k.cap);
+    float4 *stab = reinterpret_cast<float4 *>(I + k.cap);
+    int *spre = reinterpret_cast<int *>(stab + kN3Half);
+    float4 *part = reinterpret_cast<float4 *>(spre + 16);
+    const int nc = k.nc;
+    double eacc = 0.0, wacc = 0.0;
+    auto one_cell = [&](int64_t c) {
+        const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+        __syncwarp();   // the slice still holds the previous cell's data
+        const int tot = half_table(start, cx, cy, cz, nc, k.cw, stab, spre);
+        const int n_home = spre[1];
+        if (n_home == 0) return;
+        const int s_home = __float_as_int(stab[0].w);
+        int T = 0;
+        if (tot <= 2 * k.cap && n3_stage(k, pos, X, Y, Z, I, stab, spre, tot, s_home, n_home, T))
+            n3_compute<MODE, ENERGY>(k, fout, X, Y, Z, I, part, T, n_home, eacc, wacc);
+        else
+            n3_plain<MODE, ENERGY>(k, pos, fout, stab, spre, s_home, n_home, eacc, wacc);
+    };
+    if (k.grab > 0) {
+        for (;;) {
+            unsigned c0 = 0;
+            if (lane == 0) c0 = atomicAdd(k.work, (unsigned)k.grab);
+            c0 = __shfl_sync(0xffffffffu, c0, 0);
+            if ((int64_t)c0 >= k.ncell) break;
+            const int64_t c1 = min((int64_t)c0 + k.grab, k.ncell);
+            for (int64_t c = c0; c < c1; c++) one_cell(c);
+        }
+    } else {
+        const int64_t nwarps = (int64_t)gridDim.x * (kN3Threads / 32);
+        for (int64_t c = (int64_t)blockIdx.x * (kN3Threads / 32) + warp; c < k.ncell; c += nwarps) one_cell(c);
+    }
+    if constexpr (ENERGY) {
+        __shared__ double red[2 * (kN3Threads / 32)];
+        for (int o = 16; o > 0; o >>= 1) {
+            eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+            wacc += __shfl_xor_sync(0xffffffffu, wacc, o);
+        }
+        if (lane == 0) {
+            red[2 * warp] = eacc;
+            red[2 * warp + 1] = wacc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double es = 0.0, ws = 0.0;
+            for (int q = 0; q < kN3Threads / 32; q++) {
+                es += red[2 * q];
+                ws += red[2 * q + 1];
+            }
+            partial[2 * blockIdx.x] = es;
+            partial[2 * blockIdx.x + 1] = ws;
+        }
+    }
+}
+
+void *n3_kernel(int mode, bool energy)
+{
+    switch (mode * 2 + (energy ? 1 : 0)) {
+        case 0: return (void *)k_force_n3<0, false>;
+        case 1: return (void *)k_force_n3<0, true>;
+        case 2: return (void *)k_force_n3<1, false>;
+        case 3: return (void *)k_force_n3<1, true>;
+        case 4: return (void *)k_force_n3<2, false>;
+        default: return (void *)k_force_n3<2, true>;
+    }
+}
+
+}  // namespace
+
+cudaError_t n3_force_configure(lj_ctx *c)
+{
+    // Staged candidates per warp: the pruned half stencil of a fluid cell
+    // (~125 at rho 0.84) plus 32 padding, with room for a Poisson spread of
+    // the raw half stencil m = 14 n_cell (4 sqrt(m) + 32), at least 192.
+    const double mean = c->ncell > 0 ? (double)c->p.n / (double)c->ncell : 0.0;
+    const double m = kN3Half * mean;
+    int cap = (int)(m + 4.0 * sqrt(m)) + 64;
+    cap = cap < 192 ? 192 : cap;
+    cap = (cap + 31) & ~31;
+    const int max_cap = ((227 * 1024 - 2 * (kN3Threads / 32) * 8) / (4 * (kN3Threads / 32)) -
+                         (4 * kN3Half + 16 + 4 * kN3Home * 32)) / 4 & ~31;
+    if (cap > max_cap) cap = max_cap;
+    c->n3cap = cap;
+    c->n3_smem = (kN3Threads / 32) * n3_slice_words(cap) * (int)sizeof(float);
+    int minblk = 1 << 30;
+    for (int mode = 0; mode < 3; mode++)
+        for (int en = 0; en < 2; en++) {
+            void *kern = n3_kernel(mode, en != 0);
+            cudaError_t e = raise_dyn_smem(kern, c->n3_smem);
+            if (e != cudaSuccess) return e;
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kN3Threads, c->n3_smem);
+            if (e != cudaSuccess) return e;
+            if (en == 0 && nb < minblk) minblk = nb;   // the energy kernels get the same grid
+        }
+    if (minblk < 1) minblk = 1;
+    int64_t need = (c->ncell + kN3Threads / 32 - 1) / (kN3Threads / 32);
+    int64_t grid = (int64_t)minblk * c->nsm;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    c->n3_grid = (int)grid;
+    return cudaSuccess;
+}
+
+cudaError_t launch_force_n3(lj_ctx *c, void *f, bool energy)
+{
+    if (c->p.n == 0) return cudaSuccess;
+    WarpParams k = warp_params_of(c);
+    k.cap = c->n3cap;
+    const float4 *pos = (const float4 *)c->pos;
+    const int32_t *start = c->start;
+    double *partial = c->partial;
+    void *args[] = {&k, (void *)&pos, (void *)&start, &f, &partial};
+    if (c->timing && c->ev_used + 2 <= c->nev) cudaEventRecord(c->ev[c->ev_used], c->stream);
+    cudaError_t e = cudaMemsetAsync(f, 0, (size_t)c->p.n * sizeof(float4), c->stream);
+    if (e == cudaSuccess)
+        e = cudaLaunchKernel(n3_kernel(c->p.shift_mode, energy), dim3(c->n3_grid), dim3(kN3Threads), args, c->n3_smem,
+                             c->stream);
+    if (c->timing && c->ev_used + 2 <= c->nev) {
+        cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+        c->ev_used += 2;
+    }
+    c->npartial = c->n3_grid;
+    c->kernel_launches++;
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}

@@ -214,6 +214,9 @@ cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
     if (c->p.precision == LJ_PREC_FP64) return launch_force_w64(c, f, energy);
     // tuning choice: stencils bulk-copied one cell ahead (lj_force_pipe.cu)
     if (c->p.cell_subdiv != 2 && c->pipe) return launch_force_pipe(c, f, energy);
+    // each pair once (lj_force_n3.cu); its atomic sums have no fixed order,
+    // so the deterministic in-cell mode keeps this 27-cell kernel
+    if (c->p.cell_subdiv != 2 && c->n3 && !c->deterministic) return launch_force_n3(c, f, energy);
     KickDriftBin kd;
     memset(&kd, 0, sizeof(kd));
     return launch_warp(c, warp_kernel(c->p.cell_subdiv, c->p.shift_mode, energy, false, c->gw), warp_params_of(c), f, kd);

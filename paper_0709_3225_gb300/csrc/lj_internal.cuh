@@ -69,6 +69,9 @@ struct lj_ctx {
     // pipelined warp kernel (lj_force_pipe.cu): slice capacities, launch shape
     int pcap, praw, pipe_smem, pipe_grid;
     int pipe;            // tuning: 1 = warp kernel with bulk-copied stencils (kernel 5)
+    // Newton's-third-law warp kernel (lj_force_n3.cu, tuning kernel 7, the
+    // FP32-mixed default for cell subdivision 1): slice capacity, launch shape
+    int n3, n3cap, n3_smem, n3_grid;
     int fuse_update;     // warp kernel applies the velocity-Verlet update (lj_step)
     int grab;            // tuning: cells per work pull in the warp kernel (0 = static)
     int w64_lcap;        // FP64 warp kernel: list entries per warp
@@ -289,3 +292,7 @@ cudaError_t launch_force_aop(lj_ctx *c, void *f, bool energy);
 // All-pairs forces (lj_n2.cu); energies into c->scalars[0..1] when energy.
 cudaError_t launch_forces_n2(lj_ctx *c, const double *x, void *f, bool energy);
 cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bool last);
+// Newton's-third-law warp kernel (lj_force_n3.cu): configuration, and a
+// launch that zeroes f and adds every pair's force to both particles.
+cudaError_t n3_force_configure(lj_ctx *c);
+cudaError_t launch_force_n3(lj_ctx *c, void *f, bool energy);

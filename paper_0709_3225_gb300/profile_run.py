@@ -2,7 +2,8 @@
 
   python -m paper_0709_3225_gb300.profile_run --op force --n-fcc 80 --reps 3
 
-Builds a jittered FCC liquid of 4 n^3 particles at rho = 0.8442, then runs
+Builds a jittered FCC liquid of 4 n^3 particles at rho = 0.8442 (or the
+lattice itself, ``--lattice``), then runs
 ``--reps`` force evaluations (``--op force``), velocity-Verlet steps
 (``--op step``) or force VJPs with a seeded Gaussian cotangent (``--op
 vjp``) through the C ABI after one untimed warm-up, and prints the
@@ -51,14 +52,19 @@ def main(argv=None) -> int:
     ap.add_argument("--flags", type=int, default=0)
     ap.add_argument("--subdiv", type=int, default=1, help="cell subdivision k (1 or 2)")
     ap.add_argument("--group-width", type=int, default=None, help="warp-kernel lane-group width (0 = per cell)")
+    ap.add_argument("--kernel", type=int, default=None, help="lj_set_tuning force kernel (default: the context's)")
+    ap.add_argument("--lattice", action="store_true", help="the FCC lattice itself instead of a jittered one")
     args = ap.parse_args(argv)
     if args.op == "batch":
         return run_batch(args.reps)
-    x, L = inputs.jittered_fcc(args.n_fcc, args.rho, 0.1, 1)
+    if args.lattice:
+        x, L = inputs.fcc(args.n_fcc, args.rho)
+    else:
+        x, L = inputs.jittered_fcc(args.n_fcc, args.rho, 0.1, 1)
     v = inputs.velocities(x.shape[0], 1.0, 1)
     s = lj.System(x, v, L, precision=args.precision, flags=args.flags, cell_subdiv=args.subdiv)
-    if args.group_width is not None:
-        lj.lj_set_tuning(s.ctx, 3, args.group_width, 4)
+    if args.group_width is not None or args.kernel is not None:
+        lj.lj_set_tuning(s.ctx, 3 if args.kernel is None else args.kernel, args.group_width or 0, 4)
     s.forces()
     g = dx = dp = None
     if args.op == "vjp":

@@ -90,7 +90,7 @@ def test_context_reuse_and_streams():
     other.close()
 
 
-@pytest.mark.parametrize("kernel,grab", [(3, 0), (3, 4), (1, 0)])
+@pytest.mark.parametrize("kernel,grab", [(3, 0), (3, 4), (1, 0), (7, 4), (7, 0)])
 def test_nonfinite_particles_go_to_the_extra_cell(oracle_mod, kernel, grab):
     """Non-finite particles are binned past the grid: the finite ones keep
     their exact cells and forces, and the error is still reported."""

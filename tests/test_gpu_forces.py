@@ -25,12 +25,13 @@ TOL = {"mixed": dict(rms=1e-5, dr=6e-7, ds=1e-5, e=2e-6, band=1e-5),
        "fp64": dict(rms=1e-12, rel=1e-10, e=1e-11, band=1e-12)}
 
 
-def _gpu_forces(x, L, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5, subdiv=1, gw=None):
+def _gpu_forces(x, L, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5, subdiv=1, gw=None, kernel=None,
+                grab=4):
     from paper_0709_3225_gb300 import lj
     s = lj.System(x, None, L, precision=precision, shift_mode=mode, flags=flags, eps=eps, sigma=sigma, rc=rc,
                   cell_subdiv=subdiv)
-    if gw is not None:
-        lj.lj_set_tuning(s.ctx, 3, gw, 4)
+    if gw is not None or kernel is not None:
+        lj.lj_set_tuning(s.ctx, 3 if kernel is None else kernel, gw or 0, grab)
     e, w = s.forces(energy=True)
     f = s.f.double().cpu().numpy()
     s.check()
@@ -38,8 +39,9 @@ def _gpu_forces(x, L, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5, su
     return f, e, w
 
 
-def _check(x, L, oracle_mod, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5, subdiv=1, gw=None):
-    f, e, w = _gpu_forces(x, L, precision, mode, flags, eps, sigma, rc, subdiv, gw)
+def _check(x, L, oracle_mod, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=2.5, subdiv=1, gw=None,
+           kernel=None, grab=4):
+    f, e, w = _gpu_forces(x, L, precision, mode, flags, eps, sigma, rc, subdiv, gw, kernel, grab)
     fo, epo, eo, wo = oracle_mod.forces_cells(x, L, eps=eps, sigma=sigma, rc=rc, mode=mode, k=subdiv)
     t = TOL[precision]
     near = oracle_mod.near_cutoff(x, L, rc=rc, band=t["band"])
@@ -68,6 +70,32 @@ def _check(x, L, oracle_mod, precision, mode=1, flags=0, eps=1.0, sigma=1.0, rc=
 def test_liquid_2k(oracle_mod, precision, mode):
     x, L = inputs.jittered_fcc(8, 0.8442, 0.1, 1)
     _check(x, L, oracle_mod, precision, mode)
+
+
+@pytest.mark.parametrize("kernel", [3, 7])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("state", ["liquid", "dense", "rho095", "cluster", "three_cells", "dilute"])
+def test_pairs_once_and_27_cell_kernels(oracle_mod, kernel, mode, state):
+    """The kernel that evaluates each pair once (Newton's third law, half
+    stencil, kernel 7: the FP32-mixed default) and the 27-cell kernel (3)
+    against the oracle: a liquid; rho = 2 (cells of ~32 particles: the
+    four-group layout and more than 32 home particles per pass); rho = 0.95
+    (cells over 16); a dense blob in a dilute gas (the plain path of cells
+    whose half stencil overflows the slice); 3 cells per side; a dilute gas."""
+    if state == "liquid":
+        x, L = inputs.jittered_fcc(8, 0.8442, 0.1, 61)
+    elif state == "dense":
+        x, L = inputs.jittered_fcc(8, 2.0, 0.05, 62)
+    elif state == "rho095":
+        x, L = inputs.jittered_fcc(9, 0.95, 0.1, 63)
+    elif state == "cluster":
+        x, L = dense_cluster_state(64)
+    elif state == "three_cells":
+        x, L = inputs.jittered_fcc(5, 0.8442, 0.1, 65)
+    else:
+        x, L = inputs.jittered_fcc(7, 0.2, 0.2, 66)
+    for grab in (0, 4):
+        _check(x, L, oracle_mod, "mixed", mode, kernel=kernel, grab=grab)
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])

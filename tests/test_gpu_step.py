@@ -38,11 +38,13 @@ def test_trajectory_matches_oracle(oracle_mod, precision, xtol, vtol, mode):
 
 
 @pytest.mark.parametrize("kernel,grab,subdiv", [(0, 0, 1), (3, 0, 1), (3, 1, 1), (3, 8, 1), (1, 0, 1),
-                                                (3, 4, 2), (0, 4, 2), (6, 1, 1), (6, 4, 1)])
+                                                (3, 4, 2), (0, 4, 2), (6, 1, 1), (6, 4, 1), (7, 0, 1), (7, 1, 1),
+                                                (7, 4, 1)])
 def test_update_paths_agree(oracle_mod, kernel, grab, subdiv):
     """The fused update (kernel 0), the separate update (3), the run kernel
-    (1) and the persistent one-launch step (6), with cell subdivision 1 or
-    2, integrate the same trajectory (force-shifted, FP32 rounding only)."""
+    (1), the persistent one-launch step (6) and the kernel that takes each
+    pair once (7), with cell subdivision 1 or 2, integrate the same
+    trajectory (force-shifted, FP32 rounding only)."""
     from paper_0709_3225_gb300 import lj
     x, v, L = _liquid(seed=17)
     xo, vo = x.copy(), v.copy()
@@ -152,7 +154,8 @@ def test_drift_131k_mixed_vs_fp64():
 
 
 @pytest.mark.parametrize("kernel,skin,det", [(3, 0.0, 0), (0, 0.0, 0), (3, 0.4, 0), (1, 0.0, 0), (3, 0.0, 1),
-                                             (0, 0.0, 1), (3, 0.4, 1), (6, 0.0, 0), (6, 0.4, 0), (6, 0.0, 1)])
+                                             (0, 0.0, 1), (3, 0.4, 1), (6, 0.0, 0), (6, 0.4, 0), (6, 0.0, 1),
+                                             (7, 0.0, 0), (7, 0.4, 0), (7, 0.0, 1)])
 def test_graph_replay_matches_oracle(oracle_mod, kernel, skin, det):
     """lj_step with graph replay of its middle steps (lj_set_graph): the same
     trajectory as the oracle, for the separate and fused updates, cells with a
@@ -174,7 +177,7 @@ def test_graph_replay_matches_oracle(oracle_mod, kernel, skin, det):
     # fresh arrays: the captured step must not be reused on the old pointers
     x2, v2, f2 = s.x.clone(), s.v.clone(), s.f.clone()
     lj.lj_step(s.ctx, x2, v2, f2, 7)
-    if kernel in (3, 6):
+    if kernel in (3, 6, 7):
         lj.lj_set_tuning(s.ctx, kernel, 8, 4)   # new configuration: captured again
     lj.lj_step(s.ctx, x2, v2, f2, 7)
     s.check()
