@@ -16,15 +16,15 @@
 //  * Staging: the half stencil's candidates are taken as one flat index
 //    space (warp-vote stencil lookup), converted to the home-cell-centre
 //    frame, pruned against the home particles' bounding box (rc plus a
-//    0.01 % margin) and appended to SoA arrays X, Y, Z with the particle
-//    index; the home particles come first, in their sorted order.
-//  * Compute ("candidate-stationary"): the warp is A groups of B = 32 / A
-//    lanes (A = 2, or 4 when a cell holds more than 16 home particles).
-//    Lane b of group a owns two candidates of the current block of 2B and
-//    keeps their reactions in registers; it holds up to 8 home particles
-//    (u A + a, u = 0..7) and their partial forces in registers as well.
-//    Every (home, candidate) pair is one packed FP32x2 evaluation; the home
-//    positions are never re-read and the candidates are read once per block.
+//    0.01 % margin; the box comes from the first staging round, where the
+//    home particles are) and appended as float4 (x, y, z, particle index);
+//    the home particles come first, in their sorted order.
+//  * Compute: the warp is A groups of B = 32 / A lanes (A = 2, or 4 when a
+//    pass holds more than 16 home particles).  Lane (a, b) holds up to 8
+//    home particles (u A + a, u = 0..7) as four FP32x2 pairs with their
+//    partial forces, and takes candidate b of each block of B; one packed
+//    evaluation covers two home particles against that candidate, whose
+//    reaction stays in registers for the block.
 //  * After a block the reactions are summed over the A groups (shuffles) and
 //    added to f[j] with one float4 atomic add per candidate (skipped when
 //    zero); after the last block the home partial forces are summed over the
@@ -60,8 +60,9 @@ __device__ __forceinline__ void half_delta(int e, int &dx, int &dy, int &dz)
     dz = idx / 9 - 1;
 }
 
-// 32-bit words of one warp's slice: X, Y, Z, I (cap each), the half-stencil
-// table (14 float4), its prefix sums (15 ints, padded to 16) and the home
+// 32-bit words of one warp's slice: the staged candidates S (cap float4:
+// x, y, z in the home frame and the particle index), the half-stencil table
+// (14 float4), its prefix sums (15 ints, padded to 16) and the home
 // transpose buffer (8 x 32 float4).
 __host__ __device__ constexpr int n3_slice_words(int cap) { return 4 * cap + 4 * kN3Half + 16 + 4 * kN3Home * 32; }
 
@@ -83,14 +84,14 @@ __device__ __forceinline__ int half_table(const int32_t *__restrict__ start, int
         uy -= uy >= nc ? nc : 0;
         uz += uz < 0 ? nc : 0;
         uz -= uz >= nc ? nc : 0;
-        const int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
-        const int s = start[cn];
-        nn = start[cn + 1] - s;
+        const int cn = ux + nc * (uy + nc * uz);   // < nc^3 < 2^31
+        const int s = __ldg(start + cn);
+        nn = __ldg(start + cn + 1) - s;
         stab[lane] = make_float4((float)dx * cw, (float)dy * cw, (float)dz * cw, __int_as_float(s));
     }
     int P = nn;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < 16; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, P, o);
         if (lane >= o) P += y;
     }
@@ -100,27 +101,28 @@ __device__ __forceinline__ int half_table(const int32_t *__restrict__ start, int
     return __shfl_sync(0xffffffffu, P, kN3Half - 1);
 }
 
-// One (home particle, candidate pair) evaluation: d = x_home - x_cand for
-// the two candidates j0, j0 + 1; the home particle's force accumulates in
-// (fx, fy, fz) (two partial sums each, combined at the end), the
-// candidates' reactions with the opposite sign in (rx, ry, rz).  SELF: the
-// block holds home particles, and a home-home pair counts only for p < j.
+// One (home pair, candidate) evaluation: d = x_home - x_cand for the two
+// home particles s0, s1 of (hx, hy, hz) and one candidate j broadcast in
+// (cx, cy, cz).  The home particles' forces accumulate in (fx, fy, fz), the
+// candidate's reaction, with the opposite sign and as two partial sums, in
+// (rx, ry, rz).  SELF: the block holds home particles, and a home-home pair
+// counts only for s < j.
 template <int MODE, bool ENERGY, bool SELF>
-__device__ __forceinline__ void pair2_n3(float hx, float hy, float hz, int p, float2 cx, float2 cy, float2 cz, int j0,
-                                         const WarpParams &k, float2 &fx, float2 &fy, float2 &fz, float2 &fe,
-                                         float2 &fw, float2 &rx, float2 &ry, float2 &rz, float2 &re)
+__device__ __forceinline__ void pair2_n3(float2 hx, float2 hy, float2 hz, int s0, int s1, float2 cx, float2 cy,
+                                         float2 cz, int j, const WarpParams &k, float2 &fx, float2 &fy, float2 &fz,
+                                         float2 &fe, float2 &fw, float2 &rx, float2 &ry, float2 &rz, float2 &re)
 {
     const float2 m1 = f2(-1.0f);
-    const float2 dx = __ffma2_rn(cx, m1, f2(hx));
-    const float2 dy = __ffma2_rn(cy, m1, f2(hy));
-    const float2 dz = __ffma2_rn(cz, m1, f2(hz));
+    const float2 dx = __ffma2_rn(cx, m1, hx);
+    const float2 dy = __ffma2_rn(cy, m1, hy);
+    const float2 dz = __ffma2_rn(cz, m1, hz);
     float2 r2 = __fmul2_rn(dx, dx);
     r2 = __ffma2_rn(dy, dy, r2);
     r2 = __ffma2_rn(dz, dz, r2);
     bool ina = r2.x < k.rc2, inb = r2.y < k.rc2;
     if constexpr (SELF) {
-        ina = ina && (j0 > p);
-        inb = inb && (j0 + 1 > p);
+        ina = ina && (j > s0);
+        inb = inb && (j > s1);
     }
     float2 ri, rinv = f2(0.0f);
     if constexpr (MODE == 2) {
@@ -158,12 +160,15 @@ __device__ __forceinline__ void add_force(float4 *fout, int idx, float4 v)
     if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f) atomicAdd(fout + idx, v);
 }
 
-// Compute phase over the staged list (T candidates, home particles at
-// 0 .. n_home-1, padded with far points to a multiple of 32).
+// Compute phase over the staged list S (T candidates, home particles at
+// 0 .. n_home-1, padded with far points to a multiple of 32).  Per pass of
+// up to 32 home particles the warp is A groups of B lanes (A = 2 for up to
+// 16 home particles, else 4); lane (a, b) holds home particles u A + a,
+// u = 0..7, as four FP32x2 pairs (u = 2h, 2h + 1) and takes candidate
+// blk B + b of each block.
 template <int MODE, bool ENERGY>
-__device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restrict__ fout, const float *X,
-                                           const float *Y, const float *Z, const int *I, float4 *part, int T,
-                                           int n_home, double &eacc, double &wacc)
+__device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restrict__ fout, const float4 *S,
+                                           float4 *part, int T, int n_home, double &eacc, double &wacc)
 {
     const int lane = threadIdx.x & 31;
     for (int p0 = 0; p0 < n_home; p0 += 32) {
@@ -171,135 +176,125 @@ __device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restri
         const int lgB = hp > 16 ? 3 : 4;
         const int B = 1 << lgB, A = 32 >> lgB;
         const int a = lane >> lgB, b = lane & (B - 1);
-        const int nu = (hp + A - 1) >> (5 - lgB);
-        float hx[kN3Home], hy[kN3Home], hz[kN3Home];
-        float2 fx[kN3Home], fy[kN3Home], fz[kN3Home], fe[kN3Home], fw[kN3Home];
+        const int nu = (hp + A - 1) >> (5 - lgB);   // home particles per lane
+        const int nh = (nu + 1) >> 1;                // home pairs per lane
+        float2 hx[kN3Home / 2], hy[kN3Home / 2], hz[kN3Home / 2];
+        float2 fx[kN3Home / 2], fy[kN3Home / 2], fz[kN3Home / 2], fe[kN3Home / 2];
+        float2 fw = f2(0.0f);
 #pragma unroll
-        for (int u = 0; u < kN3Home; u++) {
-            const int q = u * A + a;   // home particle p0 + q of this lane
-            const bool v = u < nu && q < hp;
-            hx[u] = v ? X[p0 + q] : -kFar;
-            hy[u] = v ? Y[p0 + q] : -kFar;
-            hz[u] = v ? Z[p0 + q] : -kFar;
-            fx[u] = fy[u] = fz[u] = fe[u] = fw[u] = f2(0.0f);
+        for (int h = 0; h < kN3Home / 2; h++) {
+            const int s0 = 2 * h * A + a, s1 = s0 + A;
+            const bool v0 = s0 < hp, v1 = s1 < hp;
+            const float4 q0 = S[p0 + (v0 ? s0 : 0)];
+            const float4 q1 = S[p0 + (v1 ? s1 : 0)];
+            hx[h] = make_float2(v0 ? q0.x : -kFar, v1 ? q1.x : -kFar);
+            hy[h] = make_float2(v0 ? q0.y : -kFar, v1 ? q1.y : -kFar);
+            hz[h] = make_float2(v0 ? q0.z : -kFar, v1 ? q1.z : -kFar);
+            fx[h] = fy[h] = fz[h] = fe[h] = f2(0.0f);
         }
-        const int bs = 2 * B;
-        const int nblk = (T + bs - 1) / bs;
+        const int nblk = (T + B - 1) >> lgB;
         for (int blk = 0; blk < nblk; blk++) {
-            const int j0 = blk * bs + 2 * b;
-            const float2 cx = *reinterpret_cast<const float2 *>(X + j0);
-            const float2 cy = *reinterpret_cast<const float2 *>(Y + j0);
-            const float2 cz = *reinterpret_cast<const float2 *>(Z + j0);
+            const int j = (blk << lgB) + b;
+            const float4 c = S[j];
+            const float2 cx = f2(c.x), cy = f2(c.y), cz = f2(c.z);
             float2 rx = f2(0.0f), ry = f2(0.0f), rz = f2(0.0f), re = f2(0.0f);
-            if (blk * bs < n_home) {
+            if ((blk << lgB) < n_home) {
 #pragma unroll
-                for (int u = 0; u < kN3Home; u++)
-                    if (u < nu)
-                        pair2_n3<MODE, ENERGY, true>(hx[u], hy[u], hz[u], p0 + u * A + a, cx, cy, cz, j0, k, fx[u],
-                                                     fy[u], fz[u], fe[u], fw[u], rx, ry, rz, re);
+                for (int h = 0; h < kN3Home / 2; h++)
+                    if (h < nh)
+                        pair2_n3<MODE, ENERGY, true>(hx[h], hy[h], hz[h], p0 + 2 * h * A + a, p0 + (2 * h + 1) * A + a,
+                                                     cx, cy, cz, j, k, fx[h], fy[h], fz[h], fe[h], fw, rx, ry, rz, re);
             } else {
 #pragma unroll
-                for (int u = 0; u < kN3Home; u++)
-                    if (u < nu)
-                        pair2_n3<MODE, ENERGY, false>(hx[u], hy[u], hz[u], 0, cx, cy, cz, j0, k, fx[u], fy[u], fz[u],
-                                                      fe[u], fw[u], rx, ry, rz, re);
+                for (int h = 0; h < kN3Home / 2; h++)
+                    if (h < nh)
+                        pair2_n3<MODE, ENERGY, false>(hx[h], hy[h], hz[h], 0, 0, cx, cy, cz, j, k, fx[h], fy[h], fz[h],
+                                                      fe[h], fw, rx, ry, rz, re);
             }
-            // reactions of the two candidates: sum over the A groups
+            // the candidate's reaction: its two partial sums, then the A groups
+            float sx = rx.x + rx.y, sy = ry.x + ry.y, sz = rz.x + rz.y, se = ENERGY ? re.x + re.y : 0.0f;
             for (int o = B; o < 32; o <<= 1) {
-                rx.x += __shfl_xor_sync(0xffffffffu, rx.x, o);
-                rx.y += __shfl_xor_sync(0xffffffffu, rx.y, o);
-                ry.x += __shfl_xor_sync(0xffffffffu, ry.x, o);
-                ry.y += __shfl_xor_sync(0xffffffffu, ry.y, o);
-                rz.x += __shfl_xor_sync(0xffffffffu, rz.x, o);
-                rz.y += __shfl_xor_sync(0xffffffffu, rz.y, o);
-                if constexpr (ENERGY) {
-                    re.x += __shfl_xor_sync(0xffffffffu, re.x, o);
-                    re.y += __shfl_xor_sync(0xffffffffu, re.y, o);
-                }
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                sz += __shfl_xor_sync(0xffffffffu, sz, o);
+                if constexpr (ENERGY) se += __shfl_xor_sync(0xffffffffu, se, o);
             }
-            if (a < 2) {   // group 0 adds candidate j0, group 1 candidate j0 + 1
-                const int j = j0 + a;
-                if (j < T) {
-                    const float4 v = a == 0 ? make_float4(-rx.x, -ry.x, -rz.x, ENERGY ? 0.5f * re.x : 0.0f)
-                                            : make_float4(-rx.y, -ry.y, -rz.y, ENERGY ? 0.5f * re.y : 0.0f);
-                    add_force(fout, I[j], v);
-                }
-            }
+            if (a == 0 && j < T) add_force(fout, __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
         }
-        // home forces: sum over the B lanes of each group via a transpose
-        // through shared memory (rows u, lanes a B + b)
-        int hidx = 0;
-        if (lane < hp) hidx = I[p0 + lane];
+        // home forces: sum over the B lanes of each group through a transpose
+        // in shared memory (row u, column a B + b); every lane sums 8 entries
 #pragma unroll
-        for (int u = 0; u < kN3Home; u++) {
-            if (u < nu) {
-                part[u * 32 + lane] = make_float4(fx[u].x + fx[u].y, fy[u].x + fy[u].y, fz[u].x + fz[u].y,
-                                                  ENERGY ? fe[u].x + fe[u].y : 0.0f);
-                if constexpr (ENERGY) {
-                    eacc += (double)(fe[u].x + fe[u].y);
-                    wacc += (double)(fw[u].x + fw[u].y);
-                }
+        for (int h = 0; h < kN3Home / 2; h++) {
+            if (2 * h < nu) part[(2 * h) * 32 + lane] = make_float4(fx[h].x, fy[h].x, fz[h].x, fe[h].x);
+            if (2 * h + 1 < nu) part[(2 * h + 1) * 32 + lane] = make_float4(fx[h].y, fy[h].y, fz[h].y, fe[h].y);
+            if constexpr (ENERGY) eacc += (double)(fe[h].x + fe[h].y);
+        }
+        if constexpr (ENERGY) wacc += (double)(fw.x + fw.y);
+        __syncwarp();
+        const int p = A == 2 ? lane >> 1 : lane;            // home particle of this lane
+        const int bh = A == 2 ? (lane & 1) * 8 : 0;         // its half of the B columns
+        const int u = p >> (5 - lgB), g = p & (A - 1);
+        float4 sum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (p < hp) {
+            const float4 *row = part + u * 32 + g * B + bh;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const float4 q = row[(i + lane) & 7];   // rotated: no bank conflicts
+                sum.x += q.x;
+                sum.y += q.y;
+                sum.z += q.z;
+                sum.w += q.w;
             }
         }
-        __syncwarp();
-        if (lane < hp) {
-            const int u = lane >> (5 - lgB), g = lane & (A - 1);
-            const float4 *row = part + u * 32 + g * B;
-            float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            for (int bb = 0; bb < B; bb++) {
-                const float4 q = row[(bb + lane) & (B - 1)];   // rotated: no bank conflicts
-                s.x += q.x;
-                s.y += q.y;
-                s.z += q.z;
-                s.w += q.w;
-            }
-            s.w *= 0.5f;
-            add_force(fout, hidx, s);
+        if (A == 2) {
+            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, 1);
+            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, 1);
+            sum.z += __shfl_xor_sync(0xffffffffu, sum.z, 1);
+            if constexpr (ENERGY) sum.w += __shfl_xor_sync(0xffffffffu, sum.w, 1);
+        }
+        if (p < hp && bh == 0) {
+            sum.w *= 0.5f;
+            add_force(fout, __float_as_int(S[p0 + p].w), sum);
         }
         __syncwarp();
     }
 }
 
-// Staging of the half stencil (see the file header).  Returns false, having
-// computed nothing, when the kept candidates would not fit the slice.
-__device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__restrict__ pos, float *X, float *Y,
-                                         float *Z, int *I, const float4 *stab, const int *spre, int Ttot, int s_home,
-                                         int n_home, int &T_out)
+// Staging of the half stencil (see the file header) into S.  Returns false,
+// having computed nothing, when the kept candidates would not fit the slice.
+__device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__restrict__ pos, float4 *S,
+                                         const float4 *stab, const int *spre, int Ttot, int s_home, int n_home,
+                                         int &T_out)
 {
     const int lane = threadIdx.x & 31;
     float bxl = 3.4e38f, byl = 3.4e38f, bzl = 3.4e38f, bxh = -3.4e38f, byh = -3.4e38f, bzh = -3.4e38f;
-    for (int p0 = 0; p0 < n_home; p0 += 32) {
-        if (p0 + lane < n_home) {
-            const float4 q = __ldg(pos + s_home + p0 + lane);
-            bxl = fminf(bxl, q.x);
-            byl = fminf(byl, q.y);
-            bzl = fminf(bzl, q.z);
-            bxh = fmaxf(bxh, q.x);
-            byh = fmaxf(byh, q.y);
-            bzh = fmaxf(bzh, q.z);
+    if (n_home > 32) {   // bounding box from a pass of its own; else from the first staging round
+        for (int p0 = 0; p0 < n_home; p0 += 32) {
+            if (p0 + lane < n_home) {
+                const float4 q = __ldg(pos + s_home + p0 + lane);
+                bxl = fminf(bxl, q.x);
+                byl = fminf(byl, q.y);
+                bzl = fminf(bzl, q.z);
+                bxh = fmaxf(bxh, q.x);
+                byh = fmaxf(byh, q.y);
+                bzh = fmaxf(bzh, q.z);
+            }
         }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
-        byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
-        bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
-        bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
-        byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
-        bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
     }
     const float rcut2 = k.rc2 * 1.0001f;
     const unsigned lt = (1u << lane) - 1u;
     // warp-vote stencil lookup (as the 27-cell kernel): lane e holds entry
     // e's first candidate s_e; lane j the index of the j-th non-empty entry
+    int *tmp = reinterpret_cast<int *>(S);
     const int s_e = lane < kN3Half ? spre[lane] : 0x7fffffff;
     const bool ne = lane < kN3Half && spre[lane + 1] > s_e;
     const unsigned nem = __ballot_sync(0xffffffffu, ne);
-    if (ne) I[__popc(nem & lt)] = lane;
+    if (ne) tmp[__popc(nem & lt)] = lane;
     __syncwarp();
-    const int j_entry = lane < __popc(nem) ? I[lane] : 0;
+    const int j_entry = lane < __popc(nem) ? tmp[lane] : 0;
     __syncwarp();
     const unsigned le = (2u << lane) - 1u;
+    const int last = k.n - 1;
     int T = 0;
     for (int t0 = 0; t0 < Ttot; t0 += 32 * kStageBatch) {
         float4 q[kStageBatch], sh[kStageBatch];
@@ -312,11 +307,36 @@ __device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__re
             const int jc = __popc(__ballot_sync(0xffffffffu, ne && o <= 0)) - 1 + __popc(inside & le);
             const int kc = __shfl_sync(0xffffffffu, j_entry, jc & 31);
             const int kb = __shfl_sync(0xffffffffu, s_e, kc);
-            q[u] = make_float4(kFar, kFar, kFar, 0.f);
-            sh[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (t < Ttot) {
-                sh[u] = stab[kc];
-                q[u] = __ldg(pos + __float_as_int(sh[u].w) + (t - kb));
+            sh[u] = stab[kc];
+            // past the stencil (t >= Ttot) the index is clamped into the array
+            // and the candidate is not kept
+            q[u] = __ldg(pos + min(__float_as_int(sh[u].w) + (t - kb), last));
+        }
+        if (t0 == 0 && n_home <= 32) {
+            // the home particles are candidates 0 .. n_home-1 of the first round
+            if (lane < n_home) {
+                bxl = bxh = q[0].x;
+                byl = byh = q[0].y;
+                bzl = bzh = q[0].z;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
+                byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
+                bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
+                bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
+                byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
+                bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
+            }
+        } else if (t0 == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
+                byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
+                bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
+                bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
+                byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
+                bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
             }
         }
         bool full = false;
@@ -335,13 +355,7 @@ __device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__re
             const float dz = fmaxf(fmaxf(bzl - cz, cz - bzh), 0.f);
             const bool keep = t < Ttot && dx * dx + dy * dy + dz * dz < rcut2;
             const unsigned kept = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int sl = T + __popc(kept & lt);
-                X[sl] = cx;
-                Y[sl] = cy;
-                Z[sl] = cz;
-                I[sl] = __float_as_int(q[u].w);
-            }
+            if (keep) S[T + __popc(kept & lt)] = make_float4(cx, cy, cz, q[u].w);
             T += __popc(kept);
         }
         if (full) {
@@ -349,9 +363,7 @@ __device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__re
             return false;
         }
     }
-    X[T + lane] = kFar;   // padding to the next multiple of 32 (T + 32 <= cap)
-    Y[T + lane] = kFar;
-    Z[T + lane] = kFar;
+    S[T + lane] = make_float4(kFar, kFar, kFar, 0.0f);   // padding to the next multiple of 32 (T + 32 <= cap)
     __syncwarp();
     T_out = T;
     return true;
@@ -424,33 +436,30 @@ __device__ void n3_plain(const WarpParams &k, const float4 *__restrict__ pos, fl
 }
 
 template <int MODE, bool ENERGY>
-__global__ void __launch_bounds__(kN3Threads, 4) k_force_n3(WarpParams k, const float4 *__restrict__ pos,
+__global__ void __launch_bounds__(kN3Threads, 5) k_force_n3(WarpParams k, const float4 *__restrict__ pos,
                                                          const int32_t *__restrict__ start, float4 *__restrict__ fout,
                                                          double *__restrict__ partial)
 {
     extern __shared__ __align__(16) float nsmem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float *slice = nsmem + (size_t)warp * n3_slice_words(k.cap);
-    float *X = slice;
-    float *Y = X + k.cap;
-    float *Z = Y + k.cap;
-    int *I = reinterpret_cast<int *>(Z + k.cap);
-    float4 *stab = reinterpret_cast<float4 *>(I + k.cap);
+    float4 *S = reinterpret_cast<float4 *>(nsmem + (size_t)warp * n3_slice_words(k.cap));
+    float4 *stab = S + k.cap;
     int *spre = reinterpret_cast<int *>(stab + kN3Half);
     float4 *part = reinterpret_cast<float4 *>(spre + 16);
     const int nc = k.nc;
     double eacc = 0.0, wacc = 0.0;
-    auto one_cell = [&](int64_t c) {
-        const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+    auto one_cell = [&](int64_t c64) {
+        const int c = (int)c64;   // cells < 2^31
+        const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
         __syncwarp();   // the slice still holds the previous cell's data
         const int tot = half_table(start, cx, cy, cz, nc, k.cw, stab, spre);
         const int n_home = spre[1];
         if (n_home == 0) return;
         const int s_home = __float_as_int(stab[0].w);
         int T = 0;
-        if (tot <= 2 * k.cap && n3_stage(k, pos, X, Y, Z, I, stab, spre, tot, s_home, n_home, T))
-            n3_compute<MODE, ENERGY>(k, fout, X, Y, Z, I, part, T, n_home, eacc, wacc);
+        if (tot <= 2 * k.cap && n3_stage(k, pos, S, stab, spre, tot, s_home, n_home, T))
+            n3_compute<MODE, ENERGY>(k, fout, S, part, T, n_home, eacc, wacc);
         else
             n3_plain<MODE, ENERGY>(k, pos, fout, stab, spre, s_home, n_home, eacc, wacc);
     };
@@ -517,7 +526,7 @@ cudaError_t n3_force_configure(lj_ctx *c)
     const int max_cap = ((227 * 1024 - 2 * (kN3Threads / 32) * 8) / (4 * (kN3Threads / 32)) -
                          (4 * kN3Half + 16 + 4 * kN3Home * 32)) / 4 & ~31;
     if (cap > max_cap) cap = max_cap;
-    c->n3cap = cap;
+    c->n3cap = cap;   // float4 slots
     c->n3_smem = (kN3Threads / 32) * n3_slice_words(cap) * (int)sizeof(float);
     int minblk = 1 << 30;
     for (int mode = 0; mode < 3; mode++)

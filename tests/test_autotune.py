@@ -33,7 +33,7 @@ def test_tune_system_and_batch(tmp_path):
     x_before = s.x.clone()
     r = autotune.tune_system(s, 0.8442, steps=4, warmup=3, path=path)
     assert not any("error" in t for t in r["trials"]), r["trials"]
-    assert not r["cached"] and len(r["trials"]) == 17
+    assert not r["cached"] and len(r["trials"]) == len(autotune.system_candidates("mixed"))
     assert {t["subdiv"] for t in r["trials"]} == {1, 2}
     assert torch.equal(s.x, x_before)                 # tuning works on a copy
     s.forces()
