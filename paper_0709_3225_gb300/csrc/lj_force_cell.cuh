@@ -19,6 +19,7 @@ struct WarpParams {
     int64_t ncell;
     float cw;
     float rc2, rc, a12, b6, c12, c6, uc, fc;
+    float inv_nc;                // 1 / nc (cell-id decoding of the pair-once kernel)
 };
 
 __device__ __forceinline__ float rcp_approx(float x)

@@ -66,16 +66,53 @@ __device__ __forceinline__ void half_delta(int e, int &dx, int &dy, int &dz)
 // transpose buffer (8 x 32 float4).
 __host__ __device__ constexpr int n3_slice_words(int cap) { return 4 * cap + 4 * kN3Half + 16 + 4 * kN3Home * 32; }
 
-// Half-stencil table of home cell (cx, cy, cz): stab[e] = (shift to the home
-// frame, first particle), spre[0 .. 14] exclusive prefix sums of the
-// counts.  Returns the total.  Called by all 32 lanes.
-__device__ __forceinline__ int half_table(const int32_t *__restrict__ start, int cx, int cy, int cz, int nc, float cw,
-                                          float4 *stab, int *spre)
+// (c mod n, (c / n) mod n, c / n^2) of a cell id c < 2^24 without integer
+// division: the quotient from an FP32 product (relative error < 2^-22, so
+// off by at most one) and one correction.
+__device__ __forceinline__ int div_small(int c, int n, float inv_n, int &r)
+{
+    int q = __float2int_rz((float)c * inv_n);
+    r = c - q * n;
+    if (r < 0) {
+        q -= 1;
+        r += n;
+    } else if (r >= n) {
+        q += 1;
+        r -= n;
+    }
+    return q;
+}
+
+// inv_nc = 0 (grids of 2^24 cells or more): integer division.
+__device__ __forceinline__ void cell_coords(int c, int nc, float inv_nc, int &cx, int &cy, int &cz)
+{
+    if (inv_nc > 0.0f) {
+        const int q = div_small(c, nc, inv_nc, cx);
+        cz = div_small(q, nc, inv_nc, cy);
+    } else {
+        cx = c % nc;
+        cy = (c / nc) % nc;
+        cz = c / (nc * nc);
+    }
+}
+
+// Half-stencil table, in two parts so that a cell's loads can be issued one
+// cell ahead: half_load reads, for lane e < 14, the first and end particle
+// of entry e of cell c (cell id c < 2^31); half_finish writes stab[e] =
+// (shift to the home frame, first particle) and spre[0 .. 14], the
+// exclusive prefix sums of the counts, and returns the total.  Both are
+// called by all 32 lanes.
+struct HalfLoad {
+    int s, e;
+};
+
+__device__ __forceinline__ HalfLoad half_load(const int32_t *__restrict__ start, int c, int nc, float inv_nc)
 {
     const int lane = threadIdx.x & 31;
-    int nn = 0;
+    HalfLoad t{0, 0};
     if (lane < kN3Half) {
-        int dx, dy, dz;
+        int cx, cy, cz, dx, dy, dz;
+        cell_coords(c, nc, inv_nc, cx, cy, cz);
         half_delta(lane, dx, dy, dz);
         int ux = cx + dx, uy = cy + dy, uz = cz + dz;
         ux += ux < 0 ? nc : 0;
@@ -85,9 +122,20 @@ __device__ __forceinline__ int half_table(const int32_t *__restrict__ start, int
         uz += uz < 0 ? nc : 0;
         uz -= uz >= nc ? nc : 0;
         const int cn = ux + nc * (uy + nc * uz);   // < nc^3 < 2^31
-        const int s = __ldg(start + cn);
-        nn = __ldg(start + cn + 1) - s;
-        stab[lane] = make_float4((float)dx * cw, (float)dy * cw, (float)dz * cw, __int_as_float(s));
+        t.s = __ldg(start + cn);
+        t.e = __ldg(start + cn + 1);
+    }
+    return t;
+}
+
+__device__ __forceinline__ int half_finish(HalfLoad t, float cw, float4 *stab, int *spre)
+{
+    const int lane = threadIdx.x & 31;
+    const int nn = t.e - t.s;
+    if (lane < kN3Half) {
+        int dx, dy, dz;
+        half_delta(lane, dx, dy, dz);
+        stab[lane] = make_float4((float)dx * cw, (float)dy * cw, (float)dz * cw, __int_as_float(t.s));
     }
     int P = nn;
 #pragma unroll
@@ -124,14 +172,18 @@ __device__ __forceinline__ void pair2_n3(float2 hx, float2 hy, float2 hz, int s0
         ina = ina && (j > s0);
         inb = inb && (j > s1);
     }
+    // the reciprocal (square root) of every r^2, then a select: no branch
+    // (r^2 = 0 of a pair outside the count gives inf, which is dropped)
     float2 ri, rinv = f2(0.0f);
     if constexpr (MODE == 2) {
-        rinv.x = ina ? rsqrt_approx(r2.x) : 0.0f;
-        rinv.y = inb ? rsqrt_approx(r2.y) : 0.0f;
+        const float qa = rsqrt_approx(r2.x), qb = rsqrt_approx(r2.y);
+        rinv.x = ina ? qa : 0.0f;
+        rinv.y = inb ? qb : 0.0f;
         ri = __fmul2_rn(rinv, rinv);
     } else {
-        ri.x = ina ? rcp_approx(r2.x) : 0.0f;
-        ri.y = inb ? rcp_approx(r2.y) : 0.0f;
+        const float qa = rcp_approx(r2.x), qb = rcp_approx(r2.y);
+        ri.x = ina ? qa : 0.0f;
+        ri.y = inb ? qb : 0.0f;
     }
     const float2 r6 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
     const float2 t = __ffma2_rn(f2(k.a12), r6, f2(-k.b6));
@@ -177,7 +229,6 @@ __device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restri
         const int B = 1 << lgB, A = 32 >> lgB;
         const int a = lane >> lgB, b = lane & (B - 1);
         const int nu = (hp + A - 1) >> (5 - lgB);   // home particles per lane
-        const int nh = (nu + 1) >> 1;                // home pairs per lane
         float2 hx[kN3Home / 2], hy[kN3Home / 2], hz[kN3Home / 2];
         float2 fx[kN3Home / 2], fy[kN3Home / 2], fz[kN3Home / 2], fe[kN3Home / 2];
         float2 fw = f2(0.0f);
@@ -198,18 +249,18 @@ __device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restri
             const float4 c = S[j];
             const float2 cx = f2(c.x), cy = f2(c.y), cz = f2(c.z);
             float2 rx = f2(0.0f), ry = f2(0.0f), rz = f2(0.0f), re = f2(0.0f);
+            // all four home pairs, also where a lane has fewer home particles
+            // (those sit far away and add nothing): no branches in the loop
             if ((blk << lgB) < n_home) {
 #pragma unroll
                 for (int h = 0; h < kN3Home / 2; h++)
-                    if (h < nh)
-                        pair2_n3<MODE, ENERGY, true>(hx[h], hy[h], hz[h], p0 + 2 * h * A + a, p0 + (2 * h + 1) * A + a,
-                                                     cx, cy, cz, j, k, fx[h], fy[h], fz[h], fe[h], fw, rx, ry, rz, re);
+                    pair2_n3<MODE, ENERGY, true>(hx[h], hy[h], hz[h], p0 + 2 * h * A + a, p0 + (2 * h + 1) * A + a, cx,
+                                                 cy, cz, j, k, fx[h], fy[h], fz[h], fe[h], fw, rx, ry, rz, re);
             } else {
 #pragma unroll
                 for (int h = 0; h < kN3Home / 2; h++)
-                    if (h < nh)
-                        pair2_n3<MODE, ENERGY, false>(hx[h], hy[h], hz[h], 0, 0, cx, cy, cz, j, k, fx[h], fy[h], fz[h],
-                                                      fe[h], fw, rx, ry, rz, re);
+                    pair2_n3<MODE, ENERGY, false>(hx[h], hy[h], hz[h], 0, 0, cx, cy, cz, j, k, fx[h], fy[h], fz[h],
+                                                  fe[h], fw, rx, ry, rz, re);
             }
             // the candidate's reaction: its two partial sums, then the A groups
             float sx = rx.x + rx.y, sy = ry.x + ry.y, sz = rz.x + rz.y, se = ENERGY ? re.x + re.y : 0.0f;
@@ -281,7 +332,10 @@ __device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__re
             }
         }
     }
+    // the margin of the box test (0.01 % of rc^2) covers the FP32 rounding of
+    // the centre and half extents (~1e-7 relative)
     const float rcut2 = k.rc2 * 1.0001f;
+    float bcx = 0.f, bcy = 0.f, bcz = 0.f, bhx = 0.f, bhy = 0.f, bhz = 0.f;
     const unsigned lt = (1u << lane) - 1u;
     // warp-vote stencil lookup (as the 27-cell kernel): lane e holds entry
     // e's first candidate s_e; lane j the index of the j-th non-empty entry
@@ -339,28 +393,31 @@ __device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__re
                 bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
             }
         }
-        bool full = false;
+        if (T + 32 * kStageBatch + 32 > k.cap) {   // this batch plus the padding might not fit
+            __syncwarp();
+            return false;
+        }
+        if (t0 == 0) {   // the box as centre and half extents
+            bcx = 0.5f * (bxl + bxh);
+            bcy = 0.5f * (byl + byh);
+            bcz = 0.5f * (bzl + bzh);
+            bhx = 0.5f * (bxh - bxl);
+            bhy = 0.5f * (byh - byl);
+            bhz = 0.5f * (bzh - bzl);
+        }
 #pragma unroll
         for (int u = 0; u < kStageBatch; u++) {
-            if (T + 64 > k.cap) {   // this round (<= 32) plus the padding might not fit
-                full = true;
-                break;
-            }
             const int t = t0 + 32 * u + lane;
             const float cx = q[u].x + sh[u].x;
             const float cy = q[u].y + sh[u].y;
             const float cz = q[u].z + sh[u].z;
-            const float dx = fmaxf(fmaxf(bxl - cx, cx - bxh), 0.f);
-            const float dy = fmaxf(fmaxf(byl - cy, cy - byh), 0.f);
-            const float dz = fmaxf(fmaxf(bzl - cz, cz - bzh), 0.f);
+            const float dx = fmaxf(fabsf(cx - bcx) - bhx, 0.f);
+            const float dy = fmaxf(fabsf(cy - bcy) - bhy, 0.f);
+            const float dz = fmaxf(fabsf(cz - bcz) - bhz, 0.f);
             const bool keep = t < Ttot && dx * dx + dy * dy + dz * dz < rcut2;
             const unsigned kept = __ballot_sync(0xffffffffu, keep);
             if (keep) S[T + __popc(kept & lt)] = make_float4(cx, cy, cz, q[u].w);
             T += __popc(kept);
-        }
-        if (full) {
-            __syncwarp();
-            return false;
         }
     }
     S[T + lane] = make_float4(kFar, kFar, kFar, 0.0f);   // padding to the next multiple of 32 (T + 32 <= cap)
@@ -449,11 +506,9 @@ __global__ void __launch_bounds__(kN3Threads, 5) k_force_n3(WarpParams k, const 
     float4 *part = reinterpret_cast<float4 *>(spre + 16);
     const int nc = k.nc;
     double eacc = 0.0, wacc = 0.0;
-    auto one_cell = [&](int64_t c64) {
-        const int c = (int)c64;   // cells < 2^31
-        const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    auto one_cell = [&](HalfLoad tl) {
         __syncwarp();   // the slice still holds the previous cell's data
-        const int tot = half_table(start, cx, cy, cz, nc, k.cw, stab, spre);
+        const int tot = half_finish(tl, k.cw, stab, spre);
         const int n_home = spre[1];
         if (n_home == 0) return;
         const int s_home = __float_as_int(stab[0].w);
@@ -469,12 +524,24 @@ __global__ void __launch_bounds__(kN3Threads, 5) k_force_n3(WarpParams k, const 
             if (lane == 0) c0 = atomicAdd(k.work, (unsigned)k.grab);
             c0 = __shfl_sync(0xffffffffu, c0, 0);
             if ((int64_t)c0 >= k.ncell) break;
-            const int64_t c1 = min((int64_t)c0 + k.grab, k.ncell);
-            for (int64_t c = c0; c < c1; c++) one_cell(c);
+            const int c1 = (int)min((int64_t)c0 + k.grab, k.ncell);
+            // the next cell's table loads are issued before this cell's work
+            HalfLoad nxt = half_load(start, (int)c0, nc, k.inv_nc);
+            for (int c = (int)c0; c < c1; c++) {
+                const HalfLoad cur = nxt;
+                if (c + 1 < c1) nxt = half_load(start, c + 1, nc, k.inv_nc);
+                one_cell(cur);
+            }
         }
     } else {
-        const int64_t nwarps = (int64_t)gridDim.x * (kN3Threads / 32);
-        for (int64_t c = (int64_t)blockIdx.x * (kN3Threads / 32) + warp; c < k.ncell; c += nwarps) one_cell(c);
+        const int nwarps = gridDim.x * (kN3Threads / 32);
+        int c = blockIdx.x * (kN3Threads / 32) + warp;
+        HalfLoad nxt = half_load(start, c < k.ncell ? c : 0, nc, k.inv_nc);
+        for (; c < k.ncell; c += nwarps) {
+            const HalfLoad cur = nxt;
+            if (c + nwarps < k.ncell) nxt = half_load(start, c + nwarps, nc, k.inv_nc);
+            one_cell(cur);
+        }
     }
     if constexpr (ENERGY) {
         __shared__ double red[2 * (kN3Threads / 32)];
@@ -553,6 +620,7 @@ cudaError_t launch_force_n3(lj_ctx *c, void *f, bool energy)
     if (c->p.n == 0) return cudaSuccess;
     WarpParams k = warp_params_of(c);
     k.cap = c->n3cap;
+    k.inv_nc = c->ncell < (1 << 24) ? 1.0f / (float)c->nc : 0.0f;
     const float4 *pos = (const float4 *)c->pos;
     const int32_t *start = c->start;
     double *partial = c->partial;
