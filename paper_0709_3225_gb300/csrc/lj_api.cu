@@ -87,6 +87,8 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->perm);
     cudaFree(c->pos);
     cudaFree(c->tile_sum);
+    cudaFree(c->scan_status);
+    cudaFree(c->scan_ctl);
     cudaFree(c->centre);
     cudaFree(c->work);
     cudaFree(c->thb);
@@ -360,14 +362,19 @@ int setup_grid(lj_ctx *c, int nc)
     cudaFree(c->centre);
     cudaFree(c->thb);
     cudaFree(c->tile_sum);
+    cudaFree(c->scan_status);
+    cudaFree(c->scan_ctl);
     cudaFree(c->partial);
     c->count = c->start = c->tile_sum = nullptr;
+    c->scan_status = nullptr;
+    c->scan_ctl = nullptr;
     c->centre = nullptr;
     c->thb = nullptr;
     c->partial = nullptr;
     c->nc = nc;
     c->ncell = (int64_t)nc * nc * nc;
     c->inv_cw = (double)nc / c->p.box;
+    c->inv_nc_f = c->ncell + 1 < (1 << 24) ? 1.0f / (float)nc : 0.0f;
     c->cw = c->p.box / (double)nc;
 #define LJ_GRID_CK(call)             \
     do {                             \
@@ -401,6 +408,10 @@ int setup_grid(lj_ctx *c, int nc)
     }
     c->ntiles = (int)((c->ncell + 1 + kScanTile - 1) / kScanTile);
     LJ_GRID_CK(cudaMalloc(&c->tile_sum, (size_t)c->ntiles * sizeof(int32_t)));
+    LJ_GRID_CK(cudaMalloc(&c->scan_status, (size_t)c->ntiles * sizeof(unsigned long long)));
+    LJ_GRID_CK(cudaMalloc(&c->scan_ctl, 4 * sizeof(unsigned)));
+    LJ_GRID_CK(cudaMemsetAsync(c->scan_status, 0, (size_t)c->ntiles * sizeof(unsigned long long), c->stream));
+    LJ_GRID_CK(cudaMemsetAsync(c->scan_ctl, 0, 4 * sizeof(unsigned), c->stream));
     LJ_GRID_CK(force_configure(c));
     LJ_GRID_CK(c->p.precision == LJ_PREC_MIXED ? warp_force_configure(c) : w64_force_configure(c));
     c->pipe_grid = 0;

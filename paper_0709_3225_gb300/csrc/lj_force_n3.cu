@@ -48,6 +48,7 @@ namespace {
 constexpr int kN3Threads = 128;   // 4 warps per CTA
 constexpr int kN3Home = 8;        // home particles per lane per pass
 constexpr int kN3Half = 14;       // home cell + 13 forward neighbours
+constexpr int kN3Batch = 3;       // staging rounds whose loads are in flight together (measured: 3 > 2 > 1)
 
 // Offset of half-stencil entry e: e = 0 the home cell, e = 1 .. 13 the
 // neighbours with (dz, dy, dx) > 0 lexicographically (x-fastest index
@@ -66,36 +67,6 @@ __device__ __forceinline__ void half_delta(int e, int &dx, int &dy, int &dz)
 // transpose buffer (8 x 32 float4).
 __host__ __device__ constexpr int n3_slice_words(int cap) { return 4 * cap + 4 * kN3Half + 16 + 4 * kN3Home * 32; }
 
-// (c mod n, (c / n) mod n, c / n^2) of a cell id c < 2^24 without integer
-// division: the quotient from an FP32 product (relative error < 2^-22, so
-// off by at most one) and one correction.
-__device__ __forceinline__ int div_small(int c, int n, float inv_n, int &r)
-{
-    int q = __float2int_rz((float)c * inv_n);
-    r = c - q * n;
-    if (r < 0) {
-        q -= 1;
-        r += n;
-    } else if (r >= n) {
-        q += 1;
-        r -= n;
-    }
-    return q;
-}
-
-// inv_nc = 0 (grids of 2^24 cells or more): integer division.
-__device__ __forceinline__ void cell_coords(int c, int nc, float inv_nc, int &cx, int &cy, int &cz)
-{
-    if (inv_nc > 0.0f) {
-        const int q = div_small(c, nc, inv_nc, cx);
-        cz = div_small(q, nc, inv_nc, cy);
-    } else {
-        cx = c % nc;
-        cy = (c / nc) % nc;
-        cz = c / (nc * nc);
-    }
-}
-
 // Half-stencil table, in two parts so that a cell's loads can be issued one
 // cell ahead: half_load reads, for lane e < 14, the first and end particle
 // of entry e of cell c (cell id c < 2^31); half_finish writes stab[e] =
@@ -112,7 +83,7 @@ __device__ __forceinline__ HalfLoad half_load(const int32_t *__restrict__ start,
     HalfLoad t{0, 0};
     if (lane < kN3Half) {
         int cx, cy, cz, dx, dy, dz;
-        cell_coords(c, nc, inv_nc, cx, cy, cz);
+        lj_cell_decode(c, nc, inv_nc, cx, cy, cz);
         half_delta(lane, dx, dy, dz);
         int ux = cx + dx, uy = cy + dy, uz = cz + dz;
         ux += ux < 0 ? nc : 0;
@@ -350,10 +321,10 @@ __device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__re
     const unsigned le = (2u << lane) - 1u;
     const int last = k.n - 1;
     int T = 0;
-    for (int t0 = 0; t0 < Ttot; t0 += 32 * kStageBatch) {
-        float4 q[kStageBatch], sh[kStageBatch];
+    for (int t0 = 0; t0 < Ttot; t0 += 32 * kN3Batch) {
+        float4 q[kN3Batch], sh[kN3Batch];
 #pragma unroll
-        for (int u = 0; u < kStageBatch; u++) {
+        for (int u = 0; u < kN3Batch; u++) {
             const int t = t0 + 32 * u + lane;
             const int tb = t0 + 32 * u;
             const int o = s_e - tb;
@@ -393,7 +364,7 @@ __device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__re
                 bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
             }
         }
-        if (T + 32 * kStageBatch + 32 > k.cap) {   // this batch plus the padding might not fit
+        if (T + 32 * kN3Batch + 32 > k.cap) {   // this batch plus the padding might not fit
             __syncwarp();
             return false;
         }
@@ -406,7 +377,7 @@ __device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__re
             bhz = 0.5f * (bzh - bzl);
         }
 #pragma unroll
-        for (int u = 0; u < kStageBatch; u++) {
+        for (int u = 0; u < kN3Batch; u++) {
             const int t = t0 + 32 * u + lane;
             const float cx = q[u].x + sh[u].x;
             const float cy = q[u].y + sh[u].y;
@@ -620,7 +591,7 @@ cudaError_t launch_force_n3(lj_ctx *c, void *f, bool energy)
     if (c->p.n == 0) return cudaSuccess;
     WarpParams k = warp_params_of(c);
     k.cap = c->n3cap;
-    k.inv_nc = c->ncell < (1 << 24) ? 1.0f / (float)c->nc : 0.0f;
+    k.inv_nc = c->inv_nc_f;
     const float4 *pos = (const float4 *)c->pos;
     const int32_t *start = c->start;
     double *partial = c->partial;

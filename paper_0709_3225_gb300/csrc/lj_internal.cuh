@@ -41,6 +41,7 @@ struct lj_ctx {
     int nc;              // cells per side
     int64_t ncell;       // nc^3
     double inv_cw;       // s = nc / L (cell index scale)
+    float inv_nc_f;      // 1 / nc for lj_cell_decode (0 for grids of 2^24 cells or more)
     double cw;           // cell side L / nc
     cudaStream_t stream;
     int device;
@@ -54,6 +55,10 @@ struct lj_ctx {
     double wrap_hi, wrap_lo;  // lj_wrap_fast bounds
     int32_t *tile_sum;
     int ntiles;
+    // single-pass scan: per-tile status words and [ticket, done, epoch]
+    // (NULL: the two-launch scan, as for contexts without them)
+    unsigned long long *scan_status;
+    unsigned *scan_ctl;
     double *partial;     // force-kernel per-block (energy, virial) partials
     double *ekin_partial;
     double *scalars;     // 8 doubles: [0] = E_pot, [1] = virial, [2] = E_kin, [3] = E_tot, [4] = T, [5] = P
@@ -163,6 +168,36 @@ __device__ __forceinline__ int lj_cell1(double w, double s, int nc)
     c = c < nc ? c : nc - 1;
     c = c > 0 ? c : 0;
     return c;
+}
+
+// Cell coordinates (c mod n, (c / n) mod n, c / n^2) of a linear cell id.
+// For grids of fewer than 2^24 cells inv_n = 1/n in FP32 gives the quotient
+// of c < 2^24 to within one (relative error < 2^-22), fixed by one
+// comparison; inv_n = 0 selects integer division.
+__device__ __forceinline__ int lj_div_small(int c, int n, float inv_n, int &r)
+{
+    int q = __float2int_rz((float)c * inv_n);
+    r = c - q * n;
+    if (r < 0) {
+        q -= 1;
+        r += n;
+    } else if (r >= n) {
+        q += 1;
+        r -= n;
+    }
+    return q;
+}
+
+__device__ __forceinline__ void lj_cell_decode(int c, int nc, float inv_nc, int &cx, int &cy, int &cz)
+{
+    if (inv_nc > 0.0f) {
+        const int q = lj_div_small(c, nc, inv_nc, cx);
+        cz = lj_div_small(q, nc, inv_nc, cy);
+    } else {
+        cx = c % nc;
+        cy = (c / nc) % nc;
+        cz = c / (nc * nc);
+    }
 }
 
 // Rank of a particle within its cell by one atomicAdd per distinct cell in
