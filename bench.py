@@ -72,6 +72,25 @@ def stencil_candidates(ctx) -> float:
     return candidate_pairs(count.double().view(nc, nc, nc), ctx.params.cell_subdiv or 1)
 
 
+def half_stencil_candidates(ctx) -> float:
+    """Candidate pairs the half stencil presents when each pair is taken
+    once: sum_c n_c (n_c - 1) / 2 + sum_c n_c * sum_{13 forward c'} n_c',
+    from the cell counts of the context's last binning."""
+    import torch
+    from paper_0709_3225_gb300 import lj
+    nc = ctx.nc
+    count = torch.empty(nc ** 3, dtype=torch.int32, device="cuda")
+    lj.lj_get_cells(ctx, count=count)
+    g = count.double().view(nc, nc, nc)
+    nb = torch.zeros_like(g)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if (dz, dy, dx) > (0, 0, 0):
+                    nb += torch.roll(g, shifts=(-dz, -dy, -dx), dims=(0, 1, 2))
+    return float((g * (g - 1) / 2).sum() + (g * nb).sum())
+
+
 def candidate_pairs(g, k: int) -> float:
     """sum_c g[c] * sum_{|d|_inf <= k} g[c + d] over a periodic grid of counts."""
     import torch
@@ -669,7 +688,14 @@ def run_gpu(args):
     # (kick-drift-bin 124 B, scatter 56 B, force in/out 32 B).
     other_ms = ms_step - force_avg_ms
     candidates = stencil_candidates(s.ctx)
-    issued_tflops = (CANDIDATE_FLOPS * candidates + FLOPS_PER_PAIR * 2 * pairs) / (force_avg_ms / 1e3) / 1e12
+    pair_once = tuning.get("kernel") == 7
+    if pair_once:   # each pair once over the half stencil
+        half = half_stencil_candidates(s.ctx)
+        issued_flops = CANDIDATE_FLOPS * half + FLOPS_PER_PAIR * pairs
+    else:
+        half = None
+        issued_flops = CANDIDATE_FLOPS * candidates + FLOPS_PER_PAIR * 2 * pairs
+    issued_tflops = issued_flops / (force_avg_ms / 1e3) / 1e12
 
     # ---- the same system as an equilibrated fluid ---------------------------
     # The lattice start melts within ~100 steps; 1000 steps after it the cell
@@ -748,7 +774,7 @@ def run_gpu(args):
     peaks = read_peaks()
     # the committed ncu figures describe the default kernel; report them only
     # when the tuner kept it
-    default_kernel = (tuning.get("kernel"), tuning.get("gw"), tuning.get("subdiv", 1)) == (3, 0, 1)
+    default_kernel = (tuning.get("kernel"), tuning.get("gw"), tuning.get("subdiv", 1)) == (7, 0, 1)
     traffic = force_traffic() if default_kernel else None
 
     line = {
@@ -772,17 +798,21 @@ def run_gpu(args):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "k_force_warp (mixed, default tuning)", "force_ms_per_launch": force_avg_ms,
+                     "kernel": ("k_force_n3 (each pair once, half stencil)" if pair_once else
+                                "k_force_warp (27-cell stencil)") + f", tuning kernel {tuning.get('kernel')}",
+                     "force_ms_per_launch": force_avg_ms,
                      "flops_per_launch": FLOPS_PER_PAIR * pairs,
                      "stencil_candidates_per_launch": candidates,
-                     "issued_flops_per_launch": CANDIDATE_FLOPS * candidates + FLOPS_PER_PAIR * 2 * pairs,
+                     "half_stencil_candidates_per_launch": half,
+                     "issued_flops_per_launch": issued_flops,
                      "issued_frac": issued_tflops / FP32_PEAK_TFLOPS,
-                     "issued_convention": "7 flop per full-stencil candidate + 20 per pair, both directions",
+                     "issued_convention": ("7 flop per half-stencil candidate + 20 per pair, once" if pair_once else
+                                           "7 flop per full-stencil candidate + 20 per pair, both directions"),
                      "peak_source": "measured (lj_measure_peak, FP32 FMA chains; see measured_fp_peaks)",
                      "frac_of_derived": achieved_tflops / mpk["derived_fp32_tflops"],
                      "fp32_pipe_busy": force_traffic("fp32_pipe_busy") if default_kernel else None,
                      "fp32_pipe_busy_source": "ncu sm__pipe_fmaheavy_cycles_active of the default force "
-                                              "kernel at this size (profiles/k_force_warp_traffic_fluid-4m.md)"},
+                                              "kernel at this size (profiles/k_force_n3_traffic_fluid-4m.md)"},
         "other_kernels_ms_per_step": other_ms,
         "tuning": tuning,
         "ensemble": ensemble,
@@ -828,8 +858,8 @@ def run_gpu(args):
 
 
 FORCE_SOURCES = [os.path.join(ROOT, "paper_0709_3225_gb300", "csrc", f)
-                 for f in ("lj_force_warp.cu", "lj_force_cell.cuh", "lj_internal.cuh")]
-TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_force_warp_traffic_fluid-4m.md")
+                 for f in ("lj_force_n3.cu", "lj_force_cell.cuh", "lj_internal.cuh")]
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_force_n3_traffic_fluid-4m.md")
 
 
 def force_traffic(field="dram_bytes_per_launch"):

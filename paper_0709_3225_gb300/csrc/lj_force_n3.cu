@@ -183,6 +183,45 @@ __device__ __forceinline__ void add_force(float4 *fout, int idx, float4 v)
     if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f) atomicAdd(fout + idx, v);
 }
 
+// The candidate blocks of one pass: lane (a, b) takes candidate blk B + b
+// of every block against its NH home pairs (pairs past its home particles
+// sit far away and add nothing), then the candidate's reaction is summed
+// over the A groups and added to f.
+template <int NH, int MODE, bool ENERGY>
+__device__ __forceinline__ void n3_blocks(const WarpParams &k, float4 *__restrict__ fout, const float4 *S, int T,
+                                          int n_home, int p0, int a, int b, int A, int lgB, const float2 *hx,
+                                          const float2 *hy, const float2 *hz, float2 *fx, float2 *fy, float2 *fz,
+                                          float2 *fe, float2 &fw)
+{
+    const int B = 1 << lgB;
+    const int nblk = (T + B - 1) >> lgB;
+    for (int blk = 0; blk < nblk; blk++) {
+        const int j = (blk << lgB) + b;
+        const float4 c = S[j];
+        const float2 cx = f2(c.x), cy = f2(c.y), cz = f2(c.z);
+        float2 rx = f2(0.0f), ry = f2(0.0f), rz = f2(0.0f), re = f2(0.0f);
+        if ((blk << lgB) < n_home) {
+#pragma unroll
+            for (int h = 0; h < NH; h++)
+                pair2_n3<MODE, ENERGY, true>(hx[h], hy[h], hz[h], p0 + 2 * h * A + a, p0 + (2 * h + 1) * A + a, cx, cy,
+                                             cz, j, k, fx[h], fy[h], fz[h], fe[h], fw, rx, ry, rz, re);
+        } else {
+#pragma unroll
+            for (int h = 0; h < NH; h++)
+                pair2_n3<MODE, ENERGY, false>(hx[h], hy[h], hz[h], 0, 0, cx, cy, cz, j, k, fx[h], fy[h], fz[h], fe[h],
+                                              fw, rx, ry, rz, re);
+        }
+        float sx = rx.x + rx.y, sy = ry.x + ry.y, sz = rz.x + rz.y, se = ENERGY ? re.x + re.y : 0.0f;
+        for (int o = B; o < 32; o <<= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+            if constexpr (ENERGY) se += __shfl_xor_sync(0xffffffffu, se, o);
+        }
+        if (a == 0 && j < T) add_force(fout, __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
+    }
+}
+
 // Compute phase over the staged list S (T candidates, home particles at
 // 0 .. n_home-1, padded with far points to a multiple of 32).  Per pass of
 // up to 32 home particles the warp is A groups of B lanes (A = 2 for up to
@@ -214,35 +253,15 @@ __device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restri
             hz[h] = make_float2(v0 ? q0.z : -kFar, v1 ? q1.z : -kFar);
             fx[h] = fy[h] = fz[h] = fe[h] = f2(0.0f);
         }
-        const int nblk = (T + B - 1) >> lgB;
-        for (int blk = 0; blk < nblk; blk++) {
-            const int j = (blk << lgB) + b;
-            const float4 c = S[j];
-            const float2 cx = f2(c.x), cy = f2(c.y), cz = f2(c.z);
-            float2 rx = f2(0.0f), ry = f2(0.0f), rz = f2(0.0f), re = f2(0.0f);
-            // all four home pairs, also where a lane has fewer home particles
-            // (those sit far away and add nothing): no branches in the loop
-            if ((blk << lgB) < n_home) {
-#pragma unroll
-                for (int h = 0; h < kN3Home / 2; h++)
-                    pair2_n3<MODE, ENERGY, true>(hx[h], hy[h], hz[h], p0 + 2 * h * A + a, p0 + (2 * h + 1) * A + a, cx,
-                                                 cy, cz, j, k, fx[h], fy[h], fz[h], fe[h], fw, rx, ry, rz, re);
-            } else {
-#pragma unroll
-                for (int h = 0; h < kN3Home / 2; h++)
-                    pair2_n3<MODE, ENERGY, false>(hx[h], hy[h], hz[h], 0, 0, cx, cy, cz, j, k, fx[h], fy[h], fz[h],
-                                                  fe[h], fw, rx, ry, rz, re);
-            }
-            // the candidate's reaction: its two partial sums, then the A groups
-            float sx = rx.x + rx.y, sy = ry.x + ry.y, sz = rz.x + rz.y, se = ENERGY ? re.x + re.y : 0.0f;
-            for (int o = B; o < 32; o <<= 1) {
-                sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                sy += __shfl_xor_sync(0xffffffffu, sy, o);
-                sz += __shfl_xor_sync(0xffffffffu, sz, o);
-                if constexpr (ENERGY) se += __shfl_xor_sync(0xffffffffu, se, o);
-            }
-            if (a == 0 && j < T) add_force(fout, __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
-        }
+        // the candidate blocks, compiled for the number of home pairs a lane
+        // holds (a uniform choice per pass: no branches inside the loop)
+        const int nh = (nu + 1) >> 1;
+        if (nh >= 4)
+            n3_blocks<4, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
+        else if (nh == 3)
+            n3_blocks<3, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
+        else
+            n3_blocks<2, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
         // home forces: sum over the B lanes of each group through a transpose
         // in shared memory (row u, column a B + b); every lane sums 8 entries
 #pragma unroll
