@@ -216,7 +216,14 @@ def run_ensemble(args, stream, world):
     b.relax(50, 1e-3, 0.05)
     b.forces()
     tuning = autotune.tune_batch(b, float(np.mean(e.rho)))
-    tuning.pop("trials", None)
+    trials = tuning.pop("trials", None) or []
+    b = autotune.batch_for(b, tuning)
+    # the cell-size dimension of the tuning: the fastest setting per subdivision
+    by_k = {}
+    for t in trials:
+        if t["subdiv"] not in by_k or t["ms_per_step"] < by_k[t["subdiv"]]["ms_per_step"]:
+            by_k[t["subdiv"]] = t
+    tuning["best_per_subdiv"] = {str(k): v for k, v in sorted(by_k.items())}
     b.step(args.warmup)
     b.check()
     k = max(10, min(args.steps, 200))

@@ -395,8 +395,12 @@ typedef struct lj_batch lj_batch;
 /* Create a batch: n[r] particles in a cubic box of side box[r] for
  * r < nrep; common supplies eps, sigma, rc, dt, mass, shift_mode, flags and
  * precision (must be LJ_PREC_MIXED); common->n and common->box are ignored.
- * Each replica is validated as by lj_grid.  stream: cudaStream_t (NULL =
- * legacy default stream; graph capture then uses a private stream). */
+ * Each replica is validated as by lj_grid.  common->cell_subdiv (0 or 1:
+ * cells of side >= rc and the 27-cell stencil; 2: side >= rc / 2 and the
+ * 125-cell stencil) applies to every replica, which then needs at least
+ * 2k + 1 cells per side; other values give LJ_EINVAL.  stream: cudaStream_t
+ * (NULL = legacy default stream; graph capture then uses a private
+ * stream). */
 int lj_batch_create(lj_batch **out, int32_t nrep, const int64_t *n, const double *box, const lj_params *common,
                     void *stream);
 void lj_batch_destroy(lj_batch *b);

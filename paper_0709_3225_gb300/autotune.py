@@ -16,8 +16,10 @@ It picks, by timing velocity-Verlet steps on a copy of the state:
                      per chunk; 0 = compiled default, -1 = chosen per cell)
                      and the cells per pull
                      from its work counter (0 = static striding);
-  batches         -- cells per pull from the work counter, lane-group width,
-                     graph replay or direct launches.
+  batches         -- cell subdivision k (1 or 2, as for single systems, timed
+                     on a copy of the state), cells per pull from the work
+                     counter, lane-group width, graph replay or direct
+                     launches.
 Choices are cached in a JSON file keyed by (GPU name, kind, N bucket, density
 bucket) and re-applied without timing on a cache hit.  The cache lives at
 $LJGB_TUNE_CACHE, else ~/.cache/ljgb/autotune.json.
@@ -185,33 +187,84 @@ def make_system(x, v, box: float, rho: float, *, use_cache: bool = True, path: s
 
 
 def batch_candidates() -> list[dict]:
-    out = [{"cells_per_grab": c, "gw": g, "graph": True} for c in (1, 2, 4, 8, 16) for g in (0, 8, -1)]
-    out.append({"cells_per_grab": 4, "gw": 0, "graph": False})
+    """Batch settings: cell subdivision k (1: 27-cell stencil; 2: half-size
+    cells, 125-cell stencil, group width 4 compiled in), cells per pull,
+    lane-group width, graph replay."""
+    out = [{"subdiv": 1, "cells_per_grab": c, "gw": g, "graph": True} for c in (1, 2, 4, 8, 16) for g in (0, 8, -1)]
+    out.append({"subdiv": 1, "cells_per_grab": 4, "gw": 0, "graph": False})
+    out += [{"subdiv": 2, "cells_per_grab": c, "gw": g, "graph": True} for c in (1, 4, 16) for g in (0, 2, -1)]
     return out
+
+
+def _batch_state(batch: lj.Batch):
+    x, v = batch.x.cpu().numpy(), batch.v.cpu().numpy()
+    o = batch.offsets
+    return [x[o[r]:o[r + 1]] for r in range(batch.nrep)], [v[o[r]:o[r + 1]] for r in range(batch.nrep)]
+
+
+def _clone_batch(batch: lj.Batch, subdiv: int) -> lj.Batch:
+    xs, vs = _batch_state(batch)
+    p = batch.params
+    return lj.Batch(xs, vs, batch.boxes, eps=p.eps, sigma=p.sigma, rc=p.rc, dt=p.dt, mass=p.mass,
+                    shift_mode=p.shift_mode, cell_subdiv=subdiv)
 
 
 def tune_batch(batch: lj.Batch, rho: float, steps: int = 10, warmup: int = 3, use_cache: bool = True,
                path: str | None = None) -> dict:
-    """Choose and apply the fastest batch setting for ``batch``."""
+    """Time every batch setting and apply the fastest one ``batch`` can take.
+    A cell subdivision other than the batch's is timed on a temporary copy of
+    the state; when it wins, the returned choice names it (``batch_for``
+    then builds the batch with it) and ``batch`` gets the best setting of its
+    own subdivision."""
     key = bucket_key(f"batch{batch.nrep}", batch.ntot, rho)
+    own = batch.cell_subdiv
     if use_cache:
         hit = load_cache(path).get(key)
-        if hit:
+        if hit and hit.get("subdiv", 1) == own:
             batch.set_tuning(hit["cells_per_grab"], hit["graph"], hit["gw"])
             return dict(hit, cached=True)
-    saved = (batch.x.clone(), batch.v.clone(), batch.f.clone(), batch._forces_valid)
     results = []
-    for cand in batch_candidates():
-        batch.set_tuning(cand["cells_per_grab"], cand["graph"], cand["gw"])
-        ms = _time_steps(batch.step, steps, warmup)
-        results.append(dict(cand, ms_per_step=ms))
-    batch.check()
-    batch.x.copy_(saved[0])
-    batch.v.copy_(saved[1])
-    batch.f.copy_(saved[2])
-    batch._forces_valid = saved[3]
+    copies = {own: batch}
+    try:
+        for cand in batch_candidates():
+            sub = cand["subdiv"]
+            if sub not in copies:
+                try:
+                    copies[sub] = _clone_batch(batch, sub)
+                    copies[sub].forces()
+                except lj.LJError:      # a replica too small for that subdivision
+                    copies[sub] = None
+            target = copies[sub]
+            if target is None:
+                continue
+            saved = (target.x.clone(), target.v.clone(), target.f.clone(), target._forces_valid)
+            target.set_tuning(cand["cells_per_grab"], cand["graph"], cand["gw"])
+            ms = _time_steps(target.step, steps, warmup)
+            target.check()
+            target.x.copy_(saved[0])
+            target.v.copy_(saved[1])
+            target.f.copy_(saved[2])
+            target._forces_valid = saved[3]
+            results.append(dict(cand, ms_per_step=ms))
+    finally:
+        for sub, t in copies.items():
+            if sub != own and t is not None:
+                t.close()
     best = min(results, key=lambda r: r["ms_per_step"])
-    batch.set_tuning(best["cells_per_grab"], best["graph"], best["gw"])
-    choice = {k: best[k] for k in ("cells_per_grab", "gw", "graph", "ms_per_step")}
+    best_own = min((r for r in results if r["subdiv"] == own), key=lambda r: r["ms_per_step"])
+    batch.set_tuning(best_own["cells_per_grab"], best_own["graph"], best_own["gw"])
+    choice = {k: best[k] for k in ("subdiv", "cells_per_grab", "gw", "graph", "ms_per_step")}
     store_cache(key, choice, path)
     return dict(choice, cached=False, trials=results)
+
+
+def batch_for(batch: lj.Batch, choice: dict) -> lj.Batch:
+    """``batch`` if the choice has its cell subdivision, else a new batch of the
+    same state with the chosen subdivision and setting (``batch`` is closed)."""
+    if choice.get("subdiv", 1) == batch.cell_subdiv:
+        return batch
+    nb = _clone_batch(batch, choice["subdiv"])
+    batch.close()
+    nb.set_tuning(choice["cells_per_grab"], choice["graph"], choice["gw"])
+    nb.forces()
+    return nb

@@ -250,14 +250,16 @@ __device__ void phase_scatter(const BatchDev &b, int op, const double *__restric
     }
 }
 
-// Phase 4: forces, cells pulled in chunks from the work counter.
-template <int MODE, bool ENERGY, int GFIX>
+// Phase 4: forces, cells pulled in chunks from the work counter.  R: the
+// stencil radius, the cell subdivision k of every replica's grid (1: the
+// 27-cell stencil of cells >= rc; 2: 125 cells of side >= rc / 2).
+template <int R, int MODE, bool ENERGY, int GFIX>
 __device__ void phase_force(const BatchDev &b, const WarpParams &k, float4 *__restrict__ f)
 {
     extern __shared__ __align__(16) float bsmem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float *slice = bsmem + (size_t)warp * warp_slice_words(k.cap, 1);
+    float *slice = bsmem + (size_t)warp * warp_slice_words(k.cap, R);
     double eacc = 0.0, wacc = 0.0;
     for (;;) {
         unsigned c0 = 0;
@@ -271,14 +273,15 @@ __device__ void phase_force(const BatchDev &b, const WarpParams &k, float4 *__re
             int cx, cy, cz;
             decode_cell((int)(c - b.coff[r]), nc, cx, cy, cz);
             const StoreForce<MODE, ENERGY> out{f, k.n};
-            process_home_cell<1, MODE, ENERGY, false, GFIX>(k, b.pos, b.start, out, slice, cx, cy, cz, nc, b.coff[r],
+            process_home_cell<R, MODE, ENERGY, false, GFIX>(k, b.pos, b.start, out, slice, cx, cy, cz, nc, b.coff[r],
                                                       (float)b.cw[r], eacc, wacc);
         }
     }
 }
 
-// GFIX as in k_force_warp: 16 compiled in (group width 0), 0 general.
-template <int MODE, bool ENERGY, int GFIX>
+// GFIX as in k_force_warp: the default width compiled in (group width 0:
+// 16 for the 27-cell stencil, 4 for the 125-cell one), 0 general.
+template <int R, int MODE, bool ENERGY, int GFIX>
 __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_step(BatchDev b, WarpParams k, int op, double *x,
                                                                   double *v, float4 *f)
 {
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_step(BatchDev b, War
     if (!grid_barrier(b)) return;
     phase_scatter(b, op, x);
     if (!grid_barrier(b)) return;
-    phase_force<MODE, ENERGY, GFIX>(b, k, f);
+    phase_force<R, MODE, ENERGY, GFIX>(b, k, f);
 }
 
 // Closing half kick of the last step: v += h f.
@@ -361,22 +364,24 @@ __global__ void __launch_bounds__(kReduceThreads) k_batch_energy(const double *_
     }
 }
 
-template <int G>
+template <int R, int G>
 void *batch_kernel_g(int mode, bool energy)
 {
     switch (mode * 2 + (energy ? 1 : 0)) {
-        case 0: return (void *)k_batch_step<0, false, G>;
-        case 1: return (void *)k_batch_step<0, true, G>;
-        case 2: return (void *)k_batch_step<1, false, G>;
-        case 3: return (void *)k_batch_step<1, true, G>;
-        case 4: return (void *)k_batch_step<2, false, G>;
-        default: return (void *)k_batch_step<2, true, G>;
+        case 0: return (void *)k_batch_step<R, 0, false, G>;
+        case 1: return (void *)k_batch_step<R, 0, true, G>;
+        case 2: return (void *)k_batch_step<R, 1, false, G>;
+        case 3: return (void *)k_batch_step<R, 1, true, G>;
+        case 4: return (void *)k_batch_step<R, 2, false, G>;
+        default: return (void *)k_batch_step<R, 2, true, G>;
     }
 }
 
-void *batch_kernel(int mode, bool energy, int gw)
+void *batch_kernel(int subdiv, int mode, bool energy, int gw)
 {
-    return gw == 0 ? batch_kernel_g<16>(mode, energy) : batch_kernel_g<0>(mode, energy);
+    if (subdiv == 2)
+        return gw == 0 ? batch_kernel_g<2, DefaultGroup<2>::value>(mode, energy) : batch_kernel_g<2, 0>(mode, energy);
+    return gw == 0 ? batch_kernel_g<1, DefaultGroup<1>::value>(mode, energy) : batch_kernel_g<1, 0>(mode, energy);
 }
 
 // Same threshold construction as lj_create (smallest t with t * s >= k).
@@ -449,13 +454,14 @@ cudaError_t configure(lj_batch *b)
     // denser replicas that overflow take the plain path); static shared
     // memory of the scan phases: at most 2 KB.
     const double mean_occ = b->ncell > 0 ? (double)b->ntot / (double)b->ncell : 0.0;
-    const int cap = warp_stencil_cap(mean_occ, 1, kBatchThreads, 2048);
+    const int R = b->p.cell_subdiv;
+    const int cap = warp_stencil_cap(mean_occ, R, kBatchThreads, 2048);
     b->k.cap = cap;
-    b->smem = (kBatchThreads / 32) * warp_slice_words(cap, 1) * (int)sizeof(float);
+    b->smem = (kBatchThreads / 32) * warp_slice_words(cap, R) * (int)sizeof(float);
     int minblk = 1 << 30;
     for (int mode = 0; mode < 3; mode++)
         for (int en = 0; en < 4; en++) {
-            void *kern = batch_kernel(mode, en % 2 != 0, en < 2 ? 0 : -1);
+            void *kern = batch_kernel(R, mode, en % 2 != 0, en < 2 ? 0 : -1);
             cudaError_t e = raise_dyn_smem(kern, b->smem);
             if (e != cudaSuccess) return e;
             int nb = 0;
@@ -470,7 +476,7 @@ cudaError_t configure(lj_batch *b)
 
 cudaError_t launch_step_kernel(lj_batch *b, bool energy, int op, double *x, double *v, float4 *f)
 {
-    void *kern = batch_kernel(b->p.shift_mode, energy, b->k.gw);
+    void *kern = batch_kernel(b->p.cell_subdiv, b->p.shift_mode, energy, b->k.gw);
     void *args[] = {&b->d, &b->k, &op, &x, &v, &f};
     b->launches++;
     return cudaLaunchCooperativeKernel(kern, dim3(b->grid), dim3(kBatchThreads), args, b->smem, b->stream);
@@ -506,6 +512,8 @@ extern "C" int lj_batch_create(lj_batch **out, int32_t nrep, const int64_t *n, c
     *out = nullptr;
     if (nrep < 1 || !n || !box || !common) return LJ_EINVAL;
     if (common->precision != LJ_PREC_MIXED) return LJ_EINVAL;
+    // cell subdivision k of every replica: 1 (the default, also for 0) or 2
+    if (common->cell_subdiv < 0 || common->cell_subdiv > 2) return LJ_EINVAL;
     std::vector<int32_t> ncs(nrep), poff(nrep + 1), coff(nrep + 1), thoff(nrep + 1), ceoff(nrep + 1);
     int64_t ntot = 0, ncell = 0, nth = 0, nce = 0;
     double max_occ = 0.0;
@@ -536,6 +544,7 @@ extern "C" int lj_batch_create(lj_batch **out, int32_t nrep, const int64_t *n, c
 
     lj_batch *b = new lj_batch();
     b->p = *common;
+    if (b->p.cell_subdiv == 0) b->p.cell_subdiv = 1;
     b->p.n = ntot;
     b->nrep = nrep;
     b->ntot = ntot;

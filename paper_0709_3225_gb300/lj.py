@@ -450,7 +450,7 @@ class Batch:
     float32 CUDA tensors; ``offsets[r]:offsets[r+1]`` is replica r."""
 
     def __init__(self, xs, vs, boxes, *, eps=1.0, sigma=1.0, rc=2.5, dt=0.005, mass=1.0,
-                 shift_mode=LJ_SHIFT_ENERGY, stream=None):
+                 shift_mode=LJ_SHIFT_ENERGY, cell_subdiv=1, stream=None):
         import torch
         ns = [int(np.asarray(a).shape[0]) for a in xs]
         self.nrep = len(ns)
@@ -462,7 +462,8 @@ class Batch:
         else:
             self.v = torch.as_tensor(np.concatenate([np.asarray(a, np.float64) for a in vs])).cuda().contiguous()
         self.f = torch.zeros((self.x.shape[0], 4), dtype=torch.float32, device="cuda")
-        self.params = make_params(0, 1.0, eps, sigma, rc, dt, mass, shift_mode, "mixed")
+        self.params = make_params(0, 1.0, eps, sigma, rc, dt, mass, shift_mode, "mixed", cell_subdiv)
+        self.cell_subdiv = int(cell_subdiv) or 1
         n_arr = (ctypes.c_int64 * self.nrep)(*ns)
         b_arr = (ctypes.c_double * self.nrep)(*self.boxes)
         h = ctypes.c_void_p()

@@ -48,9 +48,15 @@ def test_tune_system_and_batch(tmp_path):
     bref = b.f.clone()
     rb = autotune.tune_batch(b, float(np.mean(e.rho)), steps=3, warmup=3, path=path)
     assert not rb["cached"]
+    assert {t["subdiv"] for t in rb["trials"]} == {1, 2}    # the cell size is a tuning dimension
     b.forces()
     rms = float(bref[:, :3].double().pow(2).sum(dim=1).mean().sqrt())
     assert bool(((b.f[:, :3] - bref[:, :3]).double().abs() <= 1e-5 * (bref[:, :3].double().abs() + rms)).all())
-    assert autotune.tune_batch(b, float(np.mean(e.rho)), path=path)["cached"]
+    assert autotune.tune_batch(b, float(np.mean(e.rho)), path=path)["cached"] == (rb["subdiv"] == 1)
     b.check()
-    b.close()
+    b2 = autotune.batch_for(b, dict(rb, subdiv=2))     # the batch rebuilt with half-size cells
+    assert b2.cell_subdiv == 2
+    b2.forces()
+    assert bool(((b2.f[:, :3] - bref[:, :3]).double().abs() <= 1e-5 * (bref[:, :3].double().abs() + rms)).all())
+    b2.check()
+    b2.close()

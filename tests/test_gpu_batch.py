@@ -17,16 +17,19 @@ def _small_ensemble(seed=5, nrep=6):
     return e, xs, vs
 
 
-def test_batched_forces_match_oracle_and_single(oracle_mod):
+@pytest.mark.parametrize("subdiv", [1, 2])
+def test_batched_forces_match_oracle_and_single(oracle_mod, subdiv):
+    """Cell subdivision 1 (27-cell stencil) and 2 (half-size cells, 125-cell
+    stencil) in the batched kernel."""
     from paper_0709_3225_gb300 import lj
     e, xs, vs = _small_ensemble()
-    b = lj.Batch(xs, vs, e.box)
+    b = lj.Batch(xs, vs, e.box, cell_subdiv=subdiv)
     b.forces()
     b.check()
     f = b.f.double().cpu().numpy()[:, :3]
     for r in range(b.nrep):
         fr = b.replica(f, r)
-        fo = oracle_mod.forces_cells(xs[r], e.box[r], mode=1)[0]
+        fo = oracle_mod.forces_cells(xs[r], e.box[r], mode=1, k=subdiv)[0]
         assert rel_rms(fr, fo) <= 1e-5, r
         # the single-system per-particle bound over every particle of the
         # replica (those with a partner within 1e-5 of rc excepted)
@@ -35,16 +38,18 @@ def test_batched_forces_match_oracle_and_single(oracle_mod):
         d = np.abs(fr - fo).max(axis=1)
         bound = 6e-7 * K + 1e-5 * S
         assert np.all(d[~near] <= bound[~near]), (r, (d[~near] / bound[~near]).max())
-        s = lj.System(xs[r], None, e.box[r])
+        # the same cell subdivision in a single-system context: the same pair
+        # vectors, sums in another order
+        s = lj.System(xs[r], None, e.box[r], cell_subdiv=subdiv)
         s.forces()
         assert rel_rms(fr, s.f.double().cpu().numpy()[:, :3]) <= 1e-6, r
         s.close()
     b.close()
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-@pytest.mark.parametrize("mode", [1, 2])
-def test_batched_steps_match_oracle(oracle_mod, use_graph, mode):
+@pytest.mark.parametrize("use_graph,mode,subdiv", [(True, 1, 1), (True, 2, 1), (False, 1, 1), (False, 2, 1),
+                                                  (True, 2, 2), (False, 1, 2)])
+def test_batched_steps_match_oracle(oracle_mod, use_graph, mode, subdiv):
     """23 steps.  With the force-shifted potential the force is continuous
     and positions agree to FP32 rounding; with the energy shift a pair whose
     distance is within rounding of rc may be counted on either side, and one
@@ -52,7 +57,7 @@ def test_batched_steps_match_oracle(oracle_mod, use_graph, mode):
     bound allows 1e-4 for single particles and checks the RMS tightly."""
     from paper_0709_3225_gb300 import lj
     e, xs, vs = _small_ensemble(seed=7, nrep=5)
-    b = lj.Batch(xs, vs, e.box, shift_mode=mode)
+    b = lj.Batch(xs, vs, e.box, shift_mode=mode, cell_subdiv=subdiv)
     b.set_tuning(cells_per_grab=2, use_graph=use_graph)
     b.step(8)
     b.step(12)
@@ -145,3 +150,11 @@ def test_full_ensemble_256(oracle_mod):
     b.step(10)
     b.check()
     b.close()
+
+
+def test_batch_rejects_bad_subdivision():
+    from paper_0709_3225_gb300 import lj
+    e, xs, vs = _small_ensemble(seed=13, nrep=2)
+    with pytest.raises(lj.LJError) as ei:
+        lj.Batch(xs, vs, e.box, cell_subdiv=3)
+    assert ei.value.code == lj.LJ_EINVAL
