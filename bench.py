@@ -102,6 +102,27 @@ def candidate_pairs(g, k: int) -> float:
     return float((g * nb).sum())
 
 
+def pinned_link_gbs(nbytes: int = 256 << 20) -> dict:
+    """Host-device bandwidth of one pinned copy each way (best of 5, CUDA
+    events): the rate the end-to-end figure's copies run at."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, dst, src in (("h2d", d, h), ("d2h", h, d)):
+        best = float("inf")
+        for _ in range(5):
+            torch.cuda.synchronize()
+            ev0.record()
+            dst.copy_(src, non_blocking=True)
+            ev1.record()
+            torch.cuda.synchronize()
+            best = min(best, ev0.elapsed_time(ev1))
+        out[name] = nbytes / (best * 1e-3) / 1e9
+    return out
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -740,6 +761,7 @@ def run_gpu(args):
         lj.lj_step_host(s.ctx, xh, vh, fh, 1)
     e2e_value, t_e2e = job_rate(world, e2e_steps, time.perf_counter() - t0)
     bytes_h2d = n * (3 * 8 + 3 * 8 + 4 * 4)
+    link = pinned_link_gbs()
     s.close()
     del s
     torch.cuda.empty_cache()
@@ -844,7 +866,9 @@ def run_gpu(args):
                               "peak_source": "measured (lj_measure_peak, FP64 FMA chains)"}},
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": bytes_h2d,
                 "d2h_bytes_per_step": bytes_h2d, "steps": e2e_steps,
-                "api": "lj_step_host, pinned host x, v, f; 1 step per call"},
+                "api": "lj_step_host, pinned host x, v, f; 1 step per call",
+                "pinned_link_gbs": link,
+                "copy_ms_per_step_at_link_rate": (bytes_h2d / link["h2d"] + bytes_h2d / link["d2h"]) / 1e6},
         "clocks": clocks,
         "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
         "measured_fp_peaks": mpk,

@@ -236,7 +236,11 @@ int lj_forces_n2(lj_ctx *ctx, const double *x, void *f, double *e_pot, double *v
 int lj_step(lj_ctx *ctx, double *x, double *v, void *f, int32_t nsteps);
 
 /* As lj_step on HOST arrays (pageable or pinned): copies x, v, f to the
- * device, steps, copies them back, synchronizes. */
+ * device, steps, copies them back, synchronizes.  The copies in arrive in
+ * four parts on a second stream, and each part is kicked, drifted and
+ * binned as soon as it is there (velocity Verlet without a skin or a fused
+ * update); the copy of x back runs while the last force evaluation does.
+ * Allocates staging buffers for x, v, f on first use. */
 int lj_step_host(lj_ctx *ctx, double *x, double *v, void *f, int32_t nsteps);
 
 /* Energies of the state (x, v): out[0] = kinetic energy (1/2) m sum v^2,

@@ -103,6 +103,9 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->n2_scratch);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->ev_xfinal) cudaEventDestroy(c->ev_xfinal);
+    if (c->ev_entry) cudaEventDestroy(c->ev_entry);
+    for (int k = 0; k < 4; k++)
+        if (c->ev_chunk[k]) cudaEventDestroy(c->ev_chunk[k]);
     cudaFree(c->pos_alt);
     cudaFree(c->perm_alt);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -197,7 +200,11 @@ int one_step(lj_ctx *c, double *x, double *v, void *f, int s, int nsteps, cudaEv
         LJ_CK(launch_force_warp_fused(c, f, x, v, s == nsteps - 1));
         return LJ_OK;
     }
-    LJ_CK(launch_kick_drift_bin(c, x, v, f, s == 0 ? 1 : 2));
+    if (s == 0 && c->kdb_done) {
+        c->kdb_done = 0;   // lj_step_host ran step 0's update chunk by chunk
+    } else {
+        LJ_CK(launch_kick_drift_bin(c, x, v, f, s == 0 ? 1 : 2));
+    }
     LJ_CK(launch_scan(c));
     LJ_CK(launch_scatter(c, x, false));
     if (x_final) LJ_CK(cudaEventRecord(x_final, c->stream));   // x holds its final value
@@ -288,6 +295,8 @@ int persistent_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps, cudaE
     if (x_final) LJ_CK(cudaEventRecord(x_final, c->stream));
     return LJ_OK;
 }
+
+constexpr int kHostChunks = 4;   // parts of lj_step_host's copies in
 
 int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps, cudaEvent_t x_final = nullptr)
 {
@@ -665,17 +674,43 @@ extern "C" int lj_step_host(lj_ctx *c, double *x, double *v, void *f, int32_t ns
     int r = ensure_staging(c);
     if (r) return r;
     const size_t bx = 3 * n * sizeof(double), bf = n * force_vsize(c);
-    if (n > 0) {
+    if (!c->copy_stream) LJ_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    if (!c->ev_xfinal) LJ_CK(cudaEventCreateWithFlags(&c->ev_xfinal, cudaEventDisableTiming));
+    if (!c->ev_entry) LJ_CK(cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming));
+    for (int k = 0; k < kHostChunks; k++)
+        if (!c->ev_chunk[k]) LJ_CK(cudaEventCreateWithFlags(&c->ev_chunk[k], cudaEventDisableTiming));
+    // The regular step's first kernel (kick, drift, bin) works on each part
+    // of x, v, f as soon as its copy has arrived on the second stream; the
+    // other update paths take the whole arrays first.
+    const bool chunked = n >= (size_t)(kHostChunks * 1024) && nsteps > 0 && c->skin <= 0.0 && !fused_mode(c) &&
+                         !persistent_mode(c);
+    if (chunked) {
+        LJ_CK(cudaEventRecord(c->ev_entry, c->stream));
+        LJ_CK(cudaStreamWaitEvent(c->copy_stream, c->ev_entry, 0));
+        const size_t fv = force_vsize(c);
+        for (int k = 0; k < kHostChunks; k++) {
+            const size_t i0 = n * k / kHostChunks, i1 = n * (k + 1) / kHostChunks;
+            LJ_CK(cudaMemcpyAsync(c->xs + 3 * i0, x + 3 * i0, 3 * (i1 - i0) * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->copy_stream));
+            LJ_CK(cudaMemcpyAsync(c->vs + 3 * i0, v + 3 * i0, 3 * (i1 - i0) * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->copy_stream));
+            LJ_CK(cudaMemcpyAsync((char *)c->fs + fv * i0, (const char *)f + fv * i0, fv * (i1 - i0),
+                                  cudaMemcpyHostToDevice, c->copy_stream));
+            LJ_CK(cudaEventRecord(c->ev_chunk[k], c->copy_stream));
+            LJ_CK(cudaStreamWaitEvent(c->stream, c->ev_chunk[k], 0));
+            LJ_CK(launch_kick_drift_bin(c, c->xs, c->vs, c->fs, 1, (int64_t)i0, (int64_t)i1));
+        }
+        c->kdb_done = 1;
+    } else if (n > 0) {
         LJ_CK(cudaMemcpyAsync(c->xs, x, bx, cudaMemcpyHostToDevice, c->stream));
         LJ_CK(cudaMemcpyAsync(c->vs, v, bx, cudaMemcpyHostToDevice, c->stream));
         LJ_CK(cudaMemcpyAsync(c->fs, f, bf, cudaMemcpyHostToDevice, c->stream));
     }
-    // x is final after the last scatter: its copy back runs on a second
+    // x is final after the last scatter: its copy back runs on the second
     // stream while the last force evaluation and kick run
-    if (!c->copy_stream) LJ_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-    if (!c->ev_xfinal) LJ_CK(cudaEventCreateWithFlags(&c->ev_xfinal, cudaEventDisableTiming));
     const bool overlap = n > 0 && nsteps > 0;
     r = do_steps(c, c->xs, c->vs, c->fs, nsteps, overlap ? c->ev_xfinal : nullptr);
+    c->kdb_done = 0;
     if (r) return r;
     if (n > 0) {
         if (overlap) {

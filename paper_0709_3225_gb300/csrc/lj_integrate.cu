@@ -33,9 +33,11 @@ __global__ void __launch_bounds__(256) k_kick_drift_bin(double *__restrict__ x, 
                                                         double L, double whi, double wlo, double s, int nc,
                                                         float inv_nc, const long long *__restrict__ thb,
                                                         int32_t *__restrict__ cell_of, int32_t *__restrict__ rank,
-                                                        int32_t *__restrict__ count, int32_t *__restrict__ err)
+                                                        int32_t *__restrict__ count, int32_t *__restrict__ err,
+                                                        int i_begin)
 {
-    const int i0 = blockIdx.x * (kKdbPer * blockDim.x) + threadIdx.x;
+    // particles i_begin .. n-1 (a chunk when the host copies arrive in parts)
+    const int i0 = i_begin + blockIdx.x * (kKdbPer * blockDim.x) + threadIdx.x;
     double xr[kKdbPer][3], vr[kKdbPer][3], fr[kKdbPer][3];
     int old[kKdbPer];
 #pragma unroll
@@ -213,19 +215,22 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 
 }  // namespace
 
-cudaError_t launch_kick_drift_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick)
+cudaError_t launch_kick_drift_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick, int64_t i_begin,
+                                  int64_t i_end)
 {
-    int n = (int)c->p.n;
-    if (n == 0) return cudaSuccess;
+    const int n = (int)(i_end < 0 ? c->p.n : i_end);
+    const int b0 = (int)i_begin;
+    if (n <= b0) return cudaSuccess;
     const double hk = nkick * (0.5 * c->p.dt / c->p.mass);
+    const unsigned grid = blocks_for(n - b0, kKdbPer * 256);
     if (c->p.precision == LJ_PREC_FP64)
-        k_kick_drift_bin<double4_16a><<<blocks_for(n, kKdbPer * 256), 256, 0, c->stream>>>(
+        k_kick_drift_bin<double4_16a><<<grid, 256, 0, c->stream>>>(
             x, v, (const double4_16a *)f, n, hk, c->p.dt, c->p.box, c->wrap_hi, c->wrap_lo, c->inv_cw, c->nc,
-            c->inv_nc_f, c->thb, c->cell_of, c->rank, c->count, c->err);
+            c->inv_nc_f, c->thb, c->cell_of, c->rank, c->count, c->err, b0);
     else
-        k_kick_drift_bin<float4><<<blocks_for(n, kKdbPer * 256), 256, 0, c->stream>>>(
+        k_kick_drift_bin<float4><<<grid, 256, 0, c->stream>>>(
             x, v, (const float4 *)f, n, hk, c->p.dt, c->p.box, c->wrap_hi, c->wrap_lo, c->inv_cw, c->nc,
-            c->inv_nc_f, c->thb, c->cell_of, c->rank, c->count, c->err);
+            c->inv_nc_f, c->thb, c->cell_of, c->rank, c->count, c->err, b0);
     c->kernel_launches++;
     return cudaGetLastError();
 }

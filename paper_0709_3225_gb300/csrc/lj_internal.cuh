@@ -104,9 +104,13 @@ struct lj_ctx {
     int deterministic;
     void *pos_alt;
     int32_t *perm_alt;
-    // lj_step_host: the copy of x back overlaps the last force evaluation
+    // lj_step_host: the copy of x back overlaps the last force evaluation;
+    // the copies in arrive in 4 parts, each kicked, drifted and binned as
+    // soon as it is there (kdb_done: step 0's update is done)
     cudaStream_t copy_stream;
-    cudaEvent_t ev_xfinal;
+    cudaEvent_t ev_xfinal, ev_entry;
+    cudaEvent_t ev_chunk[4];
+    int kdb_done;
     // graph replay of the middle steps of lj_step (lj_set_graph)
     int use_graph;
     cudaGraphExec_t gexec;   // one captured middle step
@@ -270,7 +274,9 @@ cudaError_t launch_scan(lj_ctx *c, bool gated = false);
 cudaError_t launch_scatter(lj_ctx *c, const double *x, bool wrap);
 cudaError_t launch_force(lj_ctx *c, void *f, bool energy);
 cudaError_t launch_energy_reduce(lj_ctx *c);
-cudaError_t launch_kick_drift_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick);
+// Particles [i_begin, i_end) (i_end < 0: to n).
+cudaError_t launch_kick_drift_bin(lj_ctx *c, double *x, double *v, const void *f, int nkick, int64_t i_begin = 0,
+                                  int64_t i_end = -1);
 cudaError_t launch_kick(lj_ctx *c, double *v, const void *f);
 // Skin mode: kick + drift + displacement tracking, then the rebuild decision.
 cudaError_t launch_kick_drift_skin(lj_ctx *c, double *x, double *v, const void *f, int nkick);
