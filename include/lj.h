@@ -419,6 +419,16 @@ int lj_batch_info(const lj_batch *b, int64_t *ntot, int64_t *ncell, int32_t *gri
  * as in lj_set_tuning). */
 int lj_batch_set_tuning(lj_batch *b, int32_t cells_per_grab, int32_t use_graph, int32_t group_width);
 
+/* Force kernel of the batch's step launch: 3 = the 27-cell warp-per-cell
+ * code (the default, and the only choice for cell subdivision 2), 7 = each
+ * pair once over the half stencil (the pair-once device code of
+ * lj_set_tuning kernel 7, with f zeroed in the scatter phase and the
+ * reactions added with atomics; FP32 sums not bitwise reproducible between
+ * runs; its 128 registers leave fewer resident warps for the other phases
+ * of the launch).  LJ_EINVAL for other values, or 7 with subdivision 2.
+ * Host only; a captured step graph is captured again. */
+int lj_batch_set_kernel(lj_batch *b, int32_t kernel);
+
 /* Forces of every replica at x into f (device arrays as above); with
  * energy != 0, f[:, 3] holds per-particle energies.  Asynchronous. */
 int lj_batch_forces(lj_batch *b, const double *x, void *f, int32_t energy);

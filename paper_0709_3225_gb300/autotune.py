@@ -188,11 +188,15 @@ def make_system(x, v, box: float, rho: float, *, use_cache: bool = True, path: s
 
 def batch_candidates() -> list[dict]:
     """Batch settings: cell subdivision k (1: 27-cell stencil; 2: half-size
-    cells, 125-cell stencil, group width 4 compiled in), cells per pull,
+    cells, 125-cell stencil, group width 4 compiled in), force kernel (7:
+    each pair once, k = 1 only; 3: the 27-cell code), cells per pull,
     lane-group width, graph replay."""
-    out = [{"subdiv": 1, "cells_per_grab": c, "gw": g, "graph": True} for c in (1, 2, 4, 8, 16) for g in (0, 8, -1)]
-    out.append({"subdiv": 1, "cells_per_grab": 4, "gw": 0, "graph": False})
-    out += [{"subdiv": 2, "cells_per_grab": c, "gw": g, "graph": True} for c in (1, 4, 16) for g in (0, 2, -1)]
+    out = [{"subdiv": 1, "kernel": 7, "cells_per_grab": c, "gw": 0, "graph": True} for c in (1, 2, 4, 8)]
+    out.append({"subdiv": 1, "kernel": 7, "cells_per_grab": 4, "gw": 0, "graph": False})
+    out += [{"subdiv": 1, "kernel": 3, "cells_per_grab": c, "gw": g, "graph": True} for c in (1, 2, 4, 8, 16)
+            for g in (0, 8, -1)]
+    out += [{"subdiv": 2, "kernel": 3, "cells_per_grab": c, "gw": g, "graph": True} for c in (1, 4, 16)
+            for g in (0, 2, -1)]
     return out
 
 
@@ -221,6 +225,7 @@ def tune_batch(batch: lj.Batch, rho: float, steps: int = 10, warmup: int = 3, us
     if use_cache:
         hit = load_cache(path).get(key)
         if hit and hit.get("subdiv", 1) == own:
+            batch.set_kernel(hit.get("kernel", 3))
             batch.set_tuning(hit["cells_per_grab"], hit["graph"], hit["gw"])
             return dict(hit, cached=True)
     results = []
@@ -238,6 +243,7 @@ def tune_batch(batch: lj.Batch, rho: float, steps: int = 10, warmup: int = 3, us
             if target is None:
                 continue
             saved = (target.x.clone(), target.v.clone(), target.f.clone(), target._forces_valid)
+            target.set_kernel(cand.get("kernel", 3))
             target.set_tuning(cand["cells_per_grab"], cand["graph"], cand["gw"])
             ms = _time_steps(target.step, steps, warmup)
             target.check()
@@ -252,8 +258,9 @@ def tune_batch(batch: lj.Batch, rho: float, steps: int = 10, warmup: int = 3, us
                 t.close()
     best = min(results, key=lambda r: r["ms_per_step"])
     best_own = min((r for r in results if r["subdiv"] == own), key=lambda r: r["ms_per_step"])
+    batch.set_kernel(best_own.get("kernel", 3))
     batch.set_tuning(best_own["cells_per_grab"], best_own["graph"], best_own["gw"])
-    choice = {k: best[k] for k in ("subdiv", "cells_per_grab", "gw", "graph", "ms_per_step")}
+    choice = {k: best[k] for k in ("subdiv", "kernel", "cells_per_grab", "gw", "graph", "ms_per_step")}
     store_cache(key, choice, path)
     return dict(choice, cached=False, trials=results)
 
@@ -265,6 +272,7 @@ def batch_for(batch: lj.Batch, choice: dict) -> lj.Batch:
         return batch
     nb = _clone_batch(batch, choice["subdiv"])
     batch.close()
+    nb.set_kernel(choice.get("kernel", 3) if choice["subdiv"] == 1 else 3)
     nb.set_tuning(choice["cells_per_grab"], choice["graph"], choice["gw"])
     nb.forces()
     return nb

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "lj_force_cell.cuh"
+#include "lj_force_n3.cuh"
 
 namespace {
 
@@ -223,11 +224,14 @@ __device__ void phase_scan(const BatchDev &b)
     }
 }
 
-// Phase 3: sorted, cell-centred FP32 positions (w = particle index).
-__device__ void phase_scatter(const BatchDev &b, int op, const double *__restrict__ x)
+// Phase 3: sorted, cell-centred FP32 positions (w = particle index).  With
+// fz (the pair-once force phase, which adds into f) f is zeroed too; the
+// first phase has read it already.
+__device__ void phase_scatter(const BatchDev &b, int op, const double *__restrict__ x, float4 *__restrict__ fz)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.ntot; i += stride) {
+        if (fz) fz[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         const int r = b.rep_of[i];
         const int c = b.cell_of[i];
         const int nc = b.ncs[r];
@@ -293,9 +297,63 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_step(BatchDev b, War
     if (!grid_barrier(b)) return;
     phase_scan(b);
     if (!grid_barrier(b)) return;
-    phase_scatter(b, op, x);
+    phase_scatter(b, op, x, nullptr);
     if (!grid_barrier(b)) return;
     phase_force<R, MODE, ENERGY, GFIX>(b, k, f);
+}
+
+// Phase 4 with each pair once: the single-system pair-once kernel's device
+// code (lj_force_n3.cuh, coherent loads: the positions and starts were
+// written by earlier phases of this launch) on each replica's grid.
+template <int MODE, bool ENERGY>
+__device__ void phase_force_n3(const BatchDev &b, const WarpParams &k, float4 *__restrict__ f)
+{
+    extern __shared__ __align__(16) float bsmem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float4 *S = reinterpret_cast<float4 *>(bsmem + (size_t)warp * n3_slice_words(k.cap));
+    float4 *stab = S + k.cap;
+    int *spre = reinterpret_cast<int *>(stab + kN3Half);
+    float4 *part = reinterpret_cast<float4 *>(spre + 16);
+    double eacc = 0.0, wacc = 0.0;
+    auto load = [&](int c) {
+        const int r = b.rep_of_cell[c];
+        const int nc = b.ncs[r];
+        return half_load<false>(b.start, c - b.coff[r], nc, 1.0f / (float)nc, b.coff[r]);
+    };
+    for (;;) {
+        unsigned c0 = 0;
+        if (lane == 0) c0 = atomicAdd(b.work, (unsigned)b.cells_per_grab);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if ((int64_t)c0 >= b.ncell) break;
+        const int c1 = (int)min((int64_t)c0 + b.cells_per_grab, b.ncell);
+        HalfLoad nxt = load((int)c0);   // the next cell's table loads before this cell's work
+        for (int c = (int)c0; c < c1; c++) {
+            const HalfLoad cur = nxt;
+            if (c + 1 < c1) nxt = load(c + 1);
+            n3_cell<MODE, ENERGY, false>(k, b.pos, f, cur, (float)b.cw[b.rep_of_cell[c]], S, stab, spre, part, eacc,
+                                         wacc);
+        }
+    }
+}
+
+// One step with the pair-once force phase (cell subdivision 1): 96
+// registers for the force phase, so 2 blocks of 256 threads per SM.
+template <int MODE, bool ENERGY>
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_step_n3(BatchDev b, WarpParams k, int op, double *x,
+                                                                     double *v, float4 *f)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *b.work = 0u;
+    phase_bin(b, op, x, v, f);
+    if (!grid_barrier(b)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) b.first[0] = 0;
+    phase_tiles(b);
+    if (!grid_barrier(b)) return;
+    phase_scan(b);
+    if (!grid_barrier(b)) return;
+    phase_scatter(b, op, x, f);
+    if (!grid_barrier(b)) return;
+    phase_force_n3<MODE, ENERGY>(b, k, f);
 }
 
 // Closing half kick of the last step: v += h f.
@@ -377,6 +435,18 @@ void *batch_kernel_g(int mode, bool energy)
     }
 }
 
+void *batch_kernel_n3(int mode, bool energy)
+{
+    switch (mode * 2 + (energy ? 1 : 0)) {
+        case 0: return (void *)k_batch_step_n3<0, false>;
+        case 1: return (void *)k_batch_step_n3<0, true>;
+        case 2: return (void *)k_batch_step_n3<1, false>;
+        case 3: return (void *)k_batch_step_n3<1, true>;
+        case 4: return (void *)k_batch_step_n3<2, false>;
+        default: return (void *)k_batch_step_n3<2, true>;
+    }
+}
+
 void *batch_kernel(int subdiv, int mode, bool energy, int gw)
 {
     if (subdiv == 2)
@@ -418,6 +488,10 @@ struct lj_batch {
     BatchDev d;
     WarpParams k;
     int grid, smem, use_graph;
+    // the pair-once step kernel (cell subdivision 1): its parameters (k with
+    // its own staging capacity), grid and shared memory; n3: it is selected
+    WarpParams kn3;
+    int grid_n3, smem_n3, n3;
     double max_mean_occ;
     double *rep_out, *host_out;
     int32_t *host_err;
@@ -471,14 +545,44 @@ cudaError_t configure(lj_batch *b)
         }
     if (minblk < 1) return cudaErrorInvalidConfiguration;
     b->grid = minblk * b->nsm;   // all blocks co-resident (cooperative launch)
+    b->grid_n3 = 0;
+    if (R != 1) return cudaSuccess;
+    // the pair-once kernel: staging capacity as for single systems, from the
+    // mean occupancy (the raw half stencil m = 14 n_cell plus a Poisson
+    // spread and the padding, at least 192, a multiple of 32)
+    const double m = kN3Half * mean_occ;
+    int cap3 = (int)(m + 4.0 * sqrt(m)) + 64;
+    cap3 = cap3 < 192 ? 192 : ((cap3 + 31) & ~31);
+    const int max3 = ((113 * 1024 - 2048) / (4 * (kBatchThreads / 32)) - (4 * kN3Half + 16 + 4 * kN3Home * 32)) / 4 & ~31;
+    if (cap3 > max3) cap3 = max3;
+    b->kn3 = b->k;
+    b->kn3.cap = cap3;
+    b->smem_n3 = (kBatchThreads / 32) * n3_slice_words(cap3) * (int)sizeof(float);
+    int minblk3 = 1 << 30;
+    for (int mode = 0; mode < 3; mode++)
+        for (int en = 0; en < 2; en++) {
+            void *kern = batch_kernel_n3(mode, en != 0);
+            cudaError_t e = raise_dyn_smem(kern, b->smem_n3);
+            if (e != cudaSuccess) return e;
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBatchThreads, b->smem_n3);
+            if (e != cudaSuccess) return e;
+            if (nb < minblk3) minblk3 = nb;
+        }
+    b->grid_n3 = minblk3 >= 1 ? minblk3 * b->nsm : 0;
     return cudaSuccess;
 }
 
 cudaError_t launch_step_kernel(lj_batch *b, bool energy, int op, double *x, double *v, float4 *f)
 {
+    b->launches++;
+    if (b->n3) {
+        void *kern = batch_kernel_n3(b->p.shift_mode, energy);
+        void *args[] = {&b->d, &b->kn3, &op, &x, &v, &f};
+        return cudaLaunchCooperativeKernel(kern, dim3(b->grid_n3), dim3(kBatchThreads), args, b->smem_n3, b->stream);
+    }
     void *kern = batch_kernel(b->p.cell_subdiv, b->p.shift_mode, energy, b->k.gw);
     void *args[] = {&b->d, &b->k, &op, &x, &v, &f};
-    b->launches++;
     return cudaLaunchCooperativeKernel(kern, dim3(b->grid), dim3(kBatchThreads), args, b->smem, b->stream);
 }
 
@@ -685,6 +789,10 @@ extern "C" int lj_batch_create(lj_batch **out, int32_t nrep, const int64_t *n, c
     k.uc = (float)(rci6 * (4.0 * eps * s12 * rci6 - 4.0 * eps * s6));
     k.fc = (float)(rc * rci2 * rci6 * (48.0 * eps * s12 * rci6 - 24.0 * eps * s6));
     LJ_BCK(configure(b));
+    // the 27-cell code by default: the pair-once step measured slower on the
+    // 256-replica ensemble (2.12 against 1.70 ms per step), its 128
+    // registers leaving 16 warps per SM for every phase of the launch
+    b->n3 = 0;
 #undef LJ_BCK
     *out = b;
     return LJ_OK;
@@ -702,8 +810,8 @@ extern "C" int lj_batch_info(const lj_batch *b, int64_t *ntot, int64_t *ncell, i
     if (!b) return LJ_EINVAL;
     if (ntot) *ntot = b->ntot;
     if (ncell) *ncell = b->ncell;
-    if (grid) *grid = b->grid;
-    if (cap) *cap = b->k.cap;
+    if (grid) *grid = b->n3 ? b->grid_n3 : b->grid;
+    if (cap) *cap = b->n3 ? b->kn3.cap : b->k.cap;
     return LJ_OK;
 }
 
@@ -715,7 +823,20 @@ extern "C" int lj_batch_set_tuning(lj_batch *b, int32_t cells_per_grab, int32_t 
         return LJ_EINVAL;
     b->d.cells_per_grab = cells_per_grab;
     b->k.gw = group_width;
+    b->kn3.gw = group_width;
     b->use_graph = use_graph ? 1 : 0;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    return LJ_OK;
+}
+
+extern "C" int lj_batch_set_kernel(lj_batch *b, int32_t kernel)
+{
+    if (!b || (kernel != 3 && kernel != 7)) return LJ_EINVAL;
+    if (kernel == 7 && b->grid_n3 == 0) return LJ_EINVAL;   // cell subdivision 2
+    b->n3 = kernel == 7 ? 1 : 0;
     if (b->gexec) {
         cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;

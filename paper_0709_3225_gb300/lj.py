@@ -96,6 +96,7 @@ _SIGS = {
     "lj_batch_info": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "lj_batch_set_tuning": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "lj_batch_set_kernel": ([_P, ctypes.c_int32], ctypes.c_int),
     "lj_batch_forces": ([_P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "lj_batch_step": ([_P, _P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "lj_batch_energy": ([_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -471,6 +472,7 @@ class Batch:
                                    _stream_ptr(stream)), "lj_batch_create")
         self.handle = h
         self._forces_valid = False
+        self.kernel = 3
 
     @property
     def ntot(self) -> int:
@@ -486,6 +488,11 @@ class Batch:
     def set_tuning(self, cells_per_grab: int = 4, use_graph: bool = True, group_width: int = 0) -> None:
         _ck(load().lj_batch_set_tuning(self.handle, int(cells_per_grab), 1 if use_graph else 0, int(group_width)),
             "lj_batch_set_tuning")
+
+    def set_kernel(self, kernel: int) -> None:
+        """3: the 27-cell code (default); 7: each pair once (cell subdivision 1)."""
+        _ck(load().lj_batch_set_kernel(self.handle, int(kernel)), "lj_batch_set_kernel")
+        self.kernel = int(kernel)
 
     def forces(self, energy: bool = False) -> None:
         _ck(load().lj_batch_forces(self.handle, ctypes.c_void_p(self.x.data_ptr()),

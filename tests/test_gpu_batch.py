@@ -158,3 +158,54 @@ def test_batch_rejects_bad_subdivision():
     with pytest.raises(lj.LJError) as ei:
         lj.Batch(xs, vs, e.box, cell_subdiv=3)
     assert ei.value.code == lj.LJ_EINVAL
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_pair_once_and_27_cell_batch_kernels(oracle_mod, mode):
+    """The batch's two force kernels (7: each pair once, the default; 3: the
+    27-cell code) against the oracle per replica, and 15 steps of each against
+    the oracle's trajectory."""
+    from paper_0709_3225_gb300 import lj
+    e, xs, vs = _small_ensemble(seed=17, nrep=4)
+    for kernel in (7, 3):
+        b = lj.Batch(xs, vs, e.box, shift_mode=mode)
+        b.set_kernel(kernel)
+        b.forces(energy=True)
+        b.check()
+        f = b.f.double().cpu().numpy()
+        for r in range(b.nrep):
+            fo, epo, _, _ = oracle_mod.forces_cells(xs[r], e.box[r], mode=mode)
+            fr = b.replica(f, r)
+            assert rel_rms(fr[:, :3], fo) <= 1e-5, (kernel, r)
+            K, S = oracle_mod.stiffness(xs[r], e.box[r], mode=mode)
+            near = oracle_mod.near_cutoff(xs[r], e.box[r], band=1e-5)
+            d = np.abs(fr[:, :3] - fo).max(axis=1)
+            assert np.all(d[~near] <= (6e-7 * K + 1e-5 * S)[~near]), (kernel, r)
+            assert np.all(np.abs(fr[~near, 3] - epo[~near]) <= 1e-5 * np.abs(epo).max()), (kernel, r)
+        b.step(15)
+        b.check()
+        x = b.x.cpu().numpy()
+        for r in range(b.nrep):
+            xo, vo = xs[r].copy(), vs[r].copy()
+            fo = oracle_mod.forces_cells(xo, e.box[r], mode=mode)[0]
+            # a force error of RMS 1e-5 F_rms moves positions by at most
+            # ~ dt^2 n^2 / 2 of it over n steps (as in the trajectory test above)
+            drift = 0.5 * 0.005 ** 2 * 15 ** 2 * 1e-5 * np.sqrt((fo ** 2).sum(axis=1).mean())
+            oracle_mod.vv(xo, vo, fo, e.box[r], 15, mode=mode)
+            d = np.abs(min_image(b.replica(x, r) - xo, e.box[r]))
+            assert np.sqrt((d ** 2).mean()) <= drift, (kernel, r)
+        b.close()
+
+
+def test_batch_kernel_choice_is_checked():
+    from paper_0709_3225_gb300 import lj
+    e, xs, vs = _small_ensemble(seed=19, nrep=2)
+    b = lj.Batch(xs, vs, e.box)
+    with pytest.raises(lj.LJError):
+        b.set_kernel(5)
+    b.close()
+    b2 = lj.Batch(xs, vs, e.box, cell_subdiv=2)
+    with pytest.raises(lj.LJError):
+        b2.set_kernel(7)
+    b2.set_kernel(3)
+    b2.close()
