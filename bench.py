@@ -858,7 +858,7 @@ def run_gpu(args):
         "fp64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "steps": k64,
                  "force_ms_per_launch": f64_ms / max(f64_n, 1),
                  "pair_interactions_per_s": pairs * 1e3 / ms64,
-                 "kernel": "k_force_w64 (compacted in-range pair lists)",
+                 "kernel": "k_force_w64 (compacted in-range pair lists, each pair once)",
                  "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
                               "achieved": FLOPS_PER_PAIR * pairs / (f64_ms / max(f64_n, 1) / 1e3) / 1e12,
                               "frac": FLOPS_PER_PAIR * pairs / (f64_ms / max(f64_n, 1) / 1e3) / 1e12

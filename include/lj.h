@@ -88,10 +88,11 @@ typedef struct lj_params {
 } lj_params;
 
 /* lj_params.flags select the force kernel (same results; for comparison).
- * Default (0): FP32-mixed uses the warp-per-cell kernel that takes each pair
- * once over the half stencil (lj_set_tuning kernel 7; kernel 3, the 27-cell
- * stencil, for cell_subdiv 2), staged in shared memory relative to the cell
- * centre; FP64 uses the FP64 warp kernel (kernel 3).
+ * Default (0): the warp-per-cell kernels that take each pair once over the
+ * half stencil (lj_set_tuning kernel 7; kernel 3, the 27-cell stencil, for
+ * cell_subdiv 2), staged in shared memory relative to the cell centre: in
+ * FP32-mixed contexts the FP32-mixed kernel, in FP64 contexts the FP64 warp
+ * kernel in its pair-once form.
  * LJ_FLAG_RUN_STAGED: the run kernel (a CTA per run of cells along x) with its
  *   9 neighbour-row windows staged by bulk asynchronous copies.
  * LJ_FLAG_RUN_DIRECT: the run kernel reading neighbour cells from global
@@ -356,15 +357,16 @@ int lj_skin_stats(lj_ctx *ctx, int64_t *rebuilds, int64_t *steps);
  * kernel 0 = warp-per-cell kernel (FP32-mixed only) with the velocity-Verlet
  * update of lj_step fused into it, 1 = run kernel with bulk-copy staging,
  * 2 = run kernel reading global memory, 3 = warp-per-cell kernel over the
- * 27-cell stencil with the update in a separate kernel (the FP64 default: in
- * FP64 contexts the FP64 warp kernel that compacts the in-range pairs before
- * any FP64 arithmetic), 7 = warp-per-cell kernel that evaluates each pair
- * once (Newton's third law: Eq. n2_force is antisymmetric, so the pair force
- * is added to i and subtracted from j; the home cell with itself and with
- * the 13 neighbours of positive offset; the FP32-mixed default for
- * cell_subdiv 1; f is zeroed and the contributions are added with atomics,
- * so its FP32 sums are not bitwise reproducible between runs, and contexts
- * with lj_set_deterministic on take kernel 3 instead), 4 = the paper's
+ * 27-cell stencil with the update in a separate kernel (in FP64 contexts
+ * the FP64 warp kernel that compacts the in-range pairs before any FP64
+ * arithmetic), 7 = warp-per-cell kernel that evaluates each pair once
+ * (Newton's third law: Eq. n2_force is antisymmetric, so the pair force is
+ * added to i and subtracted from j; the home cell with itself and with the
+ * 13 neighbours of positive offset; the default for cell_subdiv 1, in
+ * FP32-mixed and FP64 contexts; the contributions are added with atomics,
+ * into f zeroed first (FP32-mixed) or into a context buffer in cell order
+ * then copied to f (FP64), so the sums are not bitwise reproducible between
+ * runs, and contexts with lj_set_deterministic on take kernel 3 instead), 4 = the paper's
  * fixed-capacity cell arrays (Section 3.1: 32 placeholders per cell, empty
  * ones computed as virtual particles; FP32-mixed; a cell with more than 32
  * particles latches LJ_EOVERFLOW, reported by lj_check), 5 = the warp

@@ -101,6 +101,7 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->fs);
     cudaFree(c->g4);
     cudaFree(c->n2_scratch);
+    cudaFree(c->f_sorted);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->ev_xfinal) cudaEventDestroy(c->ev_xfinal);
     if (c->ev_entry) cudaEventDestroy(c->ev_entry);
@@ -426,8 +427,11 @@ int setup_grid(lj_ctx *c, int nc)
     c->pipe_grid = 0;
     if (c->p.precision == LJ_PREC_MIXED && c->p.cell_subdiv != 2) LJ_GRID_CK(pipe_force_configure(c));
     if (c->p.precision == LJ_PREC_MIXED && c->p.cell_subdiv != 2) LJ_GRID_CK(n3_force_configure(c));
+    if (c->p.precision == LJ_PREC_FP64 && !c->f_sorted && c->p.n > 0)   // the FP64 pair-once sums, in cell order
+        LJ_GRID_CK(cudaMalloc(&c->f_sorted, (size_t)c->p.n * 4 * sizeof(double)));
     {
         int np = c->force_grid > c->wforce_grid ? c->force_grid : c->wforce_grid;
+        if (c->n3_grid > np) np = c->n3_grid;
         if (np < 32 * c->nsm) np = 32 * c->nsm;   // room for the adjoint kernel's grid
         c->npartial_cap = np;
         LJ_GRID_CK(cudaMalloc(&c->partial, 2 * (size_t)np * sizeof(double)));
@@ -460,10 +464,10 @@ extern "C" int lj_create(lj_ctx **out, const lj_params *p, void *stream)
     // force kernel (lj_set_tuning kernel 0) it measured slower at N = 4M
     // (1.35 vs 1.20 ms per step) from the scattered x, v accesses.
     c->fuse_update = 0;
-    // FP32-mixed forces with cell subdivision 1 take each pair once
-    // (Newton's third law, lj_set_tuning kernel 7) unless a flag asks for a
-    // run kernel.
-    c->n3 = (p->precision == LJ_PREC_MIXED && c->p.cell_subdiv == 1 && !c->use_run_kernel) ? 1 : 0;
+    // Forces with cell subdivision 1 take each pair once (Newton's third
+    // law, lj_set_tuning kernel 7; FP32-mixed and FP64) unless a flag asks
+    // for a run kernel.
+    c->n3 = (c->p.cell_subdiv == 1 && !c->use_run_kernel) ? 1 : 0;
 
 #define LJ_CREATE_CK(call)            \
     do {                              \
@@ -924,8 +928,8 @@ extern "C" int lj_set_tuning(lj_ctx *c, int32_t kernel, int32_t group_width, int
 {
     if (c) c->gen++;   // captured steps hold the old configuration
     if (!c || kernel < 0 || kernel > 7 || cells_per_grab < 0 || cells_per_grab > 1024) return LJ_EINVAL;
-    if (kernel == 7) {   // each pair once (Newton's third law): FP32-mixed, 27-cell stencil
-        if (c->p.precision != LJ_PREC_MIXED || c->p.cell_subdiv == 2) return LJ_EINVAL;
+    if (kernel == 7) {   // each pair once (Newton's third law), 27-cell stencil: FP32-mixed or FP64
+        if (c->p.cell_subdiv == 2) return LJ_EINVAL;
         const int r = lj_set_tuning(c, 3, group_width, cells_per_grab);   // gw: for the deterministic fallback
         if (r != LJ_OK) return r;
         c->n3 = 1;

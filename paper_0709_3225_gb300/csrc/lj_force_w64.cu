@@ -30,10 +30,26 @@
 // The same kernel, with the cotangents staged beside the positions, gives
 // the FP64 VJP of the forces (OP 2, vjp64): the pair lists are the same,
 // only the FP64 pair term and what is stored differ.
+// Pair-once form (PO, forces and energies; the default outside the
+// deterministic in-cell mode): the pair force is antisymmetric (Section 2),
+// so each pair is evaluated once.  The stencil is the home cell and its 13
+// neighbours of positive offset; Phase A lists, for home particle p, only
+// the staged candidates j > p (the home cell stages first, so this is every
+// pair of the home cell once and every pair with a neighbour cell once).
+// Phase B adds the pair force to p's running sum and its reaction to j's
+// sum by FP64 atomic adds, into a buffer in cell order (so that a cell's
+// atomics and its neighbours' stay within a few MB of L2); one more
+// coalesced kernel copies the buffer to f in particle order.  The FP64 pipe
+// is the bound: the sign of -F/r is taken into the coefficients and the
+// atomics carry no zero test, so that no FP64-pipe instruction is spent on
+// anything but the pair arithmetic (measured 7.9 -> 4.8 ms at N = 4M
+// against the 27-cell form; with zero tests and negations on the FP64 pipe
+// it measured 6.5 ms).
 #include <math.h>
 #include <string.h>
 
 #include "lj_force_cell.cuh"
+#include "lj_force_n3.cuh"
 #include "lj_pair.cuh"
 
 namespace {
@@ -61,28 +77,32 @@ struct W64Params {
 // Byte layout of one warp's shared-memory slice:
 //   X64, Y64, Z64   double[cap]   staged candidates, home frame, FP64
 //   HX64 .. HZ64    double[cap]   their cotangents (VJP only)
-//   part            double[2][kW64Comp][32]   per-lane partial sums (first, head)
+//   part            double[2][kW64Comp][32]   per-lane partial sums (first,
+//                                 head; not in the pair-once form)
 //   stab            float4[NS]    stencil table: FP32 shift xyz, start index
 //   S64             double[3][NS] stencil shifts in FP64 (padded to 16 B)
 //   X, Y, Z         float[cap]    staged candidates, home frame, FP32
 //   spre            int[NS + 1]   stencil prefix sums (padded to 4)
 //   off             int[kW64PMax + 4]   list offsets of the batch's particles
 //   list            uint16[lcap]  in-range candidate indices
+//   iw              int[cap]      sorted slot of each staged candidate (the
+//                                 pair-once form only)
 struct W64Layout {
-    int x64, h64, part, stab, s64, x32, spre, off, list, bytes;
-    __host__ __device__ W64Layout(int cap, int R, int lcap, bool vjp = false)
+    int x64, h64, part, stab, s64, x32, spre, off, list, iw, bytes;
+    __host__ __device__ W64Layout(int cap, int R, int lcap, bool vjp = false, bool po = false)
     {
         const int ns = (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
         x64 = 0;
         h64 = x64 + 24 * cap;
         part = h64 + (vjp ? 24 * cap : 0);
-        stab = part + 2 * kW64Comp * 32 * 8;
+        stab = part + (po ? 0 : 2 * kW64Comp * 32 * 8);
         s64 = stab + 16 * ns;
         x32 = s64 + ((24 * ns + 15) & ~15);
         spre = x32 + 12 * cap;
         off = spre + 4 * ((ns + 1 + 3) & ~3);
         list = off + 4 * (kW64PMax + 4);
-        bytes = (list + 2 * lcap + 15) & ~15;
+        iw = (list + 2 * lcap + 15) & ~15;
+        bytes = (iw + (po ? 4 * cap : 0) + 15) & ~15;
     }
 };
 
@@ -299,13 +319,12 @@ __device__ void w64_plain(const W64Params &k, const Coef<double> &kc, const doub
 // T, or -1 (nothing written that matters) when they would not fit the slice
 // with the 64 padding entries Phase A reads.  With HX64 (VJP) the kept
 // candidates' cotangents are staged too.
-template <int R>
+template <int NS, int P2>
 __device__ __forceinline__ int w64_stage(const W64Params &k, const double4_16a *__restrict__ pos, float *X, float *Y,
                                          float *Z, double *X64, double *Y64, double *Z64, double *HX64,
-                                         double *HY64, double *HZ64, const float4 *stab, const double *S64,
+                                         double *HY64, double *HZ64, int *Iw, const float4 *stab, const double *S64,
                                          const int *spre, int Ttot, int s_home, int n_home)
 {
-    constexpr int NS = Stencil<R>::NS, P2 = Stencil<R>::P2;
     const int lane = threadIdx.x & 31;
     float bxl = 3.4e38f, byl = 3.4e38f, bzl = 3.4e38f, bxh = -3.4e38f, byh = -3.4e38f, bzh = -3.4e38f;
     for (int p0 = 0; p0 < n_home; p0 += 32) {
@@ -391,6 +410,7 @@ __device__ __forceinline__ int w64_stage(const W64Params &k, const double4_16a *
                     HY64[sl] = h.y;
                     HZ64[sl] = h.z;
                 }
+                if (Iw) Iw[sl] = src[u];
             }
             T += __popc(kept);
         }
@@ -510,12 +530,216 @@ __device__ __forceinline__ void w64_pairs(const W64Params &k, const Coef<double>
     __syncwarp();   // part, list and off are rewritten by the next batch
 }
 
-template <int R, int MODE, int OP>
+// Half-stencil table of home cell (cx, cy, cz) for the pair-once form:
+// entries e = 0 (the home cell) .. 13 (the neighbours with (dz, dy, dx) > 0
+// lexicographically), as stencil_table writes them for the full stencil
+// (FP32 shift and first particle in stab, FP64 shifts in S64 with stride
+// kN3Half, prefix sums in spre).  Returns the total.  All 32 lanes.
+__device__ __forceinline__ int half_table64(const int32_t *__restrict__ start, int cx, int cy, int cz, int nc,
+                                            float cw, float4 *stab, int *spre, double *S64, double cw64)
+{
+    const int lane = threadIdx.x & 31;
+    int nn = 0;
+    if (lane < kN3Half) {
+        int dx, dy, dz;
+        half_delta(lane, dx, dy, dz);
+        int ux = cx + dx, uy = cy + dy, uz = cz + dz;
+        ux += ux < 0 ? nc : 0;
+        ux -= ux >= nc ? nc : 0;
+        uy += uy < 0 ? nc : 0;
+        uy -= uy >= nc ? nc : 0;
+        uz += uz < 0 ? nc : 0;
+        uz -= uz >= nc ? nc : 0;
+        const int64_t cn = ux + (int64_t)nc * (uy + (int64_t)nc * uz);
+        const int st = start[cn];
+        nn = start[cn + 1] - st;
+        stab[lane] = make_float4((float)dx * cw, (float)dy * cw, (float)dz * cw, __int_as_float(st));
+        S64[lane] = (double)dx * cw64;
+        S64[kN3Half + lane] = (double)dy * cw64;
+        S64[2 * kN3Half + lane] = (double)dz * cw64;
+    }
+    int P = nn;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, P, o);
+        if (lane >= o) P += y;
+    }
+    if (lane < kN3Half) spre[lane] = P - nn;
+    if (lane == kN3Half - 1) spre[kN3Half] = P;
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, P, kN3Half - 1);
+}
+
+// FP64 additions into the pair-once form's sums (zeroed before the launch),
+// without a test for zero: a comparison of doubles would take FP64-pipe
+// issue slots, the scarce resource here.
+template <bool ENERGY>
+__device__ __forceinline__ void add_force64(double4_16a *fs, int slot, double fx, double fy, double fz, double e)
+{
+    atomicAdd(&fs[slot].x, fx);
+    atomicAdd(&fs[slot].y, fy);
+    atomicAdd(&fs[slot].z, fz);
+    if constexpr (ENERGY) atomicAdd(&fs[slot].w, e);
+}
+
+// The pair term of the pair-once form: returns -F(r)/r (0 outside rc or
+// for r = 0), with the pair energy in u (ENERGY) and r^2.  Same formulas,
+// cutoff test and reciprocal as pair64; the sign is taken into the
+// coefficients, so that the reaction (-F/r d) and the home particle's
+// subtraction need no negation.
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ double pair64_nf(double dx, double dy, double dz, const Coef<double> &k, double &u,
+                                            double &r2)
+{
+    r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    const long long b = __double_as_longlong(r2);
+    const bool in = b < __double_as_longlong(k.rc2) && b != 0;
+    double ri, rinv = 0.0;
+    if constexpr (MODE == 2) {
+        double y = rsqrt64_approx(r2);
+        const double h = fma(-r2 * y, y, 1.0);
+        y = fma(y, h * fma(h, 0.375, 0.5), y);
+        rinv = in ? y : 0.0;
+        ri = rinv * rinv;
+    } else {
+        double y = rcp64_approx(r2);
+        const double h = fma(-r2, y, 1.0);
+        y = fma(y, fma(h, h, h), y);
+        ri = in ? y : 0.0;
+    }
+    const double r6 = ri * ri * ri;
+    double nf = ri * r6 * fma(-k.a12, r6, k.b6);
+    if constexpr (MODE == 2) nf = fma(k.fc, rinv, nf);
+    if constexpr (ENERGY) {
+        double v = r6 * (k.c12 * r6 - k.c6);
+        if constexpr (MODE >= 1) v -= k.uc;
+        if constexpr (MODE == 2) v += (r2 * rinv - k.rc) * k.fc;
+        u = in ? v : 0.0;
+    }
+    return nf;
+}
+
+// Phase B of the pair-once form over one batch: the list holds each pair
+// once (home particle p, staged candidate j > p).  A lane evaluates its
+// contiguous range of entries in FP64; the pair force goes to the home
+// particle's running sum and, with the opposite sign, to the candidate's
+// sum in fs (an FP64 atomic add per component); each running home sum is
+// added to fs when the lane's entries of that particle end.  fs is in the
+// cell order of the sorted positions, so the atomic adds of a cell and its
+// neighbours stay within a few MB of L2.  Energies: half of each pair
+// energy to both particles, the whole once to the FP64 totals.
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void w64_pairs_po(const W64Params &k, const Coef<double> &kc,
+                                             double4_16a *__restrict__ fs, const double *X64, const double *Y64,
+                                             const double *Z64, const int *Iw, const uint16_t *list, const int *off,
+                                             int E, int P, int pb, int s_home, double &eacc, double &wacc)
+{
+    const int lane = threadIdx.x & 31;
+    const int lo = (lane * E) >> 5;
+    const int hi = ((lane + 1) * E) >> 5;
+    if (lo < hi) {
+        int q = 0;
+#pragma unroll
+        for (int step = kW64PMax / 2; step > 0; step >>= 1)
+            if (q + step < P && off[q + step] <= lo) q += step;
+        int nxt = off[q + 1];
+        double xp = X64[pb + q], yp = Y64[pb + q], zp = Z64[pb + q];
+        Acc64 a;
+        a.zero();
+        auto flush = [&]() {
+            add_force64<ENERGY>(fs, s_home + pb + q, a.fx, a.fy, a.fz, 0.5 * a.e);
+            if constexpr (ENERGY) {
+                eacc += a.e;
+                wacc += a.w;
+            }
+        };
+        for (int e = lo; e < hi; e++) {
+            if (e == nxt) {
+                flush();
+                do {
+                    q++;
+                    nxt = off[q + 1];
+                } while (nxt == e);
+                xp = X64[pb + q];
+                yp = Y64[pb + q];
+                zp = Z64[pb + q];
+                a.zero();
+            }
+            const int j = list[e];
+            const double dx = xp - X64[j], dy = yp - Y64[j], dz = zp - Z64[j];
+            double u = 0.0, r2;
+            const double nf = pair64_nf<MODE, ENERGY>(dx, dy, dz, kc, u, r2);
+            const double rx = nf * dx, ry = nf * dy, rz = nf * dz;   // the reaction on j
+            a.fx -= rx;
+            a.fy -= ry;
+            a.fz -= rz;
+            if constexpr (ENERGY) {
+                a.e += u;
+                a.w = fma(-nf, r2, a.w);
+            }
+            add_force64<ENERGY>(fs, Iw[j], rx, ry, rz, 0.5 * u);
+        }
+        flush();
+    }
+    __syncwarp();   // list and off are rewritten by the next batch
+}
+
+// Plain path of the pair-once form (a cell whose pruned half stencil
+// overflows the slice): lanes own home particles, FP64 over the half
+// stencil read from global memory, each pair's reaction added by the lane
+// (fout: the sums in cell order).
+template <int MODE, bool ENERGY>
+__device__ void w64_plain_po(const W64Params &k, const Coef<double> &kc, const double4_16a *__restrict__ pos,
+                             double4_16a *__restrict__ fout, const float4 *stab, const double *S64, const int *spre,
+                             int s_home, int n_home, double &eacc, double &wacc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int p0 = 0; p0 < n_home; p0 += 32) {
+        const int i = p0 + lane;
+        const bool vi = i < n_home;
+        const double3 pi = load_xyz(pos, s_home + (vi ? i : 0));
+        Acc64 a;
+        a.zero();
+        for (int kk = 0; kk < kN3Half; kk++) {
+            const int st = __float_as_int(stab[kk].w);
+            const int nn = spre[kk + 1] - spre[kk];
+            const double xs = pi.x - S64[kk], ys = pi.y - S64[kN3Half + kk], zs = pi.z - S64[2 * kN3Half + kk];
+            for (int j = (kk == 0 ? p0 + 1 : 0); j < nn; j++) {
+                if (!vi || (kk == 0 && j <= i)) continue;
+                const double3 q = load_xyz(pos, st + j);
+                double tx = 0.0, ty = 0.0, tz = 0.0, te = 0.0, tw = 0.0;
+                pair64<MODE, ENERGY>(xs - q.x, ys - q.y, zs - q.z, kc, tx, ty, tz, te, tw);
+                a.fx += tx;
+                a.fy += ty;
+                a.fz += tz;
+                if constexpr (ENERGY) {
+                    a.e += te;
+                    a.w += tw;
+                }
+                add_force64<ENERGY>(fout, st + j, -tx, -ty, -tz, 0.5 * te);
+            }
+        }
+        if (vi) {
+            add_force64<ENERGY>(fout, s_home + i, a.fx, a.fy, a.fz, 0.5 * a.e);
+            if constexpr (ENERGY) {
+                eacc += a.e;
+                wacc += a.w;
+            }
+        }
+    }
+}
+
+// One home cell.  PO: the pair-once form (OP 0 or 1; fout is then the
+// zeroed sums in cell order), over the half stencil, each in-range pair
+// listed once.
+template <int R, int MODE, int OP, bool PO>
 __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const double4_16a *__restrict__ pos,
                          const int32_t *__restrict__ start, double4_16a *__restrict__ fout, unsigned char *slice,
                          int cx, int cy, int cz, double &eacc, double &wacc)
 {
-    const W64Layout L(k.cap, R, k.lcap, OP == 2);
+    static_assert(!PO || (OP != 2 && R == 1), "the pair-once form gives forces over the 27-cell stencil's half");
+    constexpr bool ENERGY = OP == 1;
+    const W64Layout L(k.cap, R, k.lcap, OP == 2, PO);
     double *X64 = reinterpret_cast<double *>(slice + L.x64);
     double *Y64 = X64 + k.cap;
     double *Z64 = Y64 + k.cap;
@@ -531,20 +755,30 @@ __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const doubl
     int *spre = reinterpret_cast<int *>(slice + L.spre);
     int *off = reinterpret_cast<int *>(slice + L.off);
     uint16_t *list = reinterpret_cast<uint16_t *>(slice + L.list);
+    int *Iw = PO ? reinterpret_cast<int *>(slice + L.iw) : nullptr;
     const int lane = threadIdx.x & 31;
     const int nc = k.nc;
 
     __syncwarp();   // the slice still holds the previous cell's data
-    const int carry = stencil_table<R>(start, 0, cx, cy, cz, nc, k.cwf, stab, spre, S64, k.cw);
+    const int carry = PO ? half_table64(start, cx, cy, cz, nc, k.cwf, stab, spre, S64, k.cw)
+                         : stencil_table<R>(start, 0, cx, cy, cz, nc, k.cwf, stab, spre, S64, k.cw);
     const int n_home = spre[1];
     if (n_home == 0) return;
     const int s_home = __float_as_int(stab[0].w);
-    const int T = carry <= 2 * k.cap
-                      ? w64_stage<R>(k, pos, X, Y, Z, X64, Y64, Z64, HX64, HY64, HZ64, stab, S64, spre, carry,
-                                     s_home, n_home)
-                      : -1;
+    int T = -1;
+    if (carry <= 2 * k.cap) {
+        if constexpr (PO)
+            T = w64_stage<kN3Half, 16>(k, pos, X, Y, Z, X64, Y64, Z64, nullptr, nullptr, nullptr, Iw, stab, S64,
+                                       spre, carry, s_home, n_home);
+        else
+            T = w64_stage<Stencil<R>::NS, 32>(k, pos, X, Y, Z, X64, Y64, Z64, HX64, HY64, HZ64, nullptr, stab, S64,
+                                              spre, carry, s_home, n_home);
+    }
     if (T < 0) {
-        w64_plain<R, MODE, OP>(k, kc, pos, fout, stab, S64, spre, s_home, n_home, eacc, wacc);
+        if constexpr (PO)
+            w64_plain_po<MODE, ENERGY>(k, kc, pos, fout, stab, S64, spre, s_home, n_home, eacc, wacc);
+        else
+            w64_plain<R, MODE, OP>(k, kc, pos, fout, stab, S64, spre, s_home, n_home, eacc, wacc);
         return;
     }
     const float2 *X2 = reinterpret_cast<const float2 *>(X);
@@ -571,8 +805,11 @@ __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const doubl
                 float2 r2 = __fmul2_rn(dx, dx);
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dz, dz, r2);
-                const bool ina = r2.x < k.rc2_pair && jx != p;
-                const bool inb = r2.y < k.rc2_pair && jx + 1 != p;
+                // pair-once: candidate j > p only (the home particles
+                // before p listed p already; neighbour cells stage after
+                // the home cell)
+                const bool ina = r2.x < k.rc2_pair && (PO ? jx > p : jx != p);
+                const bool inb = r2.y < k.rc2_pair && (PO ? jx + 1 > p : jx + 1 != p);
                 const unsigned ba = __ballot_sync(0xffffffffu, ina);
                 const unsigned bb = __ballot_sync(0xffffffffu, inb);
                 if (ina) list[E + __popc(ba & lt)] = (uint16_t)jx;
@@ -580,7 +817,7 @@ __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const doubl
                 E += __popc(ba) + __popc(bb);
             }
             if (lane == 0) off[p - pb + 1] = E;
-            if (OP != 2 && E == E0 && lane == 0) {
+            if (!PO && OP != 2 && E == E0 && lane == 0) {
                 // no candidate within rc: the force is zero (a VJP adds nothing)
                 Acc64 a;
                 a.zero();
@@ -590,12 +827,15 @@ __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const doubl
         }
         __syncwarp();
         // Phase B
-        w64_pairs<MODE, OP>(k, kc, pos, fout, X64, Y64, Z64, HX64, HY64, HZ64, list, off, part, E, p - pb, pb,
-                            s_home, eacc, wacc);
+        if constexpr (PO)
+            w64_pairs_po<MODE, ENERGY>(k, kc, fout, X64, Y64, Z64, Iw, list, off, E, p - pb, pb, s_home, eacc, wacc);
+        else
+            w64_pairs<MODE, OP>(k, kc, pos, fout, X64, Y64, Z64, HX64, HY64, HZ64, list, off, part, E, p - pb, pb,
+                                s_home, eacc, wacc);
     }
 }
 
-template <int R, int MODE, int OP>
+template <int R, int MODE, int OP, bool PO>
 __global__ void __launch_bounds__(kW64Threads) k_force_w64(W64Params k, const double4_16a *__restrict__ pos,
                                                            const int32_t *__restrict__ start,
                                                            double4_16a *__restrict__ fout,
@@ -604,14 +844,14 @@ __global__ void __launch_bounds__(kW64Threads) k_force_w64(W64Params k, const do
     extern __shared__ __align__(16) unsigned char w64smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const W64Layout L(k.cap, R, k.lcap, OP == 2);
+    const W64Layout L(k.cap, R, k.lcap, OP == 2, PO);
     unsigned char *slice = w64smem + (size_t)warp * L.bytes;
     const Coef<double> kc(k);
     const int nc = k.nc;
     double eacc = 0.0, wacc = 0.0;
     auto one_cell = [&](int64_t c) {
         const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
-        w64_cell<R, MODE, OP>(k, kc, pos, start, fout, slice, cx, cy, cz, eacc, wacc);
+        w64_cell<R, MODE, OP, PO>(k, kc, pos, start, fout, slice, cx, cy, cz, eacc, wacc);
     };
     if (k.grab > 0) {
         for (;;) {
@@ -649,18 +889,34 @@ __global__ void __launch_bounds__(kW64Threads) k_force_w64(W64Params k, const do
     }
 }
 
-// FP64 contexts use the 27-cell stencil (subdivision 1) only.  op: see OP.
-void *w64_kernel(int mode, int op)
+// FP64 contexts use the 27-cell stencil (subdivision 1) only.  op: see OP;
+// po: the pair-once form (op 0 or 1).
+void *w64_kernel(int mode, int op, bool po = false)
 {
-    if (op == 2) return mode == 2 ? (void *)k_force_w64<1, 2, 2> : (void *)k_force_w64<1, 0, 2>;   // modes 0, 1: same force
-    switch (mode * 2 + (op == 1 ? 1 : 0)) {
-        case 0: return (void *)k_force_w64<1, 0, 0>;
-        case 1: return (void *)k_force_w64<1, 0, 1>;
-        case 2: return (void *)k_force_w64<1, 1, 0>;
-        case 3: return (void *)k_force_w64<1, 1, 1>;
-        case 4: return (void *)k_force_w64<1, 2, 0>;
-        default: return (void *)k_force_w64<1, 2, 1>;
+    if (op == 2) return mode == 2 ? (void *)k_force_w64<1, 2, 2, false> : (void *)k_force_w64<1, 0, 2, false>;   // modes 0, 1: same force
+    switch (mode * 4 + (op == 1 ? 2 : 0) + (po ? 1 : 0)) {
+        case 0: return (void *)k_force_w64<1, 0, 0, false>;
+        case 1: return (void *)k_force_w64<1, 0, 0, true>;
+        case 2: return (void *)k_force_w64<1, 0, 1, false>;
+        case 3: return (void *)k_force_w64<1, 0, 1, true>;
+        case 4: return (void *)k_force_w64<1, 1, 0, false>;
+        case 5: return (void *)k_force_w64<1, 1, 0, true>;
+        case 6: return (void *)k_force_w64<1, 1, 1, false>;
+        case 7: return (void *)k_force_w64<1, 1, 1, true>;
+        case 8: return (void *)k_force_w64<1, 2, 0, false>;
+        case 9: return (void *)k_force_w64<1, 2, 0, true>;
+        case 10: return (void *)k_force_w64<1, 2, 1, false>;
+        default: return (void *)k_force_w64<1, 2, 1, true>;
     }
+}
+
+// f[perm[s]] = fs[s]: the pair-once form's sums from cell order to
+// particle order.
+__global__ void k_unsort64(const double4_16a *__restrict__ fs, const int32_t *__restrict__ perm,
+                           double4_16a *__restrict__ f, int n)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) f[perm[s]] = fs[s];
 }
 
 W64Params w64_params_of(const lj_ctx *c)
@@ -742,23 +998,71 @@ cudaError_t w64_force_configure(lj_ctx *c)
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     c->wforce_grid = (int)grid;
+
+    // The pair-once form stages the half stencil: m = 14 n_cell raw
+    // candidates, with the same capacity rule; its lists are half as long.
+    // Its sums go to a buffer in cell order (the context's f_sorted),
+    // copied to f in particle order after the launch.
+    const double mh = (double)kN3Half * mean;
+    int hcap = (int)(0.75 * mh + 4.0 * sqrt(mh)) + 96;
+    hcap = hcap < 160 ? 160 : hcap;
+    hcap = (hcap + 7) & ~7;
+    while (hcap > 160 && (hcap > lcap || warps * W64Layout(hcap, subdiv, lcap, false, true).bytes > limit)) hcap -= 8;
+    if (warps * W64Layout(hcap, subdiv, lcap, false, true).bytes > limit) return cudaErrorInvalidValue;
+    c->n3cap = hcap;
+    c->n3_smem = warps * W64Layout(hcap, subdiv, lcap, false, true).bytes;
+    minblk = 1 << 30;
+    for (int mode = 0; mode < 3; mode++)
+        for (int en = 0; en < 2; en++) {
+            void *kern = w64_kernel(mode, en, true);
+            cudaError_t e = raise_dyn_smem(kern, c->n3_smem);
+            if (e != cudaSuccess) return e;
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kW64Threads, c->n3_smem);
+            if (e != cudaSuccess) return e;
+            if (nb < minblk) minblk = nb;
+        }
+    if (minblk < 1) minblk = 1;
+    grid = (int64_t)minblk * c->nsm;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    c->n3_grid = (int)grid;
     return cudaSuccess;
 }
 
 cudaError_t launch_force_w64(lj_ctx *c, void *f, bool energy)
 {
+    // pair-once form (sums by atomic adds, into the context's buffer in cell
+    // order) unless the context asks for sums in a fixed order or has no
+    // such buffer
+    const bool po = c->n3 && !c->deterministic && c->f_sorted;
     W64Params k = w64_params_of(c);
+    if (po) k.cap = c->n3cap;
     const double4_16a *pos = (const double4_16a *)c->pos;
     const int32_t *start = c->start;
     double *partial = c->partial;
-    void *args[] = {&k, (void *)&pos, (void *)&start, &f, &partial};
-    void *kern = w64_kernel(c->p.shift_mode, energy ? 1 : 0);
+    void *kern = w64_kernel(c->p.shift_mode, energy ? 1 : 0, po);
+    const int grid = po ? c->n3_grid : c->wforce_grid;
+    const int smem = po ? c->n3_smem : c->wforce_smem;
+    void *fk = po ? c->f_sorted : f;
+    void *args[] = {&k, (void *)&pos, (void *)&start, &fk, &partial};
     if (c->timing && c->ev_used + 2 <= c->nev) cudaEventRecord(c->ev[c->ev_used], c->stream);
-    cudaError_t e = cudaLaunchKernel(kern, dim3(c->wforce_grid), dim3(kW64Threads), args, c->wforce_smem, c->stream);
+    cudaError_t e = cudaSuccess;
+    if (po && c->p.n > 0) e = cudaMemsetAsync(c->f_sorted, 0, (size_t)c->p.n * sizeof(double4_16a), c->stream);
+    if (e == cudaSuccess)
+        e = cudaLaunchKernel(kern, dim3(grid), dim3(kW64Threads), args, smem, c->stream);
+    if (e == cudaSuccess && po && c->p.n > 0) {
+        const int nb = (int)((c->p.n + 255) / 256);
+        k_unsort64<<<nb, 256, 0, c->stream>>>((const double4_16a *)c->f_sorted, c->perm, (double4_16a *)f,
+                                              (int)c->p.n);
+        c->kernel_launches++;
+        e = cudaGetLastError();
+    }
     if (c->timing && c->ev_used + 2 <= c->nev) {
         cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
         c->ev_used += 2;
     }
+    if (po) c->npartial = grid;
     c->kernel_launches++;
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -74,9 +74,12 @@ struct lj_ctx {
     // pipelined warp kernel (lj_force_pipe.cu): slice capacities, launch shape
     int pcap, praw, pipe_smem, pipe_grid;
     int pipe;            // tuning: 1 = warp kernel with bulk-copied stencils (kernel 5)
-    // Newton's-third-law warp kernel (lj_force_n3.cu, tuning kernel 7, the
-    // FP32-mixed default for cell subdivision 1): slice capacity, launch shape
+    // Newton's-third-law kernels (tuning kernel 7; FP32-mixed: lj_force_n3.cu,
+    // the default for cell subdivision 1; FP64: the pair-once form of
+    // lj_force_w64.cu, whose sums go to f_sorted in cell order, n x 32 B):
+    // slice capacity, launch shape
     int n3, n3cap, n3_smem, n3_grid;
+    void *f_sorted;
     int fuse_update;     // warp kernel applies the velocity-Verlet update (lj_step)
     int grab;            // tuning: cells per work pull in the warp kernel (0 = static)
     int w64_lcap;        // FP64 warp kernel: list entries per warp

@@ -72,16 +72,18 @@ def test_liquid_2k(oracle_mod, precision, mode):
     _check(x, L, oracle_mod, precision, mode)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
 @pytest.mark.parametrize("kernel", [3, 7])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("state", ["liquid", "dense", "rho095", "cluster", "three_cells", "dilute"])
-def test_pairs_once_and_27_cell_kernels(oracle_mod, kernel, mode, state):
-    """The kernel that evaluates each pair once (Newton's third law, half
-    stencil, kernel 7: the FP32-mixed default) and the 27-cell kernel (3)
+def test_pairs_once_and_27_cell_kernels(oracle_mod, precision, kernel, mode, state):
+    """The kernels that evaluate each pair once (Newton's third law, half
+    stencil, kernel 7) and the 27-cell kernels (3), FP32-mixed and FP64,
     against the oracle: a liquid; rho = 2 (cells of ~32 particles: the
-    four-group layout and more than 32 home particles per pass); rho = 0.95
-    (cells over 16); a dense blob in a dilute gas (the plain path of cells
-    whose half stencil overflows the slice); 3 cells per side; a dilute gas."""
+    four-group layout and more than 32 home particles per pass; FP64 lists
+    in several batches); rho = 0.95 (cells over 16); a dense blob in a
+    dilute gas (the plain path of cells whose half stencil overflows the
+    slice); 3 cells per side; a dilute gas."""
     if state == "liquid":
         x, L = inputs.jittered_fcc(8, 0.8442, 0.1, 61)
     elif state == "dense":
@@ -95,7 +97,7 @@ def test_pairs_once_and_27_cell_kernels(oracle_mod, kernel, mode, state):
     else:
         x, L = inputs.jittered_fcc(7, 0.2, 0.2, 66)
     for grab in (0, 4):
-        _check(x, L, oracle_mod, "mixed", mode, kernel=kernel, grab=grab)
+        _check(x, L, oracle_mod, precision, mode, kernel=kernel, grab=grab)
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
@@ -165,6 +167,7 @@ def test_fp64_pair_lists_in_batches(oracle_mod, mode):
     from paper_0709_3225_gb300 import lj
     x, L = inputs.jittered_fcc(8, 1.1, 0.05, 50 + mode)
     f, _ = _check(x, L, oracle_mod, "fp64", mode, rc=3.0)
+    _check(x, L, oracle_mod, "fp64", mode, rc=3.0, kernel=7)
     s = lj.System(x, None, L, precision="fp64", shift_mode=mode, rc=3.0)
     lj.lj_set_tuning(s.ctx, 1)
     e, w = s.forces(energy=True)
@@ -174,14 +177,16 @@ def test_fp64_pair_lists_in_batches(oracle_mod, mode):
     assert np.abs(fr - f).max() <= 1e-13 * np.abs(f).max()
 
 
+@pytest.mark.parametrize("first", [3, 7])
 @pytest.mark.parametrize("grab,mode", [(0, 1), (1, 1), (4, 1), (4, 0), (4, 2)])
-def test_fp64_kernels_agree(grab, mode):
-    """FP64 warp kernel (static striding or work pulls) against the run
-    kernel, on a liquid with empty, sparse and crowded cells."""
+def test_fp64_kernels_agree(first, grab, mode):
+    """FP64 warp kernels (27-cell or pair-once; static striding or work
+    pulls) against the run kernel, on a liquid with empty, sparse and
+    crowded cells."""
     from paper_0709_3225_gb300 import lj
     x, L = dense_cluster_state(seed=7)
     out = []
-    for kernel in (3, 1):
+    for kernel in (first, 1):
         s = lj.System(x, None, L, precision="fp64", shift_mode=mode)
         lj.lj_set_tuning(s.ctx, kernel, 0, grab)
         e, w = s.forces(energy=True)
