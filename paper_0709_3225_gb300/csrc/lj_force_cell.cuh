@@ -11,6 +11,26 @@ namespace {
 constexpr float kFar = 1.0e4f;   // padding candidate: r^2 ~ 1e8 > rc^2
 constexpr int kStageBatch = 2;   // staging rounds whose loads are in flight together (measured: 2 > 4 > 1)
 
+// Order-preserving map of a float's bits to a signed int (negative floats:
+// magnitude bits flipped), so that the warp's integer min / max reductions
+// (one instruction each) give the float min / max of a bounding box.
+// An involution: f_unord undoes it.
+__device__ __forceinline__ int f_ord(float f)
+{
+    const int i = __float_as_int(f);
+    return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float f_unord(int i) { return __int_as_float(i ^ ((i >> 31) & 0x7fffffff)); }
+__device__ __forceinline__ void box_reduce(float &bxl, float &byl, float &bzl, float &bxh, float &byh, float &bzh)
+{
+    bxl = f_unord(__reduce_min_sync(0xffffffffu, f_ord(bxl)));
+    byl = f_unord(__reduce_min_sync(0xffffffffu, f_ord(byl)));
+    bzl = f_unord(__reduce_min_sync(0xffffffffu, f_ord(bzl)));
+    bxh = f_unord(__reduce_max_sync(0xffffffffu, f_ord(bxh)));
+    byh = f_unord(__reduce_max_sync(0xffffffffu, f_ord(byh)));
+    bzh = f_unord(__reduce_max_sync(0xffffffffu, f_ord(bzh)));
+}
+
 struct WarpParams {
     int n, nc, cap;              // cap: staged candidates per warp (multiple of 8, >= 40)
     int gw;                      // lane-group width: 0 compiled default, -1 per-cell choice, 2 .. 32 fixed
@@ -326,15 +346,7 @@ __device__ __forceinline__ bool cell_staged(const WarpParams &k, const float4 *_
             bzh = fmaxf(bzh, q.z);
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
-        byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
-        bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
-        bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
-        byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
-        bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
-    }
+    box_reduce(bxl, byl, bzl, bxh, byh, bzh);
     const float rcut2 = k.rc2 * 1.0001f;
     const unsigned lt = (1u << lane) - 1u;
     // Stencil entry of a candidate t.  With one entry per lane (NS <= 32) it

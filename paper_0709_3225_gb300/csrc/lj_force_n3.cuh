@@ -26,10 +26,12 @@
 //    evaluation covers two home particles against that candidate, whose
 //    reaction stays in registers for the block.
 //  * After a block the reactions are summed over the A groups (shuffles) and
-//    added to f[j] with one float4 atomic add per candidate (skipped when
-//    zero); after the last block the home partial forces are summed over the
-//    B lanes of their group through a shared-memory transpose and added to
-//    f[i] the same way.  f is zeroed before the launch.
+//    added to f[j] with one float4 atomic add per candidate (with no test
+//    for zero: the test's four comparisons cost more issue slots than the
+//    atomics it saves); after the last block the home partial forces are
+//    summed over the B lanes of their group through a shared-memory
+//    transpose and added to f[i] (skipped when zero).  f is zeroed before
+//    the launch.
 //  * Energies: per-particle f.w gets half of each pair energy on both sides;
 //    the FP64 totals take each pair once.
 //  * A cell whose pruned half stencil does not fit the warp's slice takes a
@@ -196,20 +198,20 @@ __device__ __forceinline__ void add_force(float4 *fout, int idx, float4 v)
 // of every block against its NH home pairs (pairs past its home particles
 // sit far away and add nothing), then the candidate's reaction is summed
 // over the A groups and added to f.
-template <int NH, int MODE, bool ENERGY>
+template <int NH, int LGB, int MODE, bool ENERGY>
 __device__ __forceinline__ void n3_blocks(const WarpParams &k, float4 *__restrict__ fout, const float4 *S, int T,
                                           int n_home, int p0, int a, int b, int A, int lgB, const float2 *hx,
                                           const float2 *hy, const float2 *hz, float2 *fx, float2 *fy, float2 *fz,
                                           float2 *fe, float2 &fw)
 {
-    const int B = 1 << lgB;
-    const int nblk = (T + B - 1) >> lgB;
+    constexpr int B = 1 << LGB;
+    const int nblk = (T + B - 1) >> LGB;
     for (int blk = 0; blk < nblk; blk++) {
-        const int j = (blk << lgB) + b;
+        const int j = (blk << LGB) + b;
         const float4 c = S[j];
         const float2 cx = f2(c.x), cy = f2(c.y), cz = f2(c.z);
         float2 rx = f2(0.0f), ry = f2(0.0f), rz = f2(0.0f), re = f2(0.0f);
-        if ((blk << lgB) < n_home) {
+        if ((blk << LGB) < n_home) {
 #pragma unroll
             for (int h = 0; h < NH; h++)
                 pair2_n3<MODE, ENERGY, true>(hx[h], hy[h], hz[h], p0 + 2 * h * A + a, p0 + (2 * h + 1) * A + a, cx, cy,
@@ -221,13 +223,14 @@ __device__ __forceinline__ void n3_blocks(const WarpParams &k, float4 *__restric
                                               fw, rx, ry, rz, re);
         }
         float sx = rx.x + rx.y, sy = ry.x + ry.y, sz = rz.x + rz.y, se = ENERGY ? re.x + re.y : 0.0f;
+#pragma unroll
         for (int o = B; o < 32; o <<= 1) {
             sx += __shfl_xor_sync(0xffffffffu, sx, o);
             sy += __shfl_xor_sync(0xffffffffu, sy, o);
             sz += __shfl_xor_sync(0xffffffffu, sz, o);
             if constexpr (ENERGY) se += __shfl_xor_sync(0xffffffffu, se, o);
         }
-        if (a == 0 && j < T) add_force(fout, __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
+        if (a == 0 && j < T) atomicAdd(fout + __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
     }
 }
 
@@ -265,12 +268,21 @@ __device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restri
         // the candidate blocks, compiled for the number of home pairs a lane
         // holds (a uniform choice per pass: no branches inside the loop)
         const int nh = (nu + 1) >> 1;
-        if (nh >= 4)
-            n3_blocks<4, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
-        else if (nh == 3)
-            n3_blocks<3, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
-        else
-            n3_blocks<2, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
+        if (lgB == 4) {
+            if (nh >= 4)
+                n3_blocks<4, 4, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
+            else if (nh == 3)
+                n3_blocks<3, 4, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
+            else
+                n3_blocks<2, 4, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
+        } else {
+            if (nh >= 4)
+                n3_blocks<4, 3, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
+            else if (nh == 3)
+                n3_blocks<3, 3, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
+            else
+                n3_blocks<2, 3, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
+        }
         // home forces: sum over the B lanes of each group through a transpose
         // in shared memory (row u, column a B + b); every lane sums 8 entries
 #pragma unroll
@@ -373,25 +385,9 @@ __device__ __forceinline__ bool n3_stage(const WarpParams &k, const float4 *__re
                 byl = byh = q[0].y;
                 bzl = bzh = q[0].z;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
-                byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
-                bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
-                bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
-                byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
-                bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
-            }
+            box_reduce(bxl, byl, bzl, bxh, byh, bzh);
         } else if (t0 == 0) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
-                byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
-                bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
-                bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
-                byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
-                bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
-            }
+            box_reduce(bxl, byl, bzl, bxh, byh, bzh);
         }
         if (T + 32 * kN3Batch + 32 > k.cap) {   // this batch plus the padding might not fit
             __syncwarp();

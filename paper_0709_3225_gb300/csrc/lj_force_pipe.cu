@@ -162,15 +162,7 @@ __global__ void __launch_bounds__(kPipeThreads, 9) k_force_pipe(WarpParams k, in
                 byl = byh = ph.y;
                 bzl = bzh = ph.z;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
-                byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
-                bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
-                bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
-                byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
-                bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
-            }
+            box_reduce(bxl, byl, bzl, bxh, byh, bzh);
             // lane k (1..26) converts and prunes stencil cell k from raw
             const float rcut2 = k.rc2 * 1.0001f;
             const unsigned lt = (1u << lane) - 1u;

@@ -339,15 +339,7 @@ __device__ __forceinline__ int w64_stage(const W64Params &k, const double4_16a *
             bzh = fmaxf(bzh, qz);
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o));
-        byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o));
-        bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o));
-        bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
-        byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
-        bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
-    }
+    box_reduce(bxl, byl, bzl, bxh, byh, bzh);
     const unsigned lt = (1u << lane) - 1u;
     int T = 0;
     for (int t0 = 0; t0 < Ttot; t0 += 32 * kStageBatch) {
