@@ -285,7 +285,10 @@ int lj_set_params(lj_ctx *ctx, double eps, double sigma);
  *   dparam += scale * (dL/deps, dL/dsigma)  (device double[2]).
  * The cell list is piecewise constant in x and contributes nothing.  Pair
  * arithmetic in the context's precision; parameter sums in FP64 (FP32-mixed:
- * FP32 partial sums over groups of 32 candidates, then FP64).  Each call
+ * FP32 partial sums over groups of 32 candidates, then FP64).  FP64 contexts
+ * on lj_set_tuning kernel 7 (their default) evaluate each pair once (the
+ * contribution to j is the negative of i's, J being even in d), adding by
+ * atomics, so their last bits can differ between calls too.  Each call
  * bins x again, so with the atomic in-cell order FP32 results can differ in
  * their last bits between calls (lj_set_deterministic makes them repeat).
  * Allocates an (n)-element cotangent buffer on first use.  Asynchronous. */

@@ -44,7 +44,9 @@
 // atomics carry no zero test, so that no FP64-pipe instruction is spent on
 // anything but the pair arithmetic (measured 7.9 -> 4.8 ms at N = 4M
 // against the 27-cell form; with zero tests and negations on the FP64 pipe
-// it measured 6.5 ms).
+// it measured 6.5 ms).  The VJP (OP 2) has a pair-once form too: J_ij is
+// even in d, so j receives the negative of i's J_ij (g_i - g_j) (vjp64_po);
+// k_unsort_add64 then adds the scaled buffer to dL/dx.
 #include <math.h>
 #include <string.h>
 
@@ -611,7 +613,56 @@ __device__ __forceinline__ double pair64_nf(double dx, double dy, double dz, con
     return nf;
 }
 
-// Phase B of the pair-once form over one batch: the list holds each pair
+// The VJP term of one pair in the pair-once form: with d = x_i - x_j and
+// g = g_i - g_j (vjp64's notation), the contribution to i is J_ij g and,
+// J_ij being even in d, the one to j is its negative.  Returns the one to j,
+// r = -(phi g + (phi'(r)/r)(d . g) d), and adds the pair's two parameter
+// terms, which over both particles are phi|eps=1 (d . g) and eps
+// (dphi/dsigma) (d . g), to (ae, as).  The signs are folded into -eps, so
+// that neither r nor i's subtraction of it needs a negation.
+template <int MODE>
+__device__ __forceinline__ void vjp64_po(double dx, double dy, double dz, double gx, double gy, double gz,
+                                         const W64Params &k, double &rx, double &ry, double &rz, double &ae,
+                                         double &as)
+{
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    const long long b = __double_as_longlong(r2);
+    const bool in = b < __double_as_longlong(k.rc2) && b != 0;
+    double ri, rinv = 0.0;
+    if constexpr (MODE == 2) {
+        double y = rsqrt64_approx(r2);
+        const double h = fma(-r2 * y, y, 1.0);
+        y = fma(y, h * fma(h, 0.375, 0.5), y);
+        rinv = in ? y : 0.0;
+        ri = rinv * rinv;
+    } else {
+        double y = rcp64_approx(r2);
+        const double h = fma(-r2, y, 1.0);
+        y = fma(y, fma(h, h, h), y);
+        ri = in ? y : 0.0;
+    }
+    const double r6 = ri * ri * ri;
+    const double r8 = ri * r6;
+    double phi1 = r8 * (k.va1 * r6 - k.vb1);
+    double dphi1 = r8 * ri * (8.0 * k.vb1 - 14.0 * k.va1 * r6);
+    double dsig1 = r8 * (12.0 * k.va1 * r6 - 6.0 * k.vb1) * k.visg;
+    if constexpr (MODE == 2) {
+        phi1 -= k.vfc1 * rinv;
+        dphi1 += k.vfc1 * rinv * ri;
+        dsig1 -= k.vdfc1 * rinv;
+    }
+    const double dot = fma(dz, gz, fma(dy, gy, dx * gx));
+    const double nphi = -k.veps * phi1;
+    const double nt = (-k.veps * dphi1) * dot;
+    rx = fma(nt, dx, nphi * gx);
+    ry = fma(nt, dy, nphi * gy);
+    rz = fma(nt, dz, nphi * gz);
+    ae = fma(phi1, dot, ae);
+    as = fma(k.veps * dsig1, dot, as);
+}
+
+// Phase B of the pair-once form over one batch (OP as w64_cell; for OP 2
+// the sums are those of the VJP, vjp64_po): the list holds each pair
 // once (home particle p, staged candidate j > p).  A lane evaluates its
 // contiguous range of entries in FP64; the pair force goes to the home
 // particle's running sum and, with the opposite sign, to the candidate's
@@ -620,12 +671,14 @@ __device__ __forceinline__ double pair64_nf(double dx, double dy, double dz, con
 // cell order of the sorted positions, so the atomic adds of a cell and its
 // neighbours stay within a few MB of L2.  Energies: half of each pair
 // energy to both particles, the whole once to the FP64 totals.
-template <int MODE, bool ENERGY>
+template <int MODE, int OP>
 __device__ __forceinline__ void w64_pairs_po(const W64Params &k, const Coef<double> &kc,
                                              double4_16a *__restrict__ fs, const double *X64, const double *Y64,
-                                             const double *Z64, const int *Iw, const uint16_t *list, const int *off,
+                                             const double *Z64, const double *HX64, const double *HY64,
+                                             const double *HZ64, const int *Iw, const uint16_t *list, const int *off,
                                              int E, int P, int pb, int s_home, double &eacc, double &wacc)
 {
+    constexpr bool ENERGY = OP == 1;
     const int lane = threadIdx.x & 31;
     const int lo = (lane * E) >> 5;
     const int hi = ((lane + 1) * E) >> 5;
@@ -636,11 +689,17 @@ __device__ __forceinline__ void w64_pairs_po(const W64Params &k, const Coef<doub
             if (q + step < P && off[q + step] <= lo) q += step;
         int nxt = off[q + 1];
         double xp = X64[pb + q], yp = Y64[pb + q], zp = Z64[pb + q];
+        double gpx = 0.0, gpy = 0.0, gpz = 0.0;
+        if constexpr (OP == 2) {
+            gpx = HX64[pb + q];
+            gpy = HY64[pb + q];
+            gpz = HZ64[pb + q];
+        }
         Acc64 a;
         a.zero();
         auto flush = [&]() {
             add_force64<ENERGY>(fs, s_home + pb + q, a.fx, a.fy, a.fz, 0.5 * a.e);
-            if constexpr (ENERGY) {
+            if constexpr (OP >= 1) {   // energy and virial, or the two parameter sums: each pair once
                 eacc += a.e;
                 wacc += a.w;
             }
@@ -655,20 +714,32 @@ __device__ __forceinline__ void w64_pairs_po(const W64Params &k, const Coef<doub
                 xp = X64[pb + q];
                 yp = Y64[pb + q];
                 zp = Z64[pb + q];
+                if constexpr (OP == 2) {
+                    gpx = HX64[pb + q];
+                    gpy = HY64[pb + q];
+                    gpz = HZ64[pb + q];
+                }
                 a.zero();
             }
             const int j = list[e];
             const double dx = xp - X64[j], dy = yp - Y64[j], dz = zp - Z64[j];
-            double u = 0.0, r2;
-            const double nf = pair64_nf<MODE, ENERGY>(dx, dy, dz, kc, u, r2);
-            const double rx = nf * dx, ry = nf * dy, rz = nf * dz;   // the reaction on j
+            double rx, ry, rz, u = 0.0;
+            if constexpr (OP == 2) {
+                vjp64_po<MODE>(dx, dy, dz, gpx - HX64[j], gpy - HY64[j], gpz - HZ64[j], k, rx, ry, rz, a.e, a.w);
+            } else {
+                double r2;
+                const double nf = pair64_nf<MODE, ENERGY>(dx, dy, dz, kc, u, r2);
+                rx = nf * dx;   // the reaction on j
+                ry = nf * dy;
+                rz = nf * dz;
+                if constexpr (ENERGY) {
+                    a.e += u;
+                    a.w = fma(-nf, r2, a.w);
+                }
+            }
             a.fx -= rx;
             a.fy -= ry;
             a.fz -= rz;
-            if constexpr (ENERGY) {
-                a.e += u;
-                a.w = fma(-nf, r2, a.w);
-            }
             add_force64<ENERGY>(fs, Iw[j], rx, ry, rz, 0.5 * u);
         }
         flush();
@@ -680,16 +751,19 @@ __device__ __forceinline__ void w64_pairs_po(const W64Params &k, const Coef<doub
 // overflows the slice): lanes own home particles, FP64 over the half
 // stencil read from global memory, each pair's reaction added by the lane
 // (fout: the sums in cell order).
-template <int MODE, bool ENERGY>
+template <int MODE, int OP>
 __device__ void w64_plain_po(const W64Params &k, const Coef<double> &kc, const double4_16a *__restrict__ pos,
                              double4_16a *__restrict__ fout, const float4 *stab, const double *S64, const int *spre,
                              int s_home, int n_home, double &eacc, double &wacc)
 {
+    constexpr bool ENERGY = OP == 1;
     const int lane = threadIdx.x & 31;
     for (int p0 = 0; p0 < n_home; p0 += 32) {
         const int i = p0 + lane;
         const bool vi = i < n_home;
         const double3 pi = load_xyz(pos, s_home + (vi ? i : 0));
+        double3 gi = make_double3(0.0, 0.0, 0.0);
+        if constexpr (OP == 2) gi = load_xyz(k.g4, s_home + (vi ? i : 0));
         Acc64 a;
         a.zero();
         for (int kk = 0; kk < kN3Half; kk++) {
@@ -699,21 +773,31 @@ __device__ void w64_plain_po(const W64Params &k, const Coef<double> &kc, const d
             for (int j = (kk == 0 ? p0 + 1 : 0); j < nn; j++) {
                 if (!vi || (kk == 0 && j <= i)) continue;
                 const double3 q = load_xyz(pos, st + j);
-                double tx = 0.0, ty = 0.0, tz = 0.0, te = 0.0, tw = 0.0;
-                pair64<MODE, ENERGY>(xs - q.x, ys - q.y, zs - q.z, kc, tx, ty, tz, te, tw);
-                a.fx += tx;
-                a.fy += ty;
-                a.fz += tz;
-                if constexpr (ENERGY) {
-                    a.e += te;
-                    a.w += tw;
+                const double dx = xs - q.x, dy = ys - q.y, dz = zs - q.z;
+                double rx, ry, rz, u = 0.0;
+                if constexpr (OP == 2) {
+                    const double3 h = load_xyz(k.g4, st + j);
+                    vjp64_po<MODE>(dx, dy, dz, gi.x - h.x, gi.y - h.y, gi.z - h.z, k, rx, ry, rz, a.e, a.w);
+                } else {
+                    double r2;
+                    const double nf = pair64_nf<MODE, ENERGY>(dx, dy, dz, kc, u, r2);
+                    rx = nf * dx;
+                    ry = nf * dy;
+                    rz = nf * dz;
+                    if constexpr (ENERGY) {
+                        a.e += u;
+                        a.w = fma(-nf, r2, a.w);
+                    }
                 }
-                add_force64<ENERGY>(fout, st + j, -tx, -ty, -tz, 0.5 * te);
+                a.fx -= rx;
+                a.fy -= ry;
+                a.fz -= rz;
+                add_force64<ENERGY>(fout, st + j, rx, ry, rz, 0.5 * u);
             }
         }
         if (vi) {
             add_force64<ENERGY>(fout, s_home + i, a.fx, a.fy, a.fz, 0.5 * a.e);
-            if constexpr (ENERGY) {
+            if constexpr (OP >= 1) {
                 eacc += a.e;
                 wacc += a.w;
             }
@@ -721,16 +805,15 @@ __device__ void w64_plain_po(const W64Params &k, const Coef<double> &kc, const d
     }
 }
 
-// One home cell.  PO: the pair-once form (OP 0 or 1; fout is then the
-// zeroed sums in cell order), over the half stencil, each in-range pair
-// listed once.
+// One home cell.  PO: the pair-once form (fout is then the zeroed sums in
+// cell order: forces, or for OP 2 the VJP's dL/dx before the scale), over
+// the half stencil, each in-range pair listed once.
 template <int R, int MODE, int OP, bool PO>
 __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const double4_16a *__restrict__ pos,
                          const int32_t *__restrict__ start, double4_16a *__restrict__ fout, unsigned char *slice,
                          int cx, int cy, int cz, double &eacc, double &wacc)
 {
-    static_assert(!PO || (OP != 2 && R == 1), "the pair-once form gives forces over the 27-cell stencil's half");
-    constexpr bool ENERGY = OP == 1;
+    static_assert(!PO || R == 1, "the pair-once form takes the 27-cell stencil's half");
     const W64Layout L(k.cap, R, k.lcap, OP == 2, PO);
     double *X64 = reinterpret_cast<double *>(slice + L.x64);
     double *Y64 = X64 + k.cap;
@@ -760,15 +843,15 @@ __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const doubl
     int T = -1;
     if (carry <= 2 * k.cap) {
         if constexpr (PO)
-            T = w64_stage<kN3Half, 16>(k, pos, X, Y, Z, X64, Y64, Z64, nullptr, nullptr, nullptr, Iw, stab, S64,
-                                       spre, carry, s_home, n_home);
+            T = w64_stage<kN3Half, 16>(k, pos, X, Y, Z, X64, Y64, Z64, HX64, HY64, HZ64, Iw, stab, S64, spre,
+                                       carry, s_home, n_home);
         else
             T = w64_stage<Stencil<R>::NS, 32>(k, pos, X, Y, Z, X64, Y64, Z64, HX64, HY64, HZ64, nullptr, stab, S64,
                                               spre, carry, s_home, n_home);
     }
     if (T < 0) {
         if constexpr (PO)
-            w64_plain_po<MODE, ENERGY>(k, kc, pos, fout, stab, S64, spre, s_home, n_home, eacc, wacc);
+            w64_plain_po<MODE, OP>(k, kc, pos, fout, stab, S64, spre, s_home, n_home, eacc, wacc);
         else
             w64_plain<R, MODE, OP>(k, kc, pos, fout, stab, S64, spre, s_home, n_home, eacc, wacc);
         return;
@@ -820,7 +903,8 @@ __device__ void w64_cell(const W64Params &k, const Coef<double> &kc, const doubl
         __syncwarp();
         // Phase B
         if constexpr (PO)
-            w64_pairs_po<MODE, ENERGY>(k, kc, fout, X64, Y64, Z64, Iw, list, off, E, p - pb, pb, s_home, eacc, wacc);
+            w64_pairs_po<MODE, OP>(k, kc, fout, X64, Y64, Z64, HX64, HY64, HZ64, Iw, list, off, E, p - pb, pb, s_home,
+                                   eacc, wacc);
         else
             w64_pairs<MODE, OP>(k, kc, pos, fout, X64, Y64, Z64, HX64, HY64, HZ64, list, off, part, E, p - pb, pb,
                                 s_home, eacc, wacc);
@@ -882,10 +966,13 @@ __global__ void __launch_bounds__(kW64Threads) k_force_w64(W64Params k, const do
 }
 
 // FP64 contexts use the 27-cell stencil (subdivision 1) only.  op: see OP;
-// po: the pair-once form (op 0 or 1).
+// po: the pair-once form.
 void *w64_kernel(int mode, int op, bool po = false)
 {
-    if (op == 2) return mode == 2 ? (void *)k_force_w64<1, 2, 2, false> : (void *)k_force_w64<1, 0, 2, false>;   // modes 0, 1: same force
+    if (op == 2) {   // modes 0 and 1: the same force
+        if (po) return mode == 2 ? (void *)k_force_w64<1, 2, 2, true> : (void *)k_force_w64<1, 0, 2, true>;
+        return mode == 2 ? (void *)k_force_w64<1, 2, 2, false> : (void *)k_force_w64<1, 0, 2, false>;
+    }
     switch (mode * 4 + (op == 1 ? 2 : 0) + (po ? 1 : 0)) {
         case 0: return (void *)k_force_w64<1, 0, 0, false>;
         case 1: return (void *)k_force_w64<1, 0, 0, true>;
@@ -909,6 +996,21 @@ __global__ void k_unsort64(const double4_16a *__restrict__ fs, const int32_t *__
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < n) f[perm[s]] = fs[s];
+}
+
+// dx[perm[s]] += scale vs[s]: the pair-once VJP's sums from cell order to
+// particle order, (n, 3) rows.
+__global__ void k_unsort_add64(const double4_16a *__restrict__ vs, const int32_t *__restrict__ perm,
+                               double *__restrict__ dx, double scale, int n)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) {
+        const double4_16a v = vs[s];
+        double *o = dx + 3 * (int64_t)perm[s];
+        o[0] = fma(scale, v.x, o[0]);
+        o[1] = fma(scale, v.y, o[1]);
+        o[2] = fma(scale, v.z, o[2]);
+    }
 }
 
 W64Params w64_params_of(const lj_ctx *c)
@@ -1063,7 +1165,11 @@ cudaError_t launch_force_w64(lj_ctx *c, void *f, bool energy)
 cudaError_t launch_vjp_w64(lj_ctx *c, double scale, double *dx, double a1, double b1, double fc1, double dfc1,
                            int *grid_out)
 {
+    // pair-once form (as launch_force_w64) into the cell-order buffer, then
+    // dx += scale * the buffer in particle order
+    const bool po = c->n3 && !c->deterministic && c->f_sorted && c->n3cap > 0;
     W64Params k = w64_params_of(c);
+    if (po) k.cap = c->n3cap;
     k.g4 = (const double4_16a *)c->g4;
     k.dxo = dx;
     k.scale = scale;
@@ -1074,8 +1180,8 @@ cudaError_t launch_vjp_w64(lj_ctx *c, double scale, double *dx, double a1, doubl
     k.veps = c->p.eps;
     k.visg = 1.0 / c->p.sigma;
     k.grab = 0;   // static striding: the work counter belongs to the force kernel
-    const int smem = (kW64Threads / 32) * W64Layout(c->wcap, 1, c->w64_lcap, true).bytes;
-    void *kern = w64_kernel(c->p.shift_mode, 2);
+    const int smem = (kW64Threads / 32) * W64Layout(k.cap, 1, c->w64_lcap, true, po).bytes;
+    void *kern = w64_kernel(c->p.shift_mode, 2, po);
     cudaError_t e = raise_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
     int nb = 0;
@@ -1088,12 +1194,22 @@ cudaError_t launch_vjp_w64(lj_ctx *c, double scale, double *dx, double a1, doubl
     if (grid < 1) grid = 1;
     const double4_16a *pos = (const double4_16a *)c->pos;
     const int32_t *start = c->start;
-    double4_16a *fout = nullptr;
+    double4_16a *fout = po ? (double4_16a *)c->f_sorted : nullptr;
     double *partial = c->partial;
     void *args[] = {&k, (void *)&pos, (void *)&start, &fout, &partial};
+    if (po && c->p.n > 0) {
+        e = cudaMemsetAsync(c->f_sorted, 0, (size_t)c->p.n * sizeof(double4_16a), c->stream);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(kW64Threads), args, smem, c->stream);
     c->kernel_launches++;
     if (e != cudaSuccess) return e;
+    if (po && c->p.n > 0) {
+        const int nblk = (int)((c->p.n + 255) / 256);
+        k_unsort_add64<<<nblk, 256, 0, c->stream>>>((const double4_16a *)c->f_sorted, c->perm, dx, scale,
+                                                    (int)c->p.n);
+        c->kernel_launches++;
+    }
     *grid_out = (int)grid;
     return cudaGetLastError();
 }

@@ -19,12 +19,15 @@ from gpu_util import min_image, rel_rms
 pytestmark = pytest.mark.gpu
 
 
-def _vjp_gpu(x, L, g, precision, mode, eps, sigma, scale=1.0, calls=1, subdiv=1, deterministic=False):
+def _vjp_gpu(x, L, g, precision, mode, eps, sigma, scale=1.0, calls=1, subdiv=1, deterministic=False, rc=2.5,
+             kernel=None):
     import torch
     from paper_0709_3225_gb300 import lj
-    s = lj.System(x, None, L, precision=precision, shift_mode=mode, eps=eps, sigma=sigma, cell_subdiv=subdiv)
+    s = lj.System(x, None, L, precision=precision, shift_mode=mode, eps=eps, sigma=sigma, cell_subdiv=subdiv, rc=rc)
     if deterministic:
         lj.lj_set_deterministic(s.ctx)
+    if kernel is not None:
+        lj.lj_set_tuning(s.ctx, kernel, 0, 4)
     gt = torch.as_tensor(g, device="cuda")
     dx = torch.zeros_like(s.x)
     dp = torch.zeros(2, dtype=torch.float64, device="cuda")
@@ -68,6 +71,35 @@ def test_vjp_matches_oracle(oracle_mod, precision, mode, subdiv):
         _, ode_f, ods_f = oracle_mod.forces_vjp(x, L, fo, eps=eps, sigma=sigma, mode=mode)
         assert abs(dp_f[0] - ode_f) <= 1e-6 * abs(ode_f)
         assert abs(dp_f[1] - ods_f) <= 1e-6 * abs(ods_f)
+
+
+@pytest.mark.parametrize("kernel", [3, 7])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("state", ["liquid", "cluster", "dense_rc3"])
+def test_fp64_vjp_forms(oracle_mod, kernel, mode, state):
+    """The FP64 VJP in its pair-once form (kernel 7, the default: each pair
+    once over the half stencil, the contribution to j the negative of i's)
+    and its 27-cell form (kernel 3) against the oracle: a liquid; a dense
+    blob in a dilute gas (cells over the staging capacity take the plain
+    path); rho 1.1 with rc = 3 (pair lists taken in several batches)."""
+    from gpu_util import dense_cluster_state
+    rc = 2.5
+    if state == "liquid":
+        x, L = inputs.jittered_fcc(8, 0.8442, 0.1, 44)
+    elif state == "cluster":
+        x, L = dense_cluster_state(seed=45)
+    else:
+        x, L = inputs.jittered_fcc(8, 1.1, 0.05, 46)
+        rc = 3.0
+    g = np.random.default_rng(47).standard_normal(x.shape)
+    eps, sigma = 0.95, 1.02
+    dx, dp = _vjp_gpu(x, L, g, "fp64", mode, eps, sigma, rc=rc, kernel=kernel)
+    odx, ode, ods = oracle_mod.forces_vjp(x, L, g, eps=eps, sigma=sigma, rc=rc, mode=mode)
+    near = oracle_mod.near_cutoff(x, L, band=1e-12, rc=rc)
+    assert rel_rms(dx, odx) <= 1e-11
+    scale = np.abs(odx).max(axis=1) + np.sqrt((odx ** 2).sum(axis=1).mean())
+    assert np.all(np.abs(dx - odx).max(axis=1)[~near] <= 1e-10 * scale[~near])
+    assert abs(dp[0] - ode) <= 1e-11 * abs(ode) and abs(dp[1] - ods) <= 1e-11 * abs(ods)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
