@@ -314,7 +314,7 @@ __device__ void phase_force_n3(const BatchDev &b, const WarpParams &k, float4 *_
     float4 *S = reinterpret_cast<float4 *>(bsmem + (size_t)warp * n3_slice_words(k.cap));
     float4 *stab = S + k.cap;
     int *spre = reinterpret_cast<int *>(stab + kN3Half);
-    float4 *part = reinterpret_cast<float4 *>(spre + 16);
+    float4 *H = reinterpret_cast<float4 *>(spre + 16);
     double eacc = 0.0, wacc = 0.0;
     auto load = [&](int c) {
         const int r = b.rep_of_cell[c];
@@ -331,7 +331,7 @@ __device__ void phase_force_n3(const BatchDev &b, const WarpParams &k, float4 *_
         for (int c = (int)c0; c < c1; c++) {
             const HalfLoad cur = nxt;
             if (c + 1 < c1) nxt = load(c + 1);
-            n3_cell<MODE, ENERGY, false>(k, b.pos, f, cur, (float)b.cw[b.rep_of_cell[c]], S, stab, spre, part, eacc,
+            n3_cell<MODE, ENERGY, false>(k, b.pos, f, cur, (float)b.cw[b.rep_of_cell[c]], S, stab, spre, H, eacc,
                                          wacc);
         }
     }
@@ -549,11 +549,11 @@ cudaError_t configure(lj_batch *b)
     if (R != 1) return cudaSuccess;
     // the pair-once kernel: staging capacity as for single systems, from the
     // mean occupancy (the raw half stencil m = 14 n_cell plus a Poisson
-    // spread and the padding, at least 192, a multiple of 32)
+    // spread and the padding, at least kN3Home * 32, a multiple of 32)
     const double m = kN3Half * mean_occ;
     int cap3 = (int)(m + 4.0 * sqrt(m)) + 64;
-    cap3 = cap3 < 192 ? 192 : ((cap3 + 31) & ~31);
-    const int max3 = ((113 * 1024 - 2048) / (4 * (kBatchThreads / 32)) - (4 * kN3Half + 16 + 4 * kN3Home * 32)) / 4 & ~31;
+    cap3 = cap3 < kN3Home * 32 ? kN3Home * 32 : ((cap3 + 31) & ~31);   // S also holds the home forces' transpose
+    const int max3 = ((113 * 1024 - 2048) / (4 * (kBatchThreads / 32)) - kN3FixedWords) / 4 & ~31;
     if (cap3 > max3) cap3 = max3;
     b->kn3 = b->k;
     b->kn3.cap = cap3;

@@ -7,7 +7,7 @@
 namespace {
 
 template <int MODE, bool ENERGY>
-__global__ void __launch_bounds__(kN3Threads, 5) k_force_n3(WarpParams k, const float4 *__restrict__ pos,
+__global__ void __launch_bounds__(kN3Threads, 6) k_force_n3(WarpParams k, const float4 *__restrict__ pos,
                                                          const int32_t *__restrict__ start, float4 *__restrict__ fout,
                                                          double *__restrict__ partial)
 {
@@ -17,11 +17,11 @@ __global__ void __launch_bounds__(kN3Threads, 5) k_force_n3(WarpParams k, const 
     float4 *S = reinterpret_cast<float4 *>(nsmem + (size_t)warp * n3_slice_words(k.cap));
     float4 *stab = S + k.cap;
     int *spre = reinterpret_cast<int *>(stab + kN3Half);
-    float4 *part = reinterpret_cast<float4 *>(spre + 16);
+    float4 *H = reinterpret_cast<float4 *>(spre + 16);
     const int nc = k.nc;
     double eacc = 0.0, wacc = 0.0;
     auto one_cell = [&](HalfLoad tl) {
-        n3_cell<MODE, ENERGY, true>(k, pos, fout, tl, k.cw, S, stab, spre, part, eacc, wacc);
+        n3_cell<MODE, ENERGY, true>(k, pos, fout, tl, k.cw, S, stab, spre, H, eacc, wacc);
     };
     if (k.grab > 0) {
         for (;;) {
@@ -89,14 +89,15 @@ cudaError_t n3_force_configure(lj_ctx *c)
 {
     // Staged candidates per warp: the pruned half stencil of a fluid cell
     // (~125 at rho 0.84) plus 32 padding, with room for a Poisson spread of
-    // the raw half stencil m = 14 n_cell (4 sqrt(m) + 32), at least 192.
+    // the raw half stencil m = 14 n_cell (4 sqrt(m) + 32), and at least the
+    // home forces' transpose (kN3Home * 32), which reuses the same space.
     const double mean = c->ncell > 0 ? (double)c->p.n / (double)c->ncell : 0.0;
     const double m = kN3Half * mean;
     int cap = (int)(m + 4.0 * sqrt(m)) + 64;
-    cap = cap < 192 ? 192 : cap;
+    cap = cap < kN3Home * 32 ? kN3Home * 32 : cap;   // S also holds the home forces' transpose
     cap = (cap + 31) & ~31;
     const int max_cap = ((227 * 1024 - 2 * (kN3Threads / 32) * 8) / (4 * (kN3Threads / 32)) -
-                         (4 * kN3Half + 16 + 4 * kN3Home * 32)) / 4 & ~31;
+                         kN3FixedWords) / 4 & ~31;
     if (cap > max_cap) cap = max_cap;
     c->n3cap = cap;   // float4 slots
     c->n3_smem = (kN3Threads / 32) * n3_slice_words(cap) * (int)sizeof(float);

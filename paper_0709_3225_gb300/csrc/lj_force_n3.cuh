@@ -19,24 +19,28 @@
 //    0.01 % margin; the box comes from the first staging round, where the
 //    home particles are) and appended as float4 (x, y, z, particle index);
 //    the home particles come first, in their sorted order.
-//  * Compute: the warp is A groups of B = 32 / A lanes (A = 2, or 4 when a
-//    pass holds more than 16 home particles).  Lane (a, b) holds up to 8
-//    home particles (u A + a, u = 0..7) as four FP32x2 pairs with their
-//    partial forces, and takes candidate b of each block of B; one packed
-//    evaluation covers two home particles against that candidate, whose
-//    reaction stays in registers for the block.
+//  * Compute: the warp is A groups of B = 32 / A lanes (A = 2, or 4 when
+//    the cell holds more than 16 home particles).  Lane (a, b) takes
+//    candidate b of each block of B against the home particles u A + a,
+//    u = 0..7, as four FP32x2 pairs; one packed evaluation covers two home
+//    particles against that candidate, whose reaction stays in registers
+//    for the block.  The home pairs' positions are read from a per-warp
+//    table in shared memory at every evaluation (broadcast loads), and only
+//    their partial forces live in registers: that keeps the kernel at 79
+//    registers, 24 resident warps per SM instead of 20, and the extra
+//    loads cost less than the latency the extra warps hide.
 //  * After a block the reactions are summed over the A groups (shuffles) and
 //    added to f[j] with one float4 atomic add per candidate (with no test
 //    for zero: the test's four comparisons cost more issue slots than the
 //    atomics it saves); after the last block the home partial forces are
 //    summed over the B lanes of their group through a shared-memory
-//    transpose and added to f[i] (skipped when zero).  f is zeroed before
-//    the launch.
+//    transpose (in the staged list's space, which is free by then) and
+//    added to f[i] (skipped when zero).  f is zeroed before the launch.
 //  * Energies: per-particle f.w gets half of each pair energy on both sides;
 //    the FP64 totals take each pair once.
-//  * A cell whose pruned half stencil does not fit the warp's slice takes a
-//    plain path over global memory (home particle per lane, reactions
-//    reduced over the warp).
+//  * A cell with more than 32 home particles, or whose pruned half stencil
+//    does not fit the warp's slice, takes a plain path over global memory
+//    (home particle per lane, reactions reduced over the warp).
 // The FP32 sums of a particle's force are formed in an order set by the
 // atomics, so forces are not bitwise reproducible between runs (their
 // rounding error is that of any order); the deterministic mode uses the
@@ -44,6 +48,7 @@
 #pragma once
 
 #include "lj_force_cell.cuh"
+#include "lj_pair.cuh"
 
 namespace {
 
@@ -64,10 +69,12 @@ __device__ __forceinline__ void half_delta(int e, int &dx, int &dy, int &dz)
 }
 
 // 32-bit words of one warp's slice: the staged candidates S (cap float4:
-// x, y, z in the home frame and the particle index), the half-stencil table
-// (14 float4), its prefix sums (15 ints, padded to 16) and the home
-// transpose buffer (8 x 32 float4).
-__host__ __device__ constexpr int n3_slice_words(int cap) { return 4 * cap + 4 * kN3Half + 16 + 4 * kN3Home * 32; }
+// x, y, z in the home frame and the particle index; cap >= kN3Home * 32,
+// since S also holds the home forces' transpose), the half-stencil table
+// (14 float4), its prefix sums (15 ints, padded to 16) and the home table H
+// (4 groups x 4 pairs x 2 float4).
+constexpr int kN3FixedWords = 4 * kN3Half + 16 + 4 * 32;
+__host__ __device__ constexpr int n3_slice_words(int cap) { return 4 * cap + kN3FixedWords; }
 
 // Half-stencil table, in two parts so that a cell's loads can be issued one
 // cell ahead: half_load reads, for lane e < 14, the first and end particle
@@ -198,128 +205,149 @@ __device__ __forceinline__ void add_force(float4 *fout, int idx, float4 v)
 // of every block against its NH home pairs (pairs past its home particles
 // sit far away and add nothing), then the candidate's reaction is summed
 // over the A groups and added to f.
-template <int NH, int LGB, int MODE, bool ENERGY>
-__device__ __forceinline__ void n3_blocks(const WarpParams &k, float4 *__restrict__ fout, const float4 *S, int T,
-                                          int n_home, int p0, int a, int b, int A, int lgB, const float2 *hx,
-                                          const float2 *hy, const float2 *hz, float2 *fx, float2 *fy, float2 *fz,
+// Home pair h of lane group a, as (x0, x1, y0, y1) and (z0, z1, -, -) in
+// the warp's home table H (read per evaluation: the home positions do not
+// occupy registers across the candidate loop).
+__device__ __forceinline__ void n3_home_ld(const float4 *H, int a, int h, float2 &hx, float2 &hy, float2 &hz)
+{
+    const float4 *p = H + 2 * (4 * a + h);
+    float4 q0, q1;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(q0.x), "=f"(q0.y), "=f"(q0.z), "=f"(q0.w) : "r"(smem_addr(p)));
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(q1.x), "=f"(q1.y) : "r"(smem_addr(p + 1)));
+    hx = make_float2(q0.x, q0.y);
+    hy = make_float2(q0.z, q0.w);
+    hz = make_float2(q1.x, q1.y);
+}
+
+template <int NH, int LGB, int MODE, bool ENERGY, bool SELF>
+__device__ __forceinline__ void n3_block1(const WarpParams &k, float4 *__restrict__ fout, const float4 *S, int T, int blk,
+                                          int a, int b, int A, const float4 *H, float2 *fx, float2 *fy, float2 *fz,
                                           float2 *fe, float2 &fw)
 {
     constexpr int B = 1 << LGB;
-    const int nblk = (T + B - 1) >> LGB;
-    for (int blk = 0; blk < nblk; blk++) {
-        const int j = (blk << LGB) + b;
-        const float4 c = S[j];
-        const float2 cx = f2(c.x), cy = f2(c.y), cz = f2(c.z);
-        float2 rx = f2(0.0f), ry = f2(0.0f), rz = f2(0.0f), re = f2(0.0f);
-        if ((blk << LGB) < n_home) {
+    const int j = (blk << LGB) + b;
+    const float4 c = S[j];
+    const float2 cx = f2(c.x), cy = f2(c.y), cz = f2(c.z);
+    float2 rx = f2(0.0f), ry = f2(0.0f), rz = f2(0.0f), re = f2(0.0f);
 #pragma unroll
-            for (int h = 0; h < NH; h++)
-                pair2_n3<MODE, ENERGY, true>(hx[h], hy[h], hz[h], p0 + 2 * h * A + a, p0 + (2 * h + 1) * A + a, cx, cy,
-                                             cz, j, k, fx[h], fy[h], fz[h], fe[h], fw, rx, ry, rz, re);
-        } else {
-#pragma unroll
-            for (int h = 0; h < NH; h++)
-                pair2_n3<MODE, ENERGY, false>(hx[h], hy[h], hz[h], 0, 0, cx, cy, cz, j, k, fx[h], fy[h], fz[h], fe[h],
-                                              fw, rx, ry, rz, re);
-        }
-        float sx = rx.x + rx.y, sy = ry.x + ry.y, sz = rz.x + rz.y, se = ENERGY ? re.x + re.y : 0.0f;
-#pragma unroll
-        for (int o = B; o < 32; o <<= 1) {
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            sz += __shfl_xor_sync(0xffffffffu, sz, o);
-            if constexpr (ENERGY) se += __shfl_xor_sync(0xffffffffu, se, o);
-        }
-        if (a == 0 && j < T) atomicAdd(fout + __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
+    for (int h = 0; h < NH; h++) {
+        float2 hx, hy, hz;
+        n3_home_ld(H, a, h, hx, hy, hz);
+        pair2_n3<MODE, ENERGY, SELF>(hx, hy, hz, 2 * h * A + a, (2 * h + 1) * A + a, cx, cy, cz, j, k, fx[h], fy[h],
+                                     fz[h], fe[h], fw, rx, ry, rz, re);
     }
+    float sx = rx.x + rx.y, sy = ry.x + ry.y, sz = rz.x + rz.y, se = ENERGY ? re.x + re.y : 0.0f;
+#pragma unroll
+    for (int o = B; o < 32; o <<= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        if constexpr (ENERGY) se += __shfl_xor_sync(0xffffffffu, se, o);
+    }
+    if (a == 0 && j < T) atomicAdd(fout + __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
 }
 
-// Compute phase over the staged list S (T candidates, home particles at
-// 0 .. n_home-1, padded with far points to a multiple of 32).  Per pass of
-// up to 32 home particles the warp is A groups of B lanes (A = 2 for up to
-// 16 home particles, else 4); lane (a, b) holds home particles u A + a,
-// u = 0..7, as four FP32x2 pairs (u = 2h, 2h + 1) and takes candidate
-// blk B + b of each block.
+template <int NH, int LGB, int MODE, bool ENERGY>
+__device__ __forceinline__ void n3_blocks(const WarpParams &k, float4 *__restrict__ fout, const float4 *S, int T,
+                                          int n_home, int a, int b, int A, const float4 *H, float2 *fx, float2 *fy,
+                                          float2 *fz, float2 *fe, float2 &fw)
+{
+    constexpr int B = 1 << LGB;
+    const int nblk = (T + B - 1) >> LGB;
+    const int nself = min(nblk, (n_home + B - 1) >> LGB);   // blocks holding home particles
+    int blk = 0;
+    for (; blk < nself; blk++)
+        n3_block1<NH, LGB, MODE, ENERGY, true>(k, fout, S, T, blk, a, b, A, H, fx, fy, fz, fe, fw);
+    for (; blk < nblk; blk++)
+        n3_block1<NH, LGB, MODE, ENERGY, false>(k, fout, S, T, blk, a, b, A, H, fx, fy, fz, fe, fw);
+}
+
+// Compute phase of a cell of n_home <= 32 home particles staged in S (home
+// particles at 0 .. n_home-1, candidates after them, padded with far points
+// to a multiple of 32).  The warp is A groups of B lanes (A = 2 for up to 16
+// home particles, else 4); lane (a, b) takes candidate blk B + b of each
+// block against the home particles u A + a, u = 0..7, in FP32x2 pairs read
+// from the table H (2 kN3Home float4 per group).  The home forces' transpose
+// reuses S once the candidate blocks are done (S holds >= kN3Home * 32).
 template <int MODE, bool ENERGY>
-__device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restrict__ fout, const float4 *S,
-                                           float4 *part, int T, int n_home, double &eacc, double &wacc)
+__device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restrict__ fout, float4 *S, float4 *H,
+                                           int T, int n_home, double &eacc, double &wacc)
 {
     const int lane = threadIdx.x & 31;
-    for (int p0 = 0; p0 < n_home; p0 += 32) {
-        const int hp = min(n_home - p0, 32);
-        const int lgB = hp > 16 ? 3 : 4;
-        const int B = 1 << lgB, A = 32 >> lgB;
-        const int a = lane >> lgB, b = lane & (B - 1);
-        const int nu = (hp + A - 1) >> (5 - lgB);   // home particles per lane
-        float2 hx[kN3Home / 2], hy[kN3Home / 2], hz[kN3Home / 2];
-        float2 fx[kN3Home / 2], fy[kN3Home / 2], fz[kN3Home / 2], fe[kN3Home / 2];
-        float2 fw = f2(0.0f);
-#pragma unroll
-        for (int h = 0; h < kN3Home / 2; h++) {
-            const int s0 = 2 * h * A + a, s1 = s0 + A;
-            const bool v0 = s0 < hp, v1 = s1 < hp;
-            const float4 q0 = S[p0 + (v0 ? s0 : 0)];
-            const float4 q1 = S[p0 + (v1 ? s1 : 0)];
-            hx[h] = make_float2(v0 ? q0.x : -kFar, v1 ? q1.x : -kFar);
-            hy[h] = make_float2(v0 ? q0.y : -kFar, v1 ? q1.y : -kFar);
-            hz[h] = make_float2(v0 ? q0.z : -kFar, v1 ? q1.z : -kFar);
-            fx[h] = fy[h] = fz[h] = fe[h] = f2(0.0f);
-        }
-        // the candidate blocks, compiled for the number of home pairs a lane
-        // holds (a uniform choice per pass: no branches inside the loop)
-        const int nh = (nu + 1) >> 1;
-        if (lgB == 4) {
-            if (nh >= 4)
-                n3_blocks<4, 4, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
-            else if (nh == 3)
-                n3_blocks<3, 4, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
-            else
-                n3_blocks<2, 4, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
-        } else {
-            if (nh >= 4)
-                n3_blocks<4, 3, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
-            else if (nh == 3)
-                n3_blocks<3, 3, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
-            else
-                n3_blocks<2, 3, MODE, ENERGY>(k, fout, S, T, n_home, p0, a, b, A, lgB, hx, hy, hz, fx, fy, fz, fe, fw);
-        }
-        // home forces: sum over the B lanes of each group through a transpose
-        // in shared memory (row u, column a B + b); every lane sums 8 entries
-#pragma unroll
-        for (int h = 0; h < kN3Home / 2; h++) {
-            if (2 * h < nu) part[(2 * h) * 32 + lane] = make_float4(fx[h].x, fy[h].x, fz[h].x, fe[h].x);
-            if (2 * h + 1 < nu) part[(2 * h + 1) * 32 + lane] = make_float4(fx[h].y, fy[h].y, fz[h].y, fe[h].y);
-            if constexpr (ENERGY) eacc += (double)(fe[h].x + fe[h].y);
-        }
-        if constexpr (ENERGY) wacc += (double)(fw.x + fw.y);
-        __syncwarp();
-        const int p = A == 2 ? lane >> 1 : lane;            // home particle of this lane
-        const int bh = A == 2 ? (lane & 1) * 8 : 0;         // its half of the B columns
-        const int u = p >> (5 - lgB), g = p & (A - 1);
-        float4 sum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (p < hp) {
-            const float4 *row = part + u * 32 + g * B + bh;
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const float4 q = row[(i + lane) & 7];   // rotated: no bank conflicts
-                sum.x += q.x;
-                sum.y += q.y;
-                sum.z += q.z;
-                sum.w += q.w;
-            }
-        }
-        if (A == 2) {
-            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, 1);
-            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, 1);
-            sum.z += __shfl_xor_sync(0xffffffffu, sum.z, 1);
-            if constexpr (ENERGY) sum.w += __shfl_xor_sync(0xffffffffu, sum.w, 1);
-        }
-        if (p < hp && bh == 0) {
-            sum.w *= 0.5f;
-            add_force(fout, __float_as_int(S[p0 + p].w), sum);
-        }
-        __syncwarp();
+    const int hp = n_home;
+    const int lgB = hp > 16 ? 3 : 4;
+    const int B = 1 << lgB, A = 32 >> lgB;
+    const int a = lane >> lgB, b = lane & (B - 1);
+    const int nu = (hp + A - 1) >> (5 - lgB);   // home particles per lane
+    // the home table: lane (a, b < 4) writes pair h = b of group a
+    if (b < kN3Home / 2) {
+        const int s0 = 2 * b * A + a, s1 = s0 + A;
+        const bool v0 = s0 < hp, v1 = s1 < hp;
+        const float4 q0 = S[v0 ? s0 : 0];
+        const float4 q1 = S[v1 ? s1 : 0];
+        float4 *p = H + 2 * (4 * a + b);
+        p[0] = make_float4(v0 ? q0.x : -kFar, v1 ? q1.x : -kFar, v0 ? q0.y : -kFar, v1 ? q1.y : -kFar);
+        p[1] = make_float4(v0 ? q0.z : -kFar, v1 ? q1.z : -kFar, 0.0f, 0.0f);
     }
+    __syncwarp();
+    float2 fx[kN3Home / 2], fy[kN3Home / 2], fz[kN3Home / 2], fe[kN3Home / 2];
+    float2 fw = f2(0.0f);
+#pragma unroll
+    for (int h = 0; h < kN3Home / 2; h++) fx[h] = fy[h] = fz[h] = fe[h] = f2(0.0f);
+    const int nh = (nu + 1) >> 1;
+    if (lgB == 4) {
+        if (nh >= 4)
+            n3_blocks<4, 4, MODE, ENERGY>(k, fout, S, T, n_home, a, b, A, H, fx, fy, fz, fe, fw);
+        else if (nh == 3)
+            n3_blocks<3, 4, MODE, ENERGY>(k, fout, S, T, n_home, a, b, A, H, fx, fy, fz, fe, fw);
+        else
+            n3_blocks<2, 4, MODE, ENERGY>(k, fout, S, T, n_home, a, b, A, H, fx, fy, fz, fe, fw);
+    } else {
+        if (nh >= 4)
+            n3_blocks<4, 3, MODE, ENERGY>(k, fout, S, T, n_home, a, b, A, H, fx, fy, fz, fe, fw);
+        else if (nh == 3)
+            n3_blocks<3, 3, MODE, ENERGY>(k, fout, S, T, n_home, a, b, A, H, fx, fy, fz, fe, fw);
+        else
+            n3_blocks<2, 3, MODE, ENERGY>(k, fout, S, T, n_home, a, b, A, H, fx, fy, fz, fe, fw);
+    }
+    const int p = A == 2 ? lane >> 1 : lane;            // home particle of this lane
+    const int bh = A == 2 ? (lane & 1) * 8 : 0;         // its half of the B columns
+    const int u = p >> (5 - lgB), g = p & (A - 1);
+    const int hidx = p < hp ? __float_as_int(S[p].w) : 0;
+    __syncwarp();   // every lane is done reading S
+    float4 *part = S;
+#pragma unroll
+    for (int h = 0; h < kN3Home / 2; h++) {
+        if (2 * h < nu) part[(2 * h) * 32 + lane] = make_float4(fx[h].x, fy[h].x, fz[h].x, fe[h].x);
+        if (2 * h + 1 < nu) part[(2 * h + 1) * 32 + lane] = make_float4(fx[h].y, fy[h].y, fz[h].y, fe[h].y);
+        if constexpr (ENERGY) eacc += (double)(fe[h].x + fe[h].y);
+    }
+    if constexpr (ENERGY) wacc += (double)(fw.x + fw.y);
+    __syncwarp();
+    float4 sum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (p < hp) {
+        const float4 *row = part + u * 32 + g * B + bh;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const float4 q = row[(i + lane) & 7];   // rotated: no bank conflicts
+            sum.x += q.x;
+            sum.y += q.y;
+            sum.z += q.z;
+            sum.w += q.w;
+        }
+    }
+    if (A == 2) {
+        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, 1);
+        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, 1);
+        sum.z += __shfl_xor_sync(0xffffffffu, sum.z, 1);
+        if constexpr (ENERGY) sum.w += __shfl_xor_sync(0xffffffffu, sum.w, 1);
+    }
+    if (p < hp && bh == 0) {
+        sum.w *= 0.5f;
+        add_force(fout, hidx, sum);
+    }
+    __syncwarp();
 }
 
 // Staging of the half stencil (see the file header) into S.  Returns false,
@@ -489,13 +517,14 @@ __device__ void n3_plain(const WarpParams &k, const float4 *__restrict__ pos, fl
 }
 
 // One home cell whose table loads are tl (half_load): table, staging, and
-// the compute phase, or the plain path when the pruned half stencil does
-// not fit the slice (S, stab, spre, part: the warp's slice).  cw: the
+// the compute phase, or the plain path for a cell of more than 32 home
+// particles or whose pruned half stencil does not fit the slice (S, stab,
+// spre, H: the warp's slice).  cw: the
 // cell side of the cell's grid.  NC: read-only loads of the sorted
 // positions (not when an earlier phase of the same launch writes them).
 template <int MODE, bool ENERGY, bool NC>
 __device__ __forceinline__ void n3_cell(const WarpParams &k, const float4 *__restrict__ pos, float4 *__restrict__ fout,
-                                        HalfLoad tl, float cw, float4 *S, float4 *stab, int *spre, float4 *part,
+                                        HalfLoad tl, float cw, float4 *S, float4 *stab, int *spre, float4 *H,
                                         double &eacc, double &wacc)
 {
     __syncwarp();   // the slice still holds the previous cell's data
@@ -504,8 +533,8 @@ __device__ __forceinline__ void n3_cell(const WarpParams &k, const float4 *__res
     if (n_home == 0) return;
     const int s_home = __float_as_int(stab[0].w);
     int T = 0;
-    if (tot <= 2 * k.cap && n3_stage<NC>(k, pos, S, stab, spre, tot, s_home, n_home, T))
-        n3_compute<MODE, ENERGY>(k, fout, S, part, T, n_home, eacc, wacc);
+    if (n_home <= 32 && tot <= 2 * k.cap && n3_stage<NC>(k, pos, S, stab, spre, tot, s_home, n_home, T))
+        n3_compute<MODE, ENERGY>(k, fout, S, H, T, n_home, eacc, wacc);
     else
         n3_plain<MODE, ENERGY, NC>(k, pos, fout, stab, spre, s_home, n_home, eacc, wacc);
 }
