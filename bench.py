@@ -889,7 +889,7 @@ def run_gpu(args):
 
 
 FORCE_SOURCES = [os.path.join(ROOT, "paper_0709_3225_gb300", "csrc", f)
-                 for f in ("lj_force_n3.cu", "lj_force_n3.cuh", "lj_force_cell.cuh", "lj_internal.cuh")]
+                 for f in ("lj_force_n3.cu", "lj_force_n3.cuh", "lj_force_cell.cuh", "lj_internal.cuh", "lj_pair.cuh")]
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_force_n3_traffic_fluid-4m.md")
 
 

@@ -72,8 +72,9 @@ __device__ __forceinline__ void half_delta(int e, int &dx, int &dy, int &dz)
 // x, y, z in the home frame and the particle index; cap >= kN3Home * 32,
 // since S also holds the home forces' transpose), the half-stencil table
 // (14 float4), its prefix sums (15 ints, padded to 16) and the home table H
-// (4 groups x 4 pairs x 2 float4).
-constexpr int kN3FixedWords = 4 * kN3Half + 16 + 4 * 32;
+// (4 groups x 7 float4, laid out as n3_block1 describes).
+constexpr int kN3HomeStride = 4 + 2 + 1;   // float4 per lane group in H
+constexpr int kN3FixedWords = 4 * kN3Half + 16 + 4 * 4 * kN3HomeStride;
 __host__ __device__ constexpr int n3_slice_words(int cap) { return 4 * cap + kN3FixedWords; }
 
 // Half-stencil table, in two parts so that a cell's loads can be issued one
@@ -201,25 +202,22 @@ __device__ __forceinline__ void add_force(float4 *fout, int idx, float4 v)
     if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f) atomicAdd(fout + idx, v);
 }
 
-// The candidate blocks of one pass: lane (a, b) takes candidate blk B + b
-// of every block against its NH home pairs (pairs past its home particles
-// sit far away and add nothing), then the candidate's reaction is summed
-// over the A groups and added to f.
-// Home pair h of lane group a, as (x0, x1, y0, y1) and (z0, z1, -, -) in
-// the warp's home table H (read per evaluation: the home positions do not
-// occupy registers across the candidate loop).
-__device__ __forceinline__ void n3_home_ld(const float4 *H, int a, int h, float2 &hx, float2 &hy, float2 &hz)
+// A float4 of the home table, loaded at every use: the asm keeps the
+// compiler from hoisting the loads out of the candidate loop, so the home
+// positions do not occupy registers across it.
+__device__ __forceinline__ float4 n3_ld4(const float4 *p)
 {
-    const float4 *p = H + 2 * (4 * a + h);
-    float4 q0, q1;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(q0.x), "=f"(q0.y), "=f"(q0.z), "=f"(q0.w) : "r"(smem_addr(p)));
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(q1.x), "=f"(q1.y) : "r"(smem_addr(p + 1)));
-    hx = make_float2(q0.x, q0.y);
-    hy = make_float2(q0.z, q0.w);
-    hz = make_float2(q1.x, q1.y);
+    float4 q;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w) : "r"(smem_addr(p)));
+    return q;
 }
 
+// One candidate block: lane (a, b) takes candidate blk B + b against its NH
+// home pairs (pairs past its home particles sit far away and add nothing),
+// then the candidate's reaction is summed over the A groups and added to f.
+// Group a's home table: the (x0, x1, y0, y1) of pairs 0..3, then the z of
+// pairs (0, 1) and (2, 3), one float4 each, then a float4 of padding so
+// that the groups' simultaneous reads fall in different banks.
 template <int NH, int LGB, int MODE, bool ENERGY, bool SELF>
 __device__ __forceinline__ void n3_block1(const WarpParams &k, float4 *__restrict__ fout, const float4 *S, int T, int blk,
                                           int a, int b, int A, const float4 *H, float2 *fx, float2 *fy, float2 *fz,
@@ -230,12 +228,20 @@ __device__ __forceinline__ void n3_block1(const WarpParams &k, float4 *__restric
     const float4 c = S[j];
     const float2 cx = f2(c.x), cy = f2(c.y), cz = f2(c.z);
     float2 rx = f2(0.0f), ry = f2(0.0f), rz = f2(0.0f), re = f2(0.0f);
+    const float4 *Hg = H + kN3HomeStride * a;
 #pragma unroll
-    for (int h = 0; h < NH; h++) {
-        float2 hx, hy, hz;
-        n3_home_ld(H, a, h, hx, hy, hz);
-        pair2_n3<MODE, ENERGY, SELF>(hx, hy, hz, 2 * h * A + a, (2 * h + 1) * A + a, cx, cy, cz, j, k, fx[h], fy[h],
-                                     fz[h], fe[h], fw, rx, ry, rz, re);
+    for (int h = 0; h < NH; h += 2) {
+        const float4 z2 = n3_ld4(Hg + 4 + (h >> 1));   // z of pairs h and h + 1
+        const float4 q0 = n3_ld4(Hg + h);
+        pair2_n3<MODE, ENERGY, SELF>(make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(z2.x, z2.y),
+                                     2 * h * A + a, (2 * h + 1) * A + a, cx, cy, cz, j, k, fx[h], fy[h], fz[h], fe[h],
+                                     fw, rx, ry, rz, re);
+        if (h + 1 < NH) {
+            const float4 q1 = n3_ld4(Hg + h + 1);
+            pair2_n3<MODE, ENERGY, SELF>(make_float2(q1.x, q1.y), make_float2(q1.z, q1.w), make_float2(z2.z, z2.w),
+                                         2 * (h + 1) * A + a, (2 * (h + 1) + 1) * A + a, cx, cy, cz, j, k, fx[h + 1],
+                                         fy[h + 1], fz[h + 1], fe[h + 1], fw, rx, ry, rz, re);
+        }
     }
     float sx = rx.x + rx.y, sy = ry.x + ry.y, sz = rz.x + rz.y, se = ENERGY ? re.x + re.y : 0.0f;
 #pragma unroll
@@ -268,7 +274,7 @@ __device__ __forceinline__ void n3_blocks(const WarpParams &k, float4 *__restric
 // to a multiple of 32).  The warp is A groups of B lanes (A = 2 for up to 16
 // home particles, else 4); lane (a, b) takes candidate blk B + b of each
 // block against the home particles u A + a, u = 0..7, in FP32x2 pairs read
-// from the table H (2 kN3Home float4 per group).  The home forces' transpose
+// from the table H (kN3HomeStride float4 per group).  The home forces' transpose
 // reuses S once the candidate blocks are done (S holds >= kN3Home * 32).
 template <int MODE, bool ENERGY>
 __device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restrict__ fout, float4 *S, float4 *H,
@@ -286,9 +292,11 @@ __device__ __forceinline__ void n3_compute(const WarpParams &k, float4 *__restri
         const bool v0 = s0 < hp, v1 = s1 < hp;
         const float4 q0 = S[v0 ? s0 : 0];
         const float4 q1 = S[v1 ? s1 : 0];
-        float4 *p = H + 2 * (4 * a + b);
-        p[0] = make_float4(v0 ? q0.x : -kFar, v1 ? q1.x : -kFar, v0 ? q0.y : -kFar, v1 ? q1.y : -kFar);
-        p[1] = make_float4(v0 ? q0.z : -kFar, v1 ? q1.z : -kFar, 0.0f, 0.0f);
+        float4 *p = H + kN3HomeStride * a;
+        p[b] = make_float4(v0 ? q0.x : -kFar, v1 ? q1.x : -kFar, v0 ? q0.y : -kFar, v1 ? q1.y : -kFar);
+        float *z = reinterpret_cast<float *>(p + 4) + 2 * b;   // z of pair b at float 2b of the z block
+        z[0] = v0 ? q0.z : -kFar;
+        z[1] = v1 ? q1.z : -kFar;
     }
     __syncwarp();
     float2 fx[kN3Home / 2], fy[kN3Home / 2], fz[kN3Home / 2], fe[kN3Home / 2];
