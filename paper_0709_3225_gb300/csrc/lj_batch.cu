@@ -337,10 +337,11 @@ __device__ void phase_force_n3(const BatchDev &b, const WarpParams &k, float4 *_
     }
 }
 
-// One step with the pair-once force phase (cell subdivision 1): 96
-// registers for the force phase, so 2 blocks of 256 threads per SM.
+// One step with the pair-once force phase (cell subdivision 1): the force
+// phase reads the home positions from shared memory, which keeps the
+// kernel at 80 registers, so 3 blocks of 256 threads per SM (24 warps).
 template <int MODE, bool ENERGY>
-__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_step_n3(BatchDev b, WarpParams k, int op, double *x,
+__global__ void __launch_bounds__(kBatchThreads, 3) k_batch_step_n3(BatchDev b, WarpParams k, int op, double *x,
                                                                      double *v, float4 *f)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) *b.work = 0u;
@@ -553,7 +554,8 @@ cudaError_t configure(lj_batch *b)
     const double m = kN3Half * mean_occ;
     int cap3 = (int)(m + 4.0 * sqrt(m)) + 64;
     cap3 = cap3 < kN3Home * 32 ? kN3Home * 32 : ((cap3 + 31) & ~31);   // S also holds the home forces' transpose
-    const int max3 = ((113 * 1024 - 2048) / (4 * (kBatchThreads / 32)) - kN3FixedWords) / 4 & ~31;
+    // (3 blocks per SM: up to 75 KB of shared memory each, 2 KB of it static)
+    const int max3 = ((75 * 1024 - 2048) / (4 * (kBatchThreads / 32)) - kN3FixedWords) / 4 & ~31;
     if (cap3 > max3) cap3 = max3;
     b->kn3 = b->k;
     b->kn3.cap = cap3;
