@@ -29,13 +29,16 @@
 //    their partial forces live in registers: that keeps the kernel at 79
 //    registers, 24 resident warps per SM instead of 20, and the extra
 //    loads cost less than the latency the extra warps hide.
-//  * After a block the reactions are summed over the A groups (shuffles) and
-//    added to f[j] with one float4 atomic add per candidate (with no test
-//    for zero: the test's four comparisons cost more issue slots than the
-//    atomics it saves); after the last block the home partial forces are
-//    summed over the B lanes of their group through a shared-memory
-//    transpose (in the staged list's space, which is free by then) and
-//    added to f[i] (skipped when zero).  f is zeroed before the launch.
+//  * After a block each candidate's reaction goes to f[j] by float4 atomic
+//    adds: one per lane group with two groups, one per pair of groups (after
+//    a shuffle) with four, so two adds per candidate either way; the second
+//    add costs less than the shuffles and additions that would merge the
+//    two parts.  There is no test for zero (its four comparisons cost more
+//    issue slots than the atomics it saves).  After the last block the home
+//    partial forces are summed over the B lanes of their group through a
+//    shared-memory transpose (in the staged list's space, which is free by
+//    then) and added to f[i] (skipped when zero).  f is zeroed before the
+//    launch.
 //  * Energies: per-particle f.w gets half of each pair energy on both sides;
 //    the FP64 totals take each pair once.
 //  * A cell with more than 32 home particles, or whose pruned half stencil
@@ -139,6 +142,14 @@ __device__ __forceinline__ int half_finish(HalfLoad t, float cw, float4 *stab, i
     return __shfl_sync(0xffffffffu, P, kN3Half - 1);
 }
 
+// a b + c rounded once, clamped to [0, 1] (NaN to 0)
+__device__ __forceinline__ float fma_sat(float a, float b, float c)
+{
+    float d;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // One (home pair, candidate) evaluation: d = x_home - x_cand for the two
 // home particles s0, s1 of (hx, hy, hz) and one candidate j broadcast in
 // (cx, cy, cz).  The home particles' forces accumulate in (fx, fy, fz), the
@@ -157,6 +168,30 @@ __device__ __forceinline__ void pair2_n3(float2 hx, float2 hy, float2 hz, int s0
     float2 r2 = __fmul2_rn(dx, dx);
     r2 = __ffma2_rn(dy, dy, r2);
     r2 = __ffma2_rn(dz, dz, r2);
+    if constexpr (MODE != 2 && !ENERGY && !SELF) {
+        // the cutoff as a 0/1 factor from a saturated FMA on the FMA pipe
+        // (instead of a compare and a select on the ALU pipe): 2^100 (rc^2 -
+        // r^2) is formed exactly (2^100 rc^2 is exact and the FMA rounds
+        // once), so it clamps to 1 for every r^2 < rc^2 (the gap is at least
+        // one ulp of rc^2) and to 0 for r^2 >= rc^2 (or an overflow to -inf)
+        float2 m;
+        m.x = fma_sat(r2.x, -0x1p100f, k.rc2 * 0x1p100f);
+        m.y = fma_sat(r2.y, -0x1p100f, k.rc2 * 0x1p100f);
+        float2 ri;
+        ri.x = rcp_approx(r2.x);
+        ri.y = rcp_approx(r2.y);
+        ri = __fmul2_rn(ri, m);
+        const float2 r6 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+        const float2 t = __ffma2_rn(f2(k.a12), r6, f2(-k.b6));
+        const float2 ff = __fmul2_rn(__fmul2_rn(ri, r6), t);
+        fx = __ffma2_rn(ff, dx, fx);
+        fy = __ffma2_rn(ff, dy, fy);
+        fz = __ffma2_rn(ff, dz, fz);
+        rx = __ffma2_rn(ff, dx, rx);
+        ry = __ffma2_rn(ff, dy, ry);
+        rz = __ffma2_rn(ff, dz, rz);
+        return;
+    }
     bool ina = r2.x < k.rc2, inb = r2.y < k.rc2;
     if constexpr (SELF) {
         ina = ina && (j > s0);
@@ -214,7 +249,8 @@ __device__ __forceinline__ float4 n3_ld4(const float4 *p)
 
 // One candidate block: lane (a, b) takes candidate blk B + b against its NH
 // home pairs (pairs past its home particles sit far away and add nothing),
-// then the candidate's reaction is summed over the A groups and added to f.
+// then the candidate's reaction is added to f in two parts (see the file
+// header).
 // Group a's home table: the (x0, x1, y0, y1) of pairs 0..3, then the z of
 // pairs (0, 1) and (2, 3), one float4 each, then a float4 of padding so
 // that the groups' simultaneous reads fall in different banks.
@@ -244,14 +280,15 @@ __device__ __forceinline__ void n3_block1(const WarpParams &k, float4 *__restric
         }
     }
     float sx = rx.x + rx.y, sy = ry.x + ry.y, sz = rz.x + rz.y, se = ENERGY ? re.x + re.y : 0.0f;
-#pragma unroll
-    for (int o = B; o < 32; o <<= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
-        if constexpr (ENERGY) se += __shfl_xor_sync(0xffffffffu, se, o);
+    if constexpr (LGB == 3) {   // four groups: one shuffle level, then two groups add
+        sx += __shfl_xor_sync(0xffffffffu, sx, 8);
+        sy += __shfl_xor_sync(0xffffffffu, sy, 8);
+        sz += __shfl_xor_sync(0xffffffffu, sz, 8);
+        if constexpr (ENERGY) se += __shfl_xor_sync(0xffffffffu, se, 8);
+        if ((a & 1) == 0 && j < T) atomicAdd(fout + __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
+    } else {   // every group adds its own part of the reaction
+        if (j < T) atomicAdd(fout + __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
     }
-    if (a == 0 && j < T) atomicAdd(fout + __float_as_int(c.w), make_float4(-sx, -sy, -sz, 0.5f * se));
 }
 
 template <int NH, int LGB, int MODE, bool ENERGY>

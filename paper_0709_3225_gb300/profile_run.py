@@ -8,9 +8,10 @@ lattice itself, ``--lattice``), then runs
 (``--op step``) or force VJPs with a seeded Gaussian cotangent (``--op
 vjp``) through the C ABI after one untimed warm-up, and prints the
 CUDA-event time per call.  ``--op batch`` instead steps the 256-replica
-ensemble (one cooperative launch per step, direct launches, 1 cell per
-pull) after its 50 relaxation steps.  It reports no benchmark figures; use bench.py for
-those.
+ensemble (one cooperative launch per step, direct launches, ``--grab``
+cells per pull, the batch kernel ``--kernel`` if given: 3 the 27-cell
+code, 7 each pair once) after its 50 relaxation steps.  It reports no
+benchmark figures; use bench.py for those.
 """
 from __future__ import annotations
 
@@ -21,12 +22,14 @@ import torch
 from . import inputs, lj
 
 
-def run_batch(reps: int) -> int:
+def run_batch(reps: int, kernel: int | None = None, grab: int = 1) -> int:
     e = inputs.ensemble()
     xs, vs = inputs.ensemble_state(e)
     b = lj.Batch(xs, vs, e.box)
     b.relax(50, 1e-3, 0.05)
-    b.set_tuning(1, False, 0)
+    if kernel is not None:
+        b.set_kernel(kernel)
+    b.set_tuning(grab, False, 0)
     b.forces()
     b.step(1)
     torch.cuda.synchronize()
@@ -54,9 +57,10 @@ def main(argv=None) -> int:
     ap.add_argument("--group-width", type=int, default=None, help="warp-kernel lane-group width (0 = per cell)")
     ap.add_argument("--kernel", type=int, default=None, help="lj_set_tuning force kernel (default: the context's)")
     ap.add_argument("--lattice", action="store_true", help="the FCC lattice itself instead of a jittered one")
+    ap.add_argument("--grab", type=int, default=1, help="cells per work pull of the batched step (--op batch)")
     args = ap.parse_args(argv)
     if args.op == "batch":
-        return run_batch(args.reps)
+        return run_batch(args.reps, args.kernel, args.grab)
     if args.lattice:
         x, L = inputs.fcc(args.n_fcc, args.rho)
     else:
