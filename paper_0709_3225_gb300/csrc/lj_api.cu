@@ -103,6 +103,9 @@ void free_ctx(lj_ctx *c)
     cudaFree(c->n2_scratch);
     cudaFree(c->f_sorted);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->zero_stream) cudaStreamDestroy(c->zero_stream);
+    if (c->ev_zfork) cudaEventDestroy(c->ev_zfork);
+    if (c->ev_zjoin) cudaEventDestroy(c->ev_zjoin);
     if (c->ev_xfinal) cudaEventDestroy(c->ev_xfinal);
     if (c->ev_entry) cudaEventDestroy(c->ev_entry);
     for (int k = 0; k < 4; k++)
@@ -206,10 +209,35 @@ int one_step(lj_ctx *c, double *x, double *v, void *f, int s, int nsteps, cudaEv
     } else {
         LJ_CK(launch_kick_drift_bin(c, x, v, f, s == 0 ? 1 : 2));
     }
+    // the update has read f: the pair-once kernel's zeroing of f forks off
+    // here and overlaps the scan (latency-bound) and the scatter
+    const bool zfork = c->zero_stream && uses_force_n3(c);
+    if (zfork) {
+        LJ_CK(cudaEventRecord(c->ev_zfork, c->stream));
+        LJ_CK(cudaStreamWaitEvent(c->zero_stream, c->ev_zfork, 0));
+        LJ_CK(cudaMemsetAsync(f, 0, (size_t)c->p.n * force_vsize(c), c->zero_stream));
+        LJ_CK(cudaEventRecord(c->ev_zjoin, c->zero_stream));
+    }
     LJ_CK(launch_scan(c));
     LJ_CK(launch_scatter(c, x, false));
     if (x_final) LJ_CK(cudaEventRecord(x_final, c->stream));   // x holds its final value
-    LJ_CK(launch_force(c, f, false));
+    if (zfork) {
+        LJ_CK(cudaStreamWaitEvent(c->stream, c->ev_zjoin, 0));
+        c->f_prezeroed = 1;
+    }
+    const cudaError_t e = launch_force(c, f, false);
+    c->f_prezeroed = 0;
+    LJ_CK(e);
+    return LJ_OK;
+}
+
+// The side stream and events of the zeroing fork (outside any capture).
+int ensure_zero_stream(lj_ctx *c)
+{
+    if (c->zero_stream) return LJ_OK;
+    LJ_CK(cudaEventCreateWithFlags(&c->ev_zfork, cudaEventDisableTiming));
+    LJ_CK(cudaEventCreateWithFlags(&c->ev_zjoin, cudaEventDisableTiming));
+    LJ_CK(cudaStreamCreateWithFlags(&c->zero_stream, cudaStreamNonBlocking));
     return LJ_OK;
 }
 
@@ -304,6 +332,10 @@ int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps, cudaEvent_t x
     if (nsteps <= 0) return LJ_OK;
     if (persistent_mode(c)) return persistent_steps(c, x, v, f, nsteps, x_final);
     if (fused_mode(c)) LJ_CK(launch_kick_drift_bin(c, x, v, f, 1));
+    if (c->skin <= 0.0 && !fused_mode(c) && uses_force_n3(c)) {
+        int r = ensure_zero_stream(c);
+        if (r) return r;
+    }
     const bool graph = c->use_graph && !c->timing && nsteps >= 3;
     for (int s = 0; s < nsteps; s++) {
         // after step 0 (which does any lazy set-up outside the capture and

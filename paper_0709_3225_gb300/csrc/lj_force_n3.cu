@@ -132,7 +132,11 @@ cudaError_t launch_force_n3(lj_ctx *c, void *f, bool energy)
     double *partial = c->partial;
     void *args[] = {&k, (void *)&pos, (void *)&start, &f, &partial};
     if (c->timing && c->ev_used + 2 <= c->nev) cudaEventRecord(c->ev[c->ev_used], c->stream);
-    cudaError_t e = cudaMemsetAsync(f, 0, (size_t)c->p.n * sizeof(float4), c->stream);
+    // f must start at zero: zeroed here, unless the step zeroed it already
+    // on its side stream
+    cudaError_t e = cudaSuccess;
+    if (!c->f_prezeroed) e = cudaMemsetAsync(f, 0, (size_t)c->p.n * sizeof(float4), c->stream);
+    c->f_prezeroed = 0;
     if (e == cudaSuccess)
         e = cudaLaunchKernel(n3_kernel(c->p.shift_mode, energy), dim3(c->n3_grid), dim3(kN3Threads), args, c->n3_smem,
                              c->stream);

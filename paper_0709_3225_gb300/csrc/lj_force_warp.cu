@@ -209,6 +209,12 @@ cudaError_t launch_warp(lj_ctx *c, void *kern, WarpParams k, void *f, KickDriftB
 
 }  // namespace
 
+bool uses_force_n3(const lj_ctx *c)
+{
+    return c->p.n > 0 && !c->use_aop && !c->use_run_kernel && c->p.precision != LJ_PREC_FP64 &&
+           c->p.cell_subdiv != 2 && !c->pipe && c->n3 && !c->deterministic;
+}
+
 cudaError_t launch_force_warp(lj_ctx *c, void *f, bool energy)
 {
     if (c->p.precision == LJ_PREC_FP64) return launch_force_w64(c, f, energy);

@@ -114,6 +114,13 @@ struct lj_ctx {
     cudaEvent_t ev_xfinal, ev_entry;
     cudaEvent_t ev_chunk[4];
     int kdb_done;
+    // lj_step: the zeroing of f that the pair-once kernel needs runs on
+    // zero_stream, concurrently with the scan and the scatter (f is dead
+    // once the update has read it); f_prezeroed tells launch_force_n3 that
+    // it is done
+    cudaStream_t zero_stream;
+    cudaEvent_t ev_zfork, ev_zjoin;
+    int f_prezeroed;
     // graph replay of the middle steps of lj_step (lj_set_graph)
     int use_graph;
     cudaGraphExec_t gexec;   // one captured middle step
@@ -339,4 +346,5 @@ cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bo
 // Newton's-third-law warp kernel (lj_force_n3.cu): configuration, and a
 // launch that zeroes f and adds every pair's force to both particles.
 cudaError_t n3_force_configure(lj_ctx *c);
+bool uses_force_n3(const lj_ctx *c);   // launch_force dispatches to the pair-once kernel
 cudaError_t launch_force_n3(lj_ctx *c, void *f, bool energy);

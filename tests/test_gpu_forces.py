@@ -304,3 +304,47 @@ def test_bulk_copied_stencils(oracle_mod, gw):
         assert rel_rms(f[:, :3], fo) <= 1e-5
         assert np.all(d[~near] <= (6e-7 * K + 1e-5 * S)[~near])
         assert abs(e - eo) <= 2e-6 * np.abs(epo).sum() + 1e-12
+
+
+def _cutoff_pairs(delta):
+    """Isolated pairs at separations rc (1 - delta) and rc (1 + delta) along
+    axis, face-diagonal and body-diagonal directions, centred on a 3 x 3 x 3
+    grid whose first plane in each axis sits on the periodic boundary (those
+    pairs straddle it), in a box of 8 cells per side; every particle of one
+    pair is more than 4 sigma from those of the others."""
+    L, rc = 20.0, 2.5
+    dirs = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [0, -1, 1], [1, 1, 1], [-1, 1, -1]], float)
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    sites = np.stack(np.meshgrid(*[np.arange(3)] * 3, indexing="ij"), -1).reshape(-1, 3) * (L / 3.0)
+    x, inside = [], []
+    for q, base in enumerate(sites):
+        u = dirs[q % len(dirs)]
+        r = rc * (1.0 - delta) if q % 2 == 0 else rc * (1.0 + delta)
+        x += [base - 0.5 * r * u, base + 0.5 * r * u]
+        inside += [r < rc, r < rc]
+    x = np.array(x) % L
+    return np.ascontiguousarray(x), L, np.array(inside)
+
+
+@pytest.mark.parametrize("precision,kernel", [("mixed", None), ("mixed", 3), ("fp64", None)])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_cutoff_decision_at_rc(oracle_mod, precision, kernel, mode):
+    # r^2 < rc^2 decides a pair (strict cutoff, Section 2).  Pairs 2e-6 rc
+    # inside the cutoff feel their pair force; pairs 2e-6 rc outside feel
+    # nothing at all (the FP32 rounding of r^2 is ~1e-7 relative, far below
+    # the 4e-6 between the two sides).
+    x, L, inside = _cutoff_pairs(2e-6)
+    f, _, _ = _gpu_forces(x, L, precision, mode, kernel=kernel)
+    fo, _, _, _ = oracle_mod.forces_brute(x, L, mode=mode)
+    assert np.all(f[~inside, :3] == 0.0)
+    assert np.all(np.abs(fo[~inside]) == 0.0)
+    fin, foin = f[inside, :3], fo[inside]
+    if mode != 2:   # the force-shifted force nearly vanishes at rc
+        assert np.all(np.linalg.norm(foin, axis=1) > 0.03)
+    d = np.abs(fin - foin).max(axis=1)
+    if precision == "mixed":   # the per-particle bound of the other parity tests
+        K, S = oracle_mod.stiffness(x, L, mode=mode)
+        bound = TOL["mixed"]["dr"] * K[inside] + TOL["mixed"]["ds"] * S[inside]
+    else:
+        bound = TOL["fp64"]["rel"] * (np.abs(foin).max(axis=1) + 1e-3)
+    assert np.all(d <= bound), (d / bound).max()
