@@ -643,6 +643,16 @@ cudaError_t launch_vjp(lj_ctx *c, const double *g, double scale, double *dx, dou
     k.dfc1 = rc * (12.0 * k.a1 * pow(rc, -14.0) - 6.0 * k.b1 * pow(rc, -8.0)) / sg;
     k.eps = c->p.eps;
     k.inv_sigma = 1.0 / sg;
+    if (!fp64 && uses_vjp_n3(c) && c->f_sorted) {
+        // each pair once (lj_vjp_n3.cu); f_sorted is its float4 accumulator
+        const double coef[7] = {k.rc2, k.a1, k.b1, k.fc1, k.dfc1, k.eps, k.inv_sigma};
+        int grid = 0;
+        cudaError_t e = launch_vjp_n3(c, coef, scale, dx, (float4 *)c->f_sorted, &grid);
+        if (e != cudaSuccess) return e;
+        k_accum_params<<<1, kReduceThreads, 0, c->stream>>>(c->partial, grid, scale, dparam);
+        c->kernel_launches++;
+        return cudaGetLastError();
+    }
     if (!fp64) return launch_vjp_warp(c, k, scale, dx, dparam);
     if (c->p.cell_subdiv != 2 && c->wcap > 0 && c->w64_lcap > 0) {
         // FP64: the warp kernel with compacted in-range pair lists

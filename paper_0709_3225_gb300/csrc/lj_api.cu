@@ -357,6 +357,17 @@ int do_steps(lj_ctx *c, double *x, double *v, void *f, int nsteps, cudaEvent_t x
     return LJ_OK;
 }
 
+// The adjoint's buffers: the cell-ordered cotangents and, for the
+// pair-once FP32-mixed VJP, its float4 accumulator (in f_sorted, which
+// FP32-mixed contexts do not otherwise use).
+int ensure_vjp_buffers(lj_ctx *c)
+{
+    if (!c->g4) LJ_CK(cudaMalloc(&c->g4, (size_t)c->p.n * force_vsize(c)));
+    if (c->p.precision == LJ_PREC_MIXED && uses_vjp_n3(c) && !c->f_sorted)
+        LJ_CK(cudaMalloc(&c->f_sorted, (size_t)c->p.n * sizeof(float4)));
+    return LJ_OK;
+}
+
 int ensure_staging(lj_ctx *c)
 {
     size_t n1 = (size_t)(c->p.n > 0 ? c->p.n : 1);
@@ -851,7 +862,7 @@ extern "C" int lj_forces_vjp(lj_ctx *c, const double *x, const double *g, double
     if ((r = check_dev_ptr(x, 8)) != LJ_OK) return r;
     if ((r = check_dev_ptr(g, 8)) != LJ_OK) return r;
     if ((r = check_dev_ptr(dx, 8)) != LJ_OK) return r;
-    if (!c->g4) LJ_CK(cudaMalloc(&c->g4, (size_t)c->p.n * force_vsize(c)));
+    if ((r = ensure_vjp_buffers(c)) != LJ_OK) return r;
     if ((r = do_bin(c, x, true)) != LJ_OK) return r;
     LJ_CK(launch_vjp(c, g, scale, dx, dparam));
     return LJ_OK;
@@ -868,7 +879,7 @@ extern "C" int lj_vv_adjoint_step(lj_ctx *c, const double *x_n, const double *x_
     if ((r = check_dev_ptr(x_n1, 8)) != LJ_OK) return r;
     if ((r = check_dev_ptr(lam_x, 8)) != LJ_OK) return r;
     if ((r = check_dev_ptr(lam_v, 8)) != LJ_OK) return r;
-    if (!c->g4) LJ_CK(cudaMalloc(&c->g4, (size_t)c->p.n * force_vsize(c)));
+    if ((r = ensure_vjp_buffers(c)) != LJ_OK) return r;
     const double h = 0.5 * c->p.dt / c->p.mass;
     // v_{n+1} = v_half + h F(x_{n+1})
     if ((r = do_bin(c, x_n1, true)) != LJ_OK) return r;

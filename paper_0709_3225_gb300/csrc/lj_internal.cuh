@@ -347,4 +347,10 @@ cudaError_t launch_force_warp_fused(lj_ctx *c, void *f, double *x, double *v, bo
 // launch that zeroes f and adds every pair's force to both particles.
 cudaError_t n3_force_configure(lj_ctx *c);
 bool uses_force_n3(const lj_ctx *c);   // launch_force dispatches to the pair-once kernel
+// The pair-once FP32-mixed VJP (lj_vjp_n3.cu), used where the pair-once
+// force kernel is: coef = (rc^2, 48 sigma^12, 24 sigma^6, F(rc) rc at
+// eps = 1, its sigma-derivative, eps, 1 / sigma); sums into acc (float4
+// [n], zeroed there), parameter partials into c->partial (*grid_out).
+bool uses_vjp_n3(const lj_ctx *c);
+cudaError_t launch_vjp_n3(lj_ctx *c, const double *coef, double scale, double *dx, float4 *acc, int *grid_out);
 cudaError_t launch_force_n3(lj_ctx *c, void *f, bool energy);

@@ -102,6 +102,44 @@ def test_fp64_vjp_forms(oracle_mod, kernel, mode, state):
     assert abs(dp[0] - ode) <= 1e-11 * abs(ode) and abs(dp[1] - ods) <= 1e-11 * abs(ods)
 
 
+@pytest.mark.parametrize("kernel", [3, 7])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("state", ["liquid", "cluster", "dense_rc3"])
+def test_mixed_vjp_forms(oracle_mod, kernel, mode, state):
+    """The FP32-mixed VJP in its pair-once form (kernel 7, the default: each
+    pair once over the half stencil, the term of j the negative of i's, by
+    float atomics) and its 27-cell form (kernel 3) against the oracle, on the
+    states of the FP64 test above (the dense blob's cells take the plain
+    paths).  dx to 1e-5 relative RMS everywhere.  The parameter gradients:
+    on the liquid as in test_vjp_matches_oracle (5e-6 for random cotangents,
+    the 1e-6 target for g = F).  The blob (rho 2.2, pairs at 0.86 sigma) and
+    the rho 1.1 state are code-path cases: there the r^-14 slope amplifies
+    the FP32 rounding of the pair vectors in the cancelling sums of random
+    cotangents to 1-4e-5 relative for both forms alike (measured on these
+    seeds), so the bounds are 1e-4 for random cotangents and 5e-6 for g = F."""
+    from gpu_util import dense_cluster_state
+    rc = 2.5
+    if state == "liquid":
+        x, L = inputs.jittered_fcc(8, 0.8442, 0.1, 44)
+    elif state == "cluster":
+        x, L = dense_cluster_state(seed=45)
+    else:
+        x, L = inputs.jittered_fcc(8, 1.1, 0.05, 46)
+        rc = 3.0
+    g = np.random.default_rng(47).standard_normal(x.shape)
+    eps, sigma = 0.95, 1.02
+    dx, dp = _vjp_gpu(x, L, g, "mixed", mode, eps, sigma, rc=rc, kernel=kernel)
+    odx, ode, ods = oracle_mod.forces_vjp(x, L, g, eps=eps, sigma=sigma, rc=rc, mode=mode)
+    fo = oracle_mod.forces_cells(x, L, eps=eps, sigma=sigma, rc=rc, mode=mode)[0]
+    _, dp_f = _vjp_gpu(x, L, fo, "mixed", mode, eps, sigma, rc=rc, kernel=kernel)
+    _, ode_f, ods_f = oracle_mod.forces_vjp(x, L, fo, eps=eps, sigma=sigma, rc=rc, mode=mode)
+    tg, tf = (5e-6, 1e-6) if state == "liquid" else (1e-4, 5e-6)
+    assert rel_rms(dx, odx) <= 1e-5
+    assert abs(dp[0] - ode) <= tg * abs(ode) and abs(dp[1] - ods) <= tg * abs(ods)
+    assert abs(dp_f[0] - ode_f) <= tf * abs(ode_f)
+    assert abs(dp_f[1] - ods_f) <= tf * abs(ods_f)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_vjp_accumulates_with_scale(oracle_mod, precision):
     """Four calls with scale 1/4 add up to one call with scale 1 (every call
