@@ -285,13 +285,16 @@ int lj_set_params(lj_ctx *ctx, double eps, double sigma);
  *   dparam += scale * (dL/deps, dL/dsigma)  (device double[2]).
  * The cell list is piecewise constant in x and contributes nothing.  Pair
  * arithmetic in the context's precision; parameter sums in FP64 (FP32-mixed:
- * FP32 partial sums over groups of 32 candidates, then FP64).  FP64 contexts
- * on lj_set_tuning kernel 7 (their default) evaluate each pair once (the
- * contribution to j is the negative of i's, J being even in d), adding by
- * atomics, so their last bits can differ between calls too.  Each call
- * bins x again, so with the atomic in-cell order FP32 results can differ in
- * their last bits between calls (lj_set_deterministic makes them repeat).
- * Allocates an (n)-element cotangent buffer on first use.  Asynchronous. */
+ * FP32 partial sums over a cell or a group of 32 candidates, then FP64).
+ * Contexts on lj_set_tuning kernel 7 (the default for cell_subdiv 1, FP32-
+ * mixed and FP64) evaluate each pair once (the contribution to j is the
+ * negative of i's, J being even in d), adding by atomics, so their last bits
+ * can differ between calls too.  Each call bins x again, so with the atomic
+ * in-cell order FP32 results can differ in their last bits between calls
+ * (lj_set_deterministic makes them repeat, with the 27-cell form).
+ * Allocates an (n)-element cotangent buffer on first use, and for the
+ * pair-once FP32-mixed form an (n)-element float4 accumulator.
+ * Asynchronous. */
 int lj_forces_vjp(lj_ctx *ctx, const double *x, const double *g, double scale, double *dx, double *dparam);
 
 /* One step of the adjoint of lj_step's velocity Verlet (Section 2), from the
