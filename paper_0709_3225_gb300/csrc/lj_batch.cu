@@ -321,12 +321,18 @@ __device__ void phase_force_n3(const BatchDev &b, const WarpParams &k, float4 *_
         const int nc = b.ncs[r];
         return half_load<false>(b.start, c - b.coff[r], nc, 1.0f / (float)nc, b.coff[r]);
     };
+    // pulls of cells_per_grab cells, single cells over the last stretch (as
+    // k_force_n3)
+    const int64_t tail = 2 * (int64_t)b.cells_per_grab * gridDim.x * (kBatchThreads / 32);
+    unsigned last = 0;
     for (;;) {
+        const unsigned gr = (int64_t)last + tail >= b.ncell ? 1u : (unsigned)b.cells_per_grab;
         unsigned c0 = 0;
-        if (lane == 0) c0 = atomicAdd(b.work, (unsigned)b.cells_per_grab);
+        if (lane == 0) c0 = atomicAdd(b.work, gr);
         c0 = __shfl_sync(0xffffffffu, c0, 0);
         if ((int64_t)c0 >= b.ncell) break;
-        const int c1 = (int)min((int64_t)c0 + b.cells_per_grab, b.ncell);
+        last = c0;
+        const int c1 = (int)min((int64_t)c0 + gr, b.ncell);
         HalfLoad nxt = load((int)c0);   // the next cell's table loads before this cell's work
         for (int c = (int)c0; c < c1; c++) {
             const HalfLoad cur = nxt;

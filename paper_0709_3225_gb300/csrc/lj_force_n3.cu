@@ -24,12 +24,19 @@ __global__ void __launch_bounds__(kN3Threads, 6) k_force_n3(WarpParams k, const 
         n3_cell<MODE, ENERGY, true>(k, pos, fout, tl, k.cw, S, stab, spre, H, eacc, wacc);
     };
     if (k.grab > 0) {
+        // pulls of k.grab cells, then single cells over the last stretch (two
+        // rounds of pulls of the whole grid), so that the warps finish closer
+        // together
+        const int64_t tail = 2 * (int64_t)k.grab * gridDim.x * (kN3Threads / 32);
+        unsigned last = 0;
         for (;;) {
+            const unsigned g = (int64_t)last + tail >= k.ncell ? 1u : (unsigned)k.grab;
             unsigned c0 = 0;
-            if (lane == 0) c0 = atomicAdd(k.work, (unsigned)k.grab);
+            if (lane == 0) c0 = atomicAdd(k.work, g);
             c0 = __shfl_sync(0xffffffffu, c0, 0);
             if ((int64_t)c0 >= k.ncell) break;
-            const int c1 = (int)min((int64_t)c0 + k.grab, k.ncell);
+            last = c0;
+            const int c1 = (int)min((int64_t)c0 + g, k.ncell);
             // the next cell's table loads are issued before this cell's work
             HalfLoad nxt = half_load<true>(start, (int)c0, nc, k.inv_nc);
             for (int c = (int)c0; c < c1; c++) {

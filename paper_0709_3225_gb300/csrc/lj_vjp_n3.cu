@@ -404,12 +404,17 @@ __global__ void __launch_bounds__(kVn3Threads, 4) k_vjp_n3(VjpN3Coef k, const fl
     int *spre = reinterpret_cast<int *>(stab + kN3Half);
     float4 *H = reinterpret_cast<float4 *>(spre + 16);
     double acc_e = 0.0, acc_s = 0.0;
+    // pulls of k.grab cells, single cells over the last stretch (as k_force_n3)
+    const int64_t tail = 2 * (int64_t)k.grab * gridDim.x * (kVn3Threads / 32);
+    unsigned last = 0;
     for (;;) {
+        const unsigned gr = (int64_t)last + tail >= k.ncell ? 1u : (unsigned)k.grab;
         unsigned c0 = 0;
-        if (lane == 0) c0 = atomicAdd(k.work, (unsigned)k.grab);
+        if (lane == 0) c0 = atomicAdd(k.work, gr);
         c0 = __shfl_sync(0xffffffffu, c0, 0);
         if ((int64_t)c0 >= k.ncell) break;
-        const int c1 = (int)min((int64_t)c0 + k.grab, k.ncell);
+        last = c0;
+        const int c1 = (int)min((int64_t)c0 + gr, k.ncell);
         HalfLoad nxt = half_load<true>(start, (int)c0, k.nc, k.inv_nc);
         for (int c = (int)c0; c < c1; c++) {
             const HalfLoad cur = nxt;
