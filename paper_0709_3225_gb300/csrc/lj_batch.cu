@@ -226,31 +226,54 @@ __device__ void phase_scan(const BatchDev &b)
 
 // Phase 3: sorted, cell-centred FP32 positions (w = particle index).  With
 // fz (the pair-once force phase, which adds into f) f is zeroed too; the
-// first phase has read it already.
+// first phase has read it already.  Two particles per thread, their loads
+// issued before either is stored: the launch runs at the force phase's
+// occupancy, so this memory phase needs the extra loads in flight.
+__device__ __forceinline__ void scatter_one(const BatchDev &b, int op, int64_t i, int r, int c, int rk, double px,
+                                            double py, double pz)
+{
+    if (c >= b.ncell) {   // non-finite particle in the extra cell
+        b.pos[b.start[c] + rk] = make_float4((float)px, (float)px, (float)px, __int_as_float((int)i));
+        return;
+    }
+    const int nc = b.ncs[r];
+    int cx, cy, cz;
+    decode_cell(c - b.coff[r], nc, cx, cy, cz);
+    if (op != 0) {
+        const double L = b.L[r], whi = b.whi[r], wlo = b.wlo[r];
+        px = lj_wrap_fast(px, L, whi, wlo);
+        py = lj_wrap_fast(py, L, whi, wlo);
+        pz = lj_wrap_fast(pz, L, whi, wlo);
+    }
+    const double *ce = b.centre + b.ceoff[r];
+    b.pos[b.start[c] + rk] =
+        make_float4((float)(px - ce[cx]), (float)(py - ce[cy]), (float)(pz - ce[cz]), __int_as_float((int)i));
+}
+
 __device__ void phase_scatter(const BatchDev &b, int op, const double *__restrict__ x, float4 *__restrict__ fz)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.ntot; i += stride) {
-        if (fz) fz[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        const int r = b.rep_of[i];
-        const int c = b.cell_of[i];
-        const int nc = b.ncs[r];
-        double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
-        if (c >= b.ncell) {   // non-finite particle in the extra cell
-            b.pos[b.start[c] + b.rank[i]] = make_float4((float)px, (float)px, (float)px, __int_as_float((int)i));
-            continue;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < b.ntot; i0 += 2 * stride) {
+        const int64_t i1 = i0 + stride;
+        const bool two = i1 < b.ntot;
+        const int r0 = b.rep_of[i0], c0 = b.cell_of[i0], k0 = b.rank[i0];
+        const double x0 = x[3 * i0], y0 = x[3 * i0 + 1], z0 = x[3 * i0 + 2];
+        int r1 = 0, c1 = 0, k1 = 0;
+        double x1 = 0.0, y1 = 0.0, z1 = 0.0;
+        if (two) {
+            r1 = b.rep_of[i1];
+            c1 = b.cell_of[i1];
+            k1 = b.rank[i1];
+            x1 = x[3 * i1];
+            y1 = x[3 * i1 + 1];
+            z1 = x[3 * i1 + 2];
         }
-        int cx, cy, cz;
-        decode_cell(c - b.coff[r], nc, cx, cy, cz);
-        if (op != 0) {
-            const double L = b.L[r], whi = b.whi[r], wlo = b.wlo[r];
-            px = lj_wrap_fast(px, L, whi, wlo);
-            py = lj_wrap_fast(py, L, whi, wlo);
-            pz = lj_wrap_fast(pz, L, whi, wlo);
+        if (fz) {
+            fz[i0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (two) fz[i1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
-        const double *ce = b.centre + b.ceoff[r];
-        b.pos[b.start[c] + b.rank[i]] =
-            make_float4((float)(px - ce[cx]), (float)(py - ce[cy]), (float)(pz - ce[cz]), __int_as_float((int)i));
+        scatter_one(b, op, i0, r0, c0, k0, x0, y0, z0);
+        if (two) scatter_one(b, op, i1, r1, c1, k1, x1, y1, z1);
     }
 }
 
