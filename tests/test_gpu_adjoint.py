@@ -104,25 +104,29 @@ def test_fp64_vjp_forms(oracle_mod, kernel, mode, state):
 
 @pytest.mark.parametrize("kernel", [3, 7])
 @pytest.mark.parametrize("mode", [0, 1, 2])
-@pytest.mark.parametrize("state", ["liquid", "cluster", "dense_rc3"])
+@pytest.mark.parametrize("state", ["liquid", "cluster", "dense_rc3", "box3"])
 def test_mixed_vjp_forms(oracle_mod, kernel, mode, state):
     """The FP32-mixed VJP in its pair-once form (kernel 7, the default: each
     pair once over the half stencil, the term of j the negative of i's, by
     float atomics) and its 27-cell form (kernel 3) against the oracle, on the
     states of the FP64 test above (the dense blob's cells take the plain
-    paths).  dx to 1e-5 relative RMS everywhere.  The parameter gradients:
-    on the liquid as in test_vjp_matches_oracle (5e-6 for random cotangents,
-    the 1e-6 target for g = F).  The blob (rho 2.2, pairs at 0.86 sigma) and
-    the rho 1.1 state are code-path cases: there the r^-14 slope amplifies
-    the FP32 rounding of the pair vectors in the cancelling sums of random
-    cotangents to 1-4e-5 relative for both forms alike (measured on these
-    seeds), so the bounds are 1e-4 for random cotangents and 5e-6 for g = F."""
+    paths; box3 is the smallest grid, 3 cells per side, where the half
+    stencil wraps onto both neighbours of a cell).  dx to 1e-5 relative RMS
+    everywhere.  The parameter gradients: on the liquid as in
+    test_vjp_matches_oracle (5e-6 for random cotangents, the 1e-6 target for
+    g = F).  The other states are code-path cases, with bounds of 1e-4 for
+    random cotangents and 5e-6 for g = F: on the blob (rho 2.2, pairs at
+    0.86 sigma) and at rho 1.1 the r^-14 slope amplifies the FP32 rounding of
+    the pair vectors in the cancelling sums of random cotangents to 1-4e-5
+    relative for both forms alike (measured on these seeds)."""
     from gpu_util import dense_cluster_state
     rc = 2.5
     if state == "liquid":
         x, L = inputs.jittered_fcc(8, 0.8442, 0.1, 44)
     elif state == "cluster":
         x, L = dense_cluster_state(seed=45)
+    elif state == "box3":
+        x, L = inputs.jittered_fcc(5, 0.8442, 0.1, 48)   # L = 8.40: 3 cells per side
     else:
         x, L = inputs.jittered_fcc(8, 1.1, 0.05, 46)
         rc = 3.0
